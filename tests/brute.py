@@ -1,0 +1,98 @@
+"""Brute-force checker for tiny events (test infrastructure).
+
+An independent route to the oracle's per-seed result: every combination of one
+hit per layer (or "absent" when the layer has no hit) is fitted with
+numpy.linalg.lstsq on the weighted rows, its features are formed, the network
+is evaluated with torch in float64, and the winner is the lexicographic minimum
+of the pick key.  Valid only when every hit of the event qualifies (windows
+made huge) and no layer holds more hits than the method keeps (1 in UTaX, 2 in
+UTaU and UTbV, k1 in UTbX), so that the k-closest rules admit every combination.
+"""
+import itertools
+
+import numpy as np
+import torch
+
+
+@torch.no_grad()
+def torch_mlp(w, phi):
+    phi = torch.as_tensor(np.atleast_2d(phi), dtype=torch.float64)
+    x = (phi - torch.as_tensor(w["mean"], dtype=torch.float64)) * torch.as_tensor(w["scale"], dtype=torch.float64)
+    l1 = torch.nn.Linear(w["n_in"], w["n_h1"]).double()
+    l1.weight.data = torch.as_tensor(w["w1"], dtype=torch.float64)
+    l1.bias.data = torch.as_tensor(w["b1"], dtype=torch.float64)
+    h = torch.relu(l1(x))
+    if w["n_h2"]:
+        l2 = torch.nn.Linear(w["n_h1"], w["n_h2"]).double()
+        l2.weight.data = torch.as_tensor(w["w2"], dtype=torch.float64)
+        l2.bias.data = torch.as_tensor(w["b2"], dtype=torch.float64)
+        h = torch.relu(l2(h))
+    l3 = torch.nn.Linear(h.shape[1], 1).double()
+    l3.weight.data = torch.as_tensor(np.asarray(w["w3"])[None, :], dtype=torch.float64)
+    l3.bias.data = torch.tensor([float(w["b3"])], dtype=torch.float64)
+    return torch.sigmoid(l3(h))[:, 0].detach().numpy()
+
+
+def seed_best(batch, cfg, w, s):
+    """All candidates of seed s by exhaustive enumeration, and the winner index."""
+    e = int(np.searchsorted(batch["seed_off"], s, side="right") - 1)
+    h0, h1 = int(batch["hit_off"][e]), int(batch["hit_off"][e + 1])
+    x_s, y_s, tx, ty, qop, chi2s = (float(batch[k][s]) for k in
+                                    ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2"))
+    z = np.asarray(cfg["z_layer"]); dxdy = np.asarray(cfg["dxdy"])
+    zm = cfg["zmag"][0] + cfg["zmag"][1] * tx ** 2 + cfg["zmag"][2] * ty ** 2 + cfg["zmag"][3] * abs(qop)
+    xm = x_s + tx * (zm - cfg["z_seed"])
+    ym = y_s + ty * (zm - cfg["z_seed"])
+    yl = ym + ty * (z - zm)
+    tx_ut = tx + cfg["mp"] * cfg["kappa"] * qop * np.sqrt(1 + tx * tx + ty * ty)
+    u_bx = xm + tx_ut * (z[3] - zm) - dxdy[3] * yl[3]
+    w1 = cfg["w1a"] + cfg["w1b"] * abs(qop)
+    per_layer = [[h for h in range(h0, h1) if batch["hit_layer"][h] == l] for l in range(4)]
+    opts = [(p if p else [-1]) for p in per_layer[:3]]
+    cands = []
+    for hb in per_layer[3]:
+        for combo in itertools.product(*opts):
+            hits = list(combo) + [hb]
+            present = [l for l in range(4) if hits[l] >= 0]
+            if len(present) < 3 or (hits[0] < 0 and hits[1] < 0):
+                continue
+            rows_z = [z[l] - cfg["z_ref"] for l in present] + [zm - cfg["z_ref"]]
+            meas = [float(batch["hit_x0"][hits[l]]) + dxdy[l] * yl[l] for l in present] + [xm]
+            sw = [1 / cfg["sigma_hit"]] * len(present) + [1 / cfg["sigma_mag"]]
+            A = np.array([[1.0, dz] for dz in rows_z]) * np.array(sw)[:, None]
+            bvec = np.array(meas) * np.array(sw)
+            sol, *_ = np.linalg.lstsq(A, bvec, rcond=None)
+            xr, t = sol
+            r = bvec - A @ sol
+            chi2 = float(r @ r)
+            ndof = len(present) - 1
+            res = np.zeros(4)
+            for l in present:
+                res[l] = float(batch["hit_x0"][hits[l]]) + dxdy[l] * yl[l] - (xr + t * (z[l] - cfg["z_ref"]))
+            yr = ym + ty * (cfg["z_ref"] - zm)
+            q = cfg["mp"] * (t - tx) / cfg["kappa"] / np.sqrt(1 + t * t + ty * ty) if cfg["kappa"] != 0 else qop
+            phi = np.array([xr / 1e3, yr / 1e3, t, ty, 1e3 * q, chi2 / ndof, 1e3 * qop, chi2s,
+                            *(res / cfg["sigma_hit"]), len(present) / 4,
+                            abs(float(batch["hit_x0"][hb]) - u_bx) / w1, tx, ty])
+            cands.append(dict(hits=[h if h >= 0 else -1 for h in hits], state=[xr, yr, t, ty, q],
+                              chi2=chi2, ndof=ndof, phi=phi))
+    if not cands:
+        return cands, -1
+    f = torch_mlp(w, np.array([c["phi"][: w["n_in"]] for c in cands]))
+    for c, fv in zip(cands, f):
+        c["f"] = float(fv)
+    T = cfg["nn_threshold"]
+
+    def key(c):
+        ids = tuple(h if h >= 0 else 1 << 40 for h in c["hits"])
+        if cfg["pick_chi2"]:
+            return (c["chi2"] / c["ndof"], c["f"], ids)
+        return (c["f"], c["chi2"], ids)
+
+    elig = [i for i, c in enumerate(cands) if cfg["pick_chi2"] or c["f"] < T]
+    if not elig:
+        return cands, -1
+    best = min(elig, key=lambda i: key(cands[i]))
+    if cfg["pick_chi2"] and not cands[best]["f"] < T:
+        return cands, -1
+    return cands, best
