@@ -1,0 +1,455 @@
+"""Throughput benchmark of the Downstream tracking + two-track vertexing path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = ds_reconstruct + ds_vertex over one batch of 1000 synthetic events
+shaped like the paper's minimum-bias workload (Poisson(300) SciFi seeds, 40 %
+true, 5000 UT hits per event, 16-32-32-1 ghost killer in FP32, opposite-charge
+vertexing with DOCA < 2 mm), inputs resident in HBM.  Inputs rotate over
+replicas totalling more than three times the L2, so every step reads cold
+inputs.  Prints one JSON line (rank 0).
+
+Under torchrun each rank processes its own batch (weak scaling, no
+collective on the data path); value = all events / max-over-ranks time.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L2_BYTES = 126 * 2 ** 20
+N_EVENTS = 1000
+WORKLOAD = ("c2: 1000 events/step, Poisson(300) SciFi seeds (40% true), 5000 UT hits/event, "
+            "16-32-32-1 ghost killer FP32, opposite-charge vertexing DOCA<2mm")
+KERNELS_PER_STEP = 7
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(elapsed_s: list, events_per_rank: int, steps: int) -> dict:
+    """Whole-job throughput: every rank's events over the slowest rank's time."""
+    t = max(elapsed_s)
+    n = len(elapsed_s) * events_per_rank * steps
+    return dict(value=n / t, ms_per_step=1e3 * t / steps, events=n)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6400.0), d.get("sm_max_mhz", 2032.0), "measured"
+    return 6400.0, 2032.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, out_path: str | None):
+        self.p = None
+        self.path = out_path
+        try:
+            self.f = open(out_path, "w") if out_path else subprocess.DEVNULL
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        if self.path:
+            with open(self.path, "w") as f:
+                f.write(out)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1])); smax.append(float(c[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"])
+        return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(smax)), reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+def algorithmic(E, S, H, n_t, n_v, n_cand, n_pairs, table_stride):
+    """Algorithmic bytes (inputs once + outputs once) and FLOPs per launch."""
+    mlp_flop = 2 * (16 * 32 + 32 * 32 + 32)
+    return {
+        "k_bucket": dict(bytes=13 * H + 16 * H + 2 * table_stride * E),
+        "k_search": dict(bytes=24 * S + 16 * H + 2 * table_stride * E + 92 * S, flop=mlp_flop * n_cand),
+        "k_clone": dict(bytes=28 * S + 8 * E),
+        "k_scatter_tracks": dict(bytes=4 * S + 128 * n_t),
+        "k_vertex_small": dict(bytes=20 * n_t + 36 * n_v, flop=200 * n_pairs),
+        "k_vertex_large": dict(bytes=0),
+        "k_scatter_vertices": dict(bytes=68 * n_v),
+    }
+
+
+def traffic_for(kernel: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel's
+    source has not changed since it was taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_2503_13092_b300", "csrc", e["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != e["sha"]:
+        return None
+    return e["bytes_per_launch"]
+
+
+def run_cpu_baseline(batch, cfg, w, target_s=12.0):
+    import oracle
+    cores = os.cpu_count() or 1
+    E = batch["n_events"]
+    n = 16
+    while True:
+        ev = list(range(min(n, E)))
+        sb = _sub(batch, ev)
+        t0 = time.perf_counter()
+        r = oracle.reconstruct(sb, cfg, w, n_threads=cores)
+        tk = oracle.tracks_from(r, sb["seed_off"])
+        st = tk["state"].astype(np.float32)
+        oracle.vertex(cfg, tk["trk_off"], st[:, 0], st[:, 1], st[:, 2], st[:, 3], st[:, 4])
+        dt = time.perf_counter() - t0
+        if dt > 0.25 * target_s or n >= E:
+            break
+        n = min(E, int(n * max(2.0, 0.5 * target_s / max(dt, 1e-3))))
+    return dict(value=len(ev) / dt, unit="events/s", cores=cores, kind="oracle",
+                sample=f"first {len(ev)} events of the step's batch, reconstruct + vertex, "
+                       f"{cores} threads (one event per thread), {dt:.2f} s")
+
+
+def _sub(b, events):
+    out = dict(n_events=len(events))
+    so, ho, si, hi = [0], [0], [], []
+    for e in events:
+        s0, s1, h0, h1 = int(b["seed_off"][e]), int(b["seed_off"][e + 1]), int(b["hit_off"][e]), int(b["hit_off"][e + 1])
+        si.append(np.arange(s0, s1)); hi.append(np.arange(h0, h1))
+        so.append(so[-1] + s1 - s0); ho.append(ho[-1] + h1 - h0)
+    si, hi = np.concatenate(si), np.concatenate(hi)
+    out["seed_off"] = np.array(so, np.int32); out["hit_off"] = np.array(ho, np.int32)
+    for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2"):
+        out[k] = b[k][si]
+    for k in ("hit_x0", "hit_ybeg", "hit_yend", "hit_layer"):
+        out[k] = b[k][hi]
+    return out
+
+
+def bench_reference(args):
+    """FP64 CPU oracle, as it stands, on the host cores (rank 0 only)."""
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2503_13092_b300 import synth
+    batch = synth.config_batch("c2")
+    cfg = synth.default_config()
+    w = synth.nn_weights()
+    cores = os.cpu_count() or 1
+    per_step = max(8, min(N_EVENTS, 4 * cores))
+    times = []
+    for k in range(args.warmup + args.steps):
+        ev = [(k * per_step + i) % N_EVENTS for i in range(per_step)]
+        sb = _sub(batch, ev)
+        t0 = time.perf_counter()
+        r = oracle.reconstruct(sb, cfg, w, n_threads=cores)
+        tk = oracle.tracks_from(r, sb["seed_off"])
+        st = tk["state"].astype(np.float32)
+        oracle.vertex(cfg, tk["trk_off"], st[:, 0], st[:, 1], st[:, 2], st[:, 3], st[:, 4])
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times)
+    val = per_step * args.steps / t
+    line = dict(metric="events/s per B300 (Downstream+vertexing)", value=val, unit="events/s", n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * t / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, n_events=N_EVENTS, sample_events_per_step=per_step),
+                cpu_baseline=dict(value=val, unit="events/s", cores=cores, kind="oracle",
+                                  sample=f"{per_step} events per step of the same batch, {cores} threads"),
+                e2e=dict(value=val, unit="events/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-events", type=int, default=200)
+    ap.add_argument("--clocks-log", default=None)
+    ap.add_argument("--ncu", action="store_true",
+                    help="profiling run: warmup + steps eager steps on one batch, nothing else")
+    ap.add_argument("--events", type=int, default=N_EVENTS)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return bench_reference(args)
+
+    import torch
+    from paper_2503_13092_b300 import build, ds, synth
+    build.build()
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev_index = local if ws > 1 else 0
+    torch.cuda.set_device(dev_index)
+
+    batch = synth.config_batch("c2", seed=2 + rank, n_events=args.events)
+    cfg = synth.default_config()
+    w = synth.nn_weights()
+    E, S, H = batch["n_events"], int(batch["seed_off"][-1]), int(batch["hit_off"][-1])
+    d = ds.Downstream(cfg, w, device=dev_index)
+    ds.ds_reserve(d.ctx, E, S, H)
+    if args.ncu:
+        dv = d.to_device(batch)
+        out = d.alloc_tracks(E, S)
+        vout = d.alloc_vertices(E, 16 * S + 4096)
+        for _ in range(args.warmup + args.steps):
+            d.reconstruct(dv, out)
+            d.vertex(out, vout)
+        st = d.sync()
+        print(json.dumps(dict(ncu_run=True, steps=args.warmup + args.steps, status=st["status"],
+                              tracks=st["n_tracks"], vertices=st["n_vertices"])), flush=True)
+        d.close()
+        return 0
+    in_bytes = 24 * S + 13 * H + 8 * (E + 1)
+    R = max(2, math.ceil(3 * L2_BYTES / in_bytes))
+    devs = [d.to_device(batch) for _ in range(R)]
+    out = d.alloc_tracks(E, S)
+    # size the vertex output from one run
+    probe = d.run(batch, dev=devs[0])
+    n_t, n_v = probe["n_tracks"], probe["n_vertices"]
+    vcap = 2 * n_v + 4096
+    vout = d.alloc_vertices(E, vcap)
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        dv = devs[k % R]
+        d.reconstruct(dv, out, stream)
+        d.vertex(out, vout, stream)
+
+    for k in range(args.warmup):
+        step(k)
+    st = d.sync(stream)
+    n_cand, n_pairs, n_fp64 = st["n_candidates"] // args.warmup, st["n_pairs"] // args.warmup, \
+        st["n_pairs_fp64"] // args.warmup
+
+    # eager timing (Python + ctypes enqueue per step) for reference
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    eager_s = e0.elapsed_time(e1) / 1e3
+    d.sync(stream)
+
+    # one CUDA graph per input replica: a step is one graph launch
+    graphs = []
+    cap_stream = torch.cuda.Stream()
+    for r in range(R):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap_stream):
+            cs = torch.cuda.current_stream()
+            d.reconstruct(devs[r], out, cs)
+            d.vertex(out, vout, cs)
+        graphs.append(g)
+    for k in range(args.warmup):
+        graphs[k % R].replay()
+    d.sync(stream)
+
+    def step_graph(k):
+        graphs[k % R].replay()
+
+    # ------------------------------------------------------------- timed
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(dev_index, args.clocks_log)
+    time.sleep(0.3)
+    t0e = torch.cuda.Event(enable_timing=True)
+    t1e = torch.cuda.Event(enable_timing=True)
+    t0e.record(stream)
+    for k in range(args.steps):
+        step_graph(k)
+    t1e.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    if ws > 1:
+        dist.barrier()
+    elapsed = t0e.elapsed_time(t1e) / 1e3
+    st = d.sync(stream)
+    assert st["status"] == 0, st
+    if ws > 1:
+        tt = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        times = [float(tt.item())] * ws
+    else:
+        times = [elapsed]
+    agg = aggregate(times, E, args.steps)
+
+    # ------------------------------------------------- per-kernel roofline
+    ds.ds_profile_enable(d.ctx, True)
+    n_prof = min(args.steps, 10)
+    for k in range(n_prof):
+        step(k)
+    prof = ds.ds_profile_read(d.ctx)
+    ds.ds_profile_enable(d.ctx, False)
+    d.sync(stream)
+    table_stride = ((4 * cfg["n_sectors"] * 64 + 1) + 7) & ~7
+    alg = algorithmic(E, S, H, n_t, n_v, n_cand, n_pairs, table_stride)
+    kernels = {k: dict(launches=v[0], avg_us=1e3 * v[1] / max(v[0], 1)) for k, v in prof.items()}
+    step_us = sum(v["avg_us"] * v["launches"] for v in kernels.values()) / n_prof
+    for k, v in kernels.items():
+        v["share"] = v["avg_us"] * v["launches"] / n_prof / step_us
+        a = alg.get(k, {})
+        v["gbs"] = a.get("bytes", 0) / (v["avg_us"] * 1e-6) / 1e9 if v["avg_us"] > 0 else 0.0
+        if "flop" in a:
+            v["tflops"] = a["flop"] / (v["avg_us"] * 1e-6) / 1e12
+    dom = max(kernels, key=lambda k: kernels[k]["share"])
+    hbm, sm_mhz, src = peaks()
+    alu_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    kd = kernels[dom]
+    frac_hbm = kd["gbs"] / hbm
+    frac_alu = kd.get("tflops", 0.0) / alu_peak
+    if frac_alu > frac_hbm:
+        roof = dict(kernel=dom, bound="alu", achieved=kd["tflops"], peak=alu_peak, unit="TFLOP/s",
+                    frac=frac_alu, peak_source=f"148 SM x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} clock)",
+                    hbm_gbs=kd["gbs"], hbm_frac=frac_hbm, traffic=traffic_for(dom))
+    else:
+        roof = dict(kernel=dom, bound="hbm", achieved=kd["gbs"], peak=hbm, unit="GB/s", frac=frac_hbm,
+                    peak_source=f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback",
+                    traffic=traffic_for(dom))
+    path_bytes = 24 * S + 13 * H + 64 * n_t + 32 * n_v
+    path = dict(bytes_per_step=path_bytes, gbs=path_bytes * args.steps / max(times) / 1e9,
+                frac_of_hbm=path_bytes * args.steps / max(times) / 1e9 / hbm)
+
+    # ---------------------------------------------------------- end to end
+    pin = {}
+    for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2", "hit_x0", "hit_ybeg", "hit_yend",
+              "hit_layer", "seed_off", "hit_off"):
+        t = torch.from_numpy(np.ascontiguousarray(batch[k])).pin_memory()
+        pin[k] = t.numpy()
+    pin["n_events"] = E
+    host_out = dict(tracks=torch.zeros((S, 64), dtype=torch.uint8).pin_memory().numpy().view(ds.TRACK_DTYPE).reshape(-1),
+                    trk_off=torch.zeros(E + 1, dtype=torch.int32).pin_memory().numpy(),
+                    vertices=torch.zeros((vcap, 32), dtype=torch.uint8).pin_memory().numpy().view(ds.VERTEX_DTYPE).reshape(-1),
+                    vtx_off=torch.zeros(E + 1, dtype=torch.int32).pin_memory().numpy())
+    n_e2e = min(args.steps, 10)
+    for _ in range(2):
+        ds.ds_process_host(d.ctx, pin, S, vcap, stream, host_out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        h = ds.ds_process_host(d.ctx, pin, S, vcap, stream, host_out)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e = dict(value=ws * E / e2e_s, unit="events/s", h2d_bytes_per_step=in_bytes,
+               d2h_bytes_per_step=64 * h["n_tracks"] + 32 * h["n_vertices"] + 8 * (E + 1) + 8,
+               ms_per_step=1e3 * e2e_s)
+
+    # ------------------------------------------------ plain form (1 event/launch)
+    n_plain = min(args.plain_events, E)
+    dv = devs[0]
+    per_event = []
+    for e in range(n_plain):
+        s0, s1 = int(batch["seed_off"][e]), int(batch["seed_off"][e + 1])
+        h0, h1 = int(batch["hit_off"][e]), int(batch["hit_off"][e + 1])
+        pe = dict(n_events=1, n_seeds=s1 - s0, n_hits=h1 - h0,
+                  seed_off=torch.tensor([0, s1 - s0], dtype=torch.int32, device="cuda"),
+                  hit_off=torch.tensor([0, h1 - h0], dtype=torch.int32, device="cuda"))
+        for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2"):
+            pe[k] = dv[k][s0:s1]
+        for k in ("hit_x0", "hit_ybeg", "hit_yend", "hit_layer"):
+            pe[k] = dv[k][h0:h1]
+        per_event.append(pe)
+    pout = d.alloc_tracks(1, 4096)
+    pvout = d.alloc_vertices(1, 1 << 16)
+    for pe in per_event[:5]:
+        d.reconstruct(pe, pout, stream); d.vertex(pout, pvout, stream)
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True); p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for pe in per_event:
+        d.reconstruct(pe, pout, stream)
+        d.vertex(pout, pvout, stream)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_s = p0.elapsed_time(p1) / 1e3
+    d.sync(stream)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(batch, cfg, w)
+
+    if rank == 0:
+        line = dict(
+            metric="events/s per B300 (Downstream+vertexing)", value=agg["value"], unit="events/s", n_gpus=ws,
+            steps=args.steps, warmup=args.warmup, ms_per_step=agg["ms_per_step"], higher_is_better=True,
+            scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+            config=dict(workload=WORKLOAD, n_events=E, n_seeds=S, n_hits=H, tracks=n_t, vertices=n_v,
+                        candidates=n_cand, pairs=n_pairs, pairs_fp64=n_fp64, mlp="fp32",
+                        l2=f"inputs rotate over {R} replicas ({R * in_bytes / 2**20:.0f} MB > 3x L2)",
+                        parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
+            roofline=roof, path_roofline=path, kernels=kernels, clocks=clocks, e2e=e2e,
+            plain_form=dict(value=n_plain / plain_s, unit="events/s",
+                            note="one event per ds_reconstruct + ds_vertex call, FP32", events=n_plain),
+            eager=dict(value=ws * E * args.steps / eager_s, unit="events/s",
+                       note="same steps launched from Python without CUDA graphs"),
+            gpu_launches=KERNELS_PER_STEP * args.steps,
+            cpu_baseline=cpu)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    d.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,293 @@
+/*
+ * ds.h - C ABI of the B300 Downstream tracking + two-track vertexing library
+ * (libds.so).
+ *
+ * The calls follow the paper's statement of the problem (arXiv:2503.13092):
+ *   inputs   SciFi seeds not used by long tracks (x, y, tx, ty, q/p, chi2 at the
+ *            last SciFi station) and decoded UT hits (Algorithm Design section);
+ *   output   downstream tracks: state (x, y, tx, ty, q/p) at the UT reference
+ *            plane, chi2, UT hits and ghost-killer response (Ghost-Killer Neural
+ *            Network section);
+ *   output   two-track vertices from opposite-charge pairs (Vertexing Two
+ *            Downstream Tracks section, Eqs. 3-4; Expected Physics Impact).
+ *
+ * Conventions
+ *   - Units: mm, MeV, MeV/c; q/p in c/MeV.  Layer order: UTaX, UTaU, UTbV, UTbX.
+ *   - Batch inputs and outputs are DEVICE pointers owned by the caller (any CUDA
+ *     allocator); the library never frees them.  Host structs passed by pointer
+ *     are read during the call only and may be freed afterwards.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are asynchronous on that stream; a context is not thread safe and
+ *     must be used from one host thread at a time.  Several contexts may share a
+ *     device.
+ *   - Errors found on the host (bad arguments, missing geometry or weights, a
+ *     failed CUDA call) are returned immediately and described by
+ *     ds_last_error().  Errors found on the device (malformed offsets, hits that
+ *     break the strip/sector contract, capacity overflow, a bounded wait that ran
+ *     out) set bits in a device-side flag word that ds_sync_status() reads after
+ *     synchronising the stream.
+ *   - Workspaces are device memory owned by the context.  They are sized by
+ *     ds_reserve(); a call that needs more grows them first (a synchronous
+ *     allocation), so callers that capture CUDA graphs reserve beforehand.
+ */
+#ifndef DS_H
+#define DS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DS_API __attribute__((visibility("default")))
+#else
+#define DS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ds_ctx ds_ctx;
+
+typedef enum {
+    DS_OK = 0,
+    DS_ERR_ARG = -1,          /* invalid argument (null pointer, bad size, bad parameter) */
+    DS_ERR_CUDA = -2,         /* a CUDA runtime call failed (message in ds_last_error) */
+    DS_ERR_CAPACITY = -3,     /* an output capacity was exceeded; outputs truncated */
+    DS_ERR_NOT_READY = -4,    /* geometry or network weights not loaded */
+    DS_ERR_TIMEOUT = -5,      /* a device-side bounded wait gave up */
+    DS_ERR_DEVICE_FLAG = -6,  /* the device flagged malformed input (ds_stats.device_flags) */
+    DS_ERR_OOM = -7           /* device allocation failed */
+} ds_status;
+
+/* Device flag bits, reported in ds_stats.device_flags by ds_sync_status(). */
+enum {
+    DS_FLAG_BAD_OFFSETS = 1u << 0,   /* seed_off / hit_off not monotone or not matching totals */
+    DS_FLAG_BAD_LAYER = 1u << 1,     /* a hit with layer >= 4 or a non-finite coordinate (ignored) */
+    DS_FLAG_STRIP_SECTOR = 1u << 2,  /* a strip extent crosses its Y-sector boundary */
+    DS_FLAG_EVENT_TOO_LARGE = 1u << 3, /* an event has more than 65535 hits (event skipped) */
+    DS_FLAG_TRACK_CAPACITY = 1u << 4,  /* more tracks than ds_tracks.capacity (truncated) */
+    DS_FLAG_VERTEX_CAPACITY = 1u << 5, /* more vertices than capacity, or an event with more
+                                          than 4096 tracks (only its first 4096 are paired) */
+    DS_FLAG_TIMEOUT = 1u << 6          /* a bounded device-side wait ran out */
+};
+
+/* Geometry of the UT and of the magnet kink model (Algorithm Design section,
+ * Eq. 1; Fig. 2).  Host struct, copied into the context. */
+typedef struct {
+    double z_layer[4];     /* z of UTaX, UTaU, UTbV, UTbX (mm), strictly increasing */
+    double dxdy[4];        /* tan(stereo angle) per layer; a hit measures x0 = x - dxdy*y */
+    double y_min;          /* lower edge of the first Y sector (mm) */
+    double sector_h;       /* Y-sector height (mm) */
+    int32_t n_sectors;     /* number of Y sectors, 1..32 */
+    int32_t reserved0;
+    double x_half_bins;    /* half-range of x0 covered by the per-sector x bins (mm) */
+    double z_seed;         /* z of the SciFi seed state (mm) */
+    double zmag[4];        /* z_magnet = zmag0 + zmag1*tx^2 + zmag2*ty^2 + zmag3*|q/p| */
+    double kappa;          /* transverse momentum kick of the kink (MeV/c) */
+    double mp;             /* magnet polarity, +1 or -1 */
+    double gamma0, gamma1; /* Eq. 3: gamma(q/p) = -MP (gamma0 + gamma1*q/p); 0,0 = straight */
+    double z_ref;          /* reference plane of output states, midpoint of the UT (mm) */
+    double sigma_hit;      /* UT hit resolution (mm) */
+    double sigma_mag;      /* magnet-point resolution used in the fit (mm) */
+} ds_geometry;
+
+/* Ghost-killer network (Ghost-Killer Neural Network section): n_in inputs,
+ * one or two ReLU hidden layers, one sigmoid output.  Host pointers, row-major
+ * [out][in] per layer, FP32.  Supported shapes: n_in <= 16, n_h1 <= 32,
+ * n_h2 <= 32 (n_h2 = 0: single hidden layer, the paper's 8-14-1).  Input i is
+ * normalised as (phi_i - mean_i) * scale_i. */
+typedef struct {
+    int32_t n_in, n_h1, n_h2, reserved0;
+    const float *w1, *b1;  /* [n_h1][n_in], [n_h1] */
+    const float *w2, *b2;  /* [n_h2][n_h1], [n_h2]; ignored when n_h2 = 0 */
+    const float *w3;       /* [n_h2] (or [n_h1] when n_h2 = 0) */
+    float b3;
+    int32_t reserved1;
+    const float *mean, *scale; /* [n_in] */
+} ds_nn_weights;
+
+enum { DS_MLP_FP32 = 0, DS_MLP_BF16 = 1, DS_MLP_FP8 = 2 };
+
+/* Method parameters.  ds_default_params() fills the defaults. */
+typedef struct {
+    double w1a, w1b;       /* first (UTbX) window half-width: w1a + w1b*|q/p| (mm) */
+    double w2;             /* refined window half-width in UTaX/UTaU/UTbV (mm) */
+    double dy_tol;         /* tolerance on a strip's y extent (mm) */
+    double nn_threshold;   /* keep a track if its ghost-killer response < threshold */
+    double doca_max;       /* keep a vertex if DOCA < doca_max (mm) */
+    double nr_tol;         /* Newton-Raphson step tolerance (mm) */
+    double eps_parallel;   /* sin^2(opening angle) below which a pair is re-solved in FP64 */
+    int32_t k1;            /* UTbX hits kept per seed, 1..10 (paper: 10) */
+    int32_t first_window_origin; /* 1: window centred on the line (0,0,0)-magnet point (Dv0) */
+    int32_t pick_chi2;     /* 0: best = lowest NN response among those < threshold;
+                              1: best = lowest chi2/ndof, then the threshold cut */
+    int32_t clone_kill;    /* 1: kill clones sharing more than two UT hits */
+    int32_t training;      /* 1: fixed 100/10 mm windows, no clone killing */
+    int32_t nr_max_iter;   /* Newton-Raphson iteration limit */
+    int32_t mlp_precision; /* DS_MLP_FP32 (default), DS_MLP_BF16, DS_MLP_FP8 */
+    int32_t reserved0;
+} ds_params;
+
+/* One event batch (CSR over events).  Device pointers. */
+typedef struct {
+    int32_t n_events;
+    int32_t n_seeds;          /* = seed_off[n_events] (host copy, used for launch sizes) */
+    int32_t n_hits;           /* = hit_off[n_events] */
+    int32_t reserved0;
+    const int32_t *seed_off;  /* [n_events + 1], seed_off[0] = 0, non-decreasing */
+    const int32_t *hit_off;   /* [n_events + 1], hit_off[0] = 0, non-decreasing */
+} ds_event_batch;
+
+/* SciFi seeds, device SoA float32 [n_seeds] each, grouped by event. */
+typedef struct {
+    const float *x, *y, *tx, *ty, *qop, *chi2;
+} ds_seeds;
+
+/* UT hits, device SoA [n_hits] each, grouped by event, any order inside an
+ * event.  x0 = x at y = 0 of the strip; [ybeg, yend] = the strip's y extent,
+ * which must lie inside one Y sector [y_min + k*sector_h, y_min + (k+1)*sector_h].
+ * A hit's id is its index in these arrays. */
+typedef struct {
+    const float *x0, *ybeg, *yend;
+    const uint8_t *layer;     /* 0..3 = UTaX, UTaU, UTbV, UTbX */
+} ds_ut_hits;
+
+/* Output track record, 64 bytes. */
+typedef struct {
+    int32_t event;            /* event index in the batch */
+    int32_t seed;             /* global seed index */
+    int32_t hit[4];           /* hit ids in UTaX, UTaU, UTbV, UTbX; -1 = absent */
+    float x, y, tx, ty, qop;  /* state at z_ref */
+    float chi2;
+    int32_t ndof;
+    float nn;                 /* ghost-killer response */
+    uint32_t flags;           /* reserved, 0 */
+    int32_t n_candidates;     /* candidates scored for this seed */
+} ds_track;
+
+/* Track output buffers (device).  Tracks are packed in (event, seed) order;
+ * trk_off[e]..trk_off[e+1] are event e's tracks. */
+typedef struct {
+    ds_track *tracks;         /* [capacity] */
+    int32_t *trk_off;         /* [n_events + 1] */
+    int32_t *n_tracks;        /* device scalar: tracks produced (may exceed capacity) */
+    int32_t capacity;
+    int32_t n_events;         /* filled by ds_reconstruct; read by ds_vertex */
+} ds_tracks;
+
+/* Output vertex record, 32 bytes.  When the vertex capacity is exceeded the
+ * counts and vtx_off are still exact but which records were stored is not
+ * specified; size the capacity from *n_vertices and call again. */
+typedef struct {
+    int32_t event;
+    int32_t i, j;             /* global indices into the track output, i < j */
+    float x, y, z;            /* midpoint of the closest-approach points */
+    float doca;
+    uint32_t flags;           /* bit0: solved in FP64 (near-parallel pair); bit1: not converged */
+} ds_vertex_rec;
+
+typedef struct {
+    ds_vertex_rec *vertices;  /* [capacity], (event, i, j) order */
+    int32_t *vtx_off;         /* [n_events + 1] */
+    int32_t *n_vertices;      /* device scalar: vertices produced (may exceed capacity) */
+    int32_t capacity;
+    int32_t reserved0;
+} ds_vertices;
+
+/* Counters of the last synchronised work (ds_sync_status fills them). */
+typedef struct {
+    int64_t n_candidates;     /* candidates scored */
+    int64_t n_pairs;          /* opposite-charge pairs solved */
+    int64_t n_pairs_fp64;     /* pairs re-solved in FP64 */
+    int32_t n_tracks, n_vertices;
+    uint32_t device_flags;
+    int32_t reserved0;
+} ds_stats;
+
+/* Per-kernel device time collected when profiling is enabled. */
+typedef struct {
+    char name[32];            /* kernel name, e.g. "k_search" */
+    int32_t launches;
+    int32_t reserved0;
+    double total_ms;          /* sum of CUDA-event durations on the launching stream */
+} ds_kernel_time;
+
+/* ------------------------------------------------------------------ lifetime */
+
+/* Create a context on CUDA device `device`.  *out receives the handle. */
+DS_API ds_status ds_create(ds_ctx **out, int device);
+/* Release the context and its workspaces (synchronises its device). NULL ok. */
+DS_API void ds_destroy(ds_ctx *ctx);
+DS_API const char *ds_status_string(ds_status s);
+/* Last host-side error message of this context ("" if none). */
+DS_API const char *ds_last_error(const ds_ctx *ctx);
+/* Fill *p with the default method parameters. */
+DS_API ds_status ds_default_params(ds_params *p);
+
+/* ----------------------------------------------------------------- state */
+
+/* Copy the geometry into the context.  DS_ERR_ARG if z_layer is not increasing,
+ * n_sectors is outside 1..32, sector_h, x_half_bins or sigmas are not > 0. */
+DS_API ds_status ds_load_geometry(ds_ctx *ctx, const ds_geometry *geom);
+/* Copy the ghost-killer network into the context (FP32 master; reduced-
+ * precision copies are derived from it).  DS_ERR_ARG for unsupported shapes. */
+DS_API ds_status ds_load_nn_weights(ds_ctx *ctx, const ds_nn_weights *w);
+/* Set the method parameters.  DS_ERR_ARG if k1 is outside 1..10 or a window,
+ * tolerance or limit is not positive. */
+DS_API ds_status ds_set_params(ds_ctx *ctx, const ds_params *p);
+/* Size the workspaces for batches up to these totals (synchronous allocation).
+ * Calls on larger batches grow the workspaces themselves. */
+DS_API ds_status ds_reserve(ds_ctx *ctx, int32_t max_events, int32_t max_seeds, int32_t max_hits);
+
+/* ----------------------------------------------------------------- compute */
+
+/* Downstream tracking (Algorithm Design and Ghost-Killer sections): for every
+ * seed, magnet point -> UTbX window (k1 closest) -> refined windows (1/2/2
+ * closest) -> candidates with >= 3 hits and a station-a hit -> line fit with the
+ * magnet-point constraint -> ghost-killer response -> best candidate; then
+ * clone killing inside each event.  Writes out->tracks, out->trk_off,
+ * *out->n_tracks and sets out->n_events.  DS_ERR_NOT_READY without geometry
+ * or weights; DS_ERR_ARG for null pointers or negative sizes. */
+DS_API ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *batch, const ds_seeds *seeds,
+                         const ds_ut_hits *hits, ds_tracks *out, void *stream);
+
+/* Two-track vertexing (Vertexing section, Eqs. 3-4): for each event, every
+ * pair i < j of its tracks with opposite charge, Newton-Raphson closest
+ * approach of the two quadratic-in-x trajectories, vertex = midpoint, kept if
+ * DOCA < doca_max.  Pairs with sin^2(opening) < eps_parallel whose FP32 DOCA
+ * is near or below the cut are re-solved in FP64.  `tracks` is the output of
+ * ds_reconstruct (device), with n_events set. */
+DS_API ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tracks, ds_vertices *out, void *stream);
+
+/* Synchronise `stream`, read and clear the device flag word and counters.
+ * Returns DS_ERR_CAPACITY / DS_ERR_TIMEOUT / DS_ERR_DEVICE_FLAG when the
+ * corresponding flags are set, else DS_OK.  stats may be NULL. */
+DS_API ds_status ds_sync_status(ds_ctx *ctx, void *stream, ds_stats *stats);
+
+/* Profiling: when enabled, every kernel launch of this context is bracketed
+ * by two CUDA events on its stream.  ds_profile_read() synchronises the
+ * device, returns one entry per kernel name (at most max_out; *n_out = number
+ * of distinct kernels) and clears the records.  Profiling adds two event
+ * records per launch; leave it off for throughput measurements. */
+DS_API ds_status ds_profile_enable(ds_ctx *ctx, int32_t enable);
+DS_API ds_status ds_profile_read(ds_ctx *ctx, ds_kernel_time *out, int32_t max_out, int32_t *n_out);
+
+/* End-to-end call with HOST buffers: copies the batch to context-owned device
+ * buffers, runs ds_reconstruct and ds_vertex, copies tracks, trk_off, vertices
+ * and vtx_off back, and synchronises.  Host inputs use the layouts above (SoA
+ * float32, uint8 layer, int32 offsets); pinned memory is fastest.  On return
+ * *n_tracks / *n_vertices hold the produced counts (outputs truncated to the
+ * given capacities, DS_ERR_CAPACITY).  h_trk_off and h_vtx_off have
+ * n_events + 1 entries. */
+DS_API ds_status ds_process_host(ds_ctx *ctx, int32_t n_events, const int32_t *h_seed_off,
+                          const float *h_seed_cols[6], const int32_t *h_hit_off,
+                          const float *h_hit_cols[3], const uint8_t *h_hit_layer,
+                          ds_track *h_tracks, int32_t trk_capacity, int32_t *h_trk_off,
+                          int32_t *n_tracks, ds_vertex_rec *h_vertices, int32_t vtx_capacity,
+                          int32_t *h_vtx_off, int32_t *n_vertices, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DS_H */

@@ -216,5 +216,5 @@ def clone_kill(hits, k1, k2, enabled: bool = True, has=None) -> np.ndarray:
     k1 = np.ascontiguousarray(k1, np.float64); k2 = np.ascontiguousarray(k2, np.float64)
     st = np.zeros(n, np.int32)
     lib().or_clone_kill(C.c_int(n), _p(has), _p(hits), _p(k1), _p(k2), C.c_int(int(enabled)),
-                        _p(st), None)
+                        C.c_int(0), _p(st), None)
     return st

@@ -86,11 +86,24 @@ static void upd_margin(double *m, double a, double b, double s)
     if (r < *m) *m = r;
 }
 
+/* Key comparisons: a network response is compared on an absolute scale; a
+ * chi2 (or chi2/ndof) comparison counts in units of the chi2 tolerance, 1e-3
+ * relative, so a 1e-3 relative gap maps to a margin of 1e-5. */
+static void upd_key_margin(double *m, int is_chi2, double a, double b)
+{
+    if (is_chi2) {
+        double r = fabs(a - b) / fmax(fmax(fabs(a), fabs(b)), 1e-300) * 1e-2;
+        if (r < *m) *m = r;
+    } else {
+        upd_margin(m, a, b, 1.0);
+    }
+}
+
 /* ------------------------------------------------------------- ghost killer */
 
 /* Ghost-Killer Neural Network section: inputs -> ReLU hidden layer(s) ->
- * sigmoid output, all in double precision. */
-double or_mlp(const or_nn *nn, const double *phi)
+ * output node; or_mlp applies the sigmoid.  Double precision throughout. */
+double or_mlp_logit(const or_nn *nn, const double *phi)
 {
     double xin[32], h1[64], h2[64];
     for (int i = 0; i < nn->n_in; ++i)
@@ -113,7 +126,12 @@ double or_mlp(const or_nn *nn, const double *phi)
     }
     double out = nn->b3;
     for (int i = 0; i < n_last; ++i) out += (double)nn->w3[i] * last[i];
-    return 1.0 / (1.0 + exp(-out));
+    return out;
+}
+
+double or_mlp(const or_nn *nn, const double *phi)
+{
+    return 1.0 / (1.0 + exp(-or_mlp_logit(nn, phi)));
 }
 
 /* -------------------------------------------------------------- per seed */
@@ -124,6 +142,7 @@ typedef struct {
     double chi2;
     int ndof;
     double f;              /* ghost-killer response */
+    double logit;          /* network output before the sigmoid */
     double k1, k2;         /* pick key components */
     double phi[16];
 } or_cand;
@@ -149,7 +168,8 @@ static int cmp_ranked(const void *a, const void *b)
  * strip extent contains y (with tolerance dy_tol); rank them by (|dx|, id) and
  * keep the closest `keep`.  Returns the number kept; out[] holds local indices. */
 static int window_search(const or_config *c, const or_event_hits *ev, int l, double u_pred,
-                         double y, double w, int keep, int *out, double *out_d, double *m)
+                         double y, double w, int keep, int *out, double *out_d, double *m,
+                         double sx_seed, double sy_seed)
 {
     or_ranked *q = (or_ranked *)malloc(sizeof(or_ranked) * (size_t)(ev->n > 0 ? ev->n : 1));
     int nq = 0;
@@ -161,11 +181,11 @@ static int window_search(const or_config *c, const or_event_hits *ev, int l, dou
         double hi = (double)ev->yend[h] + c->dy_tol;
         int in_x = fabs(dx) < w;
         int in_y = (lo <= y) && (y <= hi);
-        double sx = fmax(fabs(x0), fabs(u_pred));
+        double sx = fmax(fmax(fabs(x0), fabs(u_pred)), sx_seed);
         if (in_y) upd_margin(m, fabs(dx), w, sx);
         if (in_x) {
-            upd_margin(m, y, lo, 1.0);
-            upd_margin(m, y, hi, 1.0);
+            upd_margin(m, y, lo, sy_seed);
+            upd_margin(m, y, hi, sy_seed);
         }
         if (in_x && in_y) {
             q[nq].d = fabs(dx);
@@ -175,7 +195,7 @@ static int window_search(const or_config *c, const or_event_hits *ev, int l, dou
         }
     }
     qsort(q, (size_t)nq, sizeof(or_ranked), cmp_ranked);
-    if (nq > keep) upd_margin(m, q[keep - 1].d, q[keep].d, fmax(fabs(u_pred), 1.0));
+    if (nq > keep) upd_margin(m, q[keep - 1].d, q[keep].d, fmax(fabs(u_pred), sx_seed));
     int n = nq < keep ? nq : keep;
     for (int i = 0; i < n; ++i) {
         out[i] = q[i].idx;
@@ -295,11 +315,15 @@ static int process_seed(const or_config *c, const or_nn *nn, const or_event_hits
     const double zm = pred[0], xm = pred[1], ym = pred[2], u_bx = pred[3], w1 = pred[4];
     double yl[4] = {pred[5], pred[6], pred[7], pred[8]};
     const double w2 = pred[9];
+    /* magnitudes of the intermediates behind the predictions: a window or
+     * strip decision is only as sharp as the largest coordinate it came from */
+    const double sxs = fmax(fmax(fabs(x_s), fabs(tx_s * (zm - c->z_seed))), fmax(fabs(xm), 1.0));
+    const double sys = fmax(fmax(fabs(y_s), fabs(ty_s * (zm - c->z_seed))), fmax(fabs(ym), 1.0));
 
     int bx[OR_MAX_K1];
     double bx_d[OR_MAX_K1];
     const int k1 = c->k1 < OR_MAX_K1 ? c->k1 : OR_MAX_K1;
-    int nbx = window_search(c, ev, 3, u_bx, yl[3], w1, k1, bx, bx_d, &m);
+    int nbx = window_search(c, ev, 3, u_bx, yl[3], w1, k1, bx, bx_d, &m, sxs, sys);
     if (n_bx_out) *n_bx_out = nbx;
 
     int ncand = 0;
@@ -318,7 +342,7 @@ static int process_seed(const or_config *c, const or_nn *nn, const or_event_hits
         for (int l = 0; l < 3; ++l) {
             double xl = x_h + txp * (c->z[l] - c->z[3]);
             double ul = xl - c->dxdy[l] * yl[l];
-            nsel[l] = window_search(c, ev, l, ul, yl[l], w2, keep[l], sel[l], NULL, &m);
+            nsel[l] = window_search(c, ev, l, ul, yl[l], w2, keep[l], sel[l], NULL, &m, sxs, sys);
         }
         /* options per layer: its kept hits, or "absent" only if none qualified */
         int na = nsel[0] ? nsel[0] : 1, nu = nsel[1] ? nsel[1] : 1, nv = nsel[2] ? nsel[2] : 1;
@@ -361,9 +385,13 @@ static int process_seed(const or_config *c, const or_nn *nn, const or_event_hits
                     p[12] = nh / 4.0;
                     p[13] = bx_d[j] / w1;
                     p[14] = tx_s; p[15] = ty_s;
-                    cd.f = or_mlp(nn, p);
-                    if (c->pick_chi2) { cd.k1 = chi2 / ndof; cd.k2 = cd.f; }
-                    else { cd.k1 = cd.f; cd.k2 = chi2; }
+                    /* candidates are ranked by the network output before the
+                     * sigmoid: the same order as the response, without the
+                     * sigmoid's saturation at 0 and 1 */
+                    cd.logit = or_mlp_logit(nn, p);
+                    cd.f = 1.0 / (1.0 + exp(-cd.logit));
+                    if (c->pick_chi2) { cd.k1 = chi2 / ndof; cd.k2 = cd.logit; }
+                    else { cd.k1 = cd.logit; cd.k2 = chi2; }
                     if (cands && ncand < max_c) cands[ncand] = cd;
                     all[ncand] = cd;
                     ++ncand;
@@ -385,8 +413,8 @@ static int process_seed(const or_config *c, const or_nn *nn, const or_event_hits
             if (i == wi) continue;
             int elig = c->pick_chi2 || all[i].f < T;
             if (elig) {
-                if (all[i].k1 != win.k1) upd_margin(&m, all[i].k1, win.k1, 1.0);
-                else upd_margin(&m, all[i].k2, win.k2, 1.0);
+                if (all[i].k1 != win.k1) upd_key_margin(&m, c->pick_chi2, all[i].k1, win.k1);
+                else upd_key_margin(&m, !c->pick_chi2, all[i].k2, win.k2);
             } else if (key_less(&all[i], &win)) {
                 upd_margin(&m, all[i].f, T, 1.0);
             }
@@ -410,7 +438,7 @@ static int process_seed(const or_config *c, const or_nn *nn, const or_event_hits
  * against the full set before killing, so the result does not depend on the
  * order of the pairs.  status: 0 no winner, 1 killed, 2 kept. */
 void or_clone_kill(int n, const int *has, const int *hits, const double *k1, const double *k2,
-                   int enabled, int *status, double *margin)
+                   int enabled, int k1_is_chi2, int *status, double *margin)
 {
     for (int b = 0; b < n; ++b) {
         if (!has[b]) {
@@ -424,8 +452,8 @@ void or_clone_kill(int n, const int *has, const int *hits, const double *k1, con
             for (int l = 0; l < 4; ++l) shared += hits[4 * a + l] >= 0 && hits[4 * a + l] == hits[4 * b + l];
             if (shared <= 2) continue;
             if (margin) {
-                if (k1[a] != k1[b]) upd_margin(&margin[b], k1[a], k1[b], 1.0);
-                else upd_margin(&margin[b], k2[a], k2[b], 1.0);
+                if (k1[a] != k1[b]) upd_key_margin(&margin[b], k1_is_chi2, k1[a], k1[b]);
+                else upd_key_margin(&margin[b], !k1_is_chi2, k2[a], k2[b]);
             }
             int a_better = (k1[a] < k1[b]) || (k1[a] == k1[b] && k2[a] < k2[b]) ||
                            (k1[a] == k1[b] && k2[a] == k2[b] && a < b);
@@ -480,7 +508,8 @@ void or_reconstruct(const or_config *c, const or_nn *nn, int n_events, const int
             k1[b] = win[b].k1;
             k2[b] = win[b].k2;
         }
-        or_clone_kill(ns, has, wh, k1, k2, c->clone_kill && !c->training, st, margin + s0);
+        or_clone_kill(ns, has, wh, k1, k2, c->clone_kill && !c->training, c->pick_chi2, st,
+                      margin + s0);
         for (int b = 0; b < ns; ++b) {
             int s = s0 + b;
             status[s] = st[b];

@@ -1,0 +1,622 @@
+// C ABI of libds.so: contexts, device-resident state, launches.
+// Declarations and the contract of every call are in include/ds.h.
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ds_args.cuh"
+
+struct ds_ctx {
+    int device = 0;
+    int sm_count = 148;
+    bool has_geom = false, has_nn = false;
+    ds::DevGeom g{};
+    ds::DevParams p{};
+    ds::DevNN nn{};
+    int nn_in = 16, nn_h1 = 32, nn_h2 = 32;
+    int mlp_precision = DS_MLP_FP32;
+    ds::DevCounters *d_cnt = nullptr;
+    // workspaces
+    int cap_events = 0, cap_seeds = 0, cap_hits = 0, cap_pool = 0;
+    float4 *sorted = nullptr;
+    uint16_t *bins = nullptr;
+    ds_track *trk_ws = nullptr;
+    unsigned long long *key_ws = nullptr;
+    int4 *hit_ws = nullptr;
+    int *rank_ws = nullptr;
+    int *count_trk = nullptr;
+    int *count_vtx = nullptr;
+    ds_vertex_rec *pool = nullptr;
+    int *pool_pos = nullptr;
+    // host-buffer path: device copies of inputs and outputs
+    struct {
+        int cap_events = 0, cap_seeds = 0, cap_hits = 0, cap_trk = 0, cap_vtx = 0;
+        int32_t *seed_off = nullptr, *hit_off = nullptr;
+        float *seed_cols = nullptr, *hit_cols = nullptr;
+        uint8_t *layer = nullptr;
+        ds_track *tracks = nullptr;
+        int32_t *trk_off = nullptr, *vtx_off = nullptr, *counts = nullptr;
+        ds_vertex_rec *vertices = nullptr;
+    } h;
+    ds::Prof prof;
+    std::string err;
+};
+
+namespace ds {
+
+void Prof::begin(const char *name, cudaStream_t st)
+{
+    if (!on) return;
+    Rec r{name, nullptr, nullptr};
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+    cudaEventRecord(r.a, st);
+    recs.push_back(r);
+}
+
+void Prof::end(cudaStream_t st)
+{
+    if (!on || recs.empty()) return;
+    cudaEventRecord(recs.back().b, st);
+}
+
+}  // namespace ds
+
+namespace {
+
+ds_status fail(ds_ctx *c, ds_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+ds_status cuda_fail(ds_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, DS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define DS_CUDA(call, what)                                        \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what);    \
+    } while (0)
+
+template <class T>
+ds_status grow(ds_ctx *ctx, T **p, size_t n)
+{
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (n > 0 ? n : 1));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(ctx, DS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return DS_OK;
+}
+
+bool stream_capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+ds_status ensure_workspace(ds_ctx *ctx, int E, int S, int H, cudaStream_t st)
+{
+    if (E <= ctx->cap_events && S <= ctx->cap_seeds && H <= ctx->cap_hits) return DS_OK;
+    if (stream_capturing(st))
+        return fail(ctx, DS_ERR_ARG, "workspace too small during stream capture; call ds_reserve first");
+    return ds_reserve(ctx, E, S, H);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ds_status_string(ds_status s)
+{
+    switch (s) {
+    case DS_OK: return "ok";
+    case DS_ERR_ARG: return "invalid argument";
+    case DS_ERR_CUDA: return "CUDA error";
+    case DS_ERR_CAPACITY: return "output capacity exceeded";
+    case DS_ERR_NOT_READY: return "geometry or network weights not loaded";
+    case DS_ERR_TIMEOUT: return "device-side wait timed out";
+    case DS_ERR_DEVICE_FLAG: return "device flagged malformed input";
+    case DS_ERR_OOM: return "device out of memory";
+    }
+    return "unknown status";
+}
+
+const char *ds_last_error(const ds_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+ds_status ds_default_params(ds_params *p)
+{
+    if (!p) return DS_ERR_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->w1a = 3.0;
+    p->w1b = 1.7e5;
+    p->w2 = 2.0;
+    p->dy_tol = 2.0;
+    p->nn_threshold = 0.5;
+    p->doca_max = 2.0;
+    p->nr_tol = 1e-6;
+    p->eps_parallel = 1e-3;
+    p->k1 = 10;
+    p->first_window_origin = 0;
+    p->pick_chi2 = 0;
+    p->clone_kill = 1;
+    p->training = 0;
+    p->nr_max_iter = 10;
+    p->mlp_precision = DS_MLP_FP32;
+    return DS_OK;
+}
+
+ds_status ds_create(ds_ctx **out, int device)
+{
+    if (!out) return DS_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return DS_ERR_CUDA;
+    ds_ctx *ctx = new ds_ctx();
+    ctx->device = device;
+    DS_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc((void **)&ctx->d_cnt, sizeof(ds::DevCounters)) != cudaSuccess) {
+        delete ctx;
+        return DS_ERR_OOM;
+    }
+    cudaMemset(ctx->d_cnt, 0, sizeof(ds::DevCounters));
+    if (ds::init_vertex_attributes() != cudaSuccess) {
+        cudaFree(ctx->d_cnt);
+        delete ctx;
+        return DS_ERR_CUDA;
+    }
+    ds_params p;
+    ds_default_params(&p);
+    ds_set_params(ctx, &p);
+    *out = ctx;
+    return DS_OK;
+}
+
+void ds_destroy(ds_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    void *ptrs[] = {ctx->d_cnt, ctx->sorted, ctx->bins, ctx->trk_ws, ctx->key_ws, ctx->hit_ws,
+                    ctx->rank_ws, ctx->count_trk, ctx->count_vtx, ctx->pool, ctx->pool_pos,
+                    ctx->h.seed_off, ctx->h.hit_off, ctx->h.seed_cols, ctx->h.hit_cols, ctx->h.layer,
+                    ctx->h.tracks, ctx->h.trk_off, ctx->h.vtx_off, ctx->h.counts, ctx->h.vertices};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    delete ctx;
+}
+
+ds_status ds_load_geometry(ds_ctx *ctx, const ds_geometry *gm)
+{
+    if (!ctx || !gm) return fail(ctx, DS_ERR_ARG, "null pointer");
+    for (int l = 0; l < 3; ++l)
+        if (!(gm->z_layer[l] < gm->z_layer[l + 1])) return fail(ctx, DS_ERR_ARG, "z_layer not increasing");
+    if (gm->n_sectors < 1 || gm->n_sectors > ds::kMaxSectors)
+        return fail(ctx, DS_ERR_ARG, "n_sectors outside 1..32");
+    if (!(gm->sector_h > 0) || !(gm->x_half_bins > 0) || !(gm->sigma_hit > 0) || !(gm->sigma_mag > 0))
+        return fail(ctx, DS_ERR_ARG, "sector_h, x_half_bins and sigmas must be > 0");
+    ds::DevGeom &g = ctx->g;
+    for (int l = 0; l < 4; ++l) {
+        g.z[l] = (float)gm->z_layer[l];
+        g.dxdy[l] = (float)gm->dxdy[l];
+        g.zmag[l] = (float)gm->zmag[l];
+    }
+    g.y_min = (float)gm->y_min;
+    g.sector_h = (float)gm->sector_h;
+    g.inv_sector_h = (float)(1.0 / gm->sector_h);
+    g.n_sec = gm->n_sectors;
+    g.x_half = (float)gm->x_half_bins;
+    g.inv_xbin = (float)(ds::kNXB / (2.0 * gm->x_half_bins));
+    g.z_seed = (float)gm->z_seed;
+    g.kappa = (float)gm->kappa;
+    g.mp = (float)gm->mp;
+    g.gamma0 = (float)gm->gamma0;
+    g.gamma1 = (float)gm->gamma1;
+    g.z_ref = (float)gm->z_ref;
+    g.w_hit = (float)(1.0 / (gm->sigma_hit * gm->sigma_hit));
+    g.w_mag = (float)(1.0 / (gm->sigma_mag * gm->sigma_mag));
+    g.inv_sigma_hit = (float)(1.0 / gm->sigma_hit);
+    const int nb = 4 * g.n_sec * ds::kNXB + 1;
+    g.table_stride = (nb + 7) & ~7;
+    ctx->has_geom = true;
+    ctx->cap_events = 0;   // bin table stride may have changed
+    return DS_OK;
+}
+
+ds_status ds_load_nn_weights(ds_ctx *ctx, const ds_nn_weights *w)
+{
+    if (!ctx || !w || !w->w1 || !w->b1 || !w->w3 || !w->mean || !w->scale)
+        return fail(ctx, DS_ERR_ARG, "null pointer");
+    if (w->n_in < 1 || w->n_in > 16 || w->n_h1 < 1 || w->n_h1 > 32 || w->n_h2 < 0 || w->n_h2 > 32)
+        return fail(ctx, DS_ERR_ARG, "unsupported network shape (n_in<=16, n_h1<=32, n_h2<=32)");
+    if (w->n_h2 > 0 && (!w->w2 || !w->b2)) return fail(ctx, DS_ERR_ARG, "null w2/b2");
+    ds::DevNN &nn = ctx->nn;
+    std::memset(&nn, 0, sizeof(nn));
+    for (int o = 0; o < w->n_h1; ++o) {
+        nn.b1[o] = w->b1[o];
+        for (int i = 0; i < w->n_in; ++i) nn.w1[o][i] = w->w1[o * w->n_in + i];
+    }
+    const int nl = w->n_h2 > 0 ? w->n_h2 : w->n_h1;
+    if (w->n_h2 > 0) {
+        for (int o = 0; o < w->n_h2; ++o) {
+            nn.b2[o] = w->b2[o];
+            for (int i = 0; i < w->n_h1; ++i) nn.w2[o][i] = w->w2[o * w->n_h1 + i];
+        }
+    }
+    for (int i = 0; i < nl; ++i) nn.w3[i] = w->w3[i];
+    nn.b3 = w->b3;
+    for (int i = 0; i < w->n_in; ++i) {
+        nn.mean[i] = w->mean[i];
+        nn.scale[i] = w->scale[i];
+    }
+    // the single-hidden-layer kernel is compiled for 8 inputs x 16 hidden
+    if (w->n_h2 == 0 && (w->n_in > 8 || w->n_h1 > 16)) {
+        // run it through the two-layer kernel: identity second layer (exact: h1 >= 0)
+        for (int o = 0; o < w->n_h1; ++o) {
+            nn.w2[o][o] = 1.f;
+            nn.b2[o] = 0.f;
+        }
+        ctx->nn_h2 = 32;
+    } else {
+        ctx->nn_h2 = w->n_h2;
+    }
+    ctx->nn_in = w->n_in;
+    ctx->nn_h1 = w->n_h1;
+    ctx->has_nn = true;
+    return DS_OK;
+}
+
+ds_status ds_set_params(ds_ctx *ctx, const ds_params *p)
+{
+    if (!ctx || !p) return fail(ctx, DS_ERR_ARG, "null pointer");
+    if (p->k1 < 1 || p->k1 > ds::kK1Max) return fail(ctx, DS_ERR_ARG, "k1 outside 1..10");
+    if (!(p->w1a >= 0) || !(p->w1b >= 0) || !(p->w2 > 0) || !(p->dy_tol >= 0) || !(p->doca_max > 0) ||
+        !(p->nr_tol > 0) || p->nr_max_iter < 1 || !(p->eps_parallel >= 0))
+        return fail(ctx, DS_ERR_ARG, "window, tolerance or limit not positive");
+    if (p->mlp_precision != DS_MLP_FP32 && p->mlp_precision != DS_MLP_BF16 && p->mlp_precision != DS_MLP_FP8)
+        return fail(ctx, DS_ERR_ARG, "unknown mlp_precision");
+    ds::DevParams &d = ctx->p;
+    d.w1a = (float)p->w1a;
+    d.w1b = (float)p->w1b;
+    d.w2 = (float)p->w2;
+    d.dy_tol = (float)p->dy_tol;
+    d.nn_threshold = (float)p->nn_threshold;
+    if (p->nn_threshold <= 0.0)
+        d.thr_logit = -INFINITY;
+    else if (p->nn_threshold >= 1.0)
+        d.thr_logit = INFINITY;
+    else
+        d.thr_logit = (float)std::log(p->nn_threshold / (1.0 - p->nn_threshold));
+    d.doca_max = (float)p->doca_max;
+    d.nr_tol = (float)p->nr_tol;
+    d.eps_par = (float)p->eps_parallel;
+    d.k1 = p->k1;
+    d.origin = p->first_window_origin ? 1 : 0;
+    d.pick_chi2 = p->pick_chi2 ? 1 : 0;
+    d.clone_kill = p->clone_kill ? 1 : 0;
+    d.training = p->training ? 1 : 0;
+    d.nr_max_iter = p->nr_max_iter;
+    ctx->mlp_precision = p->mlp_precision;
+    return DS_OK;
+}
+
+ds_status ds_reserve(ds_ctx *ctx, int32_t E, int32_t S, int32_t H)
+{
+    if (!ctx || E < 0 || S < 0 || H < 0) return fail(ctx, DS_ERR_ARG, "negative size");
+    if (!ctx->has_geom) return fail(ctx, DS_ERR_NOT_READY, "load the geometry before ds_reserve");
+    DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    DS_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    ds_status st;
+    if (E > ctx->cap_events || ctx->cap_events == 0) {
+        E = E > ctx->cap_events ? E : ctx->cap_events;
+        if ((st = grow(ctx, &ctx->bins, (size_t)E * ctx->g.table_stride)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->count_trk, (size_t)E)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->count_vtx, (size_t)E)) != DS_OK) return st;
+        ctx->cap_events = E;
+    }
+    if (S > ctx->cap_seeds) {
+        if ((st = grow(ctx, &ctx->trk_ws, (size_t)S)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->key_ws, (size_t)S)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->hit_ws, (size_t)S)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->rank_ws, (size_t)S)) != DS_OK) return st;
+        ctx->cap_seeds = S;
+    }
+    if (H > ctx->cap_hits) {
+        if ((st = grow(ctx, &ctx->sorted, (size_t)H)) != DS_OK) return st;
+        ctx->cap_hits = H;
+    }
+    return DS_OK;
+}
+
+ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *sd, const ds_ut_hits *ht,
+                         ds_tracks *out, void *stream)
+{
+    if (!ctx || !b || !sd || !ht || !out) return fail(ctx, DS_ERR_ARG, "null pointer");
+    if (!ctx->has_geom || !ctx->has_nn) return fail(ctx, DS_ERR_NOT_READY, "geometry or weights not loaded");
+    if (b->n_events < 0 || b->n_seeds < 0 || b->n_hits < 0 || out->capacity < 0)
+        return fail(ctx, DS_ERR_ARG, "negative size");
+    if (b->n_events > 0 && (!b->seed_off || !b->hit_off || !out->trk_off || !out->n_tracks))
+        return fail(ctx, DS_ERR_ARG, "null offsets or outputs");
+    if (b->n_seeds > 0 && (!sd->x || !sd->y || !sd->tx || !sd->ty || !sd->qop || !sd->chi2))
+        return fail(ctx, DS_ERR_ARG, "null seed column");
+    if (b->n_hits > 0 && (!ht->x0 || !ht->ybeg || !ht->yend || !ht->layer))
+        return fail(ctx, DS_ERR_ARG, "null hit column");
+    if (out->capacity > 0 && !out->tracks) return fail(ctx, DS_ERR_ARG, "null track buffer");
+    if (ctx->mlp_precision != DS_MLP_FP32)
+        return fail(ctx, DS_ERR_ARG, "reduced-precision network not built in this library");
+    cudaStream_t st = (cudaStream_t)stream;
+    DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ds_status s = ensure_workspace(ctx, b->n_events, b->n_seeds, b->n_hits, st);
+    if (s != DS_OK) return s;
+    out->n_events = b->n_events;
+    if (b->n_events == 0) return DS_OK;
+
+    ds::BucketArgs ba{};
+    ba.g = ctx->g;
+    ba.n_events = b->n_events;
+    ba.n_hits = b->n_hits;
+    ba.hit_off = b->hit_off;
+    ba.x0 = ht->x0;
+    ba.ybeg = ht->ybeg;
+    ba.yend = ht->yend;
+    ba.layer = ht->layer;
+    ba.sorted = ctx->sorted;
+    ba.bins = ctx->bins;
+    ba.cnt = ctx->d_cnt;
+    DS_CUDA(ds::launch_bucket(ba, st, &ctx->prof), "bucket kernel");
+
+    ds::SearchArgs sa{};
+    sa.g = ctx->g;
+    sa.p = ctx->p;
+    sa.nn = ctx->nn;
+    sa.n_events = b->n_events;
+    sa.n_seeds = b->n_seeds;
+    sa.n_hits = b->n_hits;
+    sa.seed_off = b->seed_off;
+    sa.hit_off = b->hit_off;
+    sa.sx = sd->x; sa.sy = sd->y; sa.stx = sd->tx; sa.sty = sd->ty; sa.sqop = sd->qop; sa.schi2 = sd->chi2;
+    sa.sorted = ctx->sorted;
+    sa.bins = ctx->bins;
+    sa.trk_ws = ctx->trk_ws;
+    sa.key_ws = ctx->key_ws;
+    sa.hit_ws = ctx->hit_ws;
+    sa.rank_ws = ctx->rank_ws;
+    sa.cnt = ctx->d_cnt;
+    DS_CUDA(ds::launch_search(sa, ctx->nn_in, ctx->nn_h2, st, &ctx->prof), "search kernel");
+
+    ds::CloneArgs ca{};
+    ca.n_events = b->n_events;
+    ca.n_seeds = b->n_seeds;
+    ca.clone_kill = ctx->p.clone_kill && !ctx->p.training;
+    ca.seed_off = b->seed_off;
+    ca.key_ws = ctx->key_ws;
+    ca.hit_ws = ctx->hit_ws;
+    ca.rank_ws = ctx->rank_ws;
+    ca.count_ws = ctx->count_trk;
+    ca.trk_off = out->trk_off;
+    ca.n_tracks = out->n_tracks;
+    ca.capacity = out->capacity;
+    ca.cnt = ctx->d_cnt;
+    ds::ScatterTrkArgs xa{};
+    xa.n_seeds = b->n_seeds;
+    xa.trk_ws = ctx->trk_ws;
+    xa.rank_ws = ctx->rank_ws;
+    xa.trk_off = out->trk_off;
+    xa.out = out->tracks;
+    xa.capacity = out->capacity;
+    DS_CUDA(ds::launch_clone(ca, xa, st, &ctx->prof), "clone kernel");
+    return DS_OK;
+}
+
+ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tr, ds_vertices *out, void *stream)
+{
+    if (!ctx || !tr || !out) return fail(ctx, DS_ERR_ARG, "null pointer");
+    if (!ctx->has_geom) return fail(ctx, DS_ERR_NOT_READY, "geometry not loaded");
+    if (tr->n_events < 0 || out->capacity < 0) return fail(ctx, DS_ERR_ARG, "negative size");
+    if (tr->n_events == 0) return DS_OK;
+    if (!tr->trk_off || !tr->n_tracks || !out->vtx_off || !out->n_vertices)
+        return fail(ctx, DS_ERR_ARG, "null offsets");
+    if (tr->capacity > 0 && !tr->tracks) return fail(ctx, DS_ERR_ARG, "null track buffer");
+    if (out->capacity > 0 && !out->vertices) return fail(ctx, DS_ERR_ARG, "null vertex buffer");
+    cudaStream_t st = (cudaStream_t)stream;
+    DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int E = tr->n_events;
+    if (E > ctx->cap_events || ctx->cap_pool < out->capacity) {
+        if (stream_capturing(st))
+            return fail(ctx, DS_ERR_ARG, "workspace too small during stream capture; call ds_reserve first");
+        ds_status s = ds_reserve(ctx, E, ctx->cap_seeds, ctx->cap_hits);
+        if (s != DS_OK) return s;
+        if (ctx->cap_pool < out->capacity) {
+            if ((s = grow(ctx, &ctx->pool, (size_t)out->capacity)) != DS_OK) return s;
+            if ((s = grow(ctx, &ctx->pool_pos, (size_t)out->capacity)) != DS_OK) return s;
+            ctx->cap_pool = out->capacity;
+        }
+    }
+    static_assert(offsetof(ds::DevCounters, vtx_queue) == offsetof(ds::DevCounters, pool_used) + sizeof(int),
+                  "pool_used and the vertex queues are cleared together");
+    DS_CUDA(cudaMemsetAsync(&ctx->d_cnt->pool_used, 0, 3 * sizeof(int), st), "memset");
+    ds::VertexArgs va{};
+    va.g = ctx->g;
+    va.p = ctx->p;
+    va.n_events = E;
+    va.trk_capacity = tr->capacity;
+    va.tracks = tr->tracks;
+    va.trk_off = tr->trk_off;
+    va.n_tracks = tr->n_tracks;
+    va.pool = ctx->pool;
+    va.pool_pos = ctx->pool_pos;
+    va.pool_cap = out->capacity;
+    va.count_ws = ctx->count_vtx;
+    va.vtx_off = out->vtx_off;
+    va.n_vertices = out->n_vertices;
+    va.capacity = out->capacity;
+    va.cnt = ctx->d_cnt;
+    ds::ScatterVtxArgs xa{};
+    xa.pool = ctx->pool;
+    xa.pool_pos = ctx->pool_pos;
+    xa.pool_cap = out->capacity;
+    xa.vtx_off = out->vtx_off;
+    xa.out = out->vertices;
+    xa.capacity = out->capacity;
+    xa.cnt = ctx->d_cnt;
+    DS_CUDA(ds::launch_vertex(va, xa, ctx->sm_count, st, &ctx->prof), "vertex kernel");
+    return DS_OK;
+}
+
+ds_status ds_sync_status(ds_ctx *ctx, void *stream, ds_stats *stats)
+{
+    if (!ctx) return DS_ERR_ARG;
+    DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    DS_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+    ds::DevCounters c;
+    DS_CUDA(cudaMemcpy(&c, ctx->d_cnt, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
+    DS_CUDA(cudaMemset(ctx->d_cnt, 0, sizeof(c)), "clear counters");
+    if (stats) {
+        stats->n_candidates = (int64_t)c.n_candidates;
+        stats->n_pairs = (int64_t)c.n_pairs;
+        stats->n_pairs_fp64 = (int64_t)c.n_pairs_fp64;
+        stats->n_tracks = c.n_tracks;
+        stats->n_vertices = c.n_vertices;
+        stats->device_flags = c.flags;
+    }
+    if (c.flags & DS_FLAG_TIMEOUT) return fail(ctx, DS_ERR_TIMEOUT, "device wait timed out");
+    if (c.flags & (DS_FLAG_BAD_OFFSETS | DS_FLAG_BAD_LAYER | DS_FLAG_STRIP_SECTOR | DS_FLAG_EVENT_TOO_LARGE)) {
+        char buf[96];
+        std::snprintf(buf, sizeof(buf), "device flags 0x%x", c.flags);
+        return fail(ctx, DS_ERR_DEVICE_FLAG, buf);
+    }
+    if (c.flags & (DS_FLAG_TRACK_CAPACITY | DS_FLAG_VERTEX_CAPACITY))
+        return fail(ctx, DS_ERR_CAPACITY, "output capacity exceeded");
+    return DS_OK;
+}
+
+ds_status ds_profile_enable(ds_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return DS_ERR_ARG;
+    ctx->prof.on = enable != 0;
+    return DS_OK;
+}
+
+ds_status ds_profile_read(ds_ctx *ctx, ds_kernel_time *out, int32_t max_out, int32_t *n_out)
+{
+    if (!ctx || !n_out || max_out < 0 || (max_out > 0 && !out)) return fail(ctx, DS_ERR_ARG, "null pointer");
+    DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    DS_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    std::vector<ds_kernel_time> acc;
+    for (auto &r : ctx->prof.recs) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, r.a, r.b);
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+        if (e != cudaSuccess) continue;
+        ds_kernel_time *k = nullptr;
+        for (auto &q : acc)
+            if (std::strncmp(q.name, r.name, sizeof(q.name)) == 0) k = &q;
+        if (!k) {
+            ds_kernel_time z{};
+            std::strncpy(z.name, r.name, sizeof(z.name) - 1);
+            acc.push_back(z);
+            k = &acc.back();
+        }
+        k->launches += 1;
+        k->total_ms += ms;
+    }
+    ctx->prof.recs.clear();
+    *n_out = (int32_t)acc.size();
+    for (int i = 0; i < (int)acc.size() && i < max_out; ++i) out[i] = acc[i];
+    return DS_OK;
+}
+
+ds_status ds_process_host(ds_ctx *ctx, int32_t E, const int32_t *h_seed_off, const float *h_seed_cols[6],
+                          const int32_t *h_hit_off, const float *h_hit_cols[3], const uint8_t *h_layer,
+                          ds_track *h_tracks, int32_t trk_cap, int32_t *h_trk_off, int32_t *n_tracks,
+                          ds_vertex_rec *h_vertices, int32_t vtx_cap, int32_t *h_vtx_off, int32_t *n_vertices,
+                          void *stream)
+{
+    if (!ctx || E < 0 || !h_seed_off || !h_seed_cols || !h_hit_off || !h_hit_cols || !h_layer || !h_trk_off ||
+        !h_vtx_off || !n_tracks || !n_vertices || trk_cap < 0 || vtx_cap < 0)
+        return fail(ctx, DS_ERR_ARG, "null pointer or negative size");
+    cudaStream_t st = (cudaStream_t)stream;
+    DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int S = h_seed_off[E], H = h_hit_off[E];
+    if (S < 0 || H < 0) return fail(ctx, DS_ERR_ARG, "negative totals in offsets");
+    auto &h = ctx->h;
+    ds_status s;
+    if (E + 1 > h.cap_events) {
+        if ((s = grow(ctx, &h.seed_off, (size_t)E + 1)) != DS_OK) return s;
+        if ((s = grow(ctx, &h.hit_off, (size_t)E + 1)) != DS_OK) return s;
+        if ((s = grow(ctx, &h.trk_off, (size_t)E + 1)) != DS_OK) return s;
+        if ((s = grow(ctx, &h.vtx_off, (size_t)E + 1)) != DS_OK) return s;
+        if ((s = grow(ctx, &h.counts, (size_t)2)) != DS_OK) return s;
+        h.cap_events = E + 1;
+    }
+    if (S > h.cap_seeds) {
+        if ((s = grow(ctx, &h.seed_cols, (size_t)6 * S)) != DS_OK) return s;
+        h.cap_seeds = S;
+    }
+    if (H > h.cap_hits) {
+        if ((s = grow(ctx, &h.hit_cols, (size_t)3 * H)) != DS_OK) return s;
+        if ((s = grow(ctx, &h.layer, (size_t)H)) != DS_OK) return s;
+        h.cap_hits = H;
+    }
+    if (trk_cap > h.cap_trk) {
+        if ((s = grow(ctx, &h.tracks, (size_t)trk_cap)) != DS_OK) return s;
+        h.cap_trk = trk_cap;
+    }
+    if (vtx_cap > h.cap_vtx) {
+        if ((s = grow(ctx, &h.vertices, (size_t)vtx_cap)) != DS_OK) return s;
+        h.cap_vtx = vtx_cap;
+    }
+    DS_CUDA(cudaMemcpyAsync(h.seed_off, h_seed_off, sizeof(int32_t) * (E + 1), cudaMemcpyHostToDevice, st), "H2D");
+    DS_CUDA(cudaMemcpyAsync(h.hit_off, h_hit_off, sizeof(int32_t) * (E + 1), cudaMemcpyHostToDevice, st), "H2D");
+    for (int k = 0; k < 6 && S > 0; ++k)
+        DS_CUDA(cudaMemcpyAsync(h.seed_cols + (size_t)k * S, h_seed_cols[k], sizeof(float) * S,
+                                cudaMemcpyHostToDevice, st), "H2D");
+    for (int k = 0; k < 3 && H > 0; ++k)
+        DS_CUDA(cudaMemcpyAsync(h.hit_cols + (size_t)k * H, h_hit_cols[k], sizeof(float) * H,
+                                cudaMemcpyHostToDevice, st), "H2D");
+    if (H > 0) DS_CUDA(cudaMemcpyAsync(h.layer, h_layer, H, cudaMemcpyHostToDevice, st), "H2D");
+
+    ds_event_batch b{E, S, H, 0, h.seed_off, h.hit_off};
+    ds_seeds sd{h.seed_cols, h.seed_cols + S, h.seed_cols + 2 * (size_t)S, h.seed_cols + 3 * (size_t)S,
+                h.seed_cols + 4 * (size_t)S, h.seed_cols + 5 * (size_t)S};
+    ds_ut_hits ht{h.hit_cols, h.hit_cols + H, h.hit_cols + 2 * (size_t)H, h.layer};
+    ds_tracks tr{h.tracks, h.trk_off, h.counts, trk_cap, 0};
+    if ((s = ds_reconstruct(ctx, &b, &sd, &ht, &tr, stream)) != DS_OK) return s;
+    ds_vertices vx{h.vertices, h.vtx_off, h.counts + 1, vtx_cap, 0};
+    if ((s = ds_vertex(ctx, &tr, &vx, stream)) != DS_OK) return s;
+    int32_t counts[2] = {0, 0};
+    if (E > 0) {
+        DS_CUDA(cudaMemcpyAsync(counts, h.counts, sizeof(counts), cudaMemcpyDeviceToHost, st), "D2H");
+        DS_CUDA(cudaStreamSynchronize(st), "sync");
+    }
+    *n_tracks = counts[0];
+    *n_vertices = counts[1];
+    const int nt = counts[0] < trk_cap ? counts[0] : trk_cap;
+    const int nv = counts[1] < vtx_cap ? counts[1] : vtx_cap;
+    if (E > 0) {
+        DS_CUDA(cudaMemcpyAsync(h_trk_off, h.trk_off, sizeof(int32_t) * (E + 1), cudaMemcpyDeviceToHost, st), "D2H");
+        DS_CUDA(cudaMemcpyAsync(h_vtx_off, h.vtx_off, sizeof(int32_t) * (E + 1), cudaMemcpyDeviceToHost, st), "D2H");
+    } else {
+        h_trk_off[0] = 0;
+        h_vtx_off[0] = 0;
+    }
+    if (nt > 0) DS_CUDA(cudaMemcpyAsync(h_tracks, h.tracks, sizeof(ds_track) * nt, cudaMemcpyDeviceToHost, st), "D2H");
+    if (nv > 0)
+        DS_CUDA(cudaMemcpyAsync(h_vertices, h.vertices, sizeof(ds_vertex_rec) * nv, cudaMemcpyDeviceToHost, st), "D2H");
+    DS_CUDA(cudaStreamSynchronize(st), "sync");
+    if (counts[0] > trk_cap || counts[1] > vtx_cap) return fail(ctx, DS_ERR_CAPACITY, "output capacity exceeded");
+    return DS_OK;
+}
+
+}  // extern "C"

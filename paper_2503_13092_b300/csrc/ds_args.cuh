@@ -1,0 +1,112 @@
+// Kernel argument blocks (passed by value as __grid_constant__ parameters)
+// and the launch functions of libds.so's kernels.
+#pragma once
+
+#include <vector>
+
+#include "ds_common.cuh"
+
+namespace ds {
+
+// Host-side launch recorder: CUDA events around each kernel when enabled.
+struct Prof {
+    struct Rec {
+        const char *name;
+        cudaEvent_t a, b;
+    };
+    bool on = false;
+    std::vector<Rec> recs;
+    void begin(const char *name, cudaStream_t st);
+    void end(cudaStream_t st);
+};
+
+struct BucketArgs {
+    DevGeom g;
+    int n_events;
+    int n_hits;
+    const int32_t *hit_off;
+    const float *x0, *ybeg, *yend;
+    const uint8_t *layer;
+    float4 *sorted;
+    uint16_t *bins;
+    DevCounters *cnt;
+};
+
+struct SearchArgs {
+    DevGeom g;
+    DevParams p;
+    DevNN nn;
+    int n_events;
+    int n_seeds;
+    int n_hits;
+    const int32_t *seed_off, *hit_off;
+    const float *sx, *sy, *stx, *sty, *sqop, *schi2;
+    const float4 *sorted;
+    const uint16_t *bins;
+    ds_track *trk_ws;
+    unsigned long long *key_ws;
+    int4 *hit_ws;
+    int *rank_ws;
+    DevCounters *cnt;
+};
+
+struct CloneArgs {
+    int n_events, n_seeds;
+    int clone_kill;
+    const int32_t *seed_off;
+    const unsigned long long *key_ws;
+    const int4 *hit_ws;
+    int *rank_ws;         // per seed: rank inside its event, -1 = not output
+    int *count_ws;        // per event
+    int32_t *trk_off;     // [n_events + 1] (caller's)
+    int32_t *n_tracks;    // caller's device scalar
+    int capacity;
+    DevCounters *cnt;
+};
+
+struct ScatterTrkArgs {
+    int n_seeds;
+    const ds_track *trk_ws;
+    const int *rank_ws;
+    const int32_t *trk_off;
+    ds_track *out;
+    int capacity;
+};
+
+struct VertexArgs {
+    DevGeom g;
+    DevParams p;
+    int n_events;
+    int trk_capacity;
+    const ds_track *tracks;
+    const int32_t *trk_off;
+    const int32_t *n_tracks;
+    ds_vertex_rec *pool;
+    int *pool_pos;
+    int pool_cap;
+    int *count_ws;          // per event
+    int32_t *vtx_off;
+    int32_t *n_vertices;
+    int capacity;
+    int n_tickets;          // CTAs of both vertex launches together
+    DevCounters *cnt;
+};
+
+struct ScatterVtxArgs {
+    const ds_vertex_rec *pool;
+    const int *pool_pos;
+    int pool_cap;
+    const int32_t *vtx_off;
+    ds_vertex_rec *out;
+    int capacity;
+    const DevCounters *cnt;
+};
+
+cudaError_t init_vertex_attributes();
+cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st, Prof *prof);
+cudaError_t launch_search(const SearchArgs &a, int n_in, int n_h2, cudaStream_t st, Prof *prof);
+cudaError_t launch_clone(const CloneArgs &a, const ScatterTrkArgs &sa, cudaStream_t st, Prof *prof);
+cudaError_t launch_vertex(const VertexArgs &a, const ScatterVtxArgs &sa, int sm_count, cudaStream_t st,
+                          Prof *prof);
+
+}  // namespace ds

@@ -1,0 +1,157 @@
+// Device-side definitions shared by the kernels of libds.so (sm_103a).
+//
+// Data layout in HBM (per batch):
+//   seeds     caller's SoA float32 (x, y, tx, ty, qop, chi2), CSR over events
+//   hits      caller's SoA (x0, ybeg, yend float32, layer u8), CSR over events
+//   sorted    float4 per hit {x0, ybeg, yend, id-bits}, grouped by event, then
+//             by (layer, Y sector, x bin): one 16-byte load per visited hit
+//   bins      uint16 offsets per event: (layer, sector, xbin) -> first sorted
+//             hit, relative to the event's first hit (<= 65535 hits per event)
+//   trk_ws    one 64-byte candidate-winner record per seed + its clone key
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ds.h"
+
+namespace ds {
+
+constexpr int kNXB = 64;             // x bins per (layer, Y sector)
+constexpr int kMaxSectors = 32;
+constexpr int kK1Max = 10;           // UTbX hits kept per seed (paper: up to 10)
+constexpr int kMaxEventHits = 65535; // uint16 offsets
+constexpr int kSearchThreads = 128;  // seeds per CTA in the search kernel
+constexpr int kMaxVertexTracks = 4096; // tracks per event staged for vertexing
+constexpr unsigned long long kNoKey = ~0ull;
+
+struct DevGeom {
+    float z[4];
+    float dxdy[4];
+    float y_min, sector_h, inv_sector_h;
+    int n_sec;
+    float x_half, inv_xbin;          // xbin = floor((x0 + x_half) * inv_xbin)
+    float z_seed;
+    float zmag[4];
+    float kappa, mp;
+    float gamma0, gamma1, z_ref;
+    float w_hit, w_mag;              // 1 / sigma^2
+    float inv_sigma_hit;
+    int table_stride;                // uint16 entries per event bin table
+};
+
+struct DevParams {
+    float w1a, w1b, w2, dy_tol;
+    float nn_threshold, doca_max, nr_tol, eps_par;
+    float thr_logit;                 // ln(T / (1 - T)): response < T <=> logit < thr_logit
+    int k1, origin, pick_chi2, clone_kill, training, nr_max_iter;
+};
+
+// Ghost-killer weights padded to the largest supported shape 16-32-32-1.
+// Padding is zero, so a smaller network gives identical results.
+struct DevNN {
+    float w1[32][16];
+    float b1[32];
+    float w2[32][32];
+    float b2[32];
+    float w3[32];
+    float b3;
+    float mean[16];
+    float scale[16];
+};
+
+struct DevCounters {                 // device-side flag word and statistics
+    unsigned int flags;
+    unsigned int done_trk;           // last-block-done tickets
+    unsigned int done_vtx;
+    int n_tracks;
+    int n_vertices;
+    int pool_used;
+    int vtx_queue[2];                // event queues of the two vertex launches
+    int pad0;
+    unsigned long long n_candidates;
+    unsigned long long n_pairs;
+    unsigned long long n_pairs_fp64;
+};
+
+// Per-seed winner record in the workspace (same 64-byte layout as ds_track).
+static_assert(sizeof(ds_track) == 64, "ds_track must be 64 bytes");
+static_assert(sizeof(ds_vertex_rec) == 32, "ds_vertex_rec must be 32 bytes");
+
+__device__ __forceinline__ void raise_flag(DevCounters *c, unsigned int bit)
+{
+    atomicOr(&c->flags, bit);
+}
+
+__device__ __forceinline__ int sector_of(const DevGeom &g, float y)
+{
+    int k = __float2int_rd((y - g.y_min) * g.inv_sector_h);
+    return min(max(k, 0), g.n_sec - 1);
+}
+
+__device__ __forceinline__ int xbin_of(const DevGeom &g, float x)
+{
+    int b = __float2int_rd((x + g.x_half) * g.inv_xbin);
+    return min(max(b, 0), kNXB - 1);
+}
+
+// Largest e in [0, n) with off[e] <= s (off non-decreasing).
+__device__ __forceinline__ int find_segment(const int32_t *__restrict__ off, int n, int s)
+{
+    int lo = 0, hi = n;          // invariant: off[lo] <= s, answer in [lo, hi)
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= s) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Order-preserving float -> uint32 map (negative values included) and back.
+__device__ __forceinline__ unsigned int ord_f32(float x)
+{
+    const unsigned int u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float unord_f32(unsigned int o)
+{
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+__device__ __forceinline__ unsigned long long pack_key(float k1, float k2)
+{
+    return ((unsigned long long)ord_f32(k1) << 32) | ord_f32(k2);
+}
+
+// Exclusive scan of one int per thread over the block; returns the prefix,
+// *total receives the block sum.  `scratch` holds >= 32 ints.  All threads call.
+__device__ __forceinline__ int block_exclusive_scan(int v, int *scratch, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) scratch[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nwarps ? scratch[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        scratch[lane] = w;         // inclusive warp totals
+    }
+    __syncthreads();
+    int base = warp > 0 ? scratch[warp - 1] : 0;
+    *total = scratch[nwarps - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+}  // namespace ds

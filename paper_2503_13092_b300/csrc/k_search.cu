@@ -1,0 +1,440 @@
+// a2-a7: magnet point, window searches, candidate fit, ghost killer, best pick.
+//
+// Per seed (Algorithm Design section, Dv0):
+//   magnet point from the SciFi state (Eq. 1 kink model), prediction in UTbX,
+//   window of half-width w1a + w1b|q/p| -> up to k1 closest hits by (|dx|, id);
+//   for each of them the trajectory through the hit and the magnet point is
+//   extrapolated to UTaX/UTaU/UTbV, windows of half-width w2 keep the 1/2/2
+//   closest hits; candidates = the UTbX hit x one option per layer ("absent"
+//   only when the layer has no hit), kept when they have >= 3 hits including
+//   one in station a (Track Types section, UT reconstructibility);
+//   each candidate is fitted (line x = x_r + t (z - z_ref) through its hits and
+//   the magnet point), scored by the ghost-killer network (Ghost-Killer Neural
+//   Network section) and the best one is kept (response < threshold, Ghost
+//   Rejection section).
+//
+// Work decomposition (B300): 128 seeds per CTA, one thread per seed for the
+// searches (binned hits: a window is a contiguous range per Y sector), then
+// every candidate of the CTA is scored by one thread each so the network runs
+// with full lanes regardless of how candidates spread over seeds.  The network
+// weights live in the kernel's parameter space and are addressed with
+// compile-time indices (the paper's static network structure, GPU
+// Implementation section), so each multiply-add reads its weight straight
+// from the constant bank.  The best candidate per seed is found with 64-bit
+// shared-memory atomicMin on the packed key (response, chi2) and then on the
+// candidate index among equal keys.
+#include "ds_args.cuh"
+
+namespace ds {
+
+
+constexpr uint16_t kNone = 0xFFFFu;
+constexpr int T = kSearchThreads;
+
+template <int N>
+__device__ __forceinline__ void topn_insert(float (&d)[N], int (&id)[N], int (&p)[N], float dn,
+                                            int idn, int pn)
+{
+    if (dn < d[N - 1] || (dn == d[N - 1] && idn < id[N - 1])) {
+        d[N - 1] = dn;
+        id[N - 1] = idn;
+        p[N - 1] = pn;
+#pragma unroll
+        for (int k = N - 1; k > 0; --k) {
+            const bool sw = d[k] < d[k - 1] || (d[k] == d[k - 1] && id[k] < id[k - 1]);
+            if (sw) {
+                float td = d[k]; d[k] = d[k - 1]; d[k - 1] = td;
+                int ti = id[k]; id[k] = id[k - 1]; id[k - 1] = ti;
+                int tp = p[k]; p[k] = p[k - 1]; p[k - 1] = tp;
+            }
+        }
+    }
+}
+
+// Hits of `layer` with |x0 - u| < w whose strip extent (+- dy) contains y,
+// ranked by (|dx|, id); the N best are kept.  Returns how many qualified.
+template <int N>
+__device__ __forceinline__ int window_scan(const DevGeom &g, const float4 *__restrict__ H,
+                                           const uint16_t *__restrict__ Tb, int layer, float u,
+                                           float y, float w, float dy, float (&d)[N],
+                                           int (&id)[N], int (&p)[N])
+{
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        d[k] = __int_as_float(0x7f800000);
+        id[k] = 0x7fffffff;
+        p[k] = -1;
+    }
+    const int s_lo = sector_of(g, y - dy - 0.01f), s_hi = sector_of(g, y + dy + 0.01f);
+    const float eps = 1e-3f;
+    const int b0 = xbin_of(g, u - w - eps), b1 = xbin_of(g, u + w + eps);
+    int cnt = 0;
+    for (int s = s_lo; s <= s_hi; ++s) {
+        const int row = (layer * g.n_sec + s) * kNXB;
+        const int i0 = __ldg(Tb + row + b0), i1 = __ldg(Tb + row + b1 + 1);
+        for (int i = i0; i < i1; ++i) {
+            const float4 h = __ldg(H + i);
+            const float dx = fabsf(h.x - u);
+            if (dx < w && h.y - dy <= y && y <= h.z + dy) {
+                topn_insert<N>(d, id, p, dx, __float_as_int(h.w), i);
+                ++cnt;
+            }
+        }
+    }
+    return cnt;
+}
+
+struct SeedCtx {     // per-seed quantities reused by candidate scoring
+    float zm, xm, ym, tx, ty, qop, chi2, w1;
+    float yl[4];
+};
+
+struct CandFit {
+    float xr, yr, t, qop, chi2;
+    int ndof, nh;
+    float res[4];
+};
+
+// Weighted straight-line fit x = a + b (z - z_bX) in a frame centred on the
+// UTbX hit (keeps FP32 residuals small): one row per present hit (weight
+// 1/sigma_hit^2), one row for the magnet point (1/sigma_mag^2).
+__device__ __forceinline__ CandFit fit_candidate(const DevGeom &g, const SeedCtx &sc,
+                                                 const float4 *__restrict__ H, const int (&loc)[4])
+{
+    const float x0b = __ldg(H + loc[3]).x;
+    const float xh = x0b + g.dxdy[3] * sc.yl[3];
+    float Z[5], M[5], W[5];
+    int n = 0;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        Z[l] = g.z[l] - g.z[3];
+        W[l] = 0.f;
+        M[l] = 0.f;
+        if (loc[l] >= 0) {
+            const float x0 = l == 3 ? x0b : __ldg(H + loc[l]).x;
+            M[l] = (x0 - x0b) + (g.dxdy[l] * sc.yl[l] - g.dxdy[3] * sc.yl[3]);
+            W[l] = g.w_hit;
+            ++n;
+        }
+    }
+    Z[4] = sc.zm - g.z[3];
+    M[4] = sc.xm - xh;
+    W[4] = g.w_mag;
+    float S0 = 0.f, SZ = 0.f, SM = 0.f;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        S0 += W[r];
+        SZ = fmaf(W[r], Z[r], SZ);
+        SM = fmaf(W[r], M[r], SM);
+    }
+    const float zb = SZ / S0, mb = SM / S0;
+    float Szz = 0.f, Szm = 0.f;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        const float dz = Z[r] - zb;
+        Szz = fmaf(W[r] * dz, dz, Szz);
+        Szm = fmaf(W[r] * dz, M[r] - mb, Szm);
+    }
+    const float b = Szm / Szz;
+    const float a = fmaf(-b, zb, mb);
+    CandFit f;
+    float chi2 = 0.f;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        const float res = M[r] - fmaf(b, Z[r], a);
+        if (r < 4) f.res[r] = W[r] > 0.f ? res : 0.f;
+        chi2 = fmaf(W[r] * res, res, chi2);
+    }
+    f.chi2 = chi2;
+    f.ndof = n + 1 - 2;
+    f.nh = n;
+    f.t = b;
+    f.xr = xh + fmaf(b, g.z_ref - g.z[3], a);
+    f.yr = fmaf(sc.ty, g.z_ref - sc.zm, sc.ym);
+    if (g.kappa != 0.f) {
+        const float qopz = g.mp * (b - sc.tx) / g.kappa;
+        f.qop = qopz * rsqrtf(fmaf(b, b, fmaf(sc.ty, sc.ty, 1.f)));
+    } else {
+        f.qop = sc.qop;
+    }
+    return f;
+}
+
+// Ghost-killer forward pass, FP32 on the CUDA cores.  NIN inputs, NH1 ReLU,
+// NH2 ReLU (0 = none); returns the output node before the sigmoid (candidates
+// are ranked on it: same order as the response, no saturation).
+template <int NIN, int NH1, int NH2>
+__device__ __forceinline__ float mlp_logit_fp32(const DevNN &nn, const float (&phi)[16])
+{
+    float x[NIN];
+#pragma unroll
+    for (int i = 0; i < NIN; ++i) x[i] = (phi[i] - nn.mean[i]) * nn.scale[i];
+    float h1[NH1];
+#pragma unroll
+    for (int o = 0; o < NH1; ++o) {
+        float acc = nn.b1[o];
+#pragma unroll
+        for (int i = 0; i < NIN; ++i) acc = fmaf(nn.w1[o][i], x[i], acc);
+        h1[o] = fmaxf(acc, 0.f);
+    }
+    float out = nn.b3;
+    if (NH2 > 0) {
+#pragma unroll
+        for (int o = 0; o < NH2; ++o) {
+            float acc = nn.b2[o];
+#pragma unroll
+            for (int i = 0; i < NH1; ++i) acc = fmaf(nn.w2[o][i], h1[i], acc);
+            out = fmaf(nn.w3[o], fmaxf(acc, 0.f), out);
+        }
+    } else {
+#pragma unroll
+        for (int o = 0; o < NH1; ++o) out = fmaf(nn.w3[o], h1[o], out);
+    }
+    return out;
+}
+
+__device__ __forceinline__ float sigmoid_fast(float z) { return 1.f / (1.f + __expf(-z)); }
+
+template <int NIN, int NH1, int NH2>
+__global__ void __launch_bounds__(T) k_search(const __grid_constant__ SearchArgs a)
+{
+    __shared__ uint16_t s_bx[kK1Max][T];
+    __shared__ float s_bxd[kK1Max][T];
+    __shared__ uint16_t s_sel[kK1Max][5][T];
+    __shared__ uint8_t s_nc[kK1Max][T];
+    __shared__ uint8_t s_nopt_v[kK1Max][T];
+    __shared__ SeedCtx s_sc[T];
+    __shared__ int s_h0[T];
+    __shared__ int s_base[T + 1];
+    __shared__ unsigned long long s_best[T], s_cbest[T];
+    __shared__ int s_bidx[T], s_cidx[T];
+    __shared__ int s_scan[32];
+
+    const DevGeom &g = a.g;
+    const DevParams &P = a.p;
+    const int tid = threadIdx.x;
+    const int s = blockIdx.x * T + tid;
+    if (s < a.n_seeds) a.rank_ws[s] = -1;     // the clone kernel ranks this call's winners
+    if (s == 0 && (__ldg(a.seed_off) != 0 || __ldg(a.seed_off + a.n_events) != a.n_seeds))
+        raise_flag(a.cnt, DS_FLAG_BAD_OFFSETS);
+
+    // ---------------------------------------------------------------- search
+    int n_cand = 0;
+    int nbx = 0;
+    if (s < a.n_seeds) {
+        const int e = find_segment(a.seed_off, a.n_events, s);
+        int h0 = __ldg(a.hit_off + e), h1 = __ldg(a.hit_off + e + 1);
+        if (h0 < 0 || h1 < h0 || h1 > a.n_hits || h1 - h0 > kMaxEventHits) h1 = h0 = 0;
+        s_h0[tid] = h0;
+        const float4 *H = a.sorted + h0;
+        const uint16_t *Tb = a.bins + (size_t)e * g.table_stride;
+
+        SeedCtx sc;
+        const float x = __ldg(a.sx + s), y = __ldg(a.sy + s);
+        sc.tx = __ldg(a.stx + s);
+        sc.ty = __ldg(a.sty + s);
+        sc.qop = __ldg(a.sqop + s);
+        sc.chi2 = __ldg(a.schi2 + s);
+        const float aq = fabsf(sc.qop);
+        // magnet point (Eq. 1 kink model): parameterised z, straight-line x, y
+        sc.zm = g.zmag[0] + g.zmag[1] * sc.tx * sc.tx + g.zmag[2] * sc.ty * sc.ty + g.zmag[3] * aq;
+        sc.xm = fmaf(sc.tx, sc.zm - g.z_seed, x);
+        sc.ym = fmaf(sc.ty, sc.zm - g.z_seed, y);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) sc.yl[l] = fmaf(sc.ty, g.z[l] - sc.zm, sc.ym);
+        const float tx_ut = P.origin ? sc.xm / sc.zm
+                                     : sc.tx + g.mp * g.kappa * sc.qop *
+                                                   sqrtf(fmaf(sc.tx, sc.tx, fmaf(sc.ty, sc.ty, 1.f)));
+        const float u_bx = fmaf(tx_ut, g.z[3] - sc.zm, sc.xm) - g.dxdy[3] * sc.yl[3];
+        sc.w1 = P.training ? 100.f : fmaf(P.w1b, aq, P.w1a);
+        const float w2 = P.training ? 10.f : P.w2;
+        s_sc[tid] = sc;
+
+        float d[kK1Max];
+        int id[kK1Max], p[kK1Max];
+        const int q = window_scan<kK1Max>(g, H, Tb, 3, u_bx, sc.yl[3], sc.w1, P.dy_tol, d, id, p);
+        nbx = min(q, P.k1);
+#pragma unroll
+        for (int j = 0; j < kK1Max; ++j) {
+            s_bx[j][tid] = (uint16_t)p[j];
+            s_bxd[j][tid] = d[j];
+        }
+        for (int j = 0; j < nbx; ++j) {
+            const float x0b = __ldg(H + s_bx[j][tid]).x;
+            const float xh = x0b + g.dxdy[3] * sc.yl[3];
+            const float txp = (xh - sc.xm) / (g.z[3] - sc.zm);
+            int sel[5];
+            {
+                float dd[1]; int ii[1], pp[1];
+                const float ul = fmaf(txp, g.z[0] - g.z[3], xh) - g.dxdy[0] * sc.yl[0];
+                const int c = window_scan<1>(g, H, Tb, 0, ul, sc.yl[0], w2, P.dy_tol, dd, ii, pp);
+                sel[0] = c > 0 ? pp[0] : -1;
+            }
+#pragma unroll
+            for (int l = 1; l <= 2; ++l) {
+                float dd[2]; int ii[2], pp[2];
+                const float ul = fmaf(txp, g.z[l] - g.z[3], xh) - g.dxdy[l] * sc.yl[l];
+                const int c = window_scan<2>(g, H, Tb, l, ul, sc.yl[l], w2, P.dy_tol, dd, ii, pp);
+                sel[2 * l - 1] = c > 0 ? pp[0] : -1;
+                sel[2 * l] = c > 1 ? pp[1] : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) s_sel[j][k][tid] = sel[k] >= 0 ? (uint16_t)sel[k] : kNone;
+            const int pa = sel[0] >= 0, pu = sel[1] >= 0, pv = sel[3] >= 0;
+            const int nu = sel[2] >= 0 ? 2 : 1, nv = sel[4] >= 0 ? 2 : 1;
+            const int valid = (1 + pa + pu + pv >= 3) && (pa || pu);
+            const int nc = valid ? nu * nv : 0;
+            s_nc[j][tid] = (uint8_t)nc;
+            s_nopt_v[j][tid] = (uint8_t)nv;
+            n_cand += nc;
+        }
+    }
+    for (int j = nbx; j < kK1Max; ++j) s_nc[j][tid] = 0;
+    s_best[tid] = kNoKey;
+    s_bidx[tid] = 0x7fffffff;
+
+    int total;
+    const int base = block_exclusive_scan(n_cand, s_scan, &total);
+    s_base[tid] = base;
+    if (tid == T - 1) s_base[T] = base + n_cand;
+    if (tid == 0 && total > 0) atomicAdd(&a.cnt->n_candidates, (unsigned long long)total);
+    __syncthreads();
+
+    // decode candidate c of the CTA: owner seed, UTbX rank j, stereo options
+    auto decode = [&](int c, int &o, int (&loc)[4], float &dxbx) {
+        int lo = 0, hi = T;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_base[mid] <= c) lo = mid;
+            else hi = mid;
+        }
+        o = lo;
+        int k = c - s_base[o];
+        int j = 0;
+        while (j < kK1Max - 1 && k >= s_nc[j][o]) {
+            k -= s_nc[j][o];
+            ++j;
+        }
+        const int nv = s_nopt_v[j][o];
+        const int iu = k / nv, iv = k - iu * nv;
+        const uint16_t a0 = s_sel[j][0][o];
+        const uint16_t u0 = s_sel[j][1 + iu][o];
+        const uint16_t v0 = s_sel[j][3 + iv][o];
+        loc[0] = a0 == kNone ? -1 : a0;
+        loc[1] = u0 == kNone ? -1 : u0;
+        loc[2] = v0 == kNone ? -1 : v0;
+        loc[3] = s_bx[j][o];
+        dxbx = s_bxd[j][o];
+    };
+
+    // ------------------------------------------------ score every candidate
+    const float thr = P.thr_logit;
+    for (int cb = 0; cb < total; cb += 4 * T) {
+        unsigned long long key[4];
+        int own[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int c = cb + r * T + tid;
+            own[r] = -1;
+            key[r] = kNoKey;
+            if (c < total) {
+                int o, loc[4];
+                float dxbx;
+                decode(c, o, loc, dxbx);
+                own[r] = o;
+                const SeedCtx sc = s_sc[o];
+                const float4 *H = a.sorted + s_h0[o];
+                const CandFit f = fit_candidate(g, sc, H, loc);
+                float phi[16];
+                phi[0] = f.xr * 1e-3f;
+                phi[1] = f.yr * 1e-3f;
+                phi[2] = f.t;
+                phi[3] = sc.ty;
+                phi[4] = 1e3f * f.qop;
+                phi[5] = f.chi2 / (float)f.ndof;
+                phi[6] = 1e3f * sc.qop;
+                phi[7] = sc.chi2;
+#pragma unroll
+                for (int l = 0; l < 4; ++l) phi[8 + l] = f.res[l] * g.inv_sigma_hit;
+                phi[12] = 0.25f * (float)f.nh;
+                phi[13] = dxbx / sc.w1;
+                phi[14] = sc.tx;
+                phi[15] = sc.ty;
+                const float lg = mlp_logit_fp32<NIN, NH1, NH2>(a.nn, phi);
+                if (P.pick_chi2) key[r] = pack_key(phi[5], lg);
+                else if (lg < thr) key[r] = pack_key(lg, f.chi2);
+            }
+        }
+        s_cbest[tid] = kNoKey;
+        s_cidx[tid] = 0x7fffffff;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (own[r] >= 0 && key[r] != kNoKey) atomicMin(&s_cbest[own[r]], key[r]);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (own[r] >= 0 && key[r] != kNoKey && key[r] == s_cbest[own[r]])
+                atomicMin(&s_cidx[own[r]], cb + r * T + tid);
+        __syncthreads();
+        if (s_cbest[tid] < s_best[tid]) {
+            s_best[tid] = s_cbest[tid];
+            s_bidx[tid] = s_cidx[tid];
+        }
+        __syncthreads();
+    }
+
+    // ------------------------------------------------------- write winners
+    if (s >= a.n_seeds) return;
+    ds_track rec;
+    rec.event = find_segment(a.seed_off, a.n_events, s);
+    rec.seed = s;
+    rec.flags = 0;
+    rec.n_candidates = n_cand;
+    unsigned long long best = s_best[tid];
+    bool have = best != kNoKey;
+    float lg_best = 0.f;
+    if (have) lg_best = P.pick_chi2 ? unord_f32((unsigned)best) : unord_f32((unsigned)(best >> 32));
+    if (have && P.pick_chi2 && !(lg_best < thr)) have = false;
+    int4 hits = make_int4(-1, -1, -1, -1);
+    if (have) {
+        int o, loc[4];
+        float dxbx;
+        decode(s_bidx[tid], o, loc, dxbx);
+        const SeedCtx sc = s_sc[o];
+        const float4 *H = a.sorted + s_h0[o];
+        const CandFit f = fit_candidate(g, sc, H, loc);
+        int gid[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) gid[l] = loc[l] >= 0 ? __float_as_int(__ldg(H + loc[l]).w) : -1;
+        hits = make_int4(gid[0], gid[1], gid[2], gid[3]);
+        rec.hit[0] = gid[0]; rec.hit[1] = gid[1]; rec.hit[2] = gid[2]; rec.hit[3] = gid[3];
+        rec.x = f.xr; rec.y = f.yr; rec.tx = f.t; rec.ty = sc.ty; rec.qop = f.qop;
+        rec.chi2 = P.pick_chi2 ? f.chi2 : unord_f32((unsigned)best);
+        rec.ndof = f.ndof;
+        rec.nn = sigmoid_fast(lg_best);
+    } else {
+        rec.hit[0] = rec.hit[1] = rec.hit[2] = rec.hit[3] = -1;
+        rec.x = rec.y = rec.tx = rec.ty = rec.qop = rec.chi2 = rec.nn = 0.f;
+        rec.ndof = 0;
+        best = kNoKey;
+    }
+    a.trk_ws[s] = rec;
+    a.key_ws[s] = best;
+    a.hit_ws[s] = hits;
+}
+
+cudaError_t launch_search(const SearchArgs &a, int n_in, int n_h2, cudaStream_t st, Prof *prof)
+{
+    if (a.n_seeds <= 0) return cudaSuccess;
+    const int grid = (a.n_seeds + T - 1) / T;
+    prof->begin("k_search", st);
+    if (n_in <= 8 && n_h2 == 0)
+        k_search<8, 16, 0><<<grid, T, 0, st>>>(a);
+    else
+        k_search<16, 32, 32><<<grid, T, 0, st>>>(a);
+    prof->end(st);
+    return cudaGetLastError();
+}
+
+}  // namespace ds

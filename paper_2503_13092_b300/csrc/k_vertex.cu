@@ -1,0 +1,372 @@
+// a9 + a10 (vertices): two-track vertexing and deterministic compaction.
+//
+// Vertexing Two Downstream Tracks section: each track is extrapolated with
+// Eq. 4, x(z) = x + tx (z - z_ref) + gamma (z - z_ref)^2, y(z) = y + ty (z - z_ref),
+// gamma from Eq. 3; the vertex is the point of closest approach found by
+// Newton-Raphson; secondary tracks must have opposite charges (Expected
+// Physics Impact section).  Start: the closed-form closest approach of the
+// two straight lines; stop when both steps are below the tolerance; vertex =
+// midpoint of the two closest points; kept if DOCA < doca_max.
+//
+// FP32 solve, written with slope differences and cross products so that the
+// near-parallel cancellation happens in exact-ish differences rather than in
+// products of large numbers; pairs whose opening satisfies sin^2 < eps_par and
+// whose FP32 DOCA is near or below the cut are re-solved in FP64 (flag bit 0).
+//
+// One CTA per event.  Tracks are staged in shared memory; opposite-charge
+// partner lists make every thread's pair valid, enumerated in (i, j) order.
+// Kept vertices of each 256-pair chunk are ranked by a block scan and written
+// to a pool slice reserved with one atomicAdd; their position inside the event
+// is recorded, so the scatter kernel places them in (event, i, j) order
+// whatever order the pool was filled in.
+#include "ds_args.cuh"
+
+namespace ds {
+
+constexpr int kVtxThreads = 256;
+constexpr int kVtxSmallCap = 512;
+
+
+struct Trk {
+    float x, y, tx, ty, q;
+};
+
+struct PairOut {
+    float x, y, z, doca;
+    unsigned int flags;
+};
+
+__device__ PairOut solve_fp64(const DevGeom &g, const DevParams &P, const Trk &A, const Trk &B)
+{
+    const double gi = -(double)g.mp * ((double)g.gamma0 + (double)g.gamma1 * (double)A.q);
+    const double gj = -(double)g.mp * ((double)g.gamma0 + (double)g.gamma1 * (double)B.q);
+    const double txi = A.tx, tyi = A.ty, txj = B.tx, tyj = B.ty;
+    const double wx = (double)A.x - (double)B.x, wy = (double)A.y - (double)B.y;
+    const double dtx = txi - txj, dty = tyi - tyj;
+    const double a = 1.0 + txi * txi + tyi * tyi, c = 1.0 + txj * txj + tyj * tyj;
+    const double b = 1.0 + txi * txj + tyi * tyj;
+    const double cz = txi * tyj - tyi * txj;
+    const double den = dtx * dtx + dty * dty + cz * cz;
+    const double d = txi * wx + tyi * wy, m = dtx * wx + dty * wy;
+    double u1 = 0.0, u2 = 0.0;
+    if (den > 1e-12 * a * c) {
+        u1 = ((txj * dtx + tyj * dty) * d - b * m) / den;
+        u2 = ((txi * dtx + tyi * dty) * d - a * m) / den;
+    }
+    bool conv = false;
+    for (int it = 0; it < P.nr_max_iter; ++it) {
+        const double du = u1 - u2;
+        const double pi = txi + 2.0 * gi * u1, pj = txj + 2.0 * gj * u2;
+        const double dx = (wx + dtx * u2) + txi * du + gi * u1 * u1 - gj * u2 * u2;
+        const double dy = (wy + dty * u2) + tyi * du;
+        const double dz = du;
+        const double dPi = dx * pi + dy * tyi + dz, dPj = dx * pj + dy * tyj + dz;
+        const double ni = pi * pi + tyi * tyi + 1.0, nj = pj * pj + tyj * tyj + 1.0;
+        const double cx = tyi - tyj, cy = pj - pi, cc = pi * tyj - tyi * pj;   // Pi x Pj
+        const double det = cx * cx + cy * cy + cc * cc + 2.0 * gi * dx * nj - 2.0 * gj * dx * ni -
+                           4.0 * gi * gj * dx * dx;
+        if (!(det > 0.0)) break;
+        // (Pj x Pi).(Pj x d) and (Pi x Pj).(Pi x d)
+        const double jd_x = tyj * dz - dy, jd_y = dx - pj * dz, jd_z = pj * dy - tyj * dx;
+        const double id_x = tyi * dz - dy, id_y = dx - pi * dz, id_z = pi * dy - tyi * dx;
+        const double n1 = -(cx * jd_x + cy * jd_y + cc * jd_z) - 2.0 * gj * dx * dPi;
+        const double n2 = -(cx * id_x + cy * id_y + cc * id_z) - 2.0 * gi * dx * dPj;
+        const double s1 = -n1 / det, s2 = -n2 / det;
+        u1 += s1;
+        u2 += s2;
+        if (fabs(s1) < (double)P.nr_tol && fabs(s2) < (double)P.nr_tol) {
+            conv = true;
+            break;
+        }
+    }
+    const double du = u1 - u2;
+    const double dx = (wx + dtx * u2) + txi * du + gi * u1 * u1 - gj * u2 * u2;
+    const double dy = (wy + dty * u2) + tyi * du;
+    PairOut o;
+    const double x1 = (double)A.x + txi * u1 + gi * u1 * u1, y1 = (double)A.y + tyi * u1;
+    o.x = (float)(x1 - 0.5 * dx);
+    o.y = (float)(y1 - 0.5 * dy);
+    o.z = (float)(0.5 * (u1 + u2) + (double)g.z_ref);
+    o.doca = (float)sqrt(dx * dx + dy * dy + du * du);
+    o.flags = 1u | (conv ? 0u : 2u);
+    return o;
+}
+
+__device__ __forceinline__ PairOut solve_fp32(const DevGeom &g, const DevParams &P, const Trk &A,
+                                              const Trk &B, float &sin2)
+{
+    const float gi = -g.mp * fmaf(g.gamma1, A.q, g.gamma0);
+    const float gj = -g.mp * fmaf(g.gamma1, B.q, g.gamma0);
+    const float txi = A.tx, tyi = A.ty, txj = B.tx, tyj = B.ty;
+    const float wx = A.x - B.x, wy = A.y - B.y;
+    const float dtx = txi - txj, dty = tyi - tyj;
+    const float a = fmaf(txi, txi, fmaf(tyi, tyi, 1.f)), c = fmaf(txj, txj, fmaf(tyj, tyj, 1.f));
+    const float b = fmaf(txi, txj, fmaf(tyi, tyj, 1.f));
+    const float cz = fmaf(txi, tyj, -tyi * txj);
+    const float den = fmaf(dtx, dtx, fmaf(dty, dty, cz * cz));
+    sin2 = den / (a * c);
+    const float d = fmaf(txi, wx, tyi * wy), m = fmaf(dtx, wx, dty * wy);
+    float u1 = 0.f, u2 = 0.f;
+    if (sin2 > 1e-12f) {
+        u1 = fmaf(fmaf(txj, dtx, tyj * dty), d, -b * m) / den;
+        u2 = fmaf(fmaf(txi, dtx, tyi * dty), d, -a * m) / den;
+    }
+    const float tol = fmaxf(P.nr_tol, 1e-3f);
+    bool conv = false;
+    for (int it = 0; it < P.nr_max_iter; ++it) {
+        const float du = u1 - u2;
+        const float pi = fmaf(2.f * gi, u1, txi), pj = fmaf(2.f * gj, u2, txj);
+        const float dx = fmaf(dtx, u2, wx) + fmaf(txi, du, fmaf(gi * u1, u1, -gj * u2 * u2));
+        const float dy = fmaf(dty, u2, wy) + tyi * du;
+        const float dz = du;
+        const float dPi = fmaf(dx, pi, fmaf(dy, tyi, dz)), dPj = fmaf(dx, pj, fmaf(dy, tyj, dz));
+        const float ni = fmaf(pi, pi, fmaf(tyi, tyi, 1.f)), nj = fmaf(pj, pj, fmaf(tyj, tyj, 1.f));
+        const float cx = tyi - tyj, cy = pj - pi, cc = fmaf(pi, tyj, -tyi * pj);
+        const float det = fmaf(cx, cx, fmaf(cy, cy, cc * cc)) +
+                          2.f * dx * (fmaf(gi, nj, -gj * ni) - 2.f * gi * gj * dx);
+        if (!(det > 0.f)) break;
+        const float jd_x = fmaf(tyj, dz, -dy), jd_y = fmaf(-pj, dz, dx), jd_z = fmaf(pj, dy, -tyj * dx);
+        const float id_x = fmaf(tyi, dz, -dy), id_y = fmaf(-pi, dz, dx), id_z = fmaf(pi, dy, -tyi * dx);
+        const float n1 = -fmaf(cx, jd_x, fmaf(cy, jd_y, cc * jd_z)) - 2.f * gj * dx * dPi;
+        const float n2 = -fmaf(cx, id_x, fmaf(cy, id_y, cc * id_z)) - 2.f * gi * dx * dPj;
+        const float s1 = -n1 / det, s2 = -n2 / det;
+        u1 += s1;
+        u2 += s2;
+        if (fabsf(s1) < tol && fabsf(s2) < tol) {
+            conv = true;
+            break;
+        }
+    }
+    const float du = u1 - u2;
+    const float dx = fmaf(dtx, u2, wx) + fmaf(txi, du, fmaf(gi * u1, u1, -gj * u2 * u2));
+    const float dy = fmaf(dty, u2, wy) + tyi * du;
+    PairOut o;
+    const float x1 = A.x + fmaf(txi, u1, gi * u1 * u1), y1 = fmaf(tyi, u1, A.y);
+    o.x = fmaf(-0.5f, dx, x1);
+    o.y = fmaf(-0.5f, dy, y1);
+    o.z = fmaf(0.5f, u1 + u2, g.z_ref);
+    o.doca = sqrtf(fmaf(dx, dx, fmaf(dy, dy, du * du)));
+    o.flags = conv ? 0u : 2u;
+    return o;
+}
+
+// First index k in [0, n) with list[k] >= v (list ascending).
+__device__ __forceinline__ int lower_bound_u16(const uint16_t *list, int n, int v)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int)list[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int CAP, bool LARGE>
+__global__ void __launch_bounds__(kVtxThreads) k_vertex(const __grid_constant__ VertexArgs a)
+{
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    __shared__ int s_scan[32];
+    __shared__ int s_pool_base;
+    __shared__ bool s_last;
+    Trk *s_trk = reinterpret_cast<Trk *>(s_dyn);
+    uint16_t *s_pos = reinterpret_cast<uint16_t *>(s_trk + CAP);
+    uint16_t *s_neg = s_pos + CAP;
+    uint16_t *s_start = s_neg + CAP;
+    int *s_row = reinterpret_cast<int *>(s_start + CAP + (CAP & 1));  // CAP + 1 entries
+
+    const DevGeom &g = a.g;
+    const DevParams &P = a.p;
+    __shared__ int s_e;
+    for (;;) {
+    if (threadIdx.x == 0) s_e = atomicAdd(&a.cnt->vtx_queue[LARGE ? 1 : 0], 1);
+    __syncthreads();
+    const int e = s_e;
+    __syncthreads();
+    if (e >= a.n_events) break;
+    const int tcap = min(__ldg(a.n_tracks), a.trk_capacity);
+    int t0 = min(__ldg(a.trk_off + e), tcap), t1 = min(__ldg(a.trk_off + e + 1), tcap);
+    if (t1 < t0) t1 = t0;
+    int nt = t1 - t0;
+    // the small-capacity launch takes events with nt <= kVtxSmallCap, the
+    // large one the rest (clamped to its capacity, flagged)
+    bool mine = LARGE ? nt > kVtxSmallCap : nt <= kVtxSmallCap;
+    if (LARGE && nt > CAP) {
+        if (threadIdx.x == 0) raise_flag(a.cnt, DS_FLAG_VERTEX_CAPACITY);
+        nt = CAP;
+    }
+    int ev_count = 0;
+    if (mine && nt >= 2) {
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+            const ds_track &r = a.tracks[t0 + i];
+            s_trk[i] = Trk{r.x, r.y, r.tx, r.ty, r.qop};
+        }
+        __syncthreads();
+        // opposite-charge partner lists, in track order
+        int npos = 0, nneg = 0;
+        for (int c0 = 0; c0 < nt; c0 += blockDim.x) {
+            const int i = c0 + threadIdx.x;
+            const float q = i < nt ? s_trk[i].q : 0.f;
+            int tp, tn;
+            const int rp = block_exclusive_scan(q > 0.f, s_scan, &tp);
+            const int rn = block_exclusive_scan(q < 0.f, s_scan, &tn);
+            if (q > 0.f) s_pos[npos + rp] = (uint16_t)i;
+            if (q < 0.f) s_neg[nneg + rn] = (uint16_t)i;
+            npos += tp;
+            nneg += tn;
+        }
+        __syncthreads();
+        // row i holds partners j > i of opposite charge
+        int run = 0;
+        for (int c0 = 0; c0 < nt; c0 += blockDim.x) {
+            const int i = c0 + threadIdx.x;
+            int cnt = 0;
+            if (i < nt) {
+                const float q = s_trk[i].q;
+                const uint16_t *opp = q > 0.f ? s_neg : s_pos;
+                const int nopp = q > 0.f ? nneg : (q < 0.f ? npos : 0);
+                const int st = lower_bound_u16(opp, nopp, i + 1);
+                s_start[i] = (uint16_t)st;
+                cnt = nopp - st;
+            }
+            int tot;
+            const int r = block_exclusive_scan(cnt, s_scan, &tot);
+            if (i < nt) s_row[i] = run + r;
+            run += tot;
+        }
+        if (threadIdx.x == 0) s_row[nt] = run;
+        __syncthreads();
+        const int npairs = run;
+        if (threadIdx.x == 0 && npairs > 0) atomicAdd(&a.cnt->n_pairs, (unsigned long long)npairs);
+        int n64 = 0;
+        for (int c0 = 0; c0 < npairs; c0 += blockDim.x) {
+            const int p = c0 + threadIdx.x;
+            int keep = 0, i = 0, j = 0;
+            PairOut o;
+            if (p < npairs) {
+                int lo = 0, hi = nt;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_row[mid] <= p) lo = mid;
+                    else hi = mid;
+                }
+                i = lo;
+                const Trk A = s_trk[i];
+                const uint16_t *opp = A.q > 0.f ? s_neg : s_pos;
+                j = opp[s_start[i] + (p - s_row[i])];
+                const Trk B = s_trk[j];
+                float sin2;
+                o = solve_fp32(g, P, A, B, sin2);
+                if (sin2 < P.eps_par && o.doca < P.doca_max + 0.05f) {
+                    o = solve_fp64(g, P, A, B);
+                    ++n64;
+                }
+                keep = o.doca < P.doca_max;
+            }
+            int tot;
+            const int r = block_exclusive_scan(keep, s_scan, &tot);
+            if (tot > 0) {
+                if (threadIdx.x == 0) s_pool_base = atomicAdd(&a.cnt->pool_used, tot);
+                __syncthreads();
+                const int slot = s_pool_base + r;
+                if (keep) {
+                    if (slot < a.pool_cap) {
+                        ds_vertex_rec v;
+                        v.event = e;
+                        v.i = t0 + i;
+                        v.j = t0 + j;
+                        v.x = o.x; v.y = o.y; v.z = o.z;
+                        v.doca = o.doca;
+                        v.flags = o.flags;
+                        a.pool[slot] = v;
+                        a.pool_pos[slot] = ev_count + r;
+                    } else {
+                        raise_flag(a.cnt, DS_FLAG_VERTEX_CAPACITY);
+                    }
+                }
+                __syncthreads();
+            }
+            ev_count += tot;
+        }
+        if (n64) atomicAdd(&a.cnt->n_pairs_fp64, (unsigned long long)n64);
+    }
+
+    if (threadIdx.x == 0 && mine) a.count_ws[e] = ev_count;
+    }   // event loop
+
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int t = atomicAdd(&a.cnt->done_vtx, 1u);
+        s_last = t == (unsigned)a.n_tickets - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    int run = 0;
+    for (int c0 = 0; c0 < a.n_events; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        const int v = i < a.n_events ? __ldcg(a.count_ws + i) : 0;
+        int tot;
+        const int r = block_exclusive_scan(v, s_scan, &tot);
+        if (i < a.n_events) a.vtx_off[i] = run + r;
+        run += tot;
+    }
+    if (threadIdx.x == 0) {
+        a.vtx_off[a.n_events] = run;
+        *a.n_vertices = run;
+        a.cnt->n_vertices = run;
+        if (run > a.capacity) raise_flag(a.cnt, DS_FLAG_VERTEX_CAPACITY);
+        a.cnt->done_vtx = 0;
+    }
+}
+
+
+__global__ void __launch_bounds__(256) k_scatter_vertices(const __grid_constant__ ScatterVtxArgs a)
+{
+    const int used = min(*(volatile const int *)&a.cnt->pool_used, a.pool_cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < used; k += gridDim.x * blockDim.x) {
+        const ds_vertex_rec v = a.pool[k];
+        const int pos = __ldg(a.vtx_off + v.event) + __ldg(a.pool_pos + k);
+        if (pos < a.capacity) a.out[pos] = v;
+    }
+}
+
+static size_t vtx_smem(int cap);
+
+cudaError_t init_vertex_attributes()
+{
+    return cudaFuncSetAttribute(k_vertex<kMaxVertexTracks, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)vtx_smem(kMaxVertexTracks));
+}
+
+static size_t vtx_smem(int cap)
+{
+    return sizeof(Trk) * cap + sizeof(uint16_t) * (3 * cap + (cap & 1)) + sizeof(int) * (cap + 1);
+}
+
+cudaError_t launch_vertex(const VertexArgs &a0, const ScatterVtxArgs &sa, int sm_count, cudaStream_t st,
+                          Prof *prof)
+{
+    if (a0.n_events <= 0) return cudaSuccess;
+    VertexArgs a = a0;
+    const size_t sm_small = vtx_smem(kVtxSmallCap), sm_large = vtx_smem(kMaxVertexTracks);
+    const int g_small = a.n_events < 4 * sm_count ? a.n_events : 4 * sm_count;
+    const int g_large = a.n_events < sm_count ? a.n_events : sm_count;
+    a.n_tickets = g_small + g_large;
+    prof->begin("k_vertex_small", st);
+    k_vertex<kVtxSmallCap, false><<<g_small, kVtxThreads, sm_small, st>>>(a);
+    prof->end(st);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    prof->begin("k_vertex_large", st);
+    k_vertex<kMaxVertexTracks, true><<<g_large, kVtxThreads, sm_large, st>>>(a);
+    prof->end(st);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    prof->begin("k_scatter_vertices", st);
+    k_scatter_vertices<<<sm_count * 4, 256, 0, st>>>(sa);
+    prof->end(st);
+    return cudaGetLastError();
+}
+
+}  // namespace ds

@@ -1,0 +1,407 @@
+"""Python binding of libds.so (ctypes).  Argument marshalling only.
+
+The functions keep the C names of include/ds.h (ds_create, ds_load_geometry,
+ds_load_nn_weights, ds_set_params, ds_reserve, ds_reconstruct, ds_vertex,
+ds_sync_status, ds_process_host, ...).  Every step of the computation runs in
+the CUDA kernels of libds.so; PyTorch only provides device memory and streams.
+There is no fallback: if the library is missing or no CUDA device is present
+the calls raise.
+
+`Downstream` is a small convenience wrapper (one context, device-resident
+geometry and weights) used by the tests, the benchmark and the server.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libds.so")
+
+DS_OK, DS_ERR_ARG, DS_ERR_CUDA, DS_ERR_CAPACITY, DS_ERR_NOT_READY, DS_ERR_TIMEOUT, \
+    DS_ERR_DEVICE_FLAG, DS_ERR_OOM = 0, -1, -2, -3, -4, -5, -6, -7
+DS_FLAG_BAD_OFFSETS, DS_FLAG_BAD_LAYER, DS_FLAG_STRIP_SECTOR, DS_FLAG_EVENT_TOO_LARGE, \
+    DS_FLAG_TRACK_CAPACITY, DS_FLAG_VERTEX_CAPACITY, DS_FLAG_TIMEOUT = (1 << k for k in range(7))
+DS_MLP_FP32, DS_MLP_BF16, DS_MLP_FP8 = 0, 1, 2
+
+
+class ds_geometry(C.Structure):
+    _fields_ = [("z_layer", C.c_double * 4), ("dxdy", C.c_double * 4), ("y_min", C.c_double),
+                ("sector_h", C.c_double), ("n_sectors", C.c_int32), ("reserved0", C.c_int32),
+                ("x_half_bins", C.c_double), ("z_seed", C.c_double), ("zmag", C.c_double * 4),
+                ("kappa", C.c_double), ("mp", C.c_double), ("gamma0", C.c_double), ("gamma1", C.c_double),
+                ("z_ref", C.c_double), ("sigma_hit", C.c_double), ("sigma_mag", C.c_double)]
+
+
+class ds_nn_weights(C.Structure):
+    _fields_ = [("n_in", C.c_int32), ("n_h1", C.c_int32), ("n_h2", C.c_int32), ("reserved0", C.c_int32),
+                ("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p),
+                ("w3", C.c_void_p), ("b3", C.c_float), ("reserved1", C.c_int32),
+                ("mean", C.c_void_p), ("scale", C.c_void_p)]
+
+
+class ds_params(C.Structure):
+    _fields_ = [("w1a", C.c_double), ("w1b", C.c_double), ("w2", C.c_double), ("dy_tol", C.c_double),
+                ("nn_threshold", C.c_double), ("doca_max", C.c_double), ("nr_tol", C.c_double),
+                ("eps_parallel", C.c_double), ("k1", C.c_int32), ("first_window_origin", C.c_int32),
+                ("pick_chi2", C.c_int32), ("clone_kill", C.c_int32), ("training", C.c_int32),
+                ("nr_max_iter", C.c_int32), ("mlp_precision", C.c_int32), ("reserved0", C.c_int32)]
+
+
+class ds_event_batch(C.Structure):
+    _fields_ = [("n_events", C.c_int32), ("n_seeds", C.c_int32), ("n_hits", C.c_int32),
+                ("reserved0", C.c_int32), ("seed_off", C.c_void_p), ("hit_off", C.c_void_p)]
+
+
+class ds_seeds(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("x", "y", "tx", "ty", "qop", "chi2")]
+
+
+class ds_ut_hits(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("x0", "ybeg", "yend", "layer")]
+
+
+class ds_tracks(C.Structure):
+    _fields_ = [("tracks", C.c_void_p), ("trk_off", C.c_void_p), ("n_tracks", C.c_void_p),
+                ("capacity", C.c_int32), ("n_events", C.c_int32)]
+
+
+class ds_vertices(C.Structure):
+    _fields_ = [("vertices", C.c_void_p), ("vtx_off", C.c_void_p), ("n_vertices", C.c_void_p),
+                ("capacity", C.c_int32), ("reserved0", C.c_int32)]
+
+
+class ds_stats(C.Structure):
+    _fields_ = [("n_candidates", C.c_int64), ("n_pairs", C.c_int64), ("n_pairs_fp64", C.c_int64),
+                ("n_tracks", C.c_int32), ("n_vertices", C.c_int32), ("device_flags", C.c_uint32),
+                ("reserved0", C.c_int32)]
+
+
+class ds_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int32), ("reserved0", C.c_int32),
+                ("total_ms", C.c_double)]
+
+
+TRACK_DTYPE = np.dtype([("event", "<i4"), ("seed", "<i4"), ("hit", "<i4", 4), ("x", "<f4"), ("y", "<f4"),
+                        ("tx", "<f4"), ("ty", "<f4"), ("qop", "<f4"), ("chi2", "<f4"), ("ndof", "<i4"),
+                        ("nn", "<f4"), ("flags", "<u4"), ("n_candidates", "<i4")])
+VERTEX_DTYPE = np.dtype([("event", "<i4"), ("i", "<i4"), ("j", "<i4"), ("x", "<f4"), ("y", "<f4"),
+                         ("z", "<f4"), ("doca", "<f4"), ("flags", "<u4")])
+assert TRACK_DTYPE.itemsize == 64 and VERTEX_DTYPE.itemsize == 32
+
+_lib = None
+
+
+class DSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def lib():
+    """Load libds.so; raise if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libds.so not found at {LIB_PATH}; run python -m paper_2503_13092_b300.build")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        sig = {
+            "ds_create": ([C.POINTER(P), C.c_int], C.c_int),
+            "ds_destroy": ([P], None),
+            "ds_status_string": ([C.c_int], C.c_char_p),
+            "ds_last_error": ([P], C.c_char_p),
+            "ds_default_params": ([C.POINTER(ds_params)], C.c_int),
+            "ds_load_geometry": ([P, C.POINTER(ds_geometry)], C.c_int),
+            "ds_load_nn_weights": ([P, C.POINTER(ds_nn_weights)], C.c_int),
+            "ds_set_params": ([P, C.POINTER(ds_params)], C.c_int),
+            "ds_reserve": ([P, C.c_int32, C.c_int32, C.c_int32], C.c_int),
+            "ds_reconstruct": ([P, C.POINTER(ds_event_batch), C.POINTER(ds_seeds), C.POINTER(ds_ut_hits),
+                                C.POINTER(ds_tracks), P], C.c_int),
+            "ds_vertex": ([P, C.POINTER(ds_tracks), C.POINTER(ds_vertices), P], C.c_int),
+            "ds_sync_status": ([P, P, C.POINTER(ds_stats)], C.c_int),
+            "ds_profile_enable": ([P, C.c_int32], C.c_int),
+            "ds_profile_read": ([P, C.POINTER(ds_kernel_time), C.c_int32, C.POINTER(C.c_int32)], C.c_int),
+            "ds_process_host": ([P, C.c_int32, P, C.POINTER(P), P, C.POINTER(P), P, P, C.c_int32, P,
+                                 C.POINTER(C.c_int32), P, C.c_int32, P, C.POINTER(C.c_int32), P], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+EXPORTED = ("ds_create", "ds_destroy", "ds_status_string", "ds_last_error", "ds_default_params",
+            "ds_load_geometry", "ds_load_nn_weights", "ds_set_params", "ds_reserve", "ds_reconstruct",
+            "ds_vertex", "ds_sync_status", "ds_process_host", "ds_profile_enable", "ds_profile_read")
+
+
+# --------------------------------------------------------------- C names, marshalled
+
+def ds_create(device: int = 0):
+    h = C.c_void_p()
+    st = lib().ds_create(C.byref(h), device)
+    if st != DS_OK:
+        raise DSError(st, f"ds_create(device={device}) failed: {lib().ds_status_string(st).decode()}")
+    return h
+
+
+def ds_destroy(ctx):
+    lib().ds_destroy(ctx)
+
+
+def ds_status_string(st: int) -> str:
+    return lib().ds_status_string(st).decode()
+
+
+def ds_last_error(ctx) -> str:
+    return lib().ds_last_error(ctx).decode()
+
+
+def _check(ctx, st, what):
+    if st != DS_OK:
+        raise DSError(st, f"{what}: {ds_status_string(st)}: {ds_last_error(ctx)}")
+    return st
+
+
+def ds_default_params() -> ds_params:
+    p = ds_params()
+    lib().ds_default_params(C.byref(p))
+    return p
+
+
+def make_geometry(cfg: dict) -> ds_geometry:
+    g = ds_geometry()
+    g.z_layer[:] = cfg["z_layer"]
+    g.dxdy[:] = cfg["dxdy"]
+    g.zmag[:] = cfg["zmag"]
+    for k in ("y_min", "sector_h", "x_half_bins", "z_seed", "kappa", "mp", "gamma0", "gamma1", "z_ref",
+              "sigma_hit", "sigma_mag"):
+        setattr(g, k, float(cfg[k]))
+    g.n_sectors = int(cfg["n_sectors"])
+    return g
+
+
+def make_params(cfg: dict, **over) -> ds_params:
+    p = ds_default_params()
+    for k in ("w1a", "w1b", "w2", "dy_tol", "nn_threshold", "doca_max", "nr_tol"):
+        setattr(p, k, float(cfg[k]))
+    for k in ("k1", "first_window_origin", "pick_chi2", "clone_kill", "training", "nr_max_iter"):
+        setattr(p, k, int(cfg[k]))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def ds_load_geometry(ctx, geom: ds_geometry):
+    return _check(ctx, lib().ds_load_geometry(ctx, C.byref(geom)), "ds_load_geometry")
+
+
+class _NN:
+    def __init__(self, w: dict):
+        f = lambda a: np.ascontiguousarray(np.asarray(a, np.float32).ravel())
+        self.keep = [f(w["w1"]), f(w["b1"]), f(w["w2"]) if w["n_h2"] else np.zeros(1, np.float32),
+                     f(w["b2"]) if w["n_h2"] else np.zeros(1, np.float32), f(w["w3"]), f(w["mean"]),
+                     f(w["scale"])]
+        s = ds_nn_weights()
+        s.n_in, s.n_h1, s.n_h2 = int(w["n_in"]), int(w["n_h1"]), int(w["n_h2"])
+        s.w1, s.b1, s.w2, s.b2, s.w3, s.mean, s.scale = [a.ctypes.data for a in self.keep]
+        s.b3 = float(w["b3"])
+        self.s = s
+
+
+def ds_load_nn_weights(ctx, w: dict):
+    nn = _NN(w)
+    return _check(ctx, lib().ds_load_nn_weights(ctx, C.byref(nn.s)), "ds_load_nn_weights")
+
+
+def ds_set_params(ctx, p: ds_params):
+    return _check(ctx, lib().ds_set_params(ctx, C.byref(p)), "ds_set_params")
+
+
+def ds_reserve(ctx, max_events: int, max_seeds: int, max_hits: int):
+    return _check(ctx, lib().ds_reserve(ctx, max_events, max_seeds, max_hits), "ds_reserve")
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def ds_reconstruct(ctx, dev: dict, out: dict, stream=None):
+    """dev: device tensors of one batch (see Downstream.to_device); out: track
+    output tensors {tracks (uint8 [cap, 64]), trk_off (int32 [E+1]), n_tracks (int32 [1])}."""
+    b = ds_event_batch(dev["n_events"], dev["n_seeds"], dev["n_hits"], 0, _ptr(dev["seed_off"]),
+                       _ptr(dev["hit_off"]))
+    sd = ds_seeds(*[_ptr(dev[k]) for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2")])
+    ht = ds_ut_hits(*[_ptr(dev[k]) for k in ("hit_x0", "hit_ybeg", "hit_yend", "hit_layer")])
+    tr = ds_tracks(_ptr(out["tracks"]), _ptr(out["trk_off"]), _ptr(out["n_tracks"]),
+                   int(out["tracks"].shape[0]), 0)
+    _check(ctx, lib().ds_reconstruct(ctx, C.byref(b), C.byref(sd), C.byref(ht), C.byref(tr), _stream(stream)),
+           "ds_reconstruct")
+    out["_struct"] = tr
+    return tr
+
+
+def ds_vertex(ctx, trk_out: dict, vout: dict, stream=None):
+    tr = trk_out["_struct"]
+    vx = ds_vertices(_ptr(vout["vertices"]), _ptr(vout["vtx_off"]), _ptr(vout["n_vertices"]),
+                     int(vout["vertices"].shape[0]), 0)
+    _check(ctx, lib().ds_vertex(ctx, C.byref(tr), C.byref(vx), _stream(stream)), "ds_vertex")
+    return vx
+
+
+def ds_sync_status(ctx, stream=None, raise_on_error: bool = True):
+    s = ds_stats()
+    st = lib().ds_sync_status(ctx, _stream(stream), C.byref(s))
+    stats = {k: getattr(s, k) for k, _ in ds_stats._fields_ if k != "reserved0"}
+    stats["status"] = st
+    if raise_on_error and st != DS_OK:
+        raise DSError(st, f"ds_sync_status: {ds_status_string(st)}: {ds_last_error(ctx)} flags=0x{s.device_flags:x}")
+    return stats
+
+
+def ds_profile_enable(ctx, enable: bool = True):
+    return _check(ctx, lib().ds_profile_enable(ctx, int(enable)), "ds_profile_enable")
+
+
+def ds_profile_read(ctx) -> dict:
+    """{kernel name: (launches, total_ms)}; synchronises the device, clears the records."""
+    buf = (ds_kernel_time * 32)()
+    n = C.c_int32()
+    _check(ctx, lib().ds_profile_read(ctx, buf, 32, C.byref(n)), "ds_profile_read")
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(min(n.value, 32))}
+
+
+def ds_process_host(ctx, batch: dict, trk_capacity: int, vtx_capacity: int, stream=None, host_out=None):
+    """End-to-end call with host (numpy, ideally pinned) buffers."""
+    E = int(batch["n_events"])
+    seed_cols = [np.ascontiguousarray(batch[k], np.float32)
+                 for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2")]
+    hit_cols = [np.ascontiguousarray(batch[k], np.float32) for k in ("hit_x0", "hit_ybeg", "hit_yend")]
+    layer = np.ascontiguousarray(batch["hit_layer"], np.uint8)
+    so = np.ascontiguousarray(batch["seed_off"], np.int32)
+    ho = np.ascontiguousarray(batch["hit_off"], np.int32)
+    if host_out is None:
+        host_out = dict(tracks=np.zeros(trk_capacity, TRACK_DTYPE), trk_off=np.zeros(E + 1, np.int32),
+                        vertices=np.zeros(vtx_capacity, VERTEX_DTYPE), vtx_off=np.zeros(E + 1, np.int32))
+    sc = (C.c_void_p * 6)(*[a.ctypes.data for a in seed_cols])
+    hc = (C.c_void_p * 3)(*[a.ctypes.data for a in hit_cols])
+    nt = C.c_int32(); nv = C.c_int32()
+    st = lib().ds_process_host(ctx, E, so.ctypes.data, sc, ho.ctypes.data, hc, layer.ctypes.data,
+                               host_out["tracks"].ctypes.data, trk_capacity, host_out["trk_off"].ctypes.data,
+                               C.byref(nt), host_out["vertices"].ctypes.data, vtx_capacity,
+                               host_out["vtx_off"].ctypes.data, C.byref(nv), _stream(stream))
+    _check(ctx, st, "ds_process_host")
+    host_out["n_tracks"] = nt.value
+    host_out["n_vertices"] = nv.value
+    return host_out
+
+
+# ------------------------------------------------------------------ convenience
+
+class Downstream:
+    """One library context with device-resident geometry and network weights."""
+
+    def __init__(self, cfg: dict, weights: dict, device: int = 0, **param_over):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (the library has no CPU path)")
+        self.torch = torch
+        self.device = device
+        self.ctx = ds_create(device)
+        self.cfg = cfg
+        ds_load_geometry(self.ctx, make_geometry(cfg))
+        ds_load_nn_weights(self.ctx, weights)
+        self.params = make_params(cfg, **param_over)
+        ds_set_params(self.ctx, self.params)
+
+    def close(self):
+        if self.ctx is not None:
+            ds_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, **over):
+        for k, v in over.items():
+            setattr(self.params, k, v)
+        ds_set_params(self.ctx, self.params)
+
+    def to_device(self, batch: dict) -> dict:
+        t = self.torch
+        dev = f"cuda:{self.device}"
+        d = dict(n_events=int(batch["n_events"]), n_seeds=int(batch["seed_off"][-1]),
+                 n_hits=int(batch["hit_off"][-1]))
+        for k in ("seed_off", "hit_off"):
+            d[k] = t.from_numpy(np.ascontiguousarray(batch[k], np.int32)).to(dev)
+        for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2", "hit_x0", "hit_ybeg",
+                  "hit_yend"):
+            d[k] = t.from_numpy(np.ascontiguousarray(batch[k], np.float32)).to(dev)
+        d["hit_layer"] = t.from_numpy(np.ascontiguousarray(batch["hit_layer"], np.uint8)).to(dev)
+        return d
+
+    def alloc_tracks(self, n_events: int, capacity: int) -> dict:
+        t = self.torch
+        dev = f"cuda:{self.device}"
+        return dict(tracks=t.zeros((max(capacity, 1), 64), dtype=t.uint8, device=dev),
+                    trk_off=t.zeros(n_events + 1, dtype=t.int32, device=dev),
+                    n_tracks=t.zeros(1, dtype=t.int32, device=dev))
+
+    def alloc_vertices(self, n_events: int, capacity: int) -> dict:
+        t = self.torch
+        dev = f"cuda:{self.device}"
+        return dict(vertices=t.zeros((max(capacity, 1), 32), dtype=t.uint8, device=dev),
+                    vtx_off=t.zeros(n_events + 1, dtype=t.int32, device=dev),
+                    n_vertices=t.zeros(1, dtype=t.int32, device=dev))
+
+    def reconstruct(self, dev: dict, out: dict, stream=None):
+        return ds_reconstruct(self.ctx, dev, out, stream)
+
+    def vertex(self, trk_out: dict, vout: dict, stream=None):
+        return ds_vertex(self.ctx, trk_out, vout, stream)
+
+    def sync(self, stream=None, raise_on_error=True):
+        return ds_sync_status(self.ctx, stream, raise_on_error)
+
+    def run(self, batch: dict, trk_capacity=None, vtx_capacity=None, dev=None):
+        """Upload, reconstruct, vertex, synchronise and decode (host numpy)."""
+        dev = dev or self.to_device(batch)
+        E = dev["n_events"]
+        trk_capacity = trk_capacity if trk_capacity is not None else max(dev["n_seeds"], 1)
+        out = self.alloc_tracks(E, trk_capacity)
+        self.reconstruct(dev, out)
+        if vtx_capacity is None:
+            vtx_capacity = 16 * trk_capacity + 4096
+        vout = self.alloc_vertices(E, vtx_capacity)
+        self.vertex(out, vout)
+        stats = self.sync()
+        return decode(out, vout) | {"stats": stats}
+
+
+def decode(out: dict, vout: dict | None = None) -> dict:
+    n = int(out["n_tracks"].cpu()[0])
+    cap = out["tracks"].shape[0]
+    raw = out["tracks"][: min(n, cap)].cpu().numpy()
+    res = dict(tracks=raw.view(TRACK_DTYPE).reshape(-1), trk_off=out["trk_off"].cpu().numpy(), n_tracks=n)
+    if vout is not None:
+        nv = int(vout["n_vertices"].cpu()[0])
+        vcap = vout["vertices"].shape[0]
+        vr = vout["vertices"][: min(nv, vcap)].cpu().numpy()
+        res.update(vertices=vr.view(VERTEX_DTYPE).reshape(-1), vtx_off=vout["vtx_off"].cpu().numpy(),
+                   n_vertices=nv)
+    return res

@@ -1,0 +1,238 @@
+"""GPU (libds.so through its C ABI) vs the FP64 oracle on the same seeded inputs.
+
+Rules (tests/parity.py): identical hit assignments except for seeds whose
+oracle decision margin is below 1e-5 (at most 0.1 % of tracks); FP32 track
+parameters within 1e-4, chi2 within 1e-3, responses within 2e-5; vertices,
+with the oracle fed the GPU's own track records, within 1 um.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_13092_b300 import synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_13092_b300 import build
+    build.build()
+    return torch
+
+
+def make(torch_cuda, cfg, w, **over):
+    from paper_2503_13092_b300 import ds
+    return ds.Downstream(cfg, w, **over)
+
+
+def run_both(dsx, b, cfg, w, n_threads=8, vtx=True):
+    g = dsx.run(b)
+    assert g["stats"]["status"] == 0, g["stats"]
+    o = oracle.reconstruct(b, cfg, w, n_threads=n_threads)
+    rep = parity.compare_tracks(b, o, g)
+    vrep = parity.compare_vertices(cfg, g) if vtx else None
+    return g, o, rep, vrep
+
+
+@pytest.mark.parametrize("pick", ["nn", "chi2"])
+def test_c1_parity(torch_cuda, weights, pick):
+    b = synth.config_batch("c1")
+    over = dict(pick_chi2=1, nn_threshold=0.9) if pick == "chi2" else {}
+    cfg = synth.default_config(**over)
+    d = make(torch_cuda, cfg, weights)
+    g, o, rep, vrep = run_both(d, b, cfg, weights)
+    assert rep["n_tracks_oracle"] > 20
+    parity.assert_tracks_match(rep)
+    parity.assert_vertices_match(vrep)
+    # every candidate scored on the GPU is counted like the oracle's
+    ok = o["margin"] >= parity.MARGIN
+    assert g["stats"]["n_candidates"] == int(o["ncand"].sum()) or not ok.all()
+
+
+@pytest.mark.parametrize("variant", ["origin", "training", "paper_net", "k1_3", "mode_b"])
+def test_method_variants(torch_cuda, variant):
+    over = {}
+    w = synth.nn_weights()
+    mode = "A"
+    if variant == "origin":
+        over = dict(first_window_origin=1, w1a=60.0)
+    elif variant == "training":
+        over = dict(training=1)
+    elif variant == "paper_net":
+        w = synth.nn_weights(8, 14, 0, seed=3)
+    elif variant == "k1_3":
+        over = dict(k1=3)
+    elif variant == "mode_b":
+        mode = "B"
+    cfg = synth.default_config(mode=mode, **over)
+    b = synth.config_batch("c2", n_events=12, mode=mode)
+    d = make(torch_cuda, cfg, w)
+    g, o, rep, vrep = run_both(d, b, cfg, w)
+    parity.assert_tracks_match(rep)
+    parity.assert_vertices_match(vrep)
+
+
+def test_c2_sample_parity(torch_cuda, weights):
+    b = synth.config_batch("c2", n_events=60)
+    cfg = synth.default_config()
+    d = make(torch_cuda, cfg, weights)
+    g, o, rep, vrep = run_both(d, b, cfg, weights)
+    assert rep["n_tracks_oracle"] > 5000
+    parity.assert_tracks_match(rep)
+    parity.assert_vertices_match(vrep)
+
+
+@pytest.mark.parametrize("name,n_events,n_sample", [("c2", 1000, 24), ("c3", 2000, 16)])
+def test_full_size_sampled(torch_cuda, weights, name, n_events, n_sample):
+    """The benchmark's launch (whole batch in one call); the oracle recomputes
+    sampled events one by one (events are independent), including the largest."""
+    b = synth.config_batch(name, n_events=n_events)
+    cfg = synth.default_config()
+    d = make(torch_cuda, cfg, weights)
+    g = d.run(b)
+    assert g["stats"]["status"] == 0
+    E = b["n_events"]
+    ns = np.diff(b["seed_off"])
+    rng = np.random.default_rng(7)
+    ev = sorted(set(rng.choice(E, n_sample - 2, replace=False).tolist()) | {int(np.argmax(ns)), E - 1})
+    sb = parity.sub_batch(b, ev)
+    o = oracle.reconstruct(sb, cfg, weights, n_threads=8)
+    # GPU output restricted to the sampled events, ids mapped into the sub-batch
+    t = g["tracks"]
+    sel = np.isin(t["event"], ev)
+    seed_new = {int(s): k for k, s in enumerate(sb["_seed_map"])}
+    hit_new = np.full(int(b["hit_off"][-1]), -1, np.int64)
+    hit_new[sb["_hit_map"]] = np.arange(len(sb["_hit_map"]))
+    tt = t[sel].copy()
+    tt["seed"] = [seed_new[int(s)] for s in tt["seed"]]
+    tt["event"] = [ev.index(int(e)) for e in tt["event"]]
+    trk_off = np.zeros(len(ev) + 1, np.int32)
+    trk_off[1:] = np.cumsum(np.bincount(tt["event"], minlength=len(ev)))
+    sub = dict(tracks=tt, trk_off=trk_off)
+    rep = parity.compare_tracks(sb, o, sub, hit_map_gpu=lambda h: hit_new[h])
+    parity.assert_tracks_match(rep)
+    # vertices of the sampled events: GPU records vs the oracle fed the same tracks
+    v = g["vertices"]
+    vsel = np.isin(v["event"], ev)
+    first = {e: int(g["trk_off"][e]) for e in ev}
+    new_first = {e: int(trk_off[k]) for k, e in enumerate(ev)}
+    vv = v[vsel].copy()
+    vv["i"] = [new_first[int(e)] + int(i) - first[int(e)] for e, i in zip(vv["event"], vv["i"])]
+    vv["j"] = [new_first[int(e)] + int(j) - first[int(e)] for e, j in zip(vv["event"], vv["j"])]
+    vv["event"] = [ev.index(int(e)) for e in vv["event"]]
+    vtx_off = np.zeros(len(ev) + 1, np.int32)
+    vtx_off[1:] = np.cumsum(np.bincount(vv["event"], minlength=len(ev)))
+    vrep = parity.compare_vertices(cfg, dict(tracks=tt, trk_off=trk_off, vertices=vv, vtx_off=vtx_off))
+    parity.assert_vertices_match(vrep)
+
+
+def test_edge_cases(torch_cuda, weights):
+    from paper_2503_13092_b300 import ds
+    cfg = synth.default_config()
+    d = make(torch_cuda, cfg, weights)
+    # empty batch
+    empty = dict(n_events=0, seed_off=np.zeros(1, np.int32), hit_off=np.zeros(1, np.int32),
+                 **{k: np.zeros(0, np.float32) for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop",
+                                                         "seed_chi2", "hit_x0", "hit_ybeg", "hit_yend")},
+                 hit_layer=np.zeros(0, np.uint8))
+    g = d.run(empty)
+    assert g["n_tracks"] == 0 and g["n_vertices"] == 0
+    # events with no seeds, no hits, a single seed; ragged sizes
+    b = synth.config_batch("c2", n_events=7)
+    parts = [parity.sub_batch(b, [0])]
+    nohit = parity.sub_batch(b, [1]); nohit["hit_off"][:] = 0
+    for k in ("hit_x0", "hit_ybeg", "hit_yend", "hit_layer", "hit_track"):
+        nohit[k] = nohit[k][:0]
+    noseed = parity.sub_batch(b, [2]); noseed["seed_off"][:] = 0
+    for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2", "seed_track"):
+        noseed[k] = noseed[k][:0]
+    one = parity.sub_batch(b, [3]); one["seed_off"][1] = 1
+    for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2", "seed_track"):
+        one[k] = one[k][:1]
+    parts += [nohit, noseed, one, parity.sub_batch(b, [4, 5, 6])]
+    mb = concat(parts)
+    g, o, rep, vrep = run_both(d, mb, cfg, weights)
+    parity.assert_tracks_match(rep)
+    parity.assert_vertices_match(vrep)
+    # determinism: a second run is bit-identical
+    g2 = d.run(mb)
+    assert g2["tracks"].tobytes() == g["tracks"].tobytes()
+    assert g2["vertices"].tobytes() == g["vertices"].tobytes()
+    # capacity: truncation is deterministic and flagged
+    full = d.run(b)
+    dev = d.to_device(b)
+    out = d.alloc_tracks(b["n_events"], 100)
+    d.reconstruct(dev, out)
+    st = d.sync(raise_on_error=False)
+    assert st["status"] == ds.DS_ERR_CAPACITY and st["device_flags"] & ds.DS_FLAG_TRACK_CAPACITY
+    small = ds.decode(out)
+    assert small["n_tracks"] == full["n_tracks"]
+    assert small["tracks"].tobytes() == full["tracks"][:100].tobytes()
+
+
+def concat(parts):
+    out = dict(n_events=sum(p["n_events"] for p in parts))
+    so, ho = [np.zeros(1, np.int32)], [np.zeros(1, np.int32)]
+    s_base = h_base = 0
+    for p in parts:
+        so.append(p["seed_off"][1:] + s_base); ho.append(p["hit_off"][1:] + h_base)
+        s_base += int(p["seed_off"][-1]); h_base += int(p["hit_off"][-1])
+    out["seed_off"] = np.concatenate(so).astype(np.int32)
+    out["hit_off"] = np.concatenate(ho).astype(np.int32)
+    for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2", "seed_track", "hit_x0",
+              "hit_ybeg", "hit_yend", "hit_layer", "hit_track"):
+        out[k] = np.concatenate([p[k] for p in parts])
+    return out
+
+
+def test_hit_permutation_and_host_path(torch_cuda, weights):
+    """Input hit order does not change the GPU result; the host-buffer entry
+    point returns what the device path returns."""
+    from paper_2503_13092_b300 import ds
+    b = synth.config_batch("c2", n_events=20)
+    cfg = synth.default_config()
+    d = make(torch_cuda, cfg, weights)
+    g = d.run(b)
+    rng = np.random.default_rng(3)
+    bp = dict(b)
+    perm = np.concatenate([h0 + rng.permutation(h1 - h0) for h0, h1 in zip(b["hit_off"][:-1], b["hit_off"][1:])])
+    for k in ("hit_x0", "hit_ybeg", "hit_yend", "hit_layer", "hit_track"):
+        bp[k] = b[k][perm]
+    gp = d.run(bp)
+    t, tp = g["tracks"], gp["tracks"]
+    assert np.array_equal(t["seed"], tp["seed"])
+    mapped = np.where(tp["hit"] >= 0, perm[np.maximum(tp["hit"], 0)], -1)
+    assert np.array_equal(mapped, t["hit"])
+    for k in ("x", "y", "tx", "ty", "qop", "chi2", "nn"):
+        assert np.array_equal(t[k], tp[k])
+    h = ds.ds_process_host(d.ctx, b, trk_capacity=int(b["seed_off"][-1]), vtx_capacity=200000)
+    assert h["n_tracks"] == g["n_tracks"] and h["n_vertices"] == g["n_vertices"]
+    assert h["tracks"][: h["n_tracks"]].tobytes() == g["tracks"].tobytes()
+    assert h["vertices"][: h["n_vertices"]].tobytes() == g["vertices"].tobytes()
+
+
+def test_malformed_input_is_flagged(torch_cuda, weights):
+    """Bad layers and strips that cross sectors are flagged, not faulted on."""
+    from paper_2503_13092_b300 import ds
+    b = synth.config_batch("c2", n_events=3)
+    cfg = synth.default_config()
+    d = make(torch_cuda, cfg, weights)
+    bad = dict(b)
+    bad["hit_layer"] = b["hit_layer"].copy()
+    bad["hit_layer"][5] = 9
+    bad["hit_yend"] = b["hit_yend"].copy()
+    bad["hit_yend"][6] += 250.0
+    dev = d.to_device(bad)
+    out = d.alloc_tracks(3, int(b["seed_off"][-1]))
+    d.reconstruct(dev, out)
+    st = d.sync(raise_on_error=False)
+    assert st["status"] == ds.DS_ERR_DEVICE_FLAG
+    assert st["device_flags"] & ds.DS_FLAG_BAD_LAYER and st["device_flags"] & ds.DS_FLAG_STRIP_SECTOR
+    # flags are cleared by the read: a clean batch afterwards is clean
+    g = d.run(b)
+    assert g["stats"]["status"] == 0
