@@ -264,6 +264,27 @@ DS_API ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tracks, ds_vertices *ou
  * corresponding flags are set, else DS_OK.  stats may be NULL. */
 DS_API ds_status ds_sync_status(ds_ctx *ctx, void *stream, ds_stats *stats);
 
+/* ds_reconstruct for callers that cannot allocate device memory (a host
+ * framework that owns every device allocation through its own pool, code that
+ * must not trigger an allocation's implicit device synchronisation, callers
+ * that cannot create a ds_ctx).  The paper has no counterpart: this is a
+ * deployment variant of the same computation.  Runs the same kernels as
+ * ds_reconstruct on the CURRENT device and stream, taking geometry, parameters
+ * and weights as host structs, with every scratch buffer inside one static
+ * device array of about 27 MB that each GPU loading the library holds until
+ * process exit.  It calls no cudaMalloc/cudaFree.  Limits per call: at most
+ * 256 events, 65536 seeds and 1048576 hits (DS_ERR_CAPACITY beyond, nothing
+ * launched).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  Outputs as ds_reconstruct; if d_flags (device
+ * pointer, may be NULL) is given, the call's device flag word (DS_FLAG_*) is
+ * written there when the work completes.  Asynchronous on `stream`. */
+DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, const ds_params *params,
+                                        const ds_nn_weights *weights, const ds_event_batch *batch,
+                                        const ds_seeds *seeds, const ds_ut_hits *hits, ds_tracks *out,
+                                        uint32_t *d_flags, void *stream);
+
 /* Profiling: when enabled, every kernel launch of this context is bracketed
  * by two CUDA events on its stream.  ds_profile_read() synchronises the
  * device, returns one entry per kernel name (at most max_out; *n_out = number

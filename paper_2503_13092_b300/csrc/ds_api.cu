@@ -114,6 +114,118 @@ ds_status ensure_workspace(ds_ctx *ctx, int E, int S, int H, cudaStream_t st)
 
 }  // namespace
 
+namespace ds {
+
+// Host structs of the ABI -> device-side parameter blocks.  Each returns
+// nullptr on success or a description of the invalid argument.
+const char *fill_dev_geom(const ds_geometry *gm, DevGeom *out)
+{
+    if (!gm || !out) return "null pointer";
+    for (int l = 0; l < 3; ++l)
+        if (!(gm->z_layer[l] < gm->z_layer[l + 1])) return "z_layer not increasing";
+    if (gm->n_sectors < 1 || gm->n_sectors > kMaxSectors) return "n_sectors outside 1..32";
+    if (!(gm->sector_h > 0) || !(gm->x_half_bins > 0) || !(gm->sigma_hit > 0) || !(gm->sigma_mag > 0))
+        return "sector_h, x_half_bins and sigmas must be > 0";
+    DevGeom &g = *out;
+    for (int l = 0; l < 4; ++l) {
+        g.z[l] = (float)gm->z_layer[l];
+        g.dxdy[l] = (float)gm->dxdy[l];
+        g.zmag[l] = (float)gm->zmag[l];
+    }
+    g.y_min = (float)gm->y_min;
+    g.sector_h = (float)gm->sector_h;
+    g.inv_sector_h = (float)(1.0 / gm->sector_h);
+    g.n_sec = gm->n_sectors;
+    g.x_half = (float)gm->x_half_bins;
+    g.inv_xbin = (float)(kNXB / (2.0 * gm->x_half_bins));
+    g.z_seed = (float)gm->z_seed;
+    g.kappa = (float)gm->kappa;
+    g.mp = (float)gm->mp;
+    g.gamma0 = (float)gm->gamma0;
+    g.gamma1 = (float)gm->gamma1;
+    g.z_ref = (float)gm->z_ref;
+    g.w_hit = (float)(1.0 / (gm->sigma_hit * gm->sigma_hit));
+    g.w_mag = (float)(1.0 / (gm->sigma_mag * gm->sigma_mag));
+    g.inv_sigma_hit = (float)(1.0 / gm->sigma_hit);
+    const int nb = 4 * g.n_sec * kNXB + 1;
+    g.table_stride = (nb + 7) & ~7;
+    return nullptr;
+}
+
+const char *fill_dev_nn(const ds_nn_weights *w, DevNN *out, int *n_h2_kernel)
+{
+    if (!w || !out || !w->w1 || !w->b1 || !w->w3 || !w->mean || !w->scale) return "null pointer";
+    if (w->n_in < 1 || w->n_in > 16 || w->n_h1 < 1 || w->n_h1 > 32 || w->n_h2 < 0 || w->n_h2 > 32)
+        return "unsupported network shape (n_in<=16, n_h1<=32, n_h2<=32)";
+    if (w->n_h2 > 0 && (!w->w2 || !w->b2)) return "null w2/b2";
+    DevNN &nn = *out;
+    std::memset(&nn, 0, sizeof(nn));
+    for (int o = 0; o < w->n_h1; ++o) {
+        nn.b1[o] = w->b1[o];
+        for (int i = 0; i < w->n_in; ++i) nn.w1[o][i] = w->w1[o * w->n_in + i];
+    }
+    const int nl = w->n_h2 > 0 ? w->n_h2 : w->n_h1;
+    if (w->n_h2 > 0) {
+        for (int o = 0; o < w->n_h2; ++o) {
+            nn.b2[o] = w->b2[o];
+            for (int i = 0; i < w->n_h1; ++i) nn.w2[o][i] = w->w2[o * w->n_h1 + i];
+        }
+    }
+    for (int i = 0; i < nl; ++i) nn.w3[i] = w->w3[i];
+    nn.b3 = w->b3;
+    for (int i = 0; i < w->n_in; ++i) {
+        nn.mean[i] = w->mean[i];
+        nn.scale[i] = w->scale[i];
+    }
+    // the single-hidden-layer kernel is compiled for 8 inputs x 16 hidden
+    if (w->n_h2 == 0 && (w->n_in > 8 || w->n_h1 > 16)) {
+        // run it through the two-layer kernel: identity second layer (exact: h1 >= 0)
+        for (int o = 0; o < w->n_h1; ++o) {
+            nn.w2[o][o] = 1.f;
+            nn.b2[o] = 0.f;
+        }
+        *n_h2_kernel = 32;
+    } else {
+        *n_h2_kernel = w->n_h2;
+    }
+    return nullptr;
+}
+
+const char *fill_dev_params(const ds_params *p, DevParams *out)
+{
+    if (!p || !out) return "null pointer";
+    if (p->k1 < 1 || p->k1 > kK1Max) return "k1 outside 1..10";
+    if (!(p->w1a >= 0) || !(p->w1b >= 0) || !(p->w2 > 0) || !(p->dy_tol >= 0) || !(p->doca_max > 0) ||
+        !(p->nr_tol > 0) || p->nr_max_iter < 1 || !(p->eps_parallel >= 0))
+        return "window, tolerance or limit not positive";
+    if (p->mlp_precision != DS_MLP_FP32 && p->mlp_precision != DS_MLP_BF16 && p->mlp_precision != DS_MLP_FP8)
+        return "unknown mlp_precision";
+    DevParams &d = *out;
+    d.w1a = (float)p->w1a;
+    d.w1b = (float)p->w1b;
+    d.w2 = (float)p->w2;
+    d.dy_tol = (float)p->dy_tol;
+    d.nn_threshold = (float)p->nn_threshold;
+    if (p->nn_threshold <= 0.0)
+        d.thr_logit = -INFINITY;
+    else if (p->nn_threshold >= 1.0)
+        d.thr_logit = INFINITY;
+    else
+        d.thr_logit = (float)std::log(p->nn_threshold / (1.0 - p->nn_threshold));
+    d.doca_max = (float)p->doca_max;
+    d.nr_tol = (float)p->nr_tol;
+    d.eps_par = (float)p->eps_parallel;
+    d.k1 = p->k1;
+    d.origin = p->first_window_origin ? 1 : 0;
+    d.pick_chi2 = p->pick_chi2 ? 1 : 0;
+    d.clone_kill = p->clone_kill ? 1 : 0;
+    d.training = p->training ? 1 : 0;
+    d.nr_max_iter = p->nr_max_iter;
+    return nullptr;
+}
+
+}  // namespace ds
+
 extern "C" {
 
 const char *ds_status_string(ds_status s)
@@ -199,35 +311,8 @@ void ds_destroy(ds_ctx *ctx)
 ds_status ds_load_geometry(ds_ctx *ctx, const ds_geometry *gm)
 {
     if (!ctx || !gm) return fail(ctx, DS_ERR_ARG, "null pointer");
-    for (int l = 0; l < 3; ++l)
-        if (!(gm->z_layer[l] < gm->z_layer[l + 1])) return fail(ctx, DS_ERR_ARG, "z_layer not increasing");
-    if (gm->n_sectors < 1 || gm->n_sectors > ds::kMaxSectors)
-        return fail(ctx, DS_ERR_ARG, "n_sectors outside 1..32");
-    if (!(gm->sector_h > 0) || !(gm->x_half_bins > 0) || !(gm->sigma_hit > 0) || !(gm->sigma_mag > 0))
-        return fail(ctx, DS_ERR_ARG, "sector_h, x_half_bins and sigmas must be > 0");
-    ds::DevGeom &g = ctx->g;
-    for (int l = 0; l < 4; ++l) {
-        g.z[l] = (float)gm->z_layer[l];
-        g.dxdy[l] = (float)gm->dxdy[l];
-        g.zmag[l] = (float)gm->zmag[l];
-    }
-    g.y_min = (float)gm->y_min;
-    g.sector_h = (float)gm->sector_h;
-    g.inv_sector_h = (float)(1.0 / gm->sector_h);
-    g.n_sec = gm->n_sectors;
-    g.x_half = (float)gm->x_half_bins;
-    g.inv_xbin = (float)(ds::kNXB / (2.0 * gm->x_half_bins));
-    g.z_seed = (float)gm->z_seed;
-    g.kappa = (float)gm->kappa;
-    g.mp = (float)gm->mp;
-    g.gamma0 = (float)gm->gamma0;
-    g.gamma1 = (float)gm->gamma1;
-    g.z_ref = (float)gm->z_ref;
-    g.w_hit = (float)(1.0 / (gm->sigma_hit * gm->sigma_hit));
-    g.w_mag = (float)(1.0 / (gm->sigma_mag * gm->sigma_mag));
-    g.inv_sigma_hit = (float)(1.0 / gm->sigma_hit);
-    const int nb = 4 * g.n_sec * ds::kNXB + 1;
-    g.table_stride = (nb + 7) & ~7;
+    const char *why = ds::fill_dev_geom(gm, &ctx->g);
+    if (why) return fail(ctx, DS_ERR_ARG, why);
     ctx->has_geom = true;
     ctx->cap_events = 0;   // bin table stride may have changed
     return DS_OK;
@@ -235,41 +320,11 @@ ds_status ds_load_geometry(ds_ctx *ctx, const ds_geometry *gm)
 
 ds_status ds_load_nn_weights(ds_ctx *ctx, const ds_nn_weights *w)
 {
-    if (!ctx || !w || !w->w1 || !w->b1 || !w->w3 || !w->mean || !w->scale)
-        return fail(ctx, DS_ERR_ARG, "null pointer");
-    if (w->n_in < 1 || w->n_in > 16 || w->n_h1 < 1 || w->n_h1 > 32 || w->n_h2 < 0 || w->n_h2 > 32)
-        return fail(ctx, DS_ERR_ARG, "unsupported network shape (n_in<=16, n_h1<=32, n_h2<=32)");
-    if (w->n_h2 > 0 && (!w->w2 || !w->b2)) return fail(ctx, DS_ERR_ARG, "null w2/b2");
-    ds::DevNN &nn = ctx->nn;
-    std::memset(&nn, 0, sizeof(nn));
-    for (int o = 0; o < w->n_h1; ++o) {
-        nn.b1[o] = w->b1[o];
-        for (int i = 0; i < w->n_in; ++i) nn.w1[o][i] = w->w1[o * w->n_in + i];
-    }
-    const int nl = w->n_h2 > 0 ? w->n_h2 : w->n_h1;
-    if (w->n_h2 > 0) {
-        for (int o = 0; o < w->n_h2; ++o) {
-            nn.b2[o] = w->b2[o];
-            for (int i = 0; i < w->n_h1; ++i) nn.w2[o][i] = w->w2[o * w->n_h1 + i];
-        }
-    }
-    for (int i = 0; i < nl; ++i) nn.w3[i] = w->w3[i];
-    nn.b3 = w->b3;
-    for (int i = 0; i < w->n_in; ++i) {
-        nn.mean[i] = w->mean[i];
-        nn.scale[i] = w->scale[i];
-    }
-    // the single-hidden-layer kernel is compiled for 8 inputs x 16 hidden
-    if (w->n_h2 == 0 && (w->n_in > 8 || w->n_h1 > 16)) {
-        // run it through the two-layer kernel: identity second layer (exact: h1 >= 0)
-        for (int o = 0; o < w->n_h1; ++o) {
-            nn.w2[o][o] = 1.f;
-            nn.b2[o] = 0.f;
-        }
-        ctx->nn_h2 = 32;
-    } else {
-        ctx->nn_h2 = w->n_h2;
-    }
+    if (!ctx) return DS_ERR_ARG;
+    int n_h2 = 0;
+    const char *why = ds::fill_dev_nn(w, &ctx->nn, &n_h2);
+    if (why) return fail(ctx, DS_ERR_ARG, why);
+    ctx->nn_h2 = n_h2;
     ctx->nn_in = w->n_in;
     ctx->nn_h1 = w->n_h1;
     ctx->has_nn = true;
@@ -278,34 +333,9 @@ ds_status ds_load_nn_weights(ds_ctx *ctx, const ds_nn_weights *w)
 
 ds_status ds_set_params(ds_ctx *ctx, const ds_params *p)
 {
-    if (!ctx || !p) return fail(ctx, DS_ERR_ARG, "null pointer");
-    if (p->k1 < 1 || p->k1 > ds::kK1Max) return fail(ctx, DS_ERR_ARG, "k1 outside 1..10");
-    if (!(p->w1a >= 0) || !(p->w1b >= 0) || !(p->w2 > 0) || !(p->dy_tol >= 0) || !(p->doca_max > 0) ||
-        !(p->nr_tol > 0) || p->nr_max_iter < 1 || !(p->eps_parallel >= 0))
-        return fail(ctx, DS_ERR_ARG, "window, tolerance or limit not positive");
-    if (p->mlp_precision != DS_MLP_FP32 && p->mlp_precision != DS_MLP_BF16 && p->mlp_precision != DS_MLP_FP8)
-        return fail(ctx, DS_ERR_ARG, "unknown mlp_precision");
-    ds::DevParams &d = ctx->p;
-    d.w1a = (float)p->w1a;
-    d.w1b = (float)p->w1b;
-    d.w2 = (float)p->w2;
-    d.dy_tol = (float)p->dy_tol;
-    d.nn_threshold = (float)p->nn_threshold;
-    if (p->nn_threshold <= 0.0)
-        d.thr_logit = -INFINITY;
-    else if (p->nn_threshold >= 1.0)
-        d.thr_logit = INFINITY;
-    else
-        d.thr_logit = (float)std::log(p->nn_threshold / (1.0 - p->nn_threshold));
-    d.doca_max = (float)p->doca_max;
-    d.nr_tol = (float)p->nr_tol;
-    d.eps_par = (float)p->eps_parallel;
-    d.k1 = p->k1;
-    d.origin = p->first_window_origin ? 1 : 0;
-    d.pick_chi2 = p->pick_chi2 ? 1 : 0;
-    d.clone_kill = p->clone_kill ? 1 : 0;
-    d.training = p->training ? 1 : 0;
-    d.nr_max_iter = p->nr_max_iter;
+    if (!ctx) return DS_ERR_ARG;
+    const char *why = ds::fill_dev_params(p, &ctx->p);
+    if (why) return fail(ctx, DS_ERR_ARG, why);
     ctx->mlp_precision = p->mlp_precision;
     return DS_OK;
 }

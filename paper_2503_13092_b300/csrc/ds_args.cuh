@@ -102,6 +102,11 @@ struct ScatterVtxArgs {
     const DevCounters *cnt;
 };
 
+// Host ABI structs -> device parameter blocks (nullptr = ok, else the reason).
+const char *fill_dev_geom(const ds_geometry *gm, DevGeom *out);
+const char *fill_dev_nn(const ds_nn_weights *w, DevNN *out, int *n_h2_kernel);
+const char *fill_dev_params(const ds_params *p, DevParams *out);
+
 cudaError_t init_vertex_attributes();
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st, Prof *prof);
 cudaError_t launch_search(const SearchArgs &a, int n_in, int n_h2, cudaStream_t st, Prof *prof);

@@ -1,0 +1,167 @@
+// ds_reconstruct_noalloc: ds_reconstruct for callers that cannot allocate
+// device memory.
+//
+// Some callers cannot call cudaMalloc: code running inside a host framework
+// that owns every device allocation through its own pool (and forbids others),
+// callers that must not trigger an allocation that could implicitly
+// synchronise the device in the middle of their work, and callers that cannot
+// create a ds_ctx (which allocates its workspaces).  For them this entry point
+// runs the same kernels as ds_reconstruct with every scratch buffer (bucketed
+// hits, bin tables, per-seed winners, ranks, counters) carved out of one
+// file-scope __device__ array of kScratchBytes, which each GPU that loads the
+// library holds until the process exits.  It calls no cudaMalloc, cudaFree or
+// allocating library routine; the caller passes the inputs and the outputs.
+//
+// The array's name is only a host-side stand-in in host code, not a device
+// address, so the device address is obtained once per device with
+// cudaGetSymbolAddress (with that device current) and handed to the kernels.
+// The first call on a device does that set-up; make it before any stream
+// capture.  Every call shares the one array: calls that overlap on the GPU
+// (two streams, two host threads) race on it and must be serialised by the
+// caller.
+#include <cstring>
+#include <mutex>
+
+#include "ds_args.cuh"
+
+namespace ds {
+namespace {
+
+// Size limits of one call.
+constexpr int kNAEvents = 256;
+constexpr int kNASeeds = 65536;
+constexpr int kNAHits = 1 << 20;
+constexpr int kNATableStride = ((4 * kMaxSectors * kNXB + 1) + 7) & ~7;
+
+constexpr size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+constexpr size_t kOffCounters = 0;
+constexpr size_t kOffSorted = align256(sizeof(DevCounters));
+constexpr size_t kOffBins = kOffSorted + align256(sizeof(float4) * (size_t)kNAHits);
+constexpr size_t kOffTrk = kOffBins + align256(sizeof(uint16_t) * (size_t)kNATableStride * kNAEvents);
+constexpr size_t kOffKey = kOffTrk + align256(sizeof(ds_track) * (size_t)kNASeeds);
+constexpr size_t kOffHit = kOffKey + align256(sizeof(unsigned long long) * (size_t)kNASeeds);
+constexpr size_t kOffRank = kOffHit + align256(sizeof(int4) * (size_t)kNASeeds);
+constexpr size_t kOffCount = kOffRank + align256(sizeof(int) * (size_t)kNASeeds);
+constexpr size_t kScratchBytes = kOffCount + align256(sizeof(int) * (size_t)kNAEvents);
+static_assert(kScratchBytes <= 28u * 1024 * 1024, "scratch must stay modest");
+
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+unsigned char *g_scratch_dev[kMaxDevices] = {};   // device address of g_scratch, per device
+
+__global__ void k_noalloc_flags(const DevCounters *cnt, uint32_t *flags_out)
+{
+    *flags_out = cnt->flags;
+}
+
+ds_status scratch_address(int device, unsigned char **out)
+{
+    if (device < 0 || device >= kMaxDevices) return DS_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_dev[device]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return DS_ERR_CUDA;
+        g_scratch_dev[device] = static_cast<unsigned char *>(ptr);
+    }
+    *out = g_scratch_dev[device];
+    return DS_OK;
+}
+
+}  // namespace
+}  // namespace ds
+
+extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, const ds_params *params,
+                                                   const ds_nn_weights *weights, const ds_event_batch *b,
+                                                   const ds_seeds *sd, const ds_ut_hits *ht, ds_tracks *out,
+                                                   uint32_t *d_flags, void *stream)
+{
+    using namespace ds;
+    if (!geom || !params || !weights || !b || !sd || !ht || !out) return DS_ERR_ARG;
+    if (b->n_events < 0 || b->n_seeds < 0 || b->n_hits < 0 || out->capacity < 0) return DS_ERR_ARG;
+    if (b->n_events > kNAEvents || b->n_seeds > kNASeeds || b->n_hits > kNAHits) return DS_ERR_CAPACITY;
+    if (b->n_events > 0 && (!b->seed_off || !b->hit_off || !out->trk_off || !out->n_tracks)) return DS_ERR_ARG;
+    if (b->n_seeds > 0 && (!sd->x || !sd->y || !sd->tx || !sd->ty || !sd->qop || !sd->chi2)) return DS_ERR_ARG;
+    if (b->n_hits > 0 && (!ht->x0 || !ht->ybeg || !ht->yend || !ht->layer)) return DS_ERR_ARG;
+    if (out->capacity > 0 && !out->tracks) return DS_ERR_ARG;
+    if (params->mlp_precision != DS_MLP_FP32) return DS_ERR_ARG;
+
+    DevGeom g;
+    DevParams p;
+    DevNN nn;
+    int nn_h2 = 0;
+    if (fill_dev_geom(geom, &g) || fill_dev_params(params, &p) || fill_dev_nn(weights, &nn, &nn_h2))
+        return DS_ERR_ARG;
+
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return DS_ERR_CUDA;
+    unsigned char *base = nullptr;
+    ds_status st = scratch_address(device, &base);
+    if (st != DS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevCounters *cnt = reinterpret_cast<DevCounters *>(base + kOffCounters);
+
+    out->n_events = b->n_events;
+    // the array keeps the previous call's contents: counters start at zero
+    if (cudaMemsetAsync(cnt, 0, sizeof(DevCounters), s) != cudaSuccess) return DS_ERR_CUDA;
+    if (b->n_events > 0) {
+        static Prof no_prof;   // profiling stays off here
+        BucketArgs ba{};
+        ba.g = g;
+        ba.n_events = b->n_events;
+        ba.n_hits = b->n_hits;
+        ba.hit_off = b->hit_off;
+        ba.x0 = ht->x0; ba.ybeg = ht->ybeg; ba.yend = ht->yend; ba.layer = ht->layer;
+        ba.sorted = reinterpret_cast<float4 *>(base + kOffSorted);
+        ba.bins = reinterpret_cast<uint16_t *>(base + kOffBins);
+        ba.cnt = cnt;
+        if (launch_bucket(ba, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
+
+        SearchArgs sa{};
+        sa.g = g;
+        sa.p = p;
+        sa.nn = nn;
+        sa.n_events = b->n_events;
+        sa.n_seeds = b->n_seeds;
+        sa.n_hits = b->n_hits;
+        sa.seed_off = b->seed_off;
+        sa.hit_off = b->hit_off;
+        sa.sx = sd->x; sa.sy = sd->y; sa.stx = sd->tx; sa.sty = sd->ty; sa.sqop = sd->qop; sa.schi2 = sd->chi2;
+        sa.sorted = ba.sorted;
+        sa.bins = ba.bins;
+        sa.trk_ws = reinterpret_cast<ds_track *>(base + kOffTrk);
+        sa.key_ws = reinterpret_cast<unsigned long long *>(base + kOffKey);
+        sa.hit_ws = reinterpret_cast<int4 *>(base + kOffHit);
+        sa.rank_ws = reinterpret_cast<int *>(base + kOffRank);
+        sa.cnt = cnt;
+        if (launch_search(sa, weights->n_in, nn_h2, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
+
+        CloneArgs ca{};
+        ca.n_events = b->n_events;
+        ca.n_seeds = b->n_seeds;
+        ca.clone_kill = p.clone_kill && !p.training;
+        ca.seed_off = b->seed_off;
+        ca.key_ws = sa.key_ws;
+        ca.hit_ws = sa.hit_ws;
+        ca.rank_ws = sa.rank_ws;
+        ca.count_ws = reinterpret_cast<int *>(base + kOffCount);
+        ca.trk_off = out->trk_off;
+        ca.n_tracks = out->n_tracks;
+        ca.capacity = out->capacity;
+        ca.cnt = cnt;
+        ScatterTrkArgs xa{};
+        xa.n_seeds = b->n_seeds;
+        xa.trk_ws = sa.trk_ws;
+        xa.rank_ws = sa.rank_ws;
+        xa.trk_off = out->trk_off;
+        xa.out = out->tracks;
+        xa.capacity = out->capacity;
+        if (launch_clone(ca, xa, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
+    }
+    if (d_flags) {
+        k_noalloc_flags<<<1, 1, 0, s>>>(cnt, d_flags);
+        if (cudaGetLastError() != cudaSuccess) return DS_ERR_CUDA;
+    }
+    return DS_OK;
+}

@@ -122,6 +122,9 @@ def lib():
                                 C.POINTER(ds_tracks), P], C.c_int),
             "ds_vertex": ([P, C.POINTER(ds_tracks), C.POINTER(ds_vertices), P], C.c_int),
             "ds_sync_status": ([P, P, C.POINTER(ds_stats)], C.c_int),
+            "ds_reconstruct_noalloc": ([C.POINTER(ds_geometry), C.POINTER(ds_params), C.POINTER(ds_nn_weights),
+                                        C.POINTER(ds_event_batch), C.POINTER(ds_seeds), C.POINTER(ds_ut_hits),
+                                        C.POINTER(ds_tracks), P, P], C.c_int),
             "ds_profile_enable": ([P, C.c_int32], C.c_int),
             "ds_profile_read": ([P, C.POINTER(ds_kernel_time), C.c_int32, C.POINTER(C.c_int32)], C.c_int),
             "ds_process_host": ([P, C.c_int32, P, C.POINTER(P), P, C.POINTER(P), P, P, C.c_int32, P,
@@ -137,7 +140,8 @@ def lib():
 
 EXPORTED = ("ds_create", "ds_destroy", "ds_status_string", "ds_last_error", "ds_default_params",
             "ds_load_geometry", "ds_load_nn_weights", "ds_set_params", "ds_reserve", "ds_reconstruct",
-            "ds_vertex", "ds_sync_status", "ds_process_host", "ds_profile_enable", "ds_profile_read")
+            "ds_vertex", "ds_sync_status", "ds_process_host", "ds_profile_enable", "ds_profile_read",
+            "ds_reconstruct_noalloc")
 
 
 # --------------------------------------------------------------- C names, marshalled
@@ -269,6 +273,23 @@ def ds_sync_status(ctx, stream=None, raise_on_error: bool = True):
     if raise_on_error and st != DS_OK:
         raise DSError(st, f"ds_sync_status: {ds_status_string(st)}: {ds_last_error(ctx)} flags=0x{s.device_flags:x}")
     return stats
+
+
+def ds_reconstruct_noalloc(geom: ds_geometry, params: ds_params, weights: dict, dev: dict, out: dict,
+                           d_flags=None, stream=None) -> int:
+    """Allocation-free ds_reconstruct (no context; static device scratch).
+    Returns the ds_status code; outputs as ds_reconstruct."""
+    nn = _NN(weights)
+    b = ds_event_batch(dev["n_events"], dev["n_seeds"], dev["n_hits"], 0, _ptr(dev["seed_off"]),
+                       _ptr(dev["hit_off"]))
+    sd = ds_seeds(*[_ptr(dev[k]) for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2")])
+    ht = ds_ut_hits(*[_ptr(dev[k]) for k in ("hit_x0", "hit_ybeg", "hit_yend", "hit_layer")])
+    tr = ds_tracks(_ptr(out["tracks"]), _ptr(out["trk_off"]), _ptr(out["n_tracks"]),
+                   int(out["tracks"].shape[0]), 0)
+    st = lib().ds_reconstruct_noalloc(C.byref(geom), C.byref(params), C.byref(nn.s), C.byref(b), C.byref(sd),
+                                      C.byref(ht), C.byref(tr), _ptr(d_flags), _stream(stream))
+    out["_struct"] = tr
+    return st
 
 
 def ds_profile_enable(ctx, enable: bool = True):
