@@ -125,7 +125,10 @@ typedef struct {
     int32_t training;      /* 1: fixed 100/10 mm windows, no clone killing */
     int32_t nr_max_iter;   /* Newton-Raphson iteration limit */
     int32_t mlp_precision; /* DS_MLP_FP32 (default), DS_MLP_BF16, DS_MLP_FP8 */
-    int32_t reserved0;
+    int32_t fault_inject;  /* 0 in normal use.  Tests of the failure path: bit 0 makes the
+                              search kernel's bounded wait for its staged data run out, so
+                              the call reports DS_ERR_TIMEOUT (flag DS_FLAG_TIMEOUT) and
+                              produces no tracks; no GPU fault is involved. */
 } ds_params;
 
 /* One event batch (CSR over events).  Device pointers. */
@@ -271,7 +274,7 @@ DS_API ds_status ds_sync_status(ds_ctx *ctx, void *stream, ds_stats *stats);
  * deployment variant of the same computation.  Runs the same kernels as
  * ds_reconstruct on the CURRENT device and stream, taking geometry, parameters
  * and weights as host structs, with every scratch buffer inside one static
- * device array of about 27 MB that each GPU loading the library holds until
+ * device array of about 31 MB that each GPU loading the library holds until
  * process exit.  It calls no cudaMalloc/cudaFree.  Limits per call: at most
  * 256 events, 65536 seeds and 1048576 hits (DS_ERR_CAPACITY beyond, nothing
  * launched).  The first call on a device looks up the array's device address

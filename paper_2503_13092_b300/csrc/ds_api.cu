@@ -22,7 +22,10 @@ struct ds_ctx {
     // workspaces
     int cap_events = 0, cap_seeds = 0, cap_hits = 0, cap_pool = 0;
     float4 *sorted = nullptr;
+    float *sx0 = nullptr;
     uint16_t *bins = nullptr;
+    int *item_cnt = nullptr;
+    int *item_off = nullptr;
     ds_track *trk_ws = nullptr;
     unsigned long long *key_ws = nullptr;
     int4 *hit_ws = nullptr;
@@ -221,6 +224,7 @@ const char *fill_dev_params(const ds_params *p, DevParams *out)
     d.clone_kill = p->clone_kill ? 1 : 0;
     d.training = p->training ? 1 : 0;
     d.nr_max_iter = p->nr_max_iter;
+    d.fault_inject = p->fault_inject;
     return nullptr;
 }
 
@@ -256,7 +260,7 @@ ds_status ds_default_params(ds_params *p)
     p->nn_threshold = 0.5;
     p->doca_max = 2.0;
     p->nr_tol = 1e-6;
-    p->eps_parallel = 1e-3;
+    p->eps_parallel = 1e-4;
     p->k1 = 10;
     p->first_window_origin = 0;
     p->pick_chi2 = 0;
@@ -282,7 +286,7 @@ ds_status ds_create(ds_ctx **out, int device)
         return DS_ERR_OOM;
     }
     cudaMemset(ctx->d_cnt, 0, sizeof(ds::DevCounters));
-    if (ds::init_vertex_attributes() != cudaSuccess) {
+    if (ds::init_vertex_attributes() != cudaSuccess || ds::init_search_attributes() != cudaSuccess) {
         cudaFree(ctx->d_cnt);
         delete ctx;
         return DS_ERR_CUDA;
@@ -299,7 +303,7 @@ void ds_destroy(ds_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    void *ptrs[] = {ctx->d_cnt, ctx->sorted, ctx->bins, ctx->trk_ws, ctx->key_ws, ctx->hit_ws,
+    void *ptrs[] = {ctx->d_cnt, ctx->sorted, ctx->sx0, ctx->item_cnt, ctx->item_off, ctx->bins, ctx->trk_ws, ctx->key_ws, ctx->hit_ws,
                     ctx->rank_ws, ctx->count_trk, ctx->count_vtx, ctx->pool, ctx->pool_pos,
                     ctx->h.seed_off, ctx->h.hit_off, ctx->h.seed_cols, ctx->h.hit_cols, ctx->h.layer,
                     ctx->h.tracks, ctx->h.trk_off, ctx->h.vtx_off, ctx->h.counts, ctx->h.vertices};
@@ -352,6 +356,8 @@ ds_status ds_reserve(ds_ctx *ctx, int32_t E, int32_t S, int32_t H)
         if ((st = grow(ctx, &ctx->bins, (size_t)E * ctx->g.table_stride)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->count_trk, (size_t)E)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->count_vtx, (size_t)E)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->item_cnt, (size_t)E)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->item_off, (size_t)E + 1)) != DS_OK) return st;
         ctx->cap_events = E;
     }
     if (S > ctx->cap_seeds) {
@@ -363,6 +369,7 @@ ds_status ds_reserve(ds_ctx *ctx, int32_t E, int32_t S, int32_t H)
     }
     if (H > ctx->cap_hits) {
         if ((st = grow(ctx, &ctx->sorted, (size_t)H)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->sx0, (size_t)H + 4)) != DS_OK) return st;   // bulk-copy tail
         ctx->cap_hits = H;
     }
     return DS_OK;
@@ -395,13 +402,18 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     ba.g = ctx->g;
     ba.n_events = b->n_events;
     ba.n_hits = b->n_hits;
+    ba.n_seeds = b->n_seeds;
     ba.hit_off = b->hit_off;
+    ba.seed_off = b->seed_off;
     ba.x0 = ht->x0;
     ba.ybeg = ht->ybeg;
     ba.yend = ht->yend;
     ba.layer = ht->layer;
     ba.sorted = ctx->sorted;
+    ba.sx0 = ctx->sx0;
     ba.bins = ctx->bins;
+    ba.item_cnt = ctx->item_cnt;
+    ba.item_off = ctx->item_off;
     ba.cnt = ctx->d_cnt;
     DS_CUDA(ds::launch_bucket(ba, st, &ctx->prof), "bucket kernel");
 
@@ -416,7 +428,9 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     sa.hit_off = b->hit_off;
     sa.sx = sd->x; sa.sy = sd->y; sa.stx = sd->tx; sa.sty = sd->ty; sa.sqop = sd->qop; sa.schi2 = sd->chi2;
     sa.sorted = ctx->sorted;
+    sa.sx0 = ctx->sx0;
     sa.bins = ctx->bins;
+    sa.item_off = ctx->item_off;
     sa.trk_ws = ctx->trk_ws;
     sa.key_ws = ctx->key_ws;
     sa.hit_ws = ctx->hit_ws;
@@ -439,6 +453,8 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     ca.cnt = ctx->d_cnt;
     ds::ScatterTrkArgs xa{};
     xa.n_seeds = b->n_seeds;
+    xa.n_events = b->n_events;
+    xa.seed_off = b->seed_off;
     xa.trk_ws = ctx->trk_ws;
     xa.rank_ws = ctx->rank_ws;
     xa.trk_off = out->trk_off;

@@ -24,11 +24,16 @@ struct BucketArgs {
     DevGeom g;
     int n_events;
     int n_hits;
+    int n_seeds;
     const int32_t *hit_off;
+    const int32_t *seed_off;
     const float *x0, *ybeg, *yend;
     const uint8_t *layer;
     float4 *sorted;
+    float *sx0;
     uint16_t *bins;
+    int *item_cnt;         // per event: search chunks
+    int *item_off;         // [n_events + 1]
     DevCounters *cnt;
 };
 
@@ -42,7 +47,9 @@ struct SearchArgs {
     const int32_t *seed_off, *hit_off;
     const float *sx, *sy, *stx, *sty, *sqop, *schi2;
     const float4 *sorted;
+    const float *sx0;
     const uint16_t *bins;
+    const int *item_off;
     ds_track *trk_ws;
     unsigned long long *key_ws;
     int4 *hit_ws;
@@ -66,6 +73,8 @@ struct CloneArgs {
 
 struct ScatterTrkArgs {
     int n_seeds;
+    int n_events;
+    const int32_t *seed_off;
     const ds_track *trk_ws;
     const int *rank_ws;
     const int32_t *trk_off;
@@ -108,6 +117,7 @@ const char *fill_dev_nn(const ds_nn_weights *w, DevNN *out, int *n_h2_kernel);
 const char *fill_dev_params(const ds_params *p, DevParams *out);
 
 cudaError_t init_vertex_attributes();
+cudaError_t init_search_attributes();
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st, Prof *prof);
 cudaError_t launch_search(const SearchArgs &a, int n_in, int n_h2, cudaStream_t st, Prof *prof);
 cudaError_t launch_clone(const CloneArgs &a, const ScatterTrkArgs &sa, cudaStream_t st, Prof *prof);

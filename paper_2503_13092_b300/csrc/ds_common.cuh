@@ -4,7 +4,11 @@
 //   seeds     caller's SoA float32 (x, y, tx, ty, qop, chi2), CSR over events
 //   hits      caller's SoA (x0, ybeg, yend float32, layer u8), CSR over events
 //   sorted    float4 per hit {x0, ybeg, yend, id-bits}, grouped by event, then
-//             by (layer, Y sector, x bin): one 16-byte load per visited hit
+//             by (layer, Y sector, x bin): one 16-byte load per hit that passes
+//             a window's x test
+//   sx0       the same order, x0 only (4 bytes per hit): staged per event in
+//             shared memory for the window scans
+//   items     search work items: (event, chunk of <= 128 of its seeds)
 //   bins      uint16 offsets per event: (layer, sector, xbin) -> first sorted
 //             hit, relative to the event's first hit (<= 65535 hits per event)
 //   trk_ws    one 64-byte candidate-winner record per seed + its clone key
@@ -22,6 +26,9 @@ constexpr int kMaxSectors = 32;
 constexpr int kK1Max = 10;           // UTbX hits kept per seed (paper: up to 10)
 constexpr int kMaxEventHits = 65535; // uint16 offsets
 constexpr int kSearchThreads = 128;  // seeds per CTA in the search kernel
+constexpr int kStageHits = 5632;     // event x0 arrays up to this size are staged in shared memory
+constexpr int kBucketThreads = 512;
+constexpr int kBucketRegHits = 12;   // hits kept in registers per bucketing thread
 constexpr int kMaxVertexTracks = 4096; // tracks per event staged for vertexing
 constexpr unsigned long long kNoKey = ~0ull;
 
@@ -45,6 +52,7 @@ struct DevParams {
     float nn_threshold, doca_max, nr_tol, eps_par;
     float thr_logit;                 // ln(T / (1 - T)): response < T <=> logit < thr_logit
     int k1, origin, pick_chi2, clone_kill, training, nr_max_iter;
+    int fault_inject;                // tests only: bit 0 stalls the staging barrier
 };
 
 // Ghost-killer weights padded to the largest supported shape 16-32-32-1.
@@ -64,11 +72,11 @@ struct DevCounters {                 // device-side flag word and statistics
     unsigned int flags;
     unsigned int done_trk;           // last-block-done tickets
     unsigned int done_vtx;
+    unsigned int done_bkt;
     int n_tracks;
     int n_vertices;
     int pool_used;
     int vtx_queue[2];                // event queues of the two vertex launches
-    int pad0;
     unsigned long long n_candidates;
     unsigned long long n_pairs;
     unsigned long long n_pairs_fp64;
@@ -123,6 +131,53 @@ __device__ __forceinline__ unsigned long long pack_key(float k1, float k2)
 {
     return ((unsigned long long)ord_f32(k1) << 32) | ord_f32(k2);
 }
+
+// ---- bulk copies (TMA) into shared memory, completion on an mbarrier ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// dst, src 16-byte aligned; bytes a multiple of 16
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true when the phase completed, false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int limit)
+{
+    for (int i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+constexpr int kWaitLimit = 1 << 22;
 
 // Exclusive scan of one int per thread over the block; returns the prefix,
 // *total receives the block sum.  `scratch` holds >= 32 ints.  All threads call.

@@ -36,14 +36,17 @@ constexpr int kNATableStride = ((4 * kMaxSectors * kNXB + 1) + 7) & ~7;
 constexpr size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 constexpr size_t kOffCounters = 0;
 constexpr size_t kOffSorted = align256(sizeof(DevCounters));
-constexpr size_t kOffBins = kOffSorted + align256(sizeof(float4) * (size_t)kNAHits);
+constexpr size_t kOffSx0 = kOffSorted + align256(sizeof(float4) * (size_t)kNAHits);
+constexpr size_t kOffBins = kOffSx0 + align256(sizeof(float) * ((size_t)kNAHits + 4));
 constexpr size_t kOffTrk = kOffBins + align256(sizeof(uint16_t) * (size_t)kNATableStride * kNAEvents);
 constexpr size_t kOffKey = kOffTrk + align256(sizeof(ds_track) * (size_t)kNASeeds);
 constexpr size_t kOffHit = kOffKey + align256(sizeof(unsigned long long) * (size_t)kNASeeds);
 constexpr size_t kOffRank = kOffHit + align256(sizeof(int4) * (size_t)kNASeeds);
 constexpr size_t kOffCount = kOffRank + align256(sizeof(int) * (size_t)kNASeeds);
-constexpr size_t kScratchBytes = kOffCount + align256(sizeof(int) * (size_t)kNAEvents);
-static_assert(kScratchBytes <= 28u * 1024 * 1024, "scratch must stay modest");
+constexpr size_t kOffItemCnt = kOffCount + align256(sizeof(int) * (size_t)kNAEvents);
+constexpr size_t kOffItemOff = kOffItemCnt + align256(sizeof(int) * (size_t)kNAEvents);
+constexpr size_t kScratchBytes = kOffItemOff + align256(sizeof(int) * (size_t)(kNAEvents + 1));
+static_assert(kScratchBytes <= 32u * 1024 * 1024, "scratch must stay modest");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -63,6 +66,7 @@ ds_status scratch_address(int device, unsigned char **out)
     if (!g_scratch_dev[device]) {
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return DS_ERR_CUDA;
+        if (init_search_attributes() != cudaSuccess) return DS_ERR_CUDA;
         g_scratch_dev[device] = static_cast<unsigned char *>(ptr);
     }
     *out = g_scratch_dev[device];
@@ -111,10 +115,15 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         ba.g = g;
         ba.n_events = b->n_events;
         ba.n_hits = b->n_hits;
+        ba.n_seeds = b->n_seeds;
         ba.hit_off = b->hit_off;
+        ba.seed_off = b->seed_off;
         ba.x0 = ht->x0; ba.ybeg = ht->ybeg; ba.yend = ht->yend; ba.layer = ht->layer;
         ba.sorted = reinterpret_cast<float4 *>(base + kOffSorted);
+        ba.sx0 = reinterpret_cast<float *>(base + kOffSx0);
         ba.bins = reinterpret_cast<uint16_t *>(base + kOffBins);
+        ba.item_cnt = reinterpret_cast<int *>(base + kOffItemCnt);
+        ba.item_off = reinterpret_cast<int *>(base + kOffItemOff);
         ba.cnt = cnt;
         if (launch_bucket(ba, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
 
@@ -129,7 +138,9 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         sa.hit_off = b->hit_off;
         sa.sx = sd->x; sa.sy = sd->y; sa.stx = sd->tx; sa.sty = sd->ty; sa.sqop = sd->qop; sa.schi2 = sd->chi2;
         sa.sorted = ba.sorted;
+        sa.sx0 = ba.sx0;
         sa.bins = ba.bins;
+        sa.item_off = ba.item_off;
         sa.trk_ws = reinterpret_cast<ds_track *>(base + kOffTrk);
         sa.key_ws = reinterpret_cast<unsigned long long *>(base + kOffKey);
         sa.hit_ws = reinterpret_cast<int4 *>(base + kOffHit);
@@ -152,6 +163,8 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         ca.cnt = cnt;
         ScatterTrkArgs xa{};
         xa.n_seeds = b->n_seeds;
+        xa.n_events = b->n_events;
+        xa.seed_off = b->seed_off;
         xa.trk_ws = sa.trk_ws;
         xa.rank_ws = sa.rank_ws;
         xa.trk_off = out->trk_off;

@@ -17,13 +17,26 @@
 namespace ds {
 
 constexpr int kCloneThreads = 256;
-constexpr int kCloneSmem = 1536;
+constexpr int kCloneSmem = 1024;
+constexpr int kCloneHashBits = 10;
 
+
+__device__ __forceinline__ int clone_hash(int id) { return (int)(((unsigned)id * 2654435761u) >> (32 - kCloneHashBits)); }
+
+__device__ __forceinline__ bool kills(unsigned long long ko, int o, unsigned long long kb, int b, int4 ho, int4 hb)
+{
+    if (!(ko < kb || (ko == kb && o < b))) return false;
+    const int shared = (ho.x >= 0 && ho.x == hb.x) + (ho.y >= 0 && ho.y == hb.y) + (ho.z >= 0 && ho.z == hb.z) +
+                       (ho.w >= 0 && ho.w == hb.w);
+    return shared > 2;
+}
 
 __global__ void __launch_bounds__(kCloneThreads) k_clone(const __grid_constant__ CloneArgs a)
 {
     __shared__ unsigned long long s_key[kCloneSmem];
     __shared__ int4 s_hit[kCloneSmem];
+    __shared__ int s_next_bx[kCloneSmem], s_next_au[kCloneSmem];
+    __shared__ int s_head_bx[1 << kCloneHashBits], s_head_au[1 << kCloneHashBits];
     __shared__ int s_scan[32];
     __shared__ bool s_last;
     const int e = blockIdx.x;
@@ -33,14 +46,22 @@ __global__ void __launch_bounds__(kCloneThreads) k_clone(const __grid_constant__
     const bool in_smem = ns <= kCloneSmem;
     const unsigned long long *K = a.key_ws + s0;
     const int4 *Hh = a.hit_ws + s0;
-    if (in_smem) {
+    if (in_smem && a.clone_kill) {
+        // two winners sharing more than two of their hits share the UTbX hit or
+        // the UTaU hit: chain the winners by those two hits
+        for (int i = threadIdx.x; i < (1 << kCloneHashBits); i += blockDim.x) s_head_bx[i] = s_head_au[i] = -1;
+        __syncthreads();
         for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-            s_key[i] = K[i];
-            s_hit[i] = Hh[i];
+            const unsigned long long k = K[i];
+            const int4 h = Hh[i];
+            s_key[i] = k;
+            s_hit[i] = h;
+            if (k != kNoKey) {
+                s_next_bx[i] = atomicExch(&s_head_bx[clone_hash(h.w)], i);
+                s_next_au[i] = h.y >= 0 ? atomicExch(&s_head_au[clone_hash(h.y)], i) : -1;
+            }
         }
         __syncthreads();
-        K = s_key;
-        Hh = s_hit;
     }
 
     int base = 0;
@@ -48,21 +69,23 @@ __global__ void __launch_bounds__(kCloneThreads) k_clone(const __grid_constant__
         const int b = c0 + threadIdx.x;
         int alive = 0;
         if (b < ns) {
-            const unsigned long long kb = K[b];
+            const unsigned long long kb = in_smem ? s_key[b] : K[b];
             if (kb != kNoKey) {
                 alive = 1;
                 if (a.clone_kill) {
-                    const int4 hb = Hh[b];
-                    for (int o = 0; o < ns; ++o) {
-                        const unsigned long long ko = K[o];
-                        if (o == b || ko == kNoKey) continue;
-                        if (!(ko < kb || (ko == kb && o < b))) continue;
-                        const int4 ho = Hh[o];
-                        const int shared = (ho.x >= 0 && ho.x == hb.x) + (ho.y >= 0 && ho.y == hb.y) +
-                                           (ho.z >= 0 && ho.z == hb.z) + (ho.w >= 0 && ho.w == hb.w);
-                        if (shared > 2) {
-                            alive = 0;
-                            break;
+                    if (in_smem) {
+                        const int4 hb = s_hit[b];
+                        for (int o = s_head_bx[clone_hash(hb.w)]; o >= 0 && alive; o = s_next_bx[o])
+                            if (o != b && s_hit[o].w == hb.w && kills(s_key[o], o, kb, b, s_hit[o], hb)) alive = 0;
+                        if (hb.y >= 0)
+                            for (int o = s_head_au[clone_hash(hb.y)]; o >= 0 && alive; o = s_next_au[o])
+                                if (o != b && s_hit[o].y == hb.y && kills(s_key[o], o, kb, b, s_hit[o], hb))
+                                    alive = 0;
+                    } else {
+                        const int4 hb = Hh[b];
+                        for (int o = 0; o < ns && alive; ++o) {
+                            const unsigned long long ko = K[o];
+                            if (o != b && ko != kNoKey && kills(ko, o, kb, b, Hh[o], hb)) alive = 0;
                         }
                     }
                 }
@@ -106,7 +129,8 @@ __global__ void __launch_bounds__(kCloneThreads) k_clone(const __grid_constant__
 __global__ void __launch_bounds__(256) k_scatter_tracks(const __grid_constant__ ScatterTrkArgs a)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.n_seeds) return;
+    // seeds outside [seed_off[0], seed_off[E]) belong to no event (flagged)
+    if (s >= a.n_seeds || s < __ldg(a.seed_off) || s >= __ldg(a.seed_off + a.n_events)) return;
     const int r = __ldg(a.rank_ws + s);
     if (r < 0) return;
     const int4 *src = reinterpret_cast<const int4 *>(a.trk_ws + s);

@@ -53,12 +53,15 @@ __device__ __forceinline__ void topn_insert(float (&d)[N], int (&id)[N], int (&p
 
 // Hits of `layer` with |x0 - u| < w whose strip extent (+- dy) contains y,
 // ranked by (|dx|, id); the N best are kept.  Returns how many qualified.
+// The x test reads the staged x0 array (shared memory for events that fit).
+// Hits passing it are collected first and their 16-byte records (y extent,
+// id) loaded together, so a window costs one round trip to L2, not one per hit.
 template <int N>
-__device__ __forceinline__ int window_scan(const DevGeom &g, const float4 *__restrict__ H,
-                                           const uint16_t *__restrict__ Tb, int layer, float u,
-                                           float y, float w, float dy, float (&d)[N],
-                                           int (&id)[N], int (&p)[N])
+__device__ __forceinline__ int window_scan(const DevGeom &g, const float *X0, const float4 *__restrict__ H,
+                                           const uint16_t *Tb, int layer, float u, float y, float w, float dy,
+                                           float (&d)[N], int (&id)[N], int (&p)[N])
 {
+    constexpr int B = 4;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         d[k] = __int_as_float(0x7f800000);
@@ -69,23 +72,44 @@ __device__ __forceinline__ int window_scan(const DevGeom &g, const float4 *__res
     const float eps = 1e-3f;
     const int b0 = xbin_of(g, u - w - eps), b1 = xbin_of(g, u + w + eps);
     int cnt = 0;
+    int qi[B];
+    float qd[B];
+    int nq = 0;
+    auto flush = [&]() {
+        float4 h[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+            if (k < nq) h[k] = __ldg(H + qi[k]);
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+            if (k < nq && h[k].y - dy <= y && y <= h[k].z + dy) {
+                topn_insert<N>(d, id, p, qd[k], __float_as_int(h[k].w), qi[k]);
+                ++cnt;
+            }
+        nq = 0;
+    };
     for (int s = s_lo; s <= s_hi; ++s) {
         const int row = (layer * g.n_sec + s) * kNXB;
-        const int i0 = __ldg(Tb + row + b0), i1 = __ldg(Tb + row + b1 + 1);
+        const int i0 = Tb[row + b0], i1 = Tb[row + b1 + 1];
         for (int i = i0; i < i1; ++i) {
-            const float4 h = __ldg(H + i);
-            const float dx = fabsf(h.x - u);
-            if (dx < w && h.y - dy <= y && y <= h.z + dy) {
-                topn_insert<N>(d, id, p, dx, __float_as_int(h.w), i);
-                ++cnt;
+            const float dx = fabsf(X0[i] - u);
+            if (dx < w) {
+#pragma unroll
+                for (int k = 0; k < B; ++k)
+                    if (k == nq) {
+                        qi[k] = i;
+                        qd[k] = dx;
+                    }
+                if (++nq == B) flush();
             }
         }
     }
+    if (nq) flush();
     return cnt;
 }
 
 struct SeedCtx {     // per-seed quantities reused by candidate scoring
-    float zm, xm, ym, tx, ty, qop, chi2, w1;
+    float zm, xm, ym, tx, ty, qop, chi2, w1, u_bx;
     float yl[4];
 };
 
@@ -98,10 +122,10 @@ struct CandFit {
 // Weighted straight-line fit x = a + b (z - z_bX) in a frame centred on the
 // UTbX hit (keeps FP32 residuals small): one row per present hit (weight
 // 1/sigma_hit^2), one row for the magnet point (1/sigma_mag^2).
-__device__ __forceinline__ CandFit fit_candidate(const DevGeom &g, const SeedCtx &sc,
-                                                 const float4 *__restrict__ H, const int (&loc)[4])
+__device__ __forceinline__ CandFit fit_candidate(const DevGeom &g, const SeedCtx &sc, const float *X0,
+                                                 const int (&loc)[4])
 {
-    const float x0b = __ldg(H + loc[3]).x;
+    const float x0b = X0[loc[3]];
     const float xh = x0b + g.dxdy[3] * sc.yl[3];
     float Z[5], M[5], W[5];
     int n = 0;
@@ -111,7 +135,7 @@ __device__ __forceinline__ CandFit fit_candidate(const DevGeom &g, const SeedCtx
         W[l] = 0.f;
         M[l] = 0.f;
         if (loc[l] >= 0) {
-            const float x0 = l == 3 ? x0b : __ldg(H + loc[l]).x;
+            const float x0 = l == 3 ? x0b : X0[loc[l]];
             M[l] = (x0 - x0b) + (g.dxdy[l] * sc.yl[l] - g.dxdy[3] * sc.yl[3]);
             W[l] = g.w_hit;
             ++n;
@@ -196,39 +220,74 @@ __device__ __forceinline__ float mlp_logit_fp32(const DevNN &nn, const float (&p
 __device__ __forceinline__ float sigmoid_fast(float z) { return 1.f / (1.f + __expf(-z)); }
 
 template <int NIN, int NH1, int NH2>
-__global__ void __launch_bounds__(T) k_search(const __grid_constant__ SearchArgs a)
+__global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchArgs a)
 {
+    extern __shared__ __align__(16) unsigned char s_dyn[];   // bin table, then staged x0
     __shared__ uint16_t s_bx[kK1Max][T];
-    __shared__ float s_bxd[kK1Max][T];
     __shared__ uint16_t s_sel[kK1Max][5][T];
     __shared__ uint8_t s_nc[kK1Max][T];
-    __shared__ uint8_t s_nopt_v[kK1Max][T];
     __shared__ SeedCtx s_sc[T];
-    __shared__ int s_h0[T];
     __shared__ int s_base[T + 1];
     __shared__ unsigned long long s_best[T], s_cbest[T];
     __shared__ int s_bidx[T], s_cidx[T];
     __shared__ int s_scan[32];
+    __shared__ int s_item[4];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ int s_jbase[T + 1];
 
     const DevGeom &g = a.g;
     const DevParams &P = a.p;
     const int tid = threadIdx.x;
-    const int s = blockIdx.x * T + tid;
-    if (s < a.n_seeds) a.rank_ws[s] = -1;     // the clone kernel ranks this call's winners
-    if (s == 0 && (__ldg(a.seed_off) != 0 || __ldg(a.seed_off + a.n_events) != a.n_seeds))
-        raise_flag(a.cnt, DS_FLAG_BAD_OFFSETS);
+
+    // work item: chunk k of event e's seeds (sizes differ by at most one)
+    const int n_items = __ldg(a.item_off + a.n_events);
+    if ((int)blockIdx.x >= n_items) return;
+    if (tid == 0) {
+        const int e = find_segment(a.item_off, a.n_events, blockIdx.x);
+        const int k = blockIdx.x - __ldg(a.item_off + e), nc = __ldg(a.item_off + e + 1) - __ldg(a.item_off + e);
+        const int s0 = __ldg(a.seed_off + e), ns = __ldg(a.seed_off + e + 1) - s0;
+        s_item[0] = e;
+        s_item[1] = s0 + (int)(((long long)k * ns) / nc);
+        s_item[2] = s0 + (int)(((long long)(k + 1) * ns) / nc);
+    }
+    __syncthreads();
+    const int e = s_item[0];
+    const int s = s_item[1] + tid;
+    const bool active = s < s_item[2];
+    int h0 = __ldg(a.hit_off + e), h1 = __ldg(a.hit_off + e + 1);
+    if (h0 < 0 || h1 < h0 || h1 > a.n_hits || h1 - h0 > kMaxEventHits) h1 = h0 = 0;
+    const int nh = h1 - h0;
+    const float4 *H = a.sorted + h0;
+
+    // stage the event's bin table and (if it fits) its x0 array with two bulk
+    // copies (TMA); the x0 copy starts at the 16-byte boundary below h0
+    uint16_t *Tb = reinterpret_cast<uint16_t *>(s_dyn);
+    float *xs = reinterpret_cast<float *>(s_dyn + sizeof(uint16_t) * g.table_stride);
+    const bool staged = nh <= kStageHits;
+    const int lead = h0 & 3;
+    const float *X0 = staged ? xs + lead : a.sx0 + h0;
+    if (tid == 0) {
+        mbar_init(&s_bar, 1);
+        const uint32_t tb_bytes = sizeof(uint16_t) * g.table_stride;
+        const uint32_t x_bytes = staged ? (uint32_t)(((lead + nh) * 4 + 15) & ~15) : 0u;
+        // fault injection (tests): expect 16 bytes that never arrive
+        mbar_expect_tx(&s_bar, tb_bytes + x_bytes + ((P.fault_inject & 1) ? 16u : 0u));
+        bulk_copy_g2s(Tb, a.bins + (size_t)e * g.table_stride, tb_bytes, &s_bar);
+        if (x_bytes) bulk_copy_g2s(xs, a.sx0 + (h0 - lead), x_bytes, &s_bar);
+    }
+    if (active) a.rank_ws[s] = -1;     // the clone kernel ranks this call's winners
+    __syncthreads();
+    // bounded wait; the decision to go on is taken by the whole block
+    const int limit = P.fault_inject ? 1024 : kWaitLimit;
+    if (!__syncthreads_and(mbar_wait_bounded(&s_bar, 0, limit))) {
+        if (tid == 0) raise_flag(a.cnt, DS_FLAG_TIMEOUT);
+        return;   // the bulk copies themselves have completed or fail on their own; nothing else is in flight
+    }
 
     // ---------------------------------------------------------------- search
     int n_cand = 0;
     int nbx = 0;
-    if (s < a.n_seeds) {
-        const int e = find_segment(a.seed_off, a.n_events, s);
-        int h0 = __ldg(a.hit_off + e), h1 = __ldg(a.hit_off + e + 1);
-        if (h0 < 0 || h1 < h0 || h1 > a.n_hits || h1 - h0 > kMaxEventHits) h1 = h0 = 0;
-        s_h0[tid] = h0;
-        const float4 *H = a.sorted + h0;
-        const uint16_t *Tb = a.bins + (size_t)e * g.table_stride;
-
+    if (active) {
         SeedCtx sc;
         const float x = __ldg(a.sx + s), y = __ldg(a.sy + s);
         sc.tx = __ldg(a.stx + s);
@@ -247,48 +306,61 @@ __global__ void __launch_bounds__(T) k_search(const __grid_constant__ SearchArgs
                                                    sqrtf(fmaf(sc.tx, sc.tx, fmaf(sc.ty, sc.ty, 1.f)));
         const float u_bx = fmaf(tx_ut, g.z[3] - sc.zm, sc.xm) - g.dxdy[3] * sc.yl[3];
         sc.w1 = P.training ? 100.f : fmaf(P.w1b, aq, P.w1a);
-        const float w2 = P.training ? 10.f : P.w2;
+        sc.u_bx = u_bx;
         s_sc[tid] = sc;
 
         float d[kK1Max];
         int id[kK1Max], p[kK1Max];
-        const int q = window_scan<kK1Max>(g, H, Tb, 3, u_bx, sc.yl[3], sc.w1, P.dy_tol, d, id, p);
+        const int q = window_scan<kK1Max>(g, X0, H, Tb, 3, u_bx, sc.yl[3], sc.w1, P.dy_tol, d, id, p);
         nbx = min(q, P.k1);
 #pragma unroll
-        for (int j = 0; j < kK1Max; ++j) {
-            s_bx[j][tid] = (uint16_t)p[j];
-            s_bxd[j][tid] = d[j];
-        }
-        for (int j = 0; j < nbx; ++j) {
-            const float x0b = __ldg(H + s_bx[j][tid]).x;
-            const float xh = x0b + g.dxdy[3] * sc.yl[3];
-            const float txp = (xh - sc.xm) / (g.z[3] - sc.zm);
-            int sel[5];
-            {
-                float dd[1]; int ii[1], pp[1];
-                const float ul = fmaf(txp, g.z[0] - g.z[3], xh) - g.dxdy[0] * sc.yl[0];
-                const int c = window_scan<1>(g, H, Tb, 0, ul, sc.yl[0], w2, P.dy_tol, dd, ii, pp);
-                sel[0] = c > 0 ? pp[0] : -1;
-            }
-#pragma unroll
-            for (int l = 1; l <= 2; ++l) {
-                float dd[2]; int ii[2], pp[2];
-                const float ul = fmaf(txp, g.z[l] - g.z[3], xh) - g.dxdy[l] * sc.yl[l];
-                const int c = window_scan<2>(g, H, Tb, l, ul, sc.yl[l], w2, P.dy_tol, dd, ii, pp);
-                sel[2 * l - 1] = c > 0 ? pp[0] : -1;
-                sel[2 * l] = c > 1 ? pp[1] : -1;
-            }
-#pragma unroll
-            for (int k = 0; k < 5; ++k) s_sel[j][k][tid] = sel[k] >= 0 ? (uint16_t)sel[k] : kNone;
-            const int pa = sel[0] >= 0, pu = sel[1] >= 0, pv = sel[3] >= 0;
-            const int nu = sel[2] >= 0 ? 2 : 1, nv = sel[4] >= 0 ? 2 : 1;
-            const int valid = (1 + pa + pu + pv >= 3) && (pa || pu);
-            const int nc = valid ? nu * nv : 0;
-            s_nc[j][tid] = (uint8_t)nc;
-            s_nopt_v[j][tid] = (uint8_t)nv;
-            n_cand += nc;
-        }
+        for (int j = 0; j < kK1Max; ++j) s_bx[j][tid] = (uint16_t)p[j];
     }
+    int total_j;
+    const int jbase = block_exclusive_scan(nbx, s_scan, &total_j);
+    s_jbase[tid] = jbase;
+    if (tid == T - 1) s_jbase[T] = jbase + nbx;
+    __syncthreads();
+
+    // refined windows, one (seed, UTbX hit) pair per thread: every lane does
+    // the same three window searches whatever the hits per seed
+    for (int t = tid; t < total_j; t += T) {
+        int lo = 0, hi = T;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_jbase[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const int o = lo, j = t - s_jbase[o];
+        const SeedCtx sc = s_sc[o];
+        const float w2 = P.training ? 10.f : P.w2;
+        const float x0b = X0[s_bx[j][o]];
+        const float xh = x0b + g.dxdy[3] * sc.yl[3];
+        const float txp = (xh - sc.xm) / (g.z[3] - sc.zm);
+        int sel[5];
+        {
+            float dd[1]; int ii[1], pp[1];
+            const float ul = fmaf(txp, g.z[0] - g.z[3], xh) - g.dxdy[0] * sc.yl[0];
+            const int c = window_scan<1>(g, X0, H, Tb, 0, ul, sc.yl[0], w2, P.dy_tol, dd, ii, pp);
+            sel[0] = c > 0 ? pp[0] : -1;
+        }
+#pragma unroll
+        for (int l = 1; l <= 2; ++l) {
+            float dd[2]; int ii[2], pp[2];
+            const float ul = fmaf(txp, g.z[l] - g.z[3], xh) - g.dxdy[l] * sc.yl[l];
+            const int c = window_scan<2>(g, X0, H, Tb, l, ul, sc.yl[l], w2, P.dy_tol, dd, ii, pp);
+            sel[2 * l - 1] = c > 0 ? pp[0] : -1;
+            sel[2 * l] = c > 1 ? pp[1] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) s_sel[j][k][o] = sel[k] >= 0 ? (uint16_t)sel[k] : kNone;
+        const int pa = sel[0] >= 0, pu = sel[1] >= 0, pv = sel[3] >= 0;
+        const int nu = sel[2] >= 0 ? 2 : 1, nv = sel[4] >= 0 ? 2 : 1;
+        const int valid = (1 + pa + pu + pv >= 3) && (pa || pu);
+        s_nc[j][o] = (uint8_t)(valid ? nu * nv : 0);
+    }
+    __syncthreads();
+    for (int j = 0; j < nbx; ++j) n_cand += s_nc[j][tid];
     for (int j = nbx; j < kK1Max; ++j) s_nc[j][tid] = 0;
     s_best[tid] = kNoKey;
     s_bidx[tid] = 0x7fffffff;
@@ -301,7 +373,7 @@ __global__ void __launch_bounds__(T) k_search(const __grid_constant__ SearchArgs
     __syncthreads();
 
     // decode candidate c of the CTA: owner seed, UTbX rank j, stereo options
-    auto decode = [&](int c, int &o, int (&loc)[4], float &dxbx) {
+    auto decode = [&](int c, int &o, int (&loc)[4]) {
         int lo = 0, hi = T;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -315,7 +387,7 @@ __global__ void __launch_bounds__(T) k_search(const __grid_constant__ SearchArgs
             k -= s_nc[j][o];
             ++j;
         }
-        const int nv = s_nopt_v[j][o];
+        const int nv = s_sel[j][4][o] != kNone ? 2 : 1;
         const int iu = k / nv, iv = k - iu * nv;
         const uint16_t a0 = s_sel[j][0][o];
         const uint16_t u0 = s_sel[j][1 + iu][o];
@@ -324,58 +396,46 @@ __global__ void __launch_bounds__(T) k_search(const __grid_constant__ SearchArgs
         loc[1] = u0 == kNone ? -1 : u0;
         loc[2] = v0 == kNone ? -1 : v0;
         loc[3] = s_bx[j][o];
-        dxbx = s_bxd[j][o];
     };
 
     // ------------------------------------------------ score every candidate
+    // one candidate per thread per chunk of T; the body is not replicated
     const float thr = P.thr_logit;
-    for (int cb = 0; cb < total; cb += 4 * T) {
-        unsigned long long key[4];
-        int own[4];
+#pragma unroll 1
+    for (int cb = 0; cb < total; cb += T) {
+        const int c = cb + tid;
+        unsigned long long key = kNoKey;
+        int own = -1;
+        if (c < total) {
+            int loc[4];
+            decode(c, own, loc);
+            const SeedCtx sc = s_sc[own];
+            const CandFit f = fit_candidate(g, sc, X0, loc);
+            float phi[16];
+            phi[0] = f.xr * 1e-3f;
+            phi[1] = f.yr * 1e-3f;
+            phi[2] = f.t;
+            phi[3] = sc.ty;
+            phi[4] = 1e3f * f.qop;
+            phi[5] = f.chi2 / (float)f.ndof;
+            phi[6] = 1e3f * sc.qop;
+            phi[7] = sc.chi2;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int c = cb + r * T + tid;
-            own[r] = -1;
-            key[r] = kNoKey;
-            if (c < total) {
-                int o, loc[4];
-                float dxbx;
-                decode(c, o, loc, dxbx);
-                own[r] = o;
-                const SeedCtx sc = s_sc[o];
-                const float4 *H = a.sorted + s_h0[o];
-                const CandFit f = fit_candidate(g, sc, H, loc);
-                float phi[16];
-                phi[0] = f.xr * 1e-3f;
-                phi[1] = f.yr * 1e-3f;
-                phi[2] = f.t;
-                phi[3] = sc.ty;
-                phi[4] = 1e3f * f.qop;
-                phi[5] = f.chi2 / (float)f.ndof;
-                phi[6] = 1e3f * sc.qop;
-                phi[7] = sc.chi2;
-#pragma unroll
-                for (int l = 0; l < 4; ++l) phi[8 + l] = f.res[l] * g.inv_sigma_hit;
-                phi[12] = 0.25f * (float)f.nh;
-                phi[13] = dxbx / sc.w1;
-                phi[14] = sc.tx;
-                phi[15] = sc.ty;
-                const float lg = mlp_logit_fp32<NIN, NH1, NH2>(a.nn, phi);
-                if (P.pick_chi2) key[r] = pack_key(phi[5], lg);
-                else if (lg < thr) key[r] = pack_key(lg, f.chi2);
-            }
+            for (int l = 0; l < 4; ++l) phi[8 + l] = f.res[l] * g.inv_sigma_hit;
+            phi[12] = 0.25f * (float)f.nh;
+            phi[13] = fabsf(X0[loc[3]] - sc.u_bx) / sc.w1;
+            phi[14] = sc.tx;
+            phi[15] = sc.ty;
+            const float lg = mlp_logit_fp32<NIN, NH1, NH2>(a.nn, phi);
+            if (P.pick_chi2) key = pack_key(phi[5], lg);
+            else if (lg < thr) key = pack_key(lg, f.chi2);
         }
         s_cbest[tid] = kNoKey;
         s_cidx[tid] = 0x7fffffff;
         __syncthreads();
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-            if (own[r] >= 0 && key[r] != kNoKey) atomicMin(&s_cbest[own[r]], key[r]);
+        if (key != kNoKey) atomicMin(&s_cbest[own], key);
         __syncthreads();
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-            if (own[r] >= 0 && key[r] != kNoKey && key[r] == s_cbest[own[r]])
-                atomicMin(&s_cidx[own[r]], cb + r * T + tid);
+        if (key != kNoKey && key == s_cbest[own]) atomicMin(&s_cidx[own], c);
         __syncthreads();
         if (s_cbest[tid] < s_best[tid]) {
             s_best[tid] = s_cbest[tid];
@@ -385,9 +445,9 @@ __global__ void __launch_bounds__(T) k_search(const __grid_constant__ SearchArgs
     }
 
     // ------------------------------------------------------- write winners
-    if (s >= a.n_seeds) return;
+    if (!active) return;
     ds_track rec;
-    rec.event = find_segment(a.seed_off, a.n_events, s);
+    rec.event = e;
     rec.seed = s;
     rec.flags = 0;
     rec.n_candidates = n_cand;
@@ -399,11 +459,9 @@ __global__ void __launch_bounds__(T) k_search(const __grid_constant__ SearchArgs
     int4 hits = make_int4(-1, -1, -1, -1);
     if (have) {
         int o, loc[4];
-        float dxbx;
-        decode(s_bidx[tid], o, loc, dxbx);
+        decode(s_bidx[tid], o, loc);
         const SeedCtx sc = s_sc[o];
-        const float4 *H = a.sorted + s_h0[o];
-        const CandFit f = fit_candidate(g, sc, H, loc);
+        const CandFit f = fit_candidate(g, sc, X0, loc);
         int gid[4];
 #pragma unroll
         for (int l = 0; l < 4; ++l) gid[l] = loc[l] >= 0 ? __float_as_int(__ldg(H + loc[l]).w) : -1;
@@ -424,15 +482,29 @@ __global__ void __launch_bounds__(T) k_search(const __grid_constant__ SearchArgs
     a.hit_ws[s] = hits;
 }
 
+cudaError_t init_search_attributes()
+{
+    // shared memory, not L1, limits residency: ask for the largest carveout
+    const int smem = (int)(sizeof(uint16_t) * (((4 * kMaxSectors * kNXB + 1) + 7) & ~7) + sizeof(float) * (kStageHits + 4));
+    cudaError_t e = cudaFuncSetAttribute(k_search<16, 32, 32>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_search<8, 16, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_search<16, 32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_search<8, 16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
 cudaError_t launch_search(const SearchArgs &a, int n_in, int n_h2, cudaStream_t st, Prof *prof)
 {
     if (a.n_seeds <= 0) return cudaSuccess;
-    const int grid = (a.n_seeds + T - 1) / T;
+    // work items = chunks of <= T seeds of one event: at most S/T + E of them
+    const int grid = (a.n_seeds + T - 1) / T + a.n_events;
+    const size_t smem = sizeof(uint16_t) * a.g.table_stride + sizeof(float) * (kStageHits + 4);
     prof->begin("k_search", st);
     if (n_in <= 8 && n_h2 == 0)
-        k_search<8, 16, 0><<<grid, T, 0, st>>>(a);
+        k_search<8, 16, 0><<<grid, T, smem, st>>>(a);
     else
-        k_search<16, 32, 32><<<grid, T, 0, st>>>(a);
+        k_search<16, 32, 32><<<grid, T, smem, st>>>(a);
     prof->end(st);
     return cudaGetLastError();
 }

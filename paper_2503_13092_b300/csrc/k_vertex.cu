@@ -8,10 +8,10 @@
 // two straight lines; stop when both steps are below the tolerance; vertex =
 // midpoint of the two closest points; kept if DOCA < doca_max.
 //
-// FP32 solve, written with slope differences and cross products so that the
-// near-parallel cancellation happens in exact-ish differences rather than in
-// products of large numbers; pairs whose opening satisfies sin^2 < eps_par and
-// whose FP32 DOCA is near or below the cut are re-solved in FP64 (flag bit 0).
+// FP32 solve with error-free residuals and a two-float Newton iterate (below),
+// so its error stays at the float32 resolution of the output coordinates;
+// pairs whose opening satisfies sin^2 < eps_par and whose FP32 DOCA is near
+// or below the cut are re-solved in FP64 (flag bit 0).
 //
 // One CTA per event.  Tracks are staged in shared memory; opposite-charge
 // partner lists make every thread's pair valid, enumerated in (i, j) order.
@@ -25,6 +25,7 @@ namespace ds {
 
 constexpr int kVtxThreads = 256;
 constexpr int kVtxSmallCap = 512;
+constexpr int kVtxSeg = 8192;          // pairs per two-phase segment
 
 
 struct Trk {
@@ -36,7 +37,7 @@ struct PairOut {
     unsigned int flags;
 };
 
-__device__ PairOut solve_fp64(const DevGeom &g, const DevParams &P, const Trk &A, const Trk &B)
+__device__ __noinline__ PairOut solve_fp64(const DevGeom &g, const DevParams &P, const Trk &A, const Trk &B)
 {
     const double gi = -(double)g.mp * ((double)g.gamma0 + (double)g.gamma1 * (double)A.q);
     const double gj = -(double)g.mp * ((double)g.gamma0 + (double)g.gamma1 * (double)B.q);
@@ -92,32 +93,78 @@ __device__ PairOut solve_fp64(const DevGeom &g, const DevParams &P, const Trk &A
     return o;
 }
 
+// Error-free transformations (Knuth TwoSum, FMA TwoProduct).  The _rn
+// intrinsics keep the compiler from contracting or reassociating them.
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    const float t = __fadd_rn(a, b);
+    const float bb = __fsub_rn(t, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(t, bb)), __fsub_rn(b, bb));
+    return t;
+}
+
+__device__ __forceinline__ float two_prod(float a, float b, float &e)
+{
+    const float p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+    return p;
+}
+
+// Transverse residual T_i(u1) - T_j(u2) along one axis:
+//   w + dt*u2 + t_i*du + g_i*u1^2 - g_j*u2^2,
+// with w = a_i - a_j and dt = t_i - t_j carried as (value, rounding error) and
+// u = uh + ul.  The large terms cancel near the solution; they are summed
+// error-free so that only the small remainder is rounded.
+__device__ __forceinline__ float residual(float w, float we, float dt, float dte, float ti, float gi, float gj,
+                                          float u1h, float u1l, float u2h, float u2l, float du, bool curved)
+{
+    float pe, se;
+    const float p = two_prod(dt, u2h, pe);
+    float s = two_sum(w, p, se);
+    float lo = we + pe + se + dte * u2h + dt * u2l + ti * du;
+    if (curved) {
+        float a1e, g1e, a2e, g2e, te, t2e;
+        const float a1 = two_prod(gi, u1h, a1e), g1 = two_prod(a1, u1h, g1e);
+        const float a2 = two_prod(gj, u2h, a2e), g2 = two_prod(a2, u2h, g2e);
+        const float t = two_sum(s, g1, te);
+        s = two_sum(t, -g2, t2e);
+        lo += te + t2e + g1e - g2e + a1e * u1h - a2e * u2h + 2.f * a1 * u1l - 2.f * a2 * u2l;
+    }
+    return s + lo;
+}
+
+// FP32 solve.  The closest-approach parameters are carried as unevaluated
+// sums u = uh + ul (the Newton steps accumulate in ul), so they are not
+// limited to one float32 ulp of |z - z_ref|; residuals are error-free as
+// above; the Hessian uses cross products of slope differences.
 __device__ __forceinline__ PairOut solve_fp32(const DevGeom &g, const DevParams &P, const Trk &A,
                                               const Trk &B, float &sin2)
 {
     const float gi = -g.mp * fmaf(g.gamma1, A.q, g.gamma0);
     const float gj = -g.mp * fmaf(g.gamma1, B.q, g.gamma0);
+    const bool curved = gi != 0.f || gj != 0.f;
     const float txi = A.tx, tyi = A.ty, txj = B.tx, tyj = B.ty;
-    const float wx = A.x - B.x, wy = A.y - B.y;
-    const float dtx = txi - txj, dty = tyi - tyj;
+    float wxe, wye, dtxe, dtye;
+    const float wx = two_sum(A.x, -B.x, wxe), wy = two_sum(A.y, -B.y, wye);
+    const float dtx = two_sum(txi, -txj, dtxe), dty = two_sum(tyi, -tyj, dtye);
     const float a = fmaf(txi, txi, fmaf(tyi, tyi, 1.f)), c = fmaf(txj, txj, fmaf(tyj, tyj, 1.f));
     const float b = fmaf(txi, txj, fmaf(tyi, tyj, 1.f));
     const float cz = fmaf(txi, tyj, -tyi * txj);
     const float den = fmaf(dtx, dtx, fmaf(dty, dty, cz * cz));
     sin2 = den / (a * c);
     const float d = fmaf(txi, wx, tyi * wy), m = fmaf(dtx, wx, dty * wy);
-    float u1 = 0.f, u2 = 0.f;
+    float u1h = 0.f, u2h = 0.f, u1l = 0.f, u2l = 0.f;
     if (sin2 > 1e-12f) {
-        u1 = fmaf(fmaf(txj, dtx, tyj * dty), d, -b * m) / den;
-        u2 = fmaf(fmaf(txi, dtx, tyi * dty), d, -a * m) / den;
+        u1h = fmaf(fmaf(txj, dtx, tyj * dty), d, -b * m) / den;
+        u2h = fmaf(fmaf(txi, dtx, tyi * dty), d, -a * m) / den;
     }
     const float tol = fmaxf(P.nr_tol, 1e-3f);
     bool conv = false;
     for (int it = 0; it < P.nr_max_iter; ++it) {
-        const float du = u1 - u2;
-        const float pi = fmaf(2.f * gi, u1, txi), pj = fmaf(2.f * gj, u2, txj);
-        const float dx = fmaf(dtx, u2, wx) + fmaf(txi, du, fmaf(gi * u1, u1, -gj * u2 * u2));
-        const float dy = fmaf(dty, u2, wy) + tyi * du;
+        const float du = (u1h - u2h) + (u1l - u2l);
+        const float pi = fmaf(2.f * gi, u1h, txi), pj = fmaf(2.f * gj, u2h, txj);
+        const float dx = residual(wx, wxe, dtx, dtxe, txi, gi, gj, u1h, u1l, u2h, u2l, du, curved);
+        const float dy = residual(wy, wye, dty, dtye, tyi, 0.f, 0.f, u1h, u1l, u2h, u2l, du, false);
         const float dz = du;
         const float dPi = fmaf(dx, pi, fmaf(dy, tyi, dz)), dPj = fmaf(dx, pj, fmaf(dy, tyj, dz));
         const float ni = fmaf(pi, pi, fmaf(tyi, tyi, 1.f)), nj = fmaf(pj, pj, fmaf(tyj, tyj, 1.f));
@@ -130,23 +177,41 @@ __device__ __forceinline__ PairOut solve_fp32(const DevGeom &g, const DevParams 
         const float n1 = -fmaf(cx, jd_x, fmaf(cy, jd_y, cc * jd_z)) - 2.f * gj * dx * dPi;
         const float n2 = -fmaf(cx, id_x, fmaf(cy, id_y, cc * id_z)) - 2.f * gi * dx * dPj;
         const float s1 = -n1 / det, s2 = -n2 / det;
-        u1 += s1;
-        u2 += s2;
+        u1h = two_sum(u1h, u1l + s1, u1l);
+        u2h = two_sum(u2h, u2l + s2, u2l);
         if (fabsf(s1) < tol && fabsf(s2) < tol) {
             conv = true;
             break;
         }
     }
-    const float du = u1 - u2;
-    const float dx = fmaf(dtx, u2, wx) + fmaf(txi, du, fmaf(gi * u1, u1, -gj * u2 * u2));
-    const float dy = fmaf(dty, u2, wy) + tyi * du;
+    const float du = (u1h - u2h) + (u1l - u2l);
+    const float dx = residual(wx, wxe, dtx, dtxe, txi, gi, gj, u1h, u1l, u2h, u2l, du, curved);
+    const float dy = residual(wy, wye, dty, dtye, tyi, 0.f, 0.f, u1h, u1l, u2h, u2l, du, false);
     PairOut o;
-    const float x1 = A.x + fmaf(txi, u1, gi * u1 * u1), y1 = fmaf(tyi, u1, A.y);
+    const float x1 = fmaf(txi, u1h, A.x) + fmaf(txi, u1l, gi * u1h * u1h);
+    const float y1 = fmaf(tyi, u1h, A.y) + tyi * u1l;
     o.x = fmaf(-0.5f, dx, x1);
     o.y = fmaf(-0.5f, dy, y1);
-    o.z = fmaf(0.5f, u1 + u2, g.z_ref);
+    float se;
+    const float S = two_sum(u1h, u2h, se);
+    o.z = fmaf(0.5f, S, g.z_ref) + 0.5f * (se + (u1l + u2l));
     o.doca = sqrtf(fmaf(dx, dx, fmaf(dy, dy, du * du)));
     o.flags = conv ? 0u : 2u;
+    return o;
+}
+
+// One pair, FP32 with the FP64 re-solve for near-parallel pairs near or below
+// the cut.  Not inlined: both phases must run the very same code.
+__device__ __noinline__ PairOut solve_pair(const DevGeom &g, const DevParams &P, const Trk &A, const Trk &B,
+                                           int &used_fp64)
+{
+    float sin2;
+    PairOut o = solve_fp32(g, P, A, B, sin2);
+    used_fp64 = 0;
+    if (sin2 < P.eps_par && o.doca < P.doca_max + 0.05f) {
+        o = solve_fp64(g, P, A, B);
+        used_fp64 = 1;
+    }
     return o;
 }
 
@@ -163,11 +228,13 @@ __device__ __forceinline__ int lower_bound_u16(const uint16_t *list, int n, int 
 }
 
 template <int CAP, bool LARGE>
-__global__ void __launch_bounds__(kVtxThreads) k_vertex(const __grid_constant__ VertexArgs a)
+__global__ void __launch_bounds__(kVtxThreads, 3) k_vertex(const __grid_constant__ VertexArgs a)
 {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ int s_scan[32];
     __shared__ int s_pool_base;
+    __shared__ unsigned s_mask[kVtxSeg / 32];
+    __shared__ int s_wbase[kVtxSeg / 32];
     __shared__ bool s_last;
     Trk *s_trk = reinterpret_cast<Trk *>(s_dyn);
     uint16_t *s_pos = reinterpret_cast<uint16_t *>(s_trk + CAP);
@@ -238,55 +305,80 @@ __global__ void __launch_bounds__(kVtxThreads) k_vertex(const __grid_constant__ 
         __syncthreads();
         const int npairs = run;
         if (threadIdx.x == 0 && npairs > 0) atomicAdd(&a.cnt->n_pairs, (unsigned long long)npairs);
+        // pair p of the event -> (i, j), i < j, opposite charges, (i, j) order
+        auto pair_of = [&](int p, int &i, int &j) {
+            int lo = 0, hi = nt;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_row[mid] <= p) lo = mid;
+                else hi = mid;
+            }
+            i = lo;
+            const uint16_t *opp = s_trk[i].q > 0.f ? s_neg : s_pos;
+            j = opp[s_start[i] + (p - s_row[i])];
+        };
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
         int n64 = 0;
-        for (int c0 = 0; c0 < npairs; c0 += blockDim.x) {
-            const int p = c0 + threadIdx.x;
-            int keep = 0, i = 0, j = 0;
-            PairOut o;
-            if (p < npairs) {
-                int lo = 0, hi = nt;
+        for (int seg0 = 0; seg0 < npairs; seg0 += kVtxSeg) {
+            const int nseg = min(kVtxSeg, npairs - seg0);
+            const int nwords = (nseg + 31) >> 5;
+            // phase 1: solve every pair of the segment, one per lane; keep bits by ballot
+            for (int w = warp; w < nwords; w += nwarps) {
+                const int p = seg0 + (w << 5) + lane;
+                int keep = 0;
+                if (p < seg0 + nseg) {
+                    int i, j, f64;
+                    pair_of(p, i, j);
+                    const PairOut o = solve_pair(g, P, s_trk[i], s_trk[j], f64);
+                    n64 += f64;
+                    keep = o.doca < P.doca_max;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (lane == 0) s_mask[w] = m;
+            }
+            __syncthreads();
+            // ranks of the kept pairs: one scan over the segment's mask words
+            int tot = 0;
+            for (int w0 = 0; w0 < nwords; w0 += blockDim.x) {
+                const int w = w0 + threadIdx.x;
+                const int c = w < nwords ? __popc(s_mask[w]) : 0;
+                int t;
+                const int r = block_exclusive_scan(c, s_scan, &t);
+                if (w < nwords) s_wbase[w] = tot + r;
+                tot += t;
+            }
+            if (threadIdx.x == 0 && tot > 0) s_pool_base = atomicAdd(&a.cnt->pool_used, tot);
+            __syncthreads();
+            // phase 2: re-solve only the kept pairs and write them in (i, j) order
+            for (int k = threadIdx.x; k < tot; k += blockDim.x) {
+                int lo = 0, hi = nwords;
                 while (hi - lo > 1) {
                     const int mid = (lo + hi) >> 1;
-                    if (s_row[mid] <= p) lo = mid;
+                    if (s_wbase[mid] <= k) lo = mid;
                     else hi = mid;
                 }
-                i = lo;
-                const Trk A = s_trk[i];
-                const uint16_t *opp = A.q > 0.f ? s_neg : s_pos;
-                j = opp[s_start[i] + (p - s_row[i])];
-                const Trk B = s_trk[j];
-                float sin2;
-                o = solve_fp32(g, P, A, B, sin2);
-                if (sin2 < P.eps_par && o.doca < P.doca_max + 0.05f) {
-                    o = solve_fp64(g, P, A, B);
-                    ++n64;
+                const int bit = __fns(s_mask[lo], 0, k - s_wbase[lo] + 1);
+                const int p = seg0 + (lo << 5) + bit;
+                int i, j, f64;
+                pair_of(p, i, j);
+                const PairOut o = solve_pair(g, P, s_trk[i], s_trk[j], f64);
+                const int slot = s_pool_base + k;
+                if (slot < a.pool_cap) {
+                    ds_vertex_rec v;
+                    v.event = e;
+                    v.i = t0 + i;
+                    v.j = t0 + j;
+                    v.x = o.x; v.y = o.y; v.z = o.z;
+                    v.doca = o.doca;
+                    v.flags = o.flags;
+                    a.pool[slot] = v;
+                    a.pool_pos[slot] = ev_count + k;
+                } else {
+                    raise_flag(a.cnt, DS_FLAG_VERTEX_CAPACITY);
                 }
-                keep = o.doca < P.doca_max;
-            }
-            int tot;
-            const int r = block_exclusive_scan(keep, s_scan, &tot);
-            if (tot > 0) {
-                if (threadIdx.x == 0) s_pool_base = atomicAdd(&a.cnt->pool_used, tot);
-                __syncthreads();
-                const int slot = s_pool_base + r;
-                if (keep) {
-                    if (slot < a.pool_cap) {
-                        ds_vertex_rec v;
-                        v.event = e;
-                        v.i = t0 + i;
-                        v.j = t0 + j;
-                        v.x = o.x; v.y = o.y; v.z = o.z;
-                        v.doca = o.doca;
-                        v.flags = o.flags;
-                        a.pool[slot] = v;
-                        a.pool_pos[slot] = ev_count + r;
-                    } else {
-                        raise_flag(a.cnt, DS_FLAG_VERTEX_CAPACITY);
-                    }
-                }
-                __syncthreads();
             }
             ev_count += tot;
+            __syncthreads();
         }
         if (n64) atomicAdd(&a.cnt->n_pairs_fp64, (unsigned long long)n64);
     }

@@ -47,7 +47,7 @@ class ds_params(C.Structure):
                 ("nn_threshold", C.c_double), ("doca_max", C.c_double), ("nr_tol", C.c_double),
                 ("eps_parallel", C.c_double), ("k1", C.c_int32), ("first_window_origin", C.c_int32),
                 ("pick_chi2", C.c_int32), ("clone_kill", C.c_int32), ("training", C.c_int32),
-                ("nr_max_iter", C.c_int32), ("mlp_precision", C.c_int32), ("reserved0", C.c_int32)]
+                ("nr_max_iter", C.c_int32), ("mlp_precision", C.c_int32), ("fault_inject", C.c_int32)]
 
 
 class ds_event_batch(C.Structure):

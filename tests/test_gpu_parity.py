@@ -236,3 +236,22 @@ def test_malformed_input_is_flagged(torch_cuda, weights):
     # flags are cleared by the read: a clean batch afterwards is clean
     g = d.run(b)
     assert g["stats"]["status"] == 0
+
+
+def test_bounded_wait_reports_timeout(torch_cuda, weights):
+    """Failure detection without a GPU fault: the staging wait is made to run
+    out (its barrier expects bytes nothing sends); the kernel gives up after a
+    bounded number of polls, flags DS_FLAG_TIMEOUT, and the context stays usable."""
+    from paper_2503_13092_b300 import ds
+    b = synth.config_batch("c2", n_events=4)
+    cfg = synth.default_config()
+    d = make(torch_cuda, cfg, weights)
+    d.set_params(fault_inject=1)
+    dev = d.to_device(b)
+    out = d.alloc_tracks(b["n_events"], int(b["seed_off"][-1]))
+    d.reconstruct(dev, out)
+    st = d.sync(raise_on_error=False)
+    assert st["status"] == ds.DS_ERR_TIMEOUT and st["device_flags"] & ds.DS_FLAG_TIMEOUT
+    d.set_params(fault_inject=0)
+    g = d.run(b)
+    assert g["stats"]["status"] == 0 and g["n_tracks"] > 0
