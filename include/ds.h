@@ -68,7 +68,9 @@ enum {
     DS_FLAG_TRACK_CAPACITY = 1u << 4,  /* more tracks than ds_tracks.capacity (truncated) */
     DS_FLAG_VERTEX_CAPACITY = 1u << 5, /* more vertices than capacity, or an event with more
                                           than 4096 tracks (only its first 4096 are paired) */
-    DS_FLAG_TIMEOUT = 1u << 6          /* a bounded device-side wait ran out */
+    DS_FLAG_TIMEOUT = 1u << 6,         /* a bounded device-side wait ran out */
+    DS_FLAG_CAND_CAPACITY = 1u << 7    /* candidate buffer full (ds_params.cand_per_seed x
+                                          seeds); the seeds concerned got no track */
 };
 
 /* Geometry of the UT and of the magnet kink model (Algorithm Design section,
@@ -129,6 +131,10 @@ typedef struct {
                               search kernel's bounded wait for its staged data run out, so
                               the call reports DS_ERR_TIMEOUT (flag DS_FLAG_TIMEOUT) and
                               produces no tracks; no GPU fault is involved. */
+    int32_t cand_per_seed; /* candidate buffer size per seed on average (default 16, max
+                              40 = 10 x 1 x 2 x 2; training mode always uses 40); exceeding
+                              it raises DS_FLAG_CAND_CAPACITY */
+    int32_t reserved1;
 } ds_params;
 
 /* One event batch (CSR over events).  Device pointers. */
@@ -274,10 +280,10 @@ DS_API ds_status ds_sync_status(ds_ctx *ctx, void *stream, ds_stats *stats);
  * deployment variant of the same computation.  Runs the same kernels as
  * ds_reconstruct on the CURRENT device and stream, taking geometry, parameters
  * and weights as host structs, with every scratch buffer inside one static
- * device array of about 31 MB that each GPU loading the library holds until
+ * device array of about 28 MB that each GPU loading the library holds until
  * process exit.  It calls no cudaMalloc/cudaFree.  Limits per call: at most
- * 256 events, 65536 seeds and 1048576 hits (DS_ERR_CAPACITY beyond, nothing
- * launched).  The first call on a device looks up the array's device address
+ * 256 events, 16384 seeds and 327680 hits (DS_ERR_CAPACITY beyond, nothing
+ * launched) and 8 candidates per seed on average (DS_FLAG_CAND_CAPACITY).  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the array: calls that overlap on the GPU race and must be
  * serialised by the caller.  Outputs as ds_reconstruct; if d_flags (device

@@ -30,6 +30,12 @@ struct ds_ctx {
     unsigned long long *key_ws = nullptr;
     int4 *hit_ws = nullptr;
     int *rank_ws = nullptr;
+    float4 *cand_feat = nullptr;
+    ds::CandMeta *cand_meta = nullptr;
+    float *cand_logit = nullptr;
+    int4 *seed_cand = nullptr;
+    int cap_cand = 0;
+    int cand_per_seed = 16;
     int *count_trk = nullptr;
     int *count_vtx = nullptr;
     ds_vertex_rec *pool = nullptr;
@@ -109,7 +115,9 @@ bool stream_capturing(cudaStream_t st)
 
 ds_status ensure_workspace(ds_ctx *ctx, int E, int S, int H, cudaStream_t st)
 {
-    if (E <= ctx->cap_events && S <= ctx->cap_seeds && H <= ctx->cap_hits) return DS_OK;
+    if (E <= ctx->cap_events && S <= ctx->cap_seeds && H <= ctx->cap_hits &&
+        (long long)S * ctx->cand_per_seed <= ctx->cap_cand)
+        return DS_OK;
     if (stream_capturing(st))
         return fail(ctx, DS_ERR_ARG, "workspace too small during stream capture; call ds_reserve first");
     return ds_reserve(ctx, E, S, H);
@@ -203,6 +211,7 @@ const char *fill_dev_params(const ds_params *p, DevParams *out)
         return "window, tolerance or limit not positive";
     if (p->mlp_precision != DS_MLP_FP32 && p->mlp_precision != DS_MLP_BF16 && p->mlp_precision != DS_MLP_FP8)
         return "unknown mlp_precision";
+    if (p->cand_per_seed < 1 || p->cand_per_seed > 40) return "cand_per_seed outside 1..40";
     DevParams &d = *out;
     d.w1a = (float)p->w1a;
     d.w1b = (float)p->w1b;
@@ -268,6 +277,7 @@ ds_status ds_default_params(ds_params *p)
     p->training = 0;
     p->nr_max_iter = 10;
     p->mlp_precision = DS_MLP_FP32;
+    p->cand_per_seed = 16;
     return DS_OK;
 }
 
@@ -303,7 +313,8 @@ void ds_destroy(ds_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    void *ptrs[] = {ctx->d_cnt, ctx->sorted, ctx->sx0, ctx->item_cnt, ctx->item_off, ctx->bins, ctx->trk_ws, ctx->key_ws, ctx->hit_ws,
+    void *ptrs[] = {ctx->d_cnt, ctx->sorted, ctx->sx0, ctx->item_cnt, ctx->item_off, ctx->bins, ctx->cand_feat,
+                    ctx->cand_meta, ctx->cand_logit, ctx->seed_cand, ctx->trk_ws, ctx->key_ws, ctx->hit_ws,
                     ctx->rank_ws, ctx->count_trk, ctx->count_vtx, ctx->pool, ctx->pool_pos,
                     ctx->h.seed_off, ctx->h.hit_off, ctx->h.seed_cols, ctx->h.hit_cols, ctx->h.layer,
                     ctx->h.tracks, ctx->h.trk_off, ctx->h.vtx_off, ctx->h.counts, ctx->h.vertices};
@@ -341,6 +352,8 @@ ds_status ds_set_params(ds_ctx *ctx, const ds_params *p)
     const char *why = ds::fill_dev_params(p, &ctx->p);
     if (why) return fail(ctx, DS_ERR_ARG, why);
     ctx->mlp_precision = p->mlp_precision;
+    // training mode (100/10 mm windows) can give every seed the maximum of 10 x 1 x 2 x 2
+    ctx->cand_per_seed = p->training ? 40 : p->cand_per_seed;
     return DS_OK;
 }
 
@@ -360,7 +373,17 @@ ds_status ds_reserve(ds_ctx *ctx, int32_t E, int32_t S, int32_t H)
         if ((st = grow(ctx, &ctx->item_off, (size_t)E + 1)) != DS_OK) return st;
         ctx->cap_events = E;
     }
+    const long long want_cand = (long long)(S > ctx->cap_seeds ? S : ctx->cap_seeds) * ctx->cand_per_seed;
+    if (want_cand > ctx->cap_cand) {
+        if (want_cand > 0x7fffffffLL / 4) return fail(ctx, DS_ERR_ARG, "candidate buffer too large");
+        const size_t n = (size_t)want_cand;
+        if ((st = grow(ctx, &ctx->cand_feat, 4 * n)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->cand_meta, n)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->cand_logit, n)) != DS_OK) return st;
+        ctx->cap_cand = (int)n;
+    }
     if (S > ctx->cap_seeds) {
+        if ((st = grow(ctx, &ctx->seed_cand, (size_t)S)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->trk_ws, (size_t)S)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->key_ws, (size_t)S)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->hit_ws, (size_t)S)) != DS_OK) return st;
@@ -397,6 +420,7 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     if (s != DS_OK) return s;
     out->n_events = b->n_events;
     if (b->n_events == 0) return DS_OK;
+    DS_CUDA(cudaMemsetAsync(&ctx->d_cnt->cand_used, 0, sizeof(int), st), "memset");
 
     ds::BucketArgs ba{};
     ba.g = ctx->g;
@@ -420,7 +444,6 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     ds::SearchArgs sa{};
     sa.g = ctx->g;
     sa.p = ctx->p;
-    sa.nn = ctx->nn;
     sa.n_events = b->n_events;
     sa.n_seeds = b->n_seeds;
     sa.n_hits = b->n_hits;
@@ -431,12 +454,34 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     sa.sx0 = ctx->sx0;
     sa.bins = ctx->bins;
     sa.item_off = ctx->item_off;
-    sa.trk_ws = ctx->trk_ws;
-    sa.key_ws = ctx->key_ws;
-    sa.hit_ws = ctx->hit_ws;
+    sa.cand_feat = ctx->cand_feat;
+    sa.cand_meta = ctx->cand_meta;
+    sa.cand_cap = ctx->cap_cand;
+    sa.seed_cand = ctx->seed_cand;
     sa.rank_ws = ctx->rank_ws;
     sa.cnt = ctx->d_cnt;
-    DS_CUDA(ds::launch_search(sa, ctx->nn_in, ctx->nn_h2, st, &ctx->prof), "search kernel");
+    DS_CUDA(ds::launch_search(sa, st, &ctx->prof), "search kernel");
+
+    ds::MlpArgs ma{};
+    ma.nn = ctx->nn;
+    ma.n_in = ctx->nn_in;
+    ma.n_h2 = ctx->nn_h2;
+    ma.feat = ctx->cand_feat;
+    ma.logit = ctx->cand_logit;
+    ma.cand_cap = ctx->cap_cand;
+    ma.cnt = ctx->d_cnt;
+    ds::PickArgs pa{};
+    pa.p = ctx->p;
+    pa.n_seeds = b->n_seeds;
+    pa.n_events = b->n_events;
+    pa.seed_off = b->seed_off;
+    pa.seed_cand = ctx->seed_cand;
+    pa.logit = ctx->cand_logit;
+    pa.meta = ctx->cand_meta;
+    pa.trk_ws = ctx->trk_ws;
+    pa.key_ws = ctx->key_ws;
+    pa.hit_ws = ctx->hit_ws;
+    DS_CUDA(ds::launch_mlp_pick(ma, pa, ctx->sm_count, st, &ctx->prof), "network kernel");
 
     ds::CloneArgs ca{};
     ca.n_events = b->n_events;
@@ -541,7 +586,7 @@ ds_status ds_sync_status(ds_ctx *ctx, void *stream, ds_stats *stats)
         std::snprintf(buf, sizeof(buf), "device flags 0x%x", c.flags);
         return fail(ctx, DS_ERR_DEVICE_FLAG, buf);
     }
-    if (c.flags & (DS_FLAG_TRACK_CAPACITY | DS_FLAG_VERTEX_CAPACITY))
+    if (c.flags & (DS_FLAG_TRACK_CAPACITY | DS_FLAG_VERTEX_CAPACITY | DS_FLAG_CAND_CAPACITY))
         return fail(ctx, DS_ERR_CAPACITY, "output capacity exceeded");
     return DS_OK;
 }

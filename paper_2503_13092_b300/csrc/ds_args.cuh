@@ -40,7 +40,6 @@ struct BucketArgs {
 struct SearchArgs {
     DevGeom g;
     DevParams p;
-    DevNN nn;
     int n_events;
     int n_seeds;
     int n_hits;
@@ -50,11 +49,33 @@ struct SearchArgs {
     const float *sx0;
     const uint16_t *bins;
     const int *item_off;
+    float4 *cand_feat;     // [cand_cap][4]: the 16 network inputs
+    CandMeta *cand_meta;   // [cand_cap]
+    int cand_cap;
+    int4 *seed_cand;       // per seed: first candidate, count, event
+    int *rank_ws;
+    DevCounters *cnt;
+};
+
+struct MlpArgs {
+    DevNN nn;
+    int n_in, n_h2;
+    const float4 *feat;
+    float *logit;
+    int cand_cap;
+    const DevCounters *cnt;
+};
+
+struct PickArgs {
+    DevParams p;
+    int n_seeds, n_events;
+    const int32_t *seed_off;
+    const int4 *seed_cand;
+    const float *logit;
+    const CandMeta *meta;
     ds_track *trk_ws;
     unsigned long long *key_ws;
     int4 *hit_ws;
-    int *rank_ws;
-    DevCounters *cnt;
 };
 
 struct CloneArgs {
@@ -119,7 +140,8 @@ const char *fill_dev_params(const ds_params *p, DevParams *out);
 cudaError_t init_vertex_attributes();
 cudaError_t init_search_attributes();
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st, Prof *prof);
-cudaError_t launch_search(const SearchArgs &a, int n_in, int n_h2, cudaStream_t st, Prof *prof);
+cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof);
+cudaError_t launch_mlp_pick(const MlpArgs &m, const PickArgs &p, int sm_count, cudaStream_t st, Prof *prof);
 cudaError_t launch_clone(const CloneArgs &a, const ScatterTrkArgs &sa, cudaStream_t st, Prof *prof);
 cudaError_t launch_vertex(const VertexArgs &a, const ScatterVtxArgs &sa, int sm_count, cudaStream_t st,
                           Prof *prof);

@@ -77,10 +77,23 @@ struct DevCounters {                 // device-side flag word and statistics
     int n_vertices;
     int pool_used;
     int vtx_queue[2];                // event queues of the two vertex launches
+    int cand_used;                   // candidates written this call
+    int pad1;
     unsigned long long n_candidates;
     unsigned long long n_pairs;
     unsigned long long n_pairs_fp64;
 };
+
+// A candidate's fit, seed and hits (the network inputs are stored beside it).
+struct __align__(16) CandMeta {
+    float xr, yr, t, qop;
+    float chi2;
+    int ndof;
+    int seed;
+    float ty;
+    int hit[4];                      // global hit ids, -1 = absent
+};
+static_assert(sizeof(CandMeta) == 48, "CandMeta is 48 bytes");
 
 // Per-seed winner record in the workspace (same 64-byte layout as ds_track).
 static_assert(sizeof(ds_track) == 64, "ds_track must be 64 bytes");

@@ -29,8 +29,10 @@ namespace {
 
 // Size limits of one call.
 constexpr int kNAEvents = 256;
-constexpr int kNASeeds = 65536;
-constexpr int kNAHits = 1 << 20;
+constexpr int kNASeeds = 16384;
+constexpr int kNAHits = 327680;
+constexpr int kNACandPerSeed = 8;
+constexpr int kNACand = kNASeeds * kNACandPerSeed;
 constexpr int kNATableStride = ((4 * kMaxSectors * kNXB + 1) + 7) & ~7;
 
 constexpr size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
@@ -42,10 +44,14 @@ constexpr size_t kOffTrk = kOffBins + align256(sizeof(uint16_t) * (size_t)kNATab
 constexpr size_t kOffKey = kOffTrk + align256(sizeof(ds_track) * (size_t)kNASeeds);
 constexpr size_t kOffHit = kOffKey + align256(sizeof(unsigned long long) * (size_t)kNASeeds);
 constexpr size_t kOffRank = kOffHit + align256(sizeof(int4) * (size_t)kNASeeds);
-constexpr size_t kOffCount = kOffRank + align256(sizeof(int) * (size_t)kNASeeds);
+constexpr size_t kOffSeedCand = kOffRank + align256(sizeof(int) * (size_t)kNASeeds);
+constexpr size_t kOffCount = kOffSeedCand + align256(sizeof(int4) * (size_t)kNASeeds);
 constexpr size_t kOffItemCnt = kOffCount + align256(sizeof(int) * (size_t)kNAEvents);
 constexpr size_t kOffItemOff = kOffItemCnt + align256(sizeof(int) * (size_t)kNAEvents);
-constexpr size_t kScratchBytes = kOffItemOff + align256(sizeof(int) * (size_t)(kNAEvents + 1));
+constexpr size_t kOffCandFeat = kOffItemOff + align256(sizeof(int) * (size_t)(kNAEvents + 1));
+constexpr size_t kOffCandMeta = kOffCandFeat + align256(sizeof(float4) * 4 * (size_t)kNACand);
+constexpr size_t kOffCandLogit = kOffCandMeta + align256(sizeof(CandMeta) * (size_t)kNACand);
+constexpr size_t kScratchBytes = kOffCandLogit + align256(sizeof(float) * (size_t)kNACand);
 static_assert(kScratchBytes <= 32u * 1024 * 1024, "scratch must stay modest");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -85,6 +91,7 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
     if (!geom || !params || !weights || !b || !sd || !ht || !out) return DS_ERR_ARG;
     if (b->n_events < 0 || b->n_seeds < 0 || b->n_hits < 0 || out->capacity < 0) return DS_ERR_ARG;
     if (b->n_events > kNAEvents || b->n_seeds > kNASeeds || b->n_hits > kNAHits) return DS_ERR_CAPACITY;
+    // candidates are limited to kNACandPerSeed per seed on average (DS_FLAG_CAND_CAPACITY beyond)
     if (b->n_events > 0 && (!b->seed_off || !b->hit_off || !out->trk_off || !out->n_tracks)) return DS_ERR_ARG;
     if (b->n_seeds > 0 && (!sd->x || !sd->y || !sd->tx || !sd->ty || !sd->qop || !sd->chi2)) return DS_ERR_ARG;
     if (b->n_hits > 0 && (!ht->x0 || !ht->ybeg || !ht->yend || !ht->layer)) return DS_ERR_ARG;
@@ -98,8 +105,9 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
     if (fill_dev_geom(geom, &g) || fill_dev_params(params, &p) || fill_dev_nn(weights, &nn, &nn_h2))
         return DS_ERR_ARG;
 
-    int device = 0;
+    int device = 0, sm_count = 148;
     if (cudaGetDevice(&device) != cudaSuccess) return DS_ERR_CUDA;
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device);
     unsigned char *base = nullptr;
     ds_status st = scratch_address(device, &base);
     if (st != DS_OK) return st;
@@ -130,7 +138,6 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         SearchArgs sa{};
         sa.g = g;
         sa.p = p;
-        sa.nn = nn;
         sa.n_events = b->n_events;
         sa.n_seeds = b->n_seeds;
         sa.n_hits = b->n_hits;
@@ -141,20 +148,42 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         sa.sx0 = ba.sx0;
         sa.bins = ba.bins;
         sa.item_off = ba.item_off;
-        sa.trk_ws = reinterpret_cast<ds_track *>(base + kOffTrk);
-        sa.key_ws = reinterpret_cast<unsigned long long *>(base + kOffKey);
-        sa.hit_ws = reinterpret_cast<int4 *>(base + kOffHit);
+        sa.cand_feat = reinterpret_cast<float4 *>(base + kOffCandFeat);
+        sa.cand_meta = reinterpret_cast<CandMeta *>(base + kOffCandMeta);
+        sa.cand_cap = kNACand;
+        sa.seed_cand = reinterpret_cast<int4 *>(base + kOffSeedCand);
         sa.rank_ws = reinterpret_cast<int *>(base + kOffRank);
         sa.cnt = cnt;
-        if (launch_search(sa, weights->n_in, nn_h2, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
+        if (launch_search(sa, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
+
+        MlpArgs ma{};
+        ma.nn = nn;
+        ma.n_in = weights->n_in;
+        ma.n_h2 = nn_h2;
+        ma.feat = sa.cand_feat;
+        ma.logit = reinterpret_cast<float *>(base + kOffCandLogit);
+        ma.cand_cap = kNACand;
+        ma.cnt = cnt;
+        PickArgs pa{};
+        pa.p = p;
+        pa.n_seeds = b->n_seeds;
+        pa.n_events = b->n_events;
+        pa.seed_off = b->seed_off;
+        pa.seed_cand = sa.seed_cand;
+        pa.logit = ma.logit;
+        pa.meta = sa.cand_meta;
+        pa.trk_ws = reinterpret_cast<ds_track *>(base + kOffTrk);
+        pa.key_ws = reinterpret_cast<unsigned long long *>(base + kOffKey);
+        pa.hit_ws = reinterpret_cast<int4 *>(base + kOffHit);
+        if (launch_mlp_pick(ma, pa, sm_count, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
 
         CloneArgs ca{};
         ca.n_events = b->n_events;
         ca.n_seeds = b->n_seeds;
         ca.clone_kill = p.clone_kill && !p.training;
         ca.seed_off = b->seed_off;
-        ca.key_ws = sa.key_ws;
-        ca.hit_ws = sa.hit_ws;
+        ca.key_ws = pa.key_ws;
+        ca.hit_ws = pa.hit_ws;
         ca.rank_ws = sa.rank_ws;
         ca.count_ws = reinterpret_cast<int *>(base + kOffCount);
         ca.trk_off = out->trk_off;
@@ -165,7 +194,7 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         xa.n_seeds = b->n_seeds;
         xa.n_events = b->n_events;
         xa.seed_off = b->seed_off;
-        xa.trk_ws = sa.trk_ws;
+        xa.trk_ws = pa.trk_ws;
         xa.rank_ws = sa.rank_ws;
         xa.trk_off = out->trk_off;
         xa.out = out->tracks;

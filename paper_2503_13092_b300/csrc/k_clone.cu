@@ -128,18 +128,28 @@ __global__ void __launch_bounds__(kCloneThreads) k_clone(const __grid_constant__
 
 __global__ void __launch_bounds__(256) k_scatter_tracks(const __grid_constant__ ScatterTrkArgs a)
 {
+    // warp-cooperative copy: 32 seeds' records move as 128 contiguous 16-byte
+    // chunks read, and contiguous runs written (consecutive survivors of an
+    // event land next to each other)
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    // seeds outside [seed_off[0], seed_off[E]) belong to no event (flagged)
-    if (s >= a.n_seeds || s < __ldg(a.seed_off) || s >= __ldg(a.seed_off + a.n_events)) return;
-    const int r = __ldg(a.rank_ws + s);
-    if (r < 0) return;
-    const int4 *src = reinterpret_cast<const int4 *>(a.trk_ws + s);
-    const int e = __ldg(&src[0].x);
-    const int pos = __ldg(a.trk_off + e) + r;
-    if (pos >= a.capacity) return;
-    int4 *dst = reinterpret_cast<int4 *>(a.out + pos);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) dst[k] = __ldg(src + k);
+    const int lane = threadIdx.x & 31;
+    const int warp_s0 = s - lane;
+    int pos = -1;
+    if (s < a.n_seeds && s >= __ldg(a.seed_off) && s < __ldg(a.seed_off + a.n_events)) {
+        const int r = __ldg(a.rank_ws + s);
+        if (r >= 0) {
+            const int e = __ldg(&reinterpret_cast<const int *>(a.trk_ws + s)[0]);
+            const int p = __ldg(a.trk_off + e) + r;
+            pos = p < a.capacity ? p : -1;
+        }
+    }
+    if (__ballot_sync(0xffffffffu, pos >= 0) == 0) return;
+    const int4 *src = reinterpret_cast<const int4 *>(a.trk_ws + warp_s0);
+    for (int k = lane; k < 128; k += 32) {
+        const int rec = k >> 2;
+        const int p = __shfl_sync(0xffffffffu, pos, rec);
+        if (p >= 0) reinterpret_cast<int4 *>(a.out + p)[k & 3] = __ldg(src + k);
+    }
 }
 
 cudaError_t launch_clone(const CloneArgs &a, const ScatterTrkArgs &sa, cudaStream_t st, Prof *prof)

@@ -1,0 +1,156 @@
+// a6-a7: ghost-killer network over all candidates of the batch, best pick.
+//
+// Ghost-Killer Neural Network section: inputs -> ReLU hidden layer(s) ->
+// sigmoid output; the response must stay below the threshold (Ghost Rejection
+// section: NN Response < 0.5).  The best candidate of each seed is the one with
+// the lowest network output before the sigmoid (same order as the response,
+// no saturation) among those under the threshold; chi2 then breaks ties, then
+// the enumeration order.  In chi2 mode the lowest chi2/ndof wins and the cut
+// is applied to the winner (Algorithm Design section: score from the distance
+// between expected and real hit positions).
+//
+// k_mlp_fp32: one candidate per thread over the whole candidate buffer (every
+// lane busy); weights in the kernel's parameter bank with compile-time indices
+// (the paper's static network structure, GPU Implementation section).
+// k_pick: one thread per seed over its contiguous candidates.
+#include "ds_args.cuh"
+
+namespace ds {
+
+template <int NIN, int NH1, int NH2>
+__device__ __forceinline__ float mlp_logit_fp32(const DevNN &nn, const float (&phi)[16])
+{
+    float x[NIN];
+#pragma unroll
+    for (int i = 0; i < NIN; ++i) x[i] = (phi[i] - nn.mean[i]) * nn.scale[i];
+    float h1[NH1];
+#pragma unroll
+    for (int o = 0; o < NH1; ++o) {
+        float acc = nn.b1[o];
+#pragma unroll
+        for (int i = 0; i < NIN; ++i) acc = fmaf(nn.w1[o][i], x[i], acc);
+        h1[o] = fmaxf(acc, 0.f);
+    }
+    float out = nn.b3;
+    if (NH2 > 0) {
+#pragma unroll
+        for (int o = 0; o < NH2; ++o) {
+            float acc = nn.b2[o];
+#pragma unroll
+            for (int i = 0; i < NH1; ++i) acc = fmaf(nn.w2[o][i], h1[i], acc);
+            out = fmaf(nn.w3[o], fmaxf(acc, 0.f), out);
+        }
+    } else {
+#pragma unroll
+        for (int o = 0; o < NH1; ++o) out = fmaf(nn.w3[o], h1[o], out);
+    }
+    return out;
+}
+
+template <int NIN, int NH1, int NH2>
+__global__ void __launch_bounds__(256) k_mlp_fp32(const __grid_constant__ MlpArgs a)
+{
+    const int n = min(*(volatile const int *)&a.cnt->cand_used, a.cand_cap);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const float4 *fp = a.feat + 4 * (size_t)c;
+        float phi[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 v = __ldg(fp + q);
+            phi[4 * q] = v.x; phi[4 * q + 1] = v.y; phi[4 * q + 2] = v.z; phi[4 * q + 3] = v.w;
+        }
+        a.logit[c] = mlp_logit_fp32<NIN, NH1, NH2>(a.nn, phi);
+    }
+}
+
+__device__ __forceinline__ float sigmoid_fast(float z) { return 1.f / (1.f + __expf(-z)); }
+
+__global__ void __launch_bounds__(256) k_pick(const __grid_constant__ PickArgs a)
+{
+    // each warp stages its 32 winner records in shared memory and writes them
+    // as contiguous 16-byte chunks (a 64-byte record per lane would scatter)
+    __shared__ __align__(16) int4 s_rec[256 / 32][32 * 4];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warp_s0 = s - lane;
+    const bool valid = s < a.n_seeds && s >= __ldg(a.seed_off) && s < __ldg(a.seed_off + a.n_events);
+    const DevParams &P = a.p;
+    unsigned long long best = kNoKey;
+    int4 hits = make_int4(-1, -1, -1, -1);
+    int4 r0 = make_int4(0, 0, -1, -1), r1 = make_int4(-1, -1, 0, 0), r2 = make_int4(0, 0, 0, 0),
+         r3 = make_int4(0, 0, 0, 0);
+    if (valid) {
+        const int4 sc = a.seed_cand[s];        // first candidate, count, event
+        const float thr = P.thr_logit;
+        int bi = -1;
+        for (int k = 0; k < sc.y; ++k) {
+            const int c = sc.x + k;
+            const float lg = __ldg(a.logit + c);
+            const float4 q = __ldg(reinterpret_cast<const float4 *>(a.meta + c) + 1);   // chi2, ndof, seed, ty
+            const float chi2 = q.x;
+            const int ndof = __float_as_int(q.y);
+            unsigned long long key = kNoKey;
+            if (P.pick_chi2) key = pack_key(chi2 / (float)ndof, lg);
+            else if (lg < thr) key = pack_key(lg, chi2);
+            if (key < best) {
+                best = key;
+                bi = c;
+            }
+        }
+        bool have = bi >= 0;
+        float lg_best = 0.f;
+        if (have) lg_best = P.pick_chi2 ? unord_f32((unsigned)best) : unord_f32((unsigned)(best >> 32));
+        if (have && P.pick_chi2 && !(lg_best < thr)) have = false;
+        r0 = make_int4(sc.z, s, -1, -1);
+        r3 = make_int4(0, 0, 0, sc.y);
+        if (have) {
+            const float4 *mp = reinterpret_cast<const float4 *>(a.meta + bi);
+            const float4 m0 = __ldg(mp), m1 = __ldg(mp + 1);
+            const int4 mh = __ldg(reinterpret_cast<const int4 *>(mp + 2));
+            hits = mh;
+            // ds_track: event, seed, hit[4], x, y, tx, ty, qop, chi2, ndof, nn, flags, n_candidates
+            r0 = make_int4(sc.z, s, mh.x, mh.y);
+            r1 = make_int4(mh.z, mh.w, __float_as_int(m0.x), __float_as_int(m0.y));
+            r2 = make_int4(__float_as_int(m0.z), __float_as_int(m1.w), __float_as_int(m0.w), __float_as_int(m1.x));
+            r3 = make_int4(__float_as_int(m1.y), __float_as_int(sigmoid_fast(lg_best)), 0, sc.y);
+        } else {
+            best = kNoKey;
+        }
+        a.key_ws[s] = best;
+        a.hit_ws[s] = hits;
+    }
+    int4 *sr = s_rec[warp];
+    sr[lane * 4 + 0] = r0;
+    sr[lane * 4 + 1] = r1;
+    sr[lane * 4 + 2] = r2;
+    sr[lane * 4 + 3] = r3;
+    __syncwarp();
+    int4 *dst = reinterpret_cast<int4 *>(a.trk_ws + warp_s0);
+    for (int k = lane; k < 128; k += 32) {
+        const int rec = k >> 2;
+        const int sg = warp_s0 + rec;
+        if (sg < a.n_seeds && sg >= 0) dst[k] = sr[k];
+    }
+}
+
+cudaError_t launch_mlp_pick(const MlpArgs &m, const PickArgs &p, int sm_count, cudaStream_t st, Prof *prof)
+{
+    if (p.n_seeds <= 0) return cudaSuccess;
+    int grid = (m.cand_cap + 255) / 256;
+    if (grid > 8 * sm_count) grid = 8 * sm_count;
+    if (grid < 1) grid = 1;
+    prof->begin("k_mlp", st);
+    if (m.n_in <= 8 && m.n_h2 == 0)
+        k_mlp_fp32<8, 16, 0><<<grid, 256, 0, st>>>(m);
+    else
+        k_mlp_fp32<16, 32, 32><<<grid, 256, 0, st>>>(m);
+    prof->end(st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    prof->begin("k_pick", st);
+    k_pick<<<(p.n_seeds + 255) / 256, 256, 0, st>>>(p);
+    prof->end(st);
+    return cudaGetLastError();
+}
+
+}  // namespace ds

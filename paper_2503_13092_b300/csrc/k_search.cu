@@ -1,4 +1,4 @@
-// a2-a7: magnet point, window searches, candidate fit, ghost killer, best pick.
+// a2-a5: magnet point, window searches, candidate fit and network inputs.
 //
 // Per seed (Algorithm Design section, Dv0):
 //   magnet point from the SciFi state (Eq. 1 kink model), prediction in UTbX,
@@ -7,22 +7,19 @@
 //   extrapolated to UTaX/UTaU/UTbV, windows of half-width w2 keep the 1/2/2
 //   closest hits; candidates = the UTbX hit x one option per layer ("absent"
 //   only when the layer has no hit), kept when they have >= 3 hits including
-//   one in station a (Track Types section, UT reconstructibility);
-//   each candidate is fitted (line x = x_r + t (z - z_ref) through its hits and
-//   the magnet point), scored by the ghost-killer network (Ghost-Killer Neural
-//   Network section) and the best one is kept (response < threshold, Ghost
-//   Rejection section).
+//   one in station a (Track Types section, UT reconstructibility); each
+//   candidate is fitted (line x = x_r + t (z - z_ref) through its hits and the
+//   magnet point) and its 16 network inputs are formed.  The network and the
+//   best pick run in k_mlp.cu over all candidates of the batch.
 //
-// Work decomposition (B300): 128 seeds per CTA, one thread per seed for the
-// searches (binned hits: a window is a contiguous range per Y sector), then
-// every candidate of the CTA is scored by one thread each so the network runs
-// with full lanes regardless of how candidates spread over seeds.  The network
-// weights live in the kernel's parameter space and are addressed with
-// compile-time indices (the paper's static network structure, GPU
-// Implementation section), so each multiply-add reads its weight straight
-// from the constant bank.  The best candidate per seed is found with 64-bit
-// shared-memory atomicMin on the packed key (response, chi2) and then on the
-// candidate index among equal keys.
+// Work decomposition (B300): one CTA per work item = up to 128 seeds of one
+// event.  The event's bin table and compact x0 array are staged in shared
+// memory by two bulk copies (TMA) on an mbarrier; every x test of every window
+// reads shared memory, and only hits passing it load their 16-byte record.
+// Three flattened phases keep lanes busy whatever the hits per seed: UTbX
+// window (thread per seed), refined windows (thread per (seed, UTbX hit)),
+// fit + features (thread per candidate).  Candidates are written to a compact
+// buffer reserved with one atomicAdd per CTA, seed by seed.
 #include "ds_args.cuh"
 
 namespace ds {
@@ -184,42 +181,6 @@ __device__ __forceinline__ CandFit fit_candidate(const DevGeom &g, const SeedCtx
     return f;
 }
 
-// Ghost-killer forward pass, FP32 on the CUDA cores.  NIN inputs, NH1 ReLU,
-// NH2 ReLU (0 = none); returns the output node before the sigmoid (candidates
-// are ranked on it: same order as the response, no saturation).
-template <int NIN, int NH1, int NH2>
-__device__ __forceinline__ float mlp_logit_fp32(const DevNN &nn, const float (&phi)[16])
-{
-    float x[NIN];
-#pragma unroll
-    for (int i = 0; i < NIN; ++i) x[i] = (phi[i] - nn.mean[i]) * nn.scale[i];
-    float h1[NH1];
-#pragma unroll
-    for (int o = 0; o < NH1; ++o) {
-        float acc = nn.b1[o];
-#pragma unroll
-        for (int i = 0; i < NIN; ++i) acc = fmaf(nn.w1[o][i], x[i], acc);
-        h1[o] = fmaxf(acc, 0.f);
-    }
-    float out = nn.b3;
-    if (NH2 > 0) {
-#pragma unroll
-        for (int o = 0; o < NH2; ++o) {
-            float acc = nn.b2[o];
-#pragma unroll
-            for (int i = 0; i < NH1; ++i) acc = fmaf(nn.w2[o][i], h1[i], acc);
-            out = fmaf(nn.w3[o], fmaxf(acc, 0.f), out);
-        }
-    } else {
-#pragma unroll
-        for (int o = 0; o < NH1; ++o) out = fmaf(nn.w3[o], h1[o], out);
-    }
-    return out;
-}
-
-__device__ __forceinline__ float sigmoid_fast(float z) { return 1.f / (1.f + __expf(-z)); }
-
-template <int NIN, int NH1, int NH2>
 __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char s_dyn[];   // bin table, then staged x0
@@ -228,8 +189,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     __shared__ uint8_t s_nc[kK1Max][T];
     __shared__ SeedCtx s_sc[T];
     __shared__ int s_base[T + 1];
-    __shared__ unsigned long long s_best[T], s_cbest[T];
-    __shared__ int s_bidx[T], s_cidx[T];
+    __shared__ int s_cand0;
     __shared__ int s_scan[32];
     __shared__ int s_item[4];
     __shared__ __align__(8) uint64_t s_bar;
@@ -362,25 +322,35 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     __syncthreads();
     for (int j = 0; j < nbx; ++j) n_cand += s_nc[j][tid];
     for (int j = nbx; j < kK1Max; ++j) s_nc[j][tid] = 0;
-    s_best[tid] = kNoKey;
-    s_bidx[tid] = 0x7fffffff;
 
     int total;
     const int base = block_exclusive_scan(n_cand, s_scan, &total);
     s_base[tid] = base;
     if (tid == T - 1) s_base[T] = base + n_cand;
-    if (tid == 0 && total > 0) atomicAdd(&a.cnt->n_candidates, (unsigned long long)total);
+    if (tid == 0) {
+        if (total > 0) atomicAdd(&a.cnt->n_candidates, (unsigned long long)total);
+        int c0 = total > 0 ? atomicAdd(&a.cnt->cand_used, total) : 0;
+        if (total > 0 && c0 + total > a.cand_cap) {   // candidate buffer full: flagged, seeds left empty
+            raise_flag(a.cnt, DS_FLAG_CAND_CAPACITY);
+            c0 = -1;
+        }
+        s_cand0 = c0;
+    }
     __syncthreads();
+    const int cand0 = s_cand0;
+    if (active) a.seed_cand[s] = cand0 >= 0 ? make_int4(cand0 + base, n_cand, e, 0) : make_int4(0, 0, e, 0);
+    if (cand0 < 0) return;
 
-    // decode candidate c of the CTA: owner seed, UTbX rank j, stereo options
-    auto decode = [&](int c, int &o, int (&loc)[4]) {
+    // fit + network inputs, one candidate per thread; candidate c of the CTA
+    // decodes to (seed, UTbX rank j, stereo options) in enumeration order
+    for (int c = tid; c < total; c += T) {
         int lo = 0, hi = T;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
             if (s_base[mid] <= c) lo = mid;
             else hi = mid;
         }
-        o = lo;
+        const int o = lo;
         int k = c - s_base[o];
         int j = 0;
         while (j < kK1Max - 1 && k >= s_nc[j][o]) {
@@ -389,122 +359,62 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
         }
         const int nv = s_sel[j][4][o] != kNone ? 2 : 1;
         const int iu = k / nv, iv = k - iu * nv;
-        const uint16_t a0 = s_sel[j][0][o];
-        const uint16_t u0 = s_sel[j][1 + iu][o];
-        const uint16_t v0 = s_sel[j][3 + iv][o];
+        const uint16_t a0 = s_sel[j][0][o], u0 = s_sel[j][1 + iu][o], v0 = s_sel[j][3 + iv][o];
+        int loc[4];
         loc[0] = a0 == kNone ? -1 : a0;
         loc[1] = u0 == kNone ? -1 : u0;
         loc[2] = v0 == kNone ? -1 : v0;
         loc[3] = s_bx[j][o];
-    };
-
-    // ------------------------------------------------ score every candidate
-    // one candidate per thread per chunk of T; the body is not replicated
-    const float thr = P.thr_logit;
-#pragma unroll 1
-    for (int cb = 0; cb < total; cb += T) {
-        const int c = cb + tid;
-        unsigned long long key = kNoKey;
-        int own = -1;
-        if (c < total) {
-            int loc[4];
-            decode(c, own, loc);
-            const SeedCtx sc = s_sc[own];
-            const CandFit f = fit_candidate(g, sc, X0, loc);
-            float phi[16];
-            phi[0] = f.xr * 1e-3f;
-            phi[1] = f.yr * 1e-3f;
-            phi[2] = f.t;
-            phi[3] = sc.ty;
-            phi[4] = 1e3f * f.qop;
-            phi[5] = f.chi2 / (float)f.ndof;
-            phi[6] = 1e3f * sc.qop;
-            phi[7] = sc.chi2;
-#pragma unroll
-            for (int l = 0; l < 4; ++l) phi[8 + l] = f.res[l] * g.inv_sigma_hit;
-            phi[12] = 0.25f * (float)f.nh;
-            phi[13] = fabsf(X0[loc[3]] - sc.u_bx) / sc.w1;
-            phi[14] = sc.tx;
-            phi[15] = sc.ty;
-            const float lg = mlp_logit_fp32<NIN, NH1, NH2>(a.nn, phi);
-            if (P.pick_chi2) key = pack_key(phi[5], lg);
-            else if (lg < thr) key = pack_key(lg, f.chi2);
-        }
-        s_cbest[tid] = kNoKey;
-        s_cidx[tid] = 0x7fffffff;
-        __syncthreads();
-        if (key != kNoKey) atomicMin(&s_cbest[own], key);
-        __syncthreads();
-        if (key != kNoKey && key == s_cbest[own]) atomicMin(&s_cidx[own], c);
-        __syncthreads();
-        if (s_cbest[tid] < s_best[tid]) {
-            s_best[tid] = s_cbest[tid];
-            s_bidx[tid] = s_cidx[tid];
-        }
-        __syncthreads();
-    }
-
-    // ------------------------------------------------------- write winners
-    if (!active) return;
-    ds_track rec;
-    rec.event = e;
-    rec.seed = s;
-    rec.flags = 0;
-    rec.n_candidates = n_cand;
-    unsigned long long best = s_best[tid];
-    bool have = best != kNoKey;
-    float lg_best = 0.f;
-    if (have) lg_best = P.pick_chi2 ? unord_f32((unsigned)best) : unord_f32((unsigned)(best >> 32));
-    if (have && P.pick_chi2 && !(lg_best < thr)) have = false;
-    int4 hits = make_int4(-1, -1, -1, -1);
-    if (have) {
-        int o, loc[4];
-        decode(s_bidx[tid], o, loc);
         const SeedCtx sc = s_sc[o];
         const CandFit f = fit_candidate(g, sc, X0, loc);
-        int gid[4];
+        float phi[16];
+        phi[0] = f.xr * 1e-3f;
+        phi[1] = f.yr * 1e-3f;
+        phi[2] = f.t;
+        phi[3] = sc.ty;
+        phi[4] = 1e3f * f.qop;
+        phi[5] = f.chi2 / (float)f.ndof;
+        phi[6] = 1e3f * sc.qop;
+        phi[7] = sc.chi2;
 #pragma unroll
-        for (int l = 0; l < 4; ++l) gid[l] = loc[l] >= 0 ? __float_as_int(__ldg(H + loc[l]).w) : -1;
-        hits = make_int4(gid[0], gid[1], gid[2], gid[3]);
-        rec.hit[0] = gid[0]; rec.hit[1] = gid[1]; rec.hit[2] = gid[2]; rec.hit[3] = gid[3];
-        rec.x = f.xr; rec.y = f.yr; rec.tx = f.t; rec.ty = sc.ty; rec.qop = f.qop;
-        rec.chi2 = P.pick_chi2 ? f.chi2 : unord_f32((unsigned)best);
-        rec.ndof = f.ndof;
-        rec.nn = sigmoid_fast(lg_best);
-    } else {
-        rec.hit[0] = rec.hit[1] = rec.hit[2] = rec.hit[3] = -1;
-        rec.x = rec.y = rec.tx = rec.ty = rec.qop = rec.chi2 = rec.nn = 0.f;
-        rec.ndof = 0;
-        best = kNoKey;
+        for (int l = 0; l < 4; ++l) phi[8 + l] = f.res[l] * g.inv_sigma_hit;
+        phi[12] = 0.25f * (float)f.nh;
+        phi[13] = fabsf(X0[loc[3]] - sc.u_bx) / sc.w1;
+        phi[14] = sc.tx;
+        phi[15] = sc.ty;
+        const int slot = cand0 + c;
+        float4 *fd = a.cand_feat + 4 * (size_t)slot;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fd[q] = make_float4(phi[4 * q], phi[4 * q + 1], phi[4 * q + 2], phi[4 * q + 3]);
+        CandMeta m;
+        m.xr = f.xr; m.yr = f.yr; m.t = f.t; m.qop = f.qop;
+        m.chi2 = f.chi2;
+        m.ndof = f.ndof;
+        m.seed = s_item[1] + o;
+        m.ty = sc.ty;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) m.hit[l] = loc[l] >= 0 ? __float_as_int(__ldg(H + loc[l]).w) : -1;
+        a.cand_meta[slot] = m;
     }
-    a.trk_ws[s] = rec;
-    a.key_ws[s] = best;
-    a.hit_ws[s] = hits;
 }
 
 cudaError_t init_search_attributes()
 {
     // shared memory, not L1, limits residency: ask for the largest carveout
     const int smem = (int)(sizeof(uint16_t) * (((4 * kMaxSectors * kNXB + 1) + 7) & ~7) + sizeof(float) * (kStageHits + 4));
-    cudaError_t e = cudaFuncSetAttribute(k_search<16, 32, 32>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_search<8, 16, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_search<16, 32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_search<8, 16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_search, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
 
-cudaError_t launch_search(const SearchArgs &a, int n_in, int n_h2, cudaStream_t st, Prof *prof)
+cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
 {
     if (a.n_seeds <= 0) return cudaSuccess;
     // work items = chunks of <= T seeds of one event: at most S/T + E of them
     const int grid = (a.n_seeds + T - 1) / T + a.n_events;
     const size_t smem = sizeof(uint16_t) * a.g.table_stride + sizeof(float) * (kStageHits + 4);
     prof->begin("k_search", st);
-    if (n_in <= 8 && n_h2 == 0)
-        k_search<8, 16, 0><<<grid, T, smem, st>>>(a);
-    else
-        k_search<16, 32, 32><<<grid, T, smem, st>>>(a);
+    k_search<<<grid, T, smem, st>>>(a);
     prof->end(st);
     return cudaGetLastError();
 }

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libds.so")
 DS_OK, DS_ERR_ARG, DS_ERR_CUDA, DS_ERR_CAPACITY, DS_ERR_NOT_READY, DS_ERR_TIMEOUT, \
     DS_ERR_DEVICE_FLAG, DS_ERR_OOM = 0, -1, -2, -3, -4, -5, -6, -7
 DS_FLAG_BAD_OFFSETS, DS_FLAG_BAD_LAYER, DS_FLAG_STRIP_SECTOR, DS_FLAG_EVENT_TOO_LARGE, \
-    DS_FLAG_TRACK_CAPACITY, DS_FLAG_VERTEX_CAPACITY, DS_FLAG_TIMEOUT = (1 << k for k in range(7))
+    DS_FLAG_TRACK_CAPACITY, DS_FLAG_VERTEX_CAPACITY, DS_FLAG_TIMEOUT, DS_FLAG_CAND_CAPACITY = (1 << k for k in range(8))
 DS_MLP_FP32, DS_MLP_BF16, DS_MLP_FP8 = 0, 1, 2
 
 
@@ -47,7 +47,8 @@ class ds_params(C.Structure):
                 ("nn_threshold", C.c_double), ("doca_max", C.c_double), ("nr_tol", C.c_double),
                 ("eps_parallel", C.c_double), ("k1", C.c_int32), ("first_window_origin", C.c_int32),
                 ("pick_chi2", C.c_int32), ("clone_kill", C.c_int32), ("training", C.c_int32),
-                ("nr_max_iter", C.c_int32), ("mlp_precision", C.c_int32), ("fault_inject", C.c_int32)]
+                ("nr_max_iter", C.c_int32), ("mlp_precision", C.c_int32), ("fault_inject", C.c_int32),
+                ("cand_per_seed", C.c_int32), ("reserved1", C.c_int32)]
 
 
 class ds_event_batch(C.Structure):
