@@ -420,7 +420,9 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     if (s != DS_OK) return s;
     out->n_events = b->n_events;
     if (b->n_events == 0) return DS_OK;
-    DS_CUDA(cudaMemsetAsync(&ctx->d_cnt->cand_used, 0, sizeof(int), st), "memset");
+    static_assert(offsetof(ds::DevCounters, search_queue) == offsetof(ds::DevCounters, cand_used) + sizeof(int),
+                  "cand_used and search_queue are cleared together");
+    DS_CUDA(cudaMemsetAsync(&ctx->d_cnt->cand_used, 0, 2 * sizeof(int), st), "memset");
 
     ds::BucketArgs ba{};
     ba.g = ctx->g;
@@ -459,6 +461,7 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     sa.cand_cap = ctx->cap_cand;
     sa.seed_cand = ctx->seed_cand;
     sa.rank_ws = ctx->rank_ws;
+    sa.sm_count = ctx->sm_count;
     sa.cnt = ctx->d_cnt;
     DS_CUDA(ds::launch_search(sa, st, &ctx->prof), "search kernel");
 

@@ -54,6 +54,7 @@ struct SearchArgs {
     int cand_cap;
     int4 *seed_cand;       // per seed: first candidate, count, event
     int *rank_ws;
+    int sm_count;
     DevCounters *cnt;
 };
 

@@ -26,6 +26,8 @@ constexpr int kMaxSectors = 32;
 constexpr int kK1Max = 10;           // UTbX hits kept per seed (paper: up to 10)
 constexpr int kMaxEventHits = 65535; // uint16 offsets
 constexpr int kSearchThreads = 128;  // seeds per CTA in the search kernel
+constexpr int kSearchGroup = 2;      // consecutive work items per queue pull
+constexpr int kSearchCtasPerSm = 4;
 constexpr int kStageHits = 5632;     // event x0 arrays up to this size are staged in shared memory
 constexpr int kBucketThreads = 512;
 constexpr int kBucketRegHits = 12;   // hits kept in registers per bucketing thread
@@ -78,7 +80,7 @@ struct DevCounters {                 // device-side flag word and statistics
     int pool_used;
     int vtx_queue[2];                // event queues of the two vertex launches
     int cand_used;                   // candidates written this call
-    int pad1;
+    int search_queue;                // next search work item
     unsigned long long n_candidates;
     unsigned long long n_pairs;
     unsigned long long n_pairs_fp64;

@@ -153,6 +153,7 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         sa.cand_cap = kNACand;
         sa.seed_cand = reinterpret_cast<int4 *>(base + kOffSeedCand);
         sa.rank_ws = reinterpret_cast<int *>(base + kOffRank);
+        sa.sm_count = sm_count;
         sa.cnt = cnt;
         if (launch_search(sa, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
 

@@ -48,43 +48,30 @@ __device__ __forceinline__ void topn_insert(float (&d)[N], int (&id)[N], int (&p
     }
 }
 
+__device__ __forceinline__ bool key_less(float da, int ia, float db, int ib)
+{
+    return da < db || (da == db && ia < ib);
+}
+
 // Hits of `layer` with |x0 - u| < w whose strip extent (+- dy) contains y,
 // ranked by (|dx|, id); the N best are kept.  Returns how many qualified.
 // The x test reads the staged x0 array (shared memory for events that fit).
-// Hits passing it are collected first and their 16-byte records (y extent,
-// id) loaded together, so a window costs one round trip to L2, not one per hit.
-template <int N>
+// Up to B hits passing it are collected during the scan; after the scan (one
+// uniform point for the whole warp) their 16-byte records are loaded together
+// for the y test and id, and the survivors are ordered by a compare-exchange
+// network.  A window with more than B x-passing hits (rare) is rescanned with
+// one insertion per hit.
+template <int N, int B>
 __device__ __forceinline__ int window_scan(const DevGeom &g, const float *X0, const float4 *__restrict__ H,
                                            const uint16_t *Tb, int layer, float u, float y, float w, float dy,
                                            float (&d)[N], int (&id)[N], int (&p)[N])
 {
-    constexpr int B = 4;
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        d[k] = __int_as_float(0x7f800000);
-        id[k] = 0x7fffffff;
-        p[k] = -1;
-    }
     const int s_lo = sector_of(g, y - dy - 0.01f), s_hi = sector_of(g, y + dy + 0.01f);
     const float eps = 1e-3f;
     const int b0 = xbin_of(g, u - w - eps), b1 = xbin_of(g, u + w + eps);
-    int cnt = 0;
     int qi[B];
     float qd[B];
     int nq = 0;
-    auto flush = [&]() {
-        float4 h[B];
-#pragma unroll
-        for (int k = 0; k < B; ++k)
-            if (k < nq) h[k] = __ldg(H + qi[k]);
-#pragma unroll
-        for (int k = 0; k < B; ++k)
-            if (k < nq && h[k].y - dy <= y && y <= h[k].z + dy) {
-                topn_insert<N>(d, id, p, qd[k], __float_as_int(h[k].w), qi[k]);
-                ++cnt;
-            }
-        nq = 0;
-    };
     for (int s = s_lo; s <= s_hi; ++s) {
         const int row = (layer * g.n_sec + s) * kNXB;
         const int i0 = Tb[row + b0], i1 = Tb[row + b1 + 1];
@@ -97,11 +84,67 @@ __device__ __forceinline__ int window_scan(const DevGeom &g, const float *X0, co
                         qi[k] = i;
                         qd[k] = dx;
                     }
-                if (++nq == B) flush();
+                ++nq;
             }
         }
     }
-    if (nq) flush();
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        d[k] = __int_as_float(0x7f800000);
+        id[k] = 0x7fffffff;
+        p[k] = -1;
+    }
+    int cnt = 0;
+    if (nq <= B) {
+        // records of the collected hits, all loads in flight together
+        float4 h[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+            if (k < nq) h[k] = __ldg(H + qi[k]);
+        int hid[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const bool ok = k < nq && h[k].y - dy <= y && y <= h[k].z + dy;
+            hid[k] = ok ? __float_as_int(h[k].w) : 0x7fffffff;
+            if (!ok) qd[k] = __int_as_float(0x7f800000);
+            cnt += ok;
+        }
+        // odd-even transposition sort of (dx, id) over the B slots
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+#pragma unroll
+            for (int k = r & 1; k + 1 < B; k += 2) {
+                if (key_less(qd[k + 1], hid[k + 1], qd[k], hid[k])) {
+                    float td = qd[k]; qd[k] = qd[k + 1]; qd[k + 1] = td;
+                    int ti = hid[k]; hid[k] = hid[k + 1]; hid[k + 1] = ti;
+                    int tq = qi[k]; qi[k] = qi[k + 1]; qi[k + 1] = tq;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < N && k < B; ++k)
+            if (k < cnt) {
+                d[k] = qd[k];
+                id[k] = hid[k];
+                p[k] = qi[k];
+            }
+        return cnt;
+    }
+    // more x-passing hits than slots: exact insertion over a rescan
+    for (int s = s_lo; s <= s_hi; ++s) {
+        const int row = (layer * g.n_sec + s) * kNXB;
+        const int i0 = Tb[row + b0], i1 = Tb[row + b1 + 1];
+        for (int i = i0; i < i1; ++i) {
+            const float dx = fabsf(X0[i] - u);
+            if (dx < w) {
+                const float4 hh = __ldg(H + i);
+                if (hh.y - dy <= y && y <= hh.z + dy) {
+                    topn_insert<N>(d, id, p, dx, __float_as_int(hh.w), i);
+                    ++cnt;
+                }
+            }
+        }
+    }
     return cnt;
 }
 
@@ -199,12 +242,29 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     const DevParams &P = a.p;
     const int tid = threadIdx.x;
 
-    // work item: chunk k of event e's seeds (sizes differ by at most one)
+    // persistent CTA: pairs of consecutive work items from a device queue;
+    // the event's data is staged again only when the event changes
     const int n_items = __ldg(a.item_off + a.n_events);
-    if ((int)blockIdx.x >= n_items) return;
+    uint16_t *Tb = reinterpret_cast<uint16_t *>(s_dyn);
+    float *xs = reinterpret_cast<float *>(s_dyn + sizeof(uint16_t) * g.table_stride);
     if (tid == 0) {
-        const int e = find_segment(a.item_off, a.n_events, blockIdx.x);
-        const int k = blockIdx.x - __ldg(a.item_off + e), nc = __ldg(a.item_off + e + 1) - __ldg(a.item_off + e);
+        mbar_init(&s_bar, 1);
+        s_item[3] = -1;               // staged event
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    const int limit = P.fault_inject ? 1024 : kWaitLimit;
+    for (;;) {
+    if (tid == 0) s_item[0] = atomicAdd(&a.cnt->search_queue, kSearchGroup);
+    __syncthreads();
+    const int b_first = s_item[0];
+    __syncthreads();
+    if (b_first >= n_items) break;
+    for (int bi = b_first; bi < b_first + kSearchGroup && bi < n_items; ++bi) {
+    // work item: chunk k of event e's seeds (sizes differ by at most one)
+    if (tid == 0) {
+        const int e = find_segment(a.item_off, a.n_events, bi);
+        const int k = bi - __ldg(a.item_off + e), nc = __ldg(a.item_off + e + 1) - __ldg(a.item_off + e);
         const int s0 = __ldg(a.seed_off + e), ns = __ldg(a.seed_off + e + 1) - s0;
         s_item[0] = e;
         s_item[1] = s0 + (int)(((long long)k * ns) / nc);
@@ -221,27 +281,29 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
 
     // stage the event's bin table and (if it fits) its x0 array with two bulk
     // copies (TMA); the x0 copy starts at the 16-byte boundary below h0
-    uint16_t *Tb = reinterpret_cast<uint16_t *>(s_dyn);
-    float *xs = reinterpret_cast<float *>(s_dyn + sizeof(uint16_t) * g.table_stride);
     const bool staged = nh <= kStageHits;
     const int lead = h0 & 3;
     const float *X0 = staged ? xs + lead : a.sx0 + h0;
-    if (tid == 0) {
-        mbar_init(&s_bar, 1);
-        const uint32_t tb_bytes = sizeof(uint16_t) * g.table_stride;
-        const uint32_t x_bytes = staged ? (uint32_t)(((lead + nh) * 4 + 15) & ~15) : 0u;
-        // fault injection (tests): expect 16 bytes that never arrive
-        mbar_expect_tx(&s_bar, tb_bytes + x_bytes + ((P.fault_inject & 1) ? 16u : 0u));
-        bulk_copy_g2s(Tb, a.bins + (size_t)e * g.table_stride, tb_bytes, &s_bar);
-        if (x_bytes) bulk_copy_g2s(xs, a.sx0 + (h0 - lead), x_bytes, &s_bar);
+    const bool restage = s_item[3] != e;
+    if (restage) {
+        if (tid == 0) {
+            const uint32_t tb_bytes = sizeof(uint16_t) * g.table_stride;
+            const uint32_t x_bytes = staged ? (uint32_t)(((lead + nh) * 4 + 15) & ~15) : 0u;
+            // fault injection (tests): expect 16 bytes that never arrive
+            mbar_expect_tx(&s_bar, tb_bytes + x_bytes + ((P.fault_inject & 1) ? 16u : 0u));
+            bulk_copy_g2s(Tb, a.bins + (size_t)e * g.table_stride, tb_bytes, &s_bar);
+            if (x_bytes) bulk_copy_g2s(xs, a.sx0 + (h0 - lead), x_bytes, &s_bar);
+        }
     }
     if (active) a.rank_ws[s] = -1;     // the clone kernel ranks this call's winners
-    __syncthreads();
-    // bounded wait; the decision to go on is taken by the whole block
-    const int limit = P.fault_inject ? 1024 : kWaitLimit;
-    if (!__syncthreads_and(mbar_wait_bounded(&s_bar, 0, limit))) {
-        if (tid == 0) raise_flag(a.cnt, DS_FLAG_TIMEOUT);
-        return;   // the bulk copies themselves have completed or fail on their own; nothing else is in flight
+    if (restage) {
+        // bounded wait; the decision to go on is taken by the whole block
+        if (!__syncthreads_and(mbar_wait_bounded(&s_bar, phase, limit))) {
+            if (tid == 0) raise_flag(a.cnt, DS_FLAG_TIMEOUT);
+            return;
+        }
+        phase ^= 1u;
+        if (tid == 0) s_item[3] = e;
     }
 
     // ---------------------------------------------------------------- search
@@ -271,7 +333,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
 
         float d[kK1Max];
         int id[kK1Max], p[kK1Max];
-        const int q = window_scan<kK1Max>(g, X0, H, Tb, 3, u_bx, sc.yl[3], sc.w1, P.dy_tol, d, id, p);
+        const int q = window_scan<kK1Max, 8>(g, X0, H, Tb, 3, u_bx, sc.yl[3], sc.w1, P.dy_tol, d, id, p);
         nbx = min(q, P.k1);
 #pragma unroll
         for (int j = 0; j < kK1Max; ++j) s_bx[j][tid] = (uint16_t)p[j];
@@ -301,14 +363,14 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
         {
             float dd[1]; int ii[1], pp[1];
             const float ul = fmaf(txp, g.z[0] - g.z[3], xh) - g.dxdy[0] * sc.yl[0];
-            const int c = window_scan<1>(g, X0, H, Tb, 0, ul, sc.yl[0], w2, P.dy_tol, dd, ii, pp);
+            const int c = window_scan<1, 4>(g, X0, H, Tb, 0, ul, sc.yl[0], w2, P.dy_tol, dd, ii, pp);
             sel[0] = c > 0 ? pp[0] : -1;
         }
 #pragma unroll
         for (int l = 1; l <= 2; ++l) {
             float dd[2]; int ii[2], pp[2];
             const float ul = fmaf(txp, g.z[l] - g.z[3], xh) - g.dxdy[l] * sc.yl[l];
-            const int c = window_scan<2>(g, X0, H, Tb, l, ul, sc.yl[l], w2, P.dy_tol, dd, ii, pp);
+            const int c = window_scan<2, 4>(g, X0, H, Tb, l, ul, sc.yl[l], w2, P.dy_tol, dd, ii, pp);
             sel[2 * l - 1] = c > 0 ? pp[0] : -1;
             sel[2 * l] = c > 1 ? pp[1] : -1;
         }
@@ -339,7 +401,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     __syncthreads();
     const int cand0 = s_cand0;
     if (active) a.seed_cand[s] = cand0 >= 0 ? make_int4(cand0 + base, n_cand, e, 0) : make_int4(0, 0, e, 0);
-    if (cand0 < 0) return;
+    if (cand0 >= 0) {
 
     // fit + network inputs, one candidate per thread; candidate c of the CTA
     // decodes to (seed, UTbX rank j, stereo options) in enumeration order
@@ -396,6 +458,10 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
         for (int l = 0; l < 4; ++l) m.hit[l] = loc[l] >= 0 ? __float_as_int(__ldg(H + loc[l]).w) : -1;
         a.cand_meta[slot] = m;
     }
+    }
+    __syncthreads();   // shared state is reused by the next item
+    }   // items of the group
+    }   // queue
 }
 
 cudaError_t init_search_attributes()
@@ -410,8 +476,10 @@ cudaError_t init_search_attributes()
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
 {
     if (a.n_seeds <= 0) return cudaSuccess;
-    // work items = chunks of <= T seeds of one event: at most S/T + E of them
-    const int grid = (a.n_seeds + T - 1) / T + a.n_events;
+    // persistent: kSearchCtasPerSm CTAs per SM pull work items from a queue
+    const int items_max = (a.n_seeds + T - 1) / T + a.n_events;
+    int grid = a.sm_count * kSearchCtasPerSm;
+    if (grid > items_max) grid = items_max;
     const size_t smem = sizeof(uint16_t) * a.g.table_stride + sizeof(float) * (kStageHits + 4);
     prof->begin("k_search", st);
     k_search<<<grid, T, smem, st>>>(a);

@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(kVtxThreads, 3) k_vertex(const __grid_constant
     __shared__ int s_scan[32];
     __shared__ int s_pool_base;
     __shared__ unsigned s_mask[kVtxSeg / 32];
+    __shared__ unsigned s_keep[kVtxSeg / 32];
     __shared__ int s_wbase[kVtxSeg / 32];
     __shared__ bool s_last;
     Trk *s_trk = reinterpret_cast<Trk *>(s_dyn);
@@ -244,6 +245,7 @@ __global__ void __launch_bounds__(kVtxThreads, 3) k_vertex(const __grid_constant
 
     const DevGeom &g = a.g;
     const DevParams &P = a.p;
+    const bool straight = g.gamma0 == 0.f && g.gamma1 == 0.f;
     __shared__ int s_e;
     for (;;) {
     if (threadIdx.x == 0) s_e = atomicAdd(&a.cnt->vtx_queue[LARGE ? 1 : 0], 1);
@@ -322,21 +324,76 @@ __global__ void __launch_bounds__(kVtxThreads, 3) k_vertex(const __grid_constant
         for (int seg0 = 0; seg0 < npairs; seg0 += kVtxSeg) {
             const int nseg = min(kVtxSeg, npairs - seg0);
             const int nwords = (nseg + 31) >> 5;
-            // phase 1: solve every pair of the segment, one per lane; keep bits by ballot
+            // phase 1a: every pair of the segment, one per lane: is it a candidate?
+            // With gamma = 0 both trajectories are lines and the solve converges to
+            // their closest approach, whose distance |w.(Di x Dj)| / |Di x Dj| is
+            // exact in closed form: pairs more than 1 um above the cut are not
+            // candidates.  With gamma != 0 every pair is a candidate.
             for (int w = warp; w < nwords; w += nwarps) {
-                const int p = seg0 + (w << 5) + lane;
-                int keep = 0;
-                if (p < seg0 + nseg) {
-                    int i, j, f64;
-                    pair_of(p, i, j);
-                    const PairOut o = solve_pair(g, P, s_trk[i], s_trk[j], f64);
-                    n64 += f64;
-                    keep = o.doca < P.doca_max;
+                const int p0 = seg0 + (w << 5);
+                int r = 0;
+                if (lane == 0) {
+                    int lo = 0, hi = nt;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (s_row[mid] <= p0) lo = mid;
+                        else hi = mid;
+                    }
+                    r = lo;
                 }
-                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                r = __shfl_sync(0xffffffffu, r, 0);
+                const int p = p0 + lane;
+                int cand = 0;
+                if (p < seg0 + nseg) {
+                    cand = 1;
+                    if (straight) {
+                        while (r + 1 < nt && s_row[r + 1] <= p) ++r;
+                        const Trk A = s_trk[r];
+                        const uint16_t *opp = A.q > 0.f ? s_neg : s_pos;
+                        const Trk B = s_trk[opp[s_start[r] + (p - s_row[r])]];
+                        const float dtx = A.tx - B.tx, dty = A.ty - B.ty;
+                        const float cz = fmaf(A.tx, B.ty, -A.ty * B.tx);
+                        const float den = fmaf(dtx, dtx, fmaf(dty, dty, cz * cz));
+                        const float num = fabsf(fmaf(A.x - B.x, dty, -(A.y - B.y) * dtx));
+                        if (den > 1e-12f && num > (P.doca_max + 1e-3f) * sqrtf(den)) cand = 0;
+                    }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, cand);
                 if (lane == 0) s_mask[w] = m;
             }
             __syncthreads();
+            // phase 1b: solve the candidates only, one per thread; keep bits
+            {
+                int ctot = 0;
+                for (int w0 = 0; w0 < nwords; w0 += blockDim.x) {
+                    const int w = w0 + threadIdx.x;
+                    const int c = w < nwords ? __popc(s_mask[w]) : 0;
+                    int t;
+                    const int r = block_exclusive_scan(c, s_scan, &t);
+                    if (w < nwords) s_wbase[w] = ctot + r;
+                    ctot += t;
+                }
+                __syncthreads();
+                for (int w = threadIdx.x; w < nwords; w += blockDim.x) s_keep[w] = 0u;
+                __syncthreads();
+                for (int k = threadIdx.x; k < ctot; k += blockDim.x) {
+                    int lo = 0, hi = nwords;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (s_wbase[mid] <= k) lo = mid;
+                        else hi = mid;
+                    }
+                    const int bit = __fns(s_mask[lo], 0, k - s_wbase[lo] + 1);
+                    int i, j, f64;
+                    pair_of(seg0 + (lo << 5) + bit, i, j);
+                    const PairOut o = solve_pair(g, P, s_trk[i], s_trk[j], f64);
+                    n64 += f64;
+                    if (o.doca < P.doca_max) atomicOr(&s_keep[lo], 1u << bit);
+                }
+                __syncthreads();
+                for (int w = threadIdx.x; w < nwords; w += blockDim.x) s_mask[w] = s_keep[w];
+                __syncthreads();
+            }
             // ranks of the kept pairs: one scan over the segment's mask words
             int tot = 0;
             for (int w0 = 0; w0 < nwords; w0 += blockDim.x) {
