@@ -33,7 +33,7 @@ L2_BYTES = 126 * 2 ** 20
 N_EVENTS = 1000
 WORKLOAD = ("c2: 1000 events/step, Poisson(300) SciFi seeds (40% true), 5000 UT hits/event, "
             "16-32-32-1 ghost killer FP32, opposite-charge vertexing DOCA<2mm")
-KERNELS_PER_STEP = 7
+KERNELS_PER_STEP = 9
 
 
 def dist_info():
@@ -104,14 +104,22 @@ class Clocks:
 
 
 def algorithmic(E, S, H, n_t, n_v, n_cand, n_pairs, table_stride):
-    """Algorithmic bytes (inputs once + outputs once) and FLOPs per launch."""
-    mlp_flop = 2 * (16 * 32 + 32 * 32 + 32)
+    """Algorithmic bytes (each input read once, each output written once) and
+    FLOPs per launch of every kernel of a step.  C = candidates, T = tracks,
+    V = vertices, P = opposite-charge pairs."""
+    tb = 2 * table_stride * E                    # per-event bin tables
+    mlp_flop = 2 * (16 * 32 + 32 * 32 + 32)      # 16-32-32-1 multiply-adds x 2
     return {
-        "k_bucket": dict(bytes=13 * H + 16 * H + 2 * table_stride * E),
-        "k_search": dict(bytes=24 * S + 16 * H + 2 * table_stride * E + 92 * S, flop=mlp_flop * n_cand),
+        # hits in (13 B) -> float4 records (16 B) + compact x0 (4 B) + tables
+        "k_bucket": dict(bytes=13 * H + 20 * H + tb),
+        # seeds (24 B), staged x0 + records (20 B/hit), tables -> candidates
+        # (64 B inputs + 48 B fit) + per-seed range and rank (20 B)
+        "k_search": dict(bytes=24 * S + 20 * H + tb + 112 * n_cand + 20 * S),
+        "k_mlp": dict(bytes=68 * n_cand, flop=mlp_flop * n_cand),
+        "k_pick": dict(bytes=16 * S + 20 * n_cand + 48 * n_t + 88 * S),
         "k_clone": dict(bytes=28 * S + 8 * E),
         "k_scatter_tracks": dict(bytes=4 * S + 128 * n_t),
-        "k_vertex_small": dict(bytes=20 * n_t + 36 * n_v, flop=200 * n_pairs),
+        "k_vertex_small": dict(bytes=20 * n_t + 36 * n_v),
         "k_vertex_large": dict(bytes=0),
         "k_scatter_vertices": dict(bytes=68 * n_v),
     }
