@@ -103,12 +103,15 @@ class Clocks:
                     samples=len(sm))
 
 
+MLP_FLOP = 2 * (16 * 32 + 32 * 32 + 32)          # 16-32-32-1 network: multiply-adds x 2
+
+
 def algorithmic(E, S, H, n_t, n_v, n_cand, n_pairs, table_stride):
     """Algorithmic bytes (each input read once, each output written once) and
     FLOPs per launch of every kernel of a step.  C = candidates, T = tracks,
     V = vertices, P = opposite-charge pairs."""
     tb = 2 * table_stride * E                    # per-event bin tables
-    mlp_flop = 2 * (16 * 32 + 32 * 32 + 32)      # 16-32-32-1 multiply-adds x 2
+    mlp_flop = MLP_FLOP
     return {
         # hits in (13 B) -> float4 records (16 B) + compact x0 (4 B) + tables
         "k_bucket": dict(bytes=13 * H + 20 * H + tb),
@@ -214,6 +217,70 @@ def bench_reference(args):
                 e2e=dict(value=val, unit="events/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
     return 0
+
+
+def reduced_precision_forms(d, ds, torch, batch, devs, ref, step, n_prof, stream, kernels, n_cand):
+    """The ghost-killer network on the tensor cores (BF16, FP8) against the FP32
+    network on the same batch: k_mlp time, share of seeds whose selected track
+    changes and the response change on tracks both keep.  Also ds_mlp_eval alone
+    on 2^20 feature rows (kernel throughput without the rest of the step)."""
+    S = int(batch["seed_off"][-1])
+
+    def per_seed(g):
+        t = g["tracks"]
+        has = np.zeros(S, bool); hits = np.full((S, 4), -1, np.int64); nn = np.zeros(S)
+        has[t["seed"]] = True; hits[t["seed"]] = t["hit"]; nn[t["seed"]] = t["nn"]
+        return has, hits, nn
+
+    h32, k32, n32 = per_seed(ref)
+    rng = np.random.default_rng(17)
+    n_rows = 1 << 20
+    feats = torch.from_numpy(rng.standard_normal((n_rows, 16)).astype(np.float32)).cuda()
+    logit = torch.empty(n_rows, dtype=torch.float32, device="cuda")
+    forms = {}
+    for name, prec in (("fp32", ds.DS_MLP_FP32), ("bf16", ds.DS_MLP_BF16), ("fp8_e4m3", ds.DS_MLP_FP8)):
+        d.set_params(mlp_precision=prec)
+        f = {}
+        if prec != ds.DS_MLP_FP32:
+            for k in range(3):      # first launches of this kernel variant load it
+                step(k)
+            d.sync(stream)
+            ds.ds_profile_enable(d.ctx, True)
+            for k in range(n_prof):
+                step(k)
+            pr = ds.ds_profile_read(d.ctx)
+            ds.ds_profile_enable(d.ctx, False)
+            d.sync(stream)
+            f["k_mlp_us"] = 1e3 * pr["k_mlp"][1] / max(pr["k_mlp"][0], 1)
+            g = d.run(batch, dev=devs[0])
+            hl, kl, nl = per_seed(g)
+            flip = (h32 != hl) | (h32 & hl & np.any(k32 != kl, axis=1))
+            both = h32 & hl & ~flip
+            dn = np.abs(nl[both] - n32[both])
+            f.update(seed_flip_rate=float(flip.mean()), tracks=int(hl.sum()),
+                     response_err_max=float(dn.max()) if dn.size else 0.0,
+                     response_err_mean=float(dn.mean()) if dn.size else 0.0)
+        else:
+            f["k_mlp_us"] = kernels["k_mlp"]["avg_us"]
+            f["tracks"] = int(h32.sum())
+        f["k_mlp_candidates_per_s"] = n_cand / (f["k_mlp_us"] * 1e-6)
+        for _ in range(3):
+            ds.ds_mlp_eval(d.ctx, feats, logit, prec, stream)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            ds.ds_mlp_eval(d.ctx, feats, logit, prec, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / 10
+        f["eval_1M_us"] = us
+        f["eval_rows_per_s"] = n_rows / (us * 1e-6)
+        f["eval_tflops"] = MLP_FLOP * n_rows / (us * 1e-6) / 1e12
+        f["eval_gbs"] = 68 * n_rows / (us * 1e-6) / 1e9
+        forms[name] = f
+    d.set_params(mlp_precision=ds.DS_MLP_FP32)
+    d.sync(stream)
+    return forms
 
 
 def main():
@@ -373,6 +440,8 @@ def main():
         roof = dict(kernel=dom, bound="hbm", achieved=kd["gbs"], peak=hbm, unit="GB/s", frac=frac_hbm,
                     peak_source=f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback",
                     traffic=traffic_for(dom))
+    mlp_forms = reduced_precision_forms(d, ds, torch, batch, devs, probe, step, n_prof, stream, kernels, n_cand)
+
     path_bytes = 24 * S + 13 * H + 64 * n_t + 32 * n_v
     path = dict(bytes_per_step=path_bytes, gbs=path_bytes * args.steps / max(times) / 1e9,
                 frac_of_hbm=path_bytes * args.steps / max(times) / 1e9 / hbm)
@@ -444,7 +513,7 @@ def main():
                         candidates=n_cand, pairs=n_pairs, pairs_fp64=n_fp64, mlp="fp32",
                         l2=f"inputs rotate over {R} replicas ({R * in_bytes / 2**20:.0f} MB > 3x L2)",
                         parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
-            roofline=roof, path_roofline=path, kernels=kernels, clocks=clocks, e2e=e2e,
+            roofline=roof, path_roofline=path, kernels=kernels, clocks=clocks, e2e=e2e, mlp_forms=mlp_forms,
             plain_form=dict(value=n_plain / plain_s, unit="events/s",
                             note="one event per ds_reconstruct + ds_vertex call, FP32", events=n_plain),
             eager=dict(value=ws * E * args.steps / eager_s, unit="events/s",

@@ -126,7 +126,9 @@ typedef struct {
     int32_t clone_kill;    /* 1: kill clones sharing more than two UT hits */
     int32_t training;      /* 1: fixed 100/10 mm windows, no clone killing */
     int32_t nr_max_iter;   /* Newton-Raphson iteration limit */
-    int32_t mlp_precision; /* DS_MLP_FP32 (default), DS_MLP_BF16, DS_MLP_FP8 */
+    int32_t mlp_precision; /* arithmetic of the ghost-killer network: DS_MLP_FP32 (default,
+                              CUDA cores), DS_MLP_BF16 or DS_MLP_FP8 (E4M3) on the tensor
+                              cores with FP32 accumulation (see ds_mlp_eval) */
     int32_t fault_inject;  /* 0 in normal use.  Tests of the failure path: bit 0 makes the
                               search kernel's bounded wait for its staged data run out, so
                               the call reports DS_ERR_TIMEOUT (flag DS_FLAG_TIMEOUT) and
@@ -267,6 +269,25 @@ DS_API ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *batch, const 
  * is near or below the cut are re-solved in FP64.  `tracks` is the output of
  * ds_reconstruct (device), with n_events set. */
 DS_API ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tracks, ds_vertices *out, void *stream);
+
+/* The ghost-killer network alone (Ghost-Killer Neural Network section: inputs
+ * normalised, ReLU hidden layers, output node) over n candidates, for tests
+ * and for measuring the reduced-precision forms.  d_features: device, n x 16
+ * FP32 row-major (the 16 inputs of one candidate contiguous, unused inputs of
+ * smaller networks ignored), 16-byte aligned.  d_logit: device, n FP32, the
+ * network output before the sigmoid (the response is its sigmoid).
+ * precision: DS_MLP_FP32 - FP32 on the CUDA cores (bit-identical to
+ * ds_reconstruct's network); DS_MLP_BF16 - inputs and first hidden layer
+ * rounded to BF16, weights to BF16, products accumulated in FP32 on the
+ * tensor cores (tcgen05), biases, ReLU and the output layer in FP32;
+ * DS_MLP_FP8 - as BF16 with E4M3 (saturating at +-448) in place of BF16 and
+ * each weight layer scaled by 448 / max|W| before rounding (the scale undone
+ * in FP32).  The paper's network runs in FP32; the reduced forms are this
+ * library's.  DS_ERR_NOT_READY without weights, DS_ERR_ARG for n < 0, null
+ * or misaligned pointers or an unknown precision.  Asynchronous on `stream`;
+ * a tensor-core wait that runs out raises DS_FLAG_TIMEOUT (ds_sync_status). */
+DS_API ds_status ds_mlp_eval(ds_ctx *ctx, const float *d_features, int32_t n, float *d_logit,
+                             int32_t precision, void *stream);
 
 /* Synchronise `stream`, read and clear the device flag word and counters.
  * Returns DS_ERR_CAPACITY / DS_ERR_TIMEOUT / DS_ERR_DEVICE_FLAG when the

@@ -62,6 +62,7 @@ def lib():
         if _lib is None:
             _lib = C.CDLL(build())
             _lib.or_mlp.restype = C.c_double
+            _lib.or_mlp_logit.restype = C.c_double
             _lib.or_gamma.restype = C.c_double
             _lib.or_poca.restype = C.c_int
             _lib.or_vertex.restype = C.c_long
@@ -105,6 +106,17 @@ def mlp(w: dict, phi) -> np.ndarray:
     L = lib()
     for i in range(phi.shape[0]):
         out[i] = L.or_mlp(C.byref(h.s), _p(phi[i]))
+    return out
+
+
+def mlp_logit(w: dict, phi) -> np.ndarray:
+    """Ghost-killer network output before the sigmoid for each row of phi (FP64)."""
+    h = _NNHolder(w)
+    phi = np.ascontiguousarray(np.atleast_2d(np.asarray(phi, np.float64)))
+    out = np.empty(phi.shape[0])
+    L = lib()
+    for i in range(phi.shape[0]):
+        out[i] = L.or_mlp_logit(C.byref(h.s), _p(phi[i]))
     return out
 
 

@@ -18,6 +18,7 @@ struct ds_ctx {
     ds::DevNN nn{};
     int nn_in = 16, nn_h1 = 32, nn_h2 = 32;
     int mlp_precision = DS_MLP_FP32;
+    ds::MlpTcWeights *d_tc = nullptr;    // tensor-core weight tiles (BF16 / FP8 network)
     ds::DevCounters *d_cnt = nullptr;
     // workspaces
     int cap_events = 0, cap_seeds = 0, cap_hits = 0, cap_pool = 0;
@@ -313,7 +314,7 @@ void ds_destroy(ds_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    void *ptrs[] = {ctx->d_cnt, ctx->sorted, ctx->sx0, ctx->item_cnt, ctx->item_off, ctx->bins, ctx->cand_feat,
+    void *ptrs[] = {ctx->d_cnt, ctx->d_tc, ctx->sorted, ctx->sx0, ctx->item_cnt, ctx->item_off, ctx->bins, ctx->cand_feat,
                     ctx->cand_meta, ctx->cand_logit, ctx->seed_cand, ctx->trk_ws, ctx->key_ws, ctx->hit_ws,
                     ctx->rank_ws, ctx->count_trk, ctx->count_vtx, ctx->pool, ctx->pool_pos,
                     ctx->h.seed_off, ctx->h.hit_off, ctx->h.seed_cols, ctx->h.hit_cols, ctx->h.layer,
@@ -342,6 +343,19 @@ ds_status ds_load_nn_weights(ds_ctx *ctx, const ds_nn_weights *w)
     ctx->nn_h2 = n_h2;
     ctx->nn_in = w->n_in;
     ctx->nn_h1 = w->n_h1;
+    ds::MlpTcWeights tc;
+    ds::prepare_tc_weights(ctx->nn, n_h2, &tc);
+    DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (!ctx->d_tc) {
+        cudaError_t e = cudaMalloc((void **)&ctx->d_tc, sizeof(tc));
+        if (e != cudaSuccess) {
+            ctx->d_tc = nullptr;
+            return fail(ctx, DS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+    }
+    // ordered after earlier work on every stream: no launch may still read the old tiles
+    DS_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    DS_CUDA(cudaMemcpy(ctx->d_tc, &tc, sizeof(tc), cudaMemcpyHostToDevice), "weight upload");
     ctx->has_nn = true;
     return DS_OK;
 }
@@ -412,8 +426,6 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     if (b->n_hits > 0 && (!ht->x0 || !ht->ybeg || !ht->yend || !ht->layer))
         return fail(ctx, DS_ERR_ARG, "null hit column");
     if (out->capacity > 0 && !out->tracks) return fail(ctx, DS_ERR_ARG, "null track buffer");
-    if (ctx->mlp_precision != DS_MLP_FP32)
-        return fail(ctx, DS_ERR_ARG, "reduced-precision network not built in this library");
     cudaStream_t st = (cudaStream_t)stream;
     DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     ds_status s = ensure_workspace(ctx, b->n_events, b->n_seeds, b->n_hits, st);
@@ -469,9 +481,12 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     ma.nn = ctx->nn;
     ma.n_in = ctx->nn_in;
     ma.n_h2 = ctx->nn_h2;
+    ma.precision = ctx->mlp_precision;
+    ma.tc = ctx->d_tc;
     ma.feat = ctx->cand_feat;
     ma.logit = ctx->cand_logit;
     ma.cand_cap = ctx->cap_cand;
+    ma.n_host = -1;
     ma.cnt = ctx->d_cnt;
     ds::PickArgs pa{};
     pa.p = ctx->p;
@@ -509,6 +524,38 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     xa.out = out->tracks;
     xa.capacity = out->capacity;
     DS_CUDA(ds::launch_clone(ca, xa, st, &ctx->prof), "clone kernel");
+    return DS_OK;
+}
+
+ds_status ds_mlp_eval(ds_ctx *ctx, const float *d_features, int32_t n, float *d_logit, int32_t precision,
+                      void *stream)
+{
+    if (!ctx) return DS_ERR_ARG;
+    if (!ctx->has_nn) return fail(ctx, DS_ERR_NOT_READY, "weights not loaded");
+    if (n < 0) return fail(ctx, DS_ERR_ARG, "negative size");
+    if (precision != DS_MLP_FP32 && precision != DS_MLP_BF16 && precision != DS_MLP_FP8)
+        return fail(ctx, DS_ERR_ARG, "unknown precision");
+    if (n == 0) return DS_OK;
+    if (!d_features || !d_logit) return fail(ctx, DS_ERR_ARG, "null pointer");
+    if (reinterpret_cast<uintptr_t>(d_features) % 16 != 0)
+        return fail(ctx, DS_ERR_ARG, "features must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ds::MlpArgs ma{};
+    ma.nn = ctx->nn;
+    ma.n_in = ctx->nn_in;
+    ma.n_h2 = ctx->nn_h2;
+    ma.precision = precision;
+    ma.tc = ctx->d_tc;
+    ma.feat = reinterpret_cast<const float4 *>(d_features);
+    ma.logit = d_logit;
+    ma.cand_cap = n;
+    ma.n_host = n;
+    ma.cnt = ctx->d_cnt;
+    ctx->prof.begin("k_mlp", st);
+    cudaError_t e = ds::launch_mlp(ma, ctx->sm_count, n, st);
+    ctx->prof.end(st);
+    DS_CUDA(e, "network kernel");
     return DS_OK;
 }
 

@@ -58,13 +58,29 @@ struct SearchArgs {
     DevCounters *cnt;
 };
 
+// Ghost-killer weights for the tensor-core kernels, in the K-major no-swizzle
+// core-matrix layout of tcgen05 operands (8 rows x 16 bytes per core matrix,
+// core matrices 128 bytes apart along K).  W1 is 32 x 16 (E4M3: padded to K =
+// 32 with zeros), W2 32 x 32.  FP8 weights are stored times 448 / max|W| of
+// their layer; inv_s1, inv_s2 undo that in the epilogue.
+struct MlpTcWeights {
+    uint8_t b1_bf16[1024];
+    uint8_t b2_bf16[2048];
+    uint8_t b1_fp8[1024];
+    uint8_t b2_fp8[1024];
+    float inv_s1, inv_s2;
+};
+
 struct MlpArgs {
     DevNN nn;
     int n_in, n_h2;
+    int precision;               // DS_MLP_FP32 / DS_MLP_BF16 / DS_MLP_FP8
+    const MlpTcWeights *tc;      // device copy (BF16 / FP8 only)
     const float4 *feat;
     float *logit;
     int cand_cap;
-    const DevCounters *cnt;
+    int n_host;                  // >= 0: number of candidates; < 0: read cnt->cand_used
+    DevCounters *cnt;
 };
 
 struct PickArgs {
@@ -143,6 +159,10 @@ cudaError_t init_search_attributes();
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st, Prof *prof);
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof);
 cudaError_t launch_mlp_pick(const MlpArgs &m, const PickArgs &p, int sm_count, cudaStream_t st, Prof *prof);
+// the network alone over n_bound candidates at most (m.n_host or the device count)
+cudaError_t launch_mlp(const MlpArgs &m, int sm_count, int n_bound, cudaStream_t st);
+cudaError_t launch_mlp_tc(const MlpArgs &m, int sm_count, int n_bound, cudaStream_t st);
+void prepare_tc_weights(const DevNN &nn, int n_h2, MlpTcWeights *out);
 cudaError_t launch_clone(const CloneArgs &a, const ScatterTrkArgs &sa, cudaStream_t st, Prof *prof);
 cudaError_t launch_vertex(const VertexArgs &a, const ScatterVtxArgs &sa, int sm_count, cudaStream_t st,
                           Prof *prof);

@@ -193,6 +193,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 }
 
 constexpr int kWaitLimit = 1 << 22;
+constexpr int kMlpTcCtasPerSm = 4;        // persistent tensor-core network CTAs per SM (64 TMEM columns each)
 
 // Exclusive scan of one int per thread over the block; returns the prefix,
 // *total receives the block sum.  `scratch` holds >= 32 ints.  All threads call.

@@ -161,9 +161,11 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         ma.nn = nn;
         ma.n_in = weights->n_in;
         ma.n_h2 = nn_h2;
+        ma.precision = DS_MLP_FP32;
         ma.feat = sa.cand_feat;
         ma.logit = reinterpret_cast<float *>(base + kOffCandLogit);
         ma.cand_cap = kNACand;
+        ma.n_host = -1;
         ma.cnt = cnt;
         PickArgs pa{};
         pa.p = p;

@@ -50,7 +50,7 @@ __device__ __forceinline__ float mlp_logit_fp32(const DevNN &nn, const float (&p
 template <int NIN, int NH1, int NH2>
 __global__ void __launch_bounds__(256) k_mlp_fp32(const __grid_constant__ MlpArgs a)
 {
-    const int n = min(*(volatile const int *)&a.cnt->cand_used, a.cand_cap);
+    const int n = a.n_host >= 0 ? a.n_host : min(*(volatile const int *)&a.cnt->cand_used, a.cand_cap);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const float4 *fp = a.feat + 4 * (size_t)c;
         float phi[16];
@@ -133,19 +133,25 @@ __global__ void __launch_bounds__(256) k_pick(const __grid_constant__ PickArgs a
     }
 }
 
-cudaError_t launch_mlp_pick(const MlpArgs &m, const PickArgs &p, int sm_count, cudaStream_t st, Prof *prof)
+cudaError_t launch_mlp(const MlpArgs &m, int sm_count, int n_bound, cudaStream_t st)
 {
-    if (p.n_seeds <= 0) return cudaSuccess;
-    int grid = (m.cand_cap + 255) / 256;
+    if (m.precision != DS_MLP_FP32) return launch_mlp_tc(m, sm_count, n_bound, st);
+    int grid = (n_bound + 255) / 256;
     if (grid > 8 * sm_count) grid = 8 * sm_count;
     if (grid < 1) grid = 1;
-    prof->begin("k_mlp", st);
     if (m.n_in <= 8 && m.n_h2 == 0)
         k_mlp_fp32<8, 16, 0><<<grid, 256, 0, st>>>(m);
     else
         k_mlp_fp32<16, 32, 32><<<grid, 256, 0, st>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_pick(const MlpArgs &m, const PickArgs &p, int sm_count, cudaStream_t st, Prof *prof)
+{
+    if (p.n_seeds <= 0) return cudaSuccess;
+    prof->begin("k_mlp", st);
+    cudaError_t e = launch_mlp(m, sm_count, m.cand_cap, st);
     prof->end(st);
-    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     prof->begin("k_pick", st);
     k_pick<<<(p.n_seeds + 255) / 256, 256, 0, st>>>(p);

@@ -123,6 +123,7 @@ def lib():
                                 C.POINTER(ds_tracks), P], C.c_int),
             "ds_vertex": ([P, C.POINTER(ds_tracks), C.POINTER(ds_vertices), P], C.c_int),
             "ds_sync_status": ([P, P, C.POINTER(ds_stats)], C.c_int),
+            "ds_mlp_eval": ([P, P, C.c_int32, P, C.c_int32, P], C.c_int),
             "ds_reconstruct_noalloc": ([C.POINTER(ds_geometry), C.POINTER(ds_params), C.POINTER(ds_nn_weights),
                                         C.POINTER(ds_event_batch), C.POINTER(ds_seeds), C.POINTER(ds_ut_hits),
                                         C.POINTER(ds_tracks), P, P], C.c_int),
@@ -142,7 +143,7 @@ def lib():
 EXPORTED = ("ds_create", "ds_destroy", "ds_status_string", "ds_last_error", "ds_default_params",
             "ds_load_geometry", "ds_load_nn_weights", "ds_set_params", "ds_reserve", "ds_reconstruct",
             "ds_vertex", "ds_sync_status", "ds_process_host", "ds_profile_enable", "ds_profile_read",
-            "ds_reconstruct_noalloc")
+            "ds_reconstruct_noalloc", "ds_mlp_eval")
 
 
 # --------------------------------------------------------------- C names, marshalled
@@ -264,6 +265,17 @@ def ds_vertex(ctx, trk_out: dict, vout: dict, stream=None):
                      int(vout["vertices"].shape[0]), 0)
     _check(ctx, lib().ds_vertex(ctx, C.byref(tr), C.byref(vx), _stream(stream)), "ds_vertex")
     return vx
+
+
+def ds_mlp_eval(ctx, features, logit, precision: int, stream=None):
+    """features: device float32 [n, 16] (contiguous); logit: device float32 [n]."""
+    n = int(features.shape[0])
+    if n and (features.dtype.itemsize != 4 or not features.is_contiguous() or tuple(features.shape[1:]) != (16,)):
+        raise ValueError("features must be a contiguous float32 [n, 16] tensor")
+    if int(logit.numel()) < n:
+        raise ValueError("logit holds fewer than n values")
+    _check(ctx, lib().ds_mlp_eval(ctx, _ptr(features), n, _ptr(logit), int(precision), _stream(stream)),
+           "ds_mlp_eval")
 
 
 def ds_sync_status(ctx, stream=None, raise_on_error: bool = True):
@@ -399,6 +411,13 @@ class Downstream:
 
     def sync(self, stream=None, raise_on_error=True):
         return ds_sync_status(self.ctx, stream, raise_on_error)
+
+    def mlp_eval(self, features, precision: int = 0, stream=None):
+        """Network output before the sigmoid for device features [n, 16]."""
+        t = self.torch
+        logit = t.empty(features.shape[0], dtype=t.float32, device=features.device)
+        ds_mlp_eval(self.ctx, features, logit, precision, stream)
+        return logit
 
     def run(self, batch: dict, trk_capacity=None, vtx_capacity=None, dev=None):
         """Upload, reconstruct, vertex, synchronise and decode (host numpy)."""
