@@ -223,6 +223,26 @@ typedef struct {
     double total_ms;          /* sum of CUDA-event durations on the launching stream */
 } ds_kernel_time;
 
+/* Launch shape of the search kernel.  The paper fixes a block per event
+ * (GPU Implementation section); here work items are chunks of one event's
+ * seeds pulled from a device queue by persistent CTAs, and their shape is a
+ * run-time choice that changes speed only: outputs are identical for every
+ * valid tuning. */
+typedef struct {
+    int32_t search_chunk;       /* max seeds per work item, 1..128 (default 128) */
+    int32_t search_ctas_per_sm; /* persistent search CTAs per SM, 1..4 (default 4) */
+    int32_t search_group;       /* consecutive work items per queue pull, 1..16 (default 2) */
+    int32_t search_stage_hits;  /* events with at most this many hits have their x0 array
+                                   staged in shared memory, 0..47104 (default 5632);
+                                   larger events read it from global memory */
+} ds_tuning;
+
+/* One configuration measured by ds_autotune. */
+typedef struct {
+    ds_tuning tuning;
+    double ms;                  /* mean ds_reconstruct time on the tuning batch */
+} ds_tune_entry;
+
 /* ------------------------------------------------------------------ lifetime */
 
 /* Create a context on CUDA device `device`.  *out receives the handle. */
@@ -322,6 +342,23 @@ DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, const ds_params
  * records per launch; leave it off for throughput measurements. */
 DS_API ds_status ds_profile_enable(ds_ctx *ctx, int32_t enable);
 DS_API ds_status ds_profile_read(ds_ctx *ctx, ds_kernel_time *out, int32_t max_out, int32_t *n_out);
+
+/* Current tuning of the context / replace it (DS_ERR_ARG outside the ranges
+ * above; nothing changed then).  Applies to later ds_reconstruct calls. */
+DS_API ds_status ds_get_tuning(ds_ctx *ctx, ds_tuning *out);
+DS_API ds_status ds_set_tuning(ds_ctx *ctx, const ds_tuning *t);
+
+/* Autotuner: times ds_reconstruct on the caller's batch (device inputs as for
+ * ds_reconstruct; `out` receives the tracks of the last run) for candidate
+ * tunings by coordinate descent over stage size, chunk size, CTAs per SM and
+ * queue group (two sweeps, each configuration run `reps` times after one
+ * warm-up run, CUDA events on `stream`), keeps the fastest in the context and
+ * copies it to *best.  Every configuration measured is written to entries
+ * (at most max_entries; *n_entries = number measured).  Synchronous; must not
+ * be called while `stream` is being captured.  Errors as ds_reconstruct. */
+DS_API ds_status ds_autotune(ds_ctx *ctx, const ds_event_batch *batch, const ds_seeds *seeds,
+                             const ds_ut_hits *hits, ds_tracks *out, int32_t reps, ds_tuning *best,
+                             ds_tune_entry *entries, int32_t max_entries, int32_t *n_entries, void *stream);
 
 /* End-to-end call with HOST buffers: copies the batch to context-owned device
  * buffers, runs ds_reconstruct and ds_vertex, copies tracks, trk_off, vertices

@@ -9,6 +9,16 @@
 
 #include "ds_args.cuh"
 
+static constexpr ds_tuning kDefaultTuning = {ds::kSearchThreads, ds::kSearchCtasPerSm, ds::kSearchGroup,
+                                             ds::kStageHits};
+
+static bool tuning_valid(const ds_tuning &t)
+{
+    return t.search_chunk >= 1 && t.search_chunk <= ds::kSearchThreads && t.search_ctas_per_sm >= 1 &&
+           t.search_ctas_per_sm <= 4 && t.search_group >= 1 && t.search_group <= 16 &&
+           t.search_stage_hits >= 0 && t.search_stage_hits <= ds::kStageHitsMax;
+}
+
 struct ds_ctx {
     int device = 0;
     int sm_count = 148;
@@ -19,6 +29,7 @@ struct ds_ctx {
     int nn_in = 16, nn_h1 = 32, nn_h2 = 32;
     int mlp_precision = DS_MLP_FP32;
     ds::MlpTcWeights *d_tc = nullptr;    // tensor-core weight tiles (BF16 / FP8 network)
+    ds_tuning tune{kDefaultTuning};
     ds::DevCounters *d_cnt = nullptr;
     // workspaces
     int cap_events = 0, cap_seeds = 0, cap_hits = 0, cap_pool = 0;
@@ -452,6 +463,7 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     ba.bins = ctx->bins;
     ba.item_cnt = ctx->item_cnt;
     ba.item_off = ctx->item_off;
+    ba.chunk = ctx->tune.search_chunk;
     ba.cnt = ctx->d_cnt;
     DS_CUDA(ds::launch_bucket(ba, st, &ctx->prof), "bucket kernel");
 
@@ -474,6 +486,9 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     sa.seed_cand = ctx->seed_cand;
     sa.rank_ws = ctx->rank_ws;
     sa.sm_count = ctx->sm_count;
+    sa.ctas_per_sm = ctx->tune.search_ctas_per_sm;
+    sa.group = ctx->tune.search_group;
+    sa.stage_hits = ctx->tune.search_stage_hits;
     sa.cnt = ctx->d_cnt;
     DS_CUDA(ds::launch_search(sa, st, &ctx->prof), "search kernel");
 
@@ -639,6 +654,91 @@ ds_status ds_sync_status(ds_ctx *ctx, void *stream, ds_stats *stats)
     if (c.flags & (DS_FLAG_TRACK_CAPACITY | DS_FLAG_VERTEX_CAPACITY | DS_FLAG_CAND_CAPACITY))
         return fail(ctx, DS_ERR_CAPACITY, "output capacity exceeded");
     return DS_OK;
+}
+
+ds_status ds_get_tuning(ds_ctx *ctx, ds_tuning *out)
+{
+    if (!ctx || !out) return fail(ctx, DS_ERR_ARG, "null pointer");
+    *out = ctx->tune;
+    return DS_OK;
+}
+
+ds_status ds_set_tuning(ds_ctx *ctx, const ds_tuning *t)
+{
+    if (!ctx || !t) return fail(ctx, DS_ERR_ARG, "null pointer");
+    if (!tuning_valid(*t)) return fail(ctx, DS_ERR_ARG, "tuning outside its ranges");
+    ctx->tune = *t;
+    return DS_OK;
+}
+
+ds_status ds_autotune(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *sd, const ds_ut_hits *ht,
+                      ds_tracks *out, int32_t reps, ds_tuning *best, ds_tune_entry *entries, int32_t max_entries,
+                      int32_t *n_entries, void *stream)
+{
+    if (!ctx || !b || !sd || !ht || !out || reps < 1 || max_entries < 0 || (max_entries > 0 && !entries))
+        return fail(ctx, DS_ERR_ARG, "null pointer or bad count");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (stream_capturing(st)) return fail(ctx, DS_ERR_ARG, "ds_autotune during stream capture");
+    DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    cudaEvent_t e0, e1;
+    DS_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, DS_ERR_CUDA, "cudaEventCreate");
+    }
+    const bool prof_on = ctx->prof.on;
+    ctx->prof.on = false;
+    int n = 0;
+    ds_status rs = DS_OK;
+    auto measure = [&](const ds_tuning &t, double *ms) -> ds_status {
+        ctx->tune = t;
+        ds_status s = ds_reconstruct(ctx, b, sd, ht, out, stream);   // warm-up (and workspace growth)
+        if (s != DS_OK) return s;
+        if (cudaEventRecord(e0, st) != cudaSuccess) return fail(ctx, DS_ERR_CUDA, "cudaEventRecord");
+        for (int r = 0; r < reps; ++r)
+            if ((s = ds_reconstruct(ctx, b, sd, ht, out, stream)) != DS_OK) return s;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+            return fail(ctx, DS_ERR_CUDA, "timing event");
+        float f = 0.f;
+        cudaEventElapsedTime(&f, e0, e1);
+        *ms = (double)f / reps;
+        if (n < max_entries) entries[n] = ds_tune_entry{t, *ms};
+        ++n;
+        return DS_OK;
+    };
+    ds_tuning cur = ctx->tune;
+    double cur_ms = 0.0;
+    rs = measure(cur, &cur_ms);
+    static const int stage_opts[] = {2048, 5632, 8192, 12288, 16384, 24576, 32768};
+    static const int chunk_opts[] = {32, 64, 96, 128};
+    static const int ctas_opts[] = {1, 2, 3, 4};
+    static const int group_opts[] = {1, 2, 4, 8};
+    for (int sweep = 0; sweep < 2 && rs == DS_OK; ++sweep) {
+        for (int dim = 0; dim < 4 && rs == DS_OK; ++dim) {
+            const int *opts = dim == 0 ? stage_opts : dim == 1 ? chunk_opts : dim == 2 ? ctas_opts : group_opts;
+            const int n_opts = dim == 0 ? 7 : 4;
+            for (int k = 0; k < n_opts && rs == DS_OK; ++k) {
+                ds_tuning t = cur;
+                int32_t *field = dim == 0 ? &t.search_stage_hits : dim == 1 ? &t.search_chunk
+                                 : dim == 2 ? &t.search_ctas_per_sm : &t.search_group;
+                if (*field == opts[k]) continue;
+                *field = opts[k];
+                double ms = 0.0;
+                rs = measure(t, &ms);
+                if (rs == DS_OK && ms < cur_ms) {
+                    cur = t;
+                    cur_ms = ms;
+                }
+            }
+        }
+    }
+    ctx->tune = cur;
+    ctx->prof.on = prof_on;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_entries) *n_entries = n;
+    if (best) *best = cur;
+    return rs;
 }
 
 ds_status ds_profile_enable(ds_ctx *ctx, int32_t enable)

@@ -34,6 +34,7 @@ struct BucketArgs {
     uint16_t *bins;
     int *item_cnt;         // per event: search chunks
     int *item_off;         // [n_events + 1]
+    int chunk;             // max seeds per search work item (<= kSearchThreads)
     DevCounters *cnt;
 };
 
@@ -55,6 +56,9 @@ struct SearchArgs {
     int4 *seed_cand;       // per seed: first candidate, count, event
     int *rank_ws;
     int sm_count;
+    int ctas_per_sm;       // persistent CTAs per SM
+    int group;             // work items per queue pull
+    int stage_hits;        // events with at most this many hits are staged in shared memory
     DevCounters *cnt;
 };
 

@@ -132,6 +132,7 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         ba.bins = reinterpret_cast<uint16_t *>(base + kOffBins);
         ba.item_cnt = reinterpret_cast<int *>(base + kOffItemCnt);
         ba.item_off = reinterpret_cast<int *>(base + kOffItemOff);
+        ba.chunk = kSearchThreads;
         ba.cnt = cnt;
         if (launch_bucket(ba, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
 
@@ -154,6 +155,9 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         sa.seed_cand = reinterpret_cast<int4 *>(base + kOffSeedCand);
         sa.rank_ws = reinterpret_cast<int *>(base + kOffRank);
         sa.sm_count = sm_count;
+        sa.ctas_per_sm = kSearchCtasPerSm;
+        sa.group = kSearchGroup;
+        sa.stage_hits = kStageHits;
         sa.cnt = cnt;
         if (launch_search(sa, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
 

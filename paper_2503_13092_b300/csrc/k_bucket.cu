@@ -12,7 +12,7 @@
 // offsets (written out as the event's bin table), pass 2 scatters float4
 // {x0, ybeg, yend, id} records and a compact x0 array in the same order.  The
 // last CTA also turns per-event seed counts into the search kernel's work
-// items (chunks of at most 128 seeds of one event).  The order inside a bin comes
+// items (chunks of at most `chunk` <= 128 seeds of one event).  The order inside a bin comes
 // from atomics and is not deterministic; every consumer ranks hits by
 // (|dx|, id), which does not depend on it.
 #include "ds_args.cuh"
@@ -139,12 +139,12 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
         }
     }
 
-    // search work items of this event: chunks of at most kSearchThreads seeds;
+    // search work items of this event: chunks of at most a.chunk seeds;
     // the last CTA to finish scans them into item_off
     if (threadIdx.x == 0) {
         const int s0 = __ldg(a.seed_off + e), s1 = __ldg(a.seed_off + e + 1);
         const int ns = (s0 < 0 || s1 < s0 || s1 > a.n_seeds) ? 0 : s1 - s0;
-        a.item_cnt[e] = (ns + kSearchThreads - 1) / kSearchThreads;
+        a.item_cnt[e] = (ns + a.chunk - 1) / a.chunk;
         __threadfence();
         const unsigned int t = atomicAdd(&a.cnt->done_bkt, 1u);
         s_last = t == gridDim.x - 1;

@@ -255,12 +255,12 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     uint32_t phase = 0;
     const int limit = P.fault_inject ? 1024 : kWaitLimit;
     for (;;) {
-    if (tid == 0) s_item[0] = atomicAdd(&a.cnt->search_queue, kSearchGroup);
+    if (tid == 0) s_item[0] = atomicAdd(&a.cnt->search_queue, a.group);
     __syncthreads();
     const int b_first = s_item[0];
     __syncthreads();
     if (b_first >= n_items) break;
-    for (int bi = b_first; bi < b_first + kSearchGroup && bi < n_items; ++bi) {
+    for (int bi = b_first; bi < b_first + a.group && bi < n_items; ++bi) {
     // work item: chunk k of event e's seeds (sizes differ by at most one)
     if (tid == 0) {
         const int e = find_segment(a.item_off, a.n_events, bi);
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
 
     // stage the event's bin table and (if it fits) its x0 array with two bulk
     // copies (TMA); the x0 copy starts at the 16-byte boundary below h0
-    const bool staged = nh <= kStageHits;
+    const bool staged = nh <= a.stage_hits;
     const int lead = h0 & 3;
     const float *X0 = staged ? xs + lead : a.sx0 + h0;
     const bool restage = s_item[3] != e;
@@ -467,8 +467,15 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
 cudaError_t init_search_attributes()
 {
     // shared memory, not L1, limits residency: ask for the largest carveout
-    const int smem = (int)(sizeof(uint16_t) * (((4 * kMaxSectors * kNXB + 1) + 7) & ~7) + sizeof(float) * (kStageHits + 4));
-    cudaError_t e = cudaFuncSetAttribute(k_search, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    const int smem = (int)(sizeof(uint16_t) * (((4 * kMaxSectors * kNXB + 1) + 7) & ~7) + sizeof(float) * (kStageHitsMax + 4));
+    cudaFuncAttributes fa;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_search);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if ((size_t)smem + fa.sharedSizeBytes > (size_t)optin) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(k_search, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
@@ -476,11 +483,13 @@ cudaError_t init_search_attributes()
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
 {
     if (a.n_seeds <= 0) return cudaSuccess;
-    // persistent: kSearchCtasPerSm CTAs per SM pull work items from a queue
-    const int items_max = (a.n_seeds + T - 1) / T + a.n_events;
-    int grid = a.sm_count * kSearchCtasPerSm;
+    // persistent: ctas_per_sm CTAs per SM pull work items from a queue
+    if (a.group < 1 || a.ctas_per_sm < 1 || a.stage_hits < 0 || a.stage_hits > kStageHitsMax)
+        return cudaErrorInvalidValue;
+    const int items_max = a.n_seeds + a.n_events;
+    int grid = a.sm_count * a.ctas_per_sm;
     if (grid > items_max) grid = items_max;
-    const size_t smem = sizeof(uint16_t) * a.g.table_stride + sizeof(float) * (kStageHits + 4);
+    const size_t smem = sizeof(uint16_t) * a.g.table_stride + sizeof(float) * (a.stage_hits + 4);
     prof->begin("k_search", st);
     k_search<<<grid, T, smem, st>>>(a);
     prof->end(st);

@@ -85,6 +85,18 @@ class ds_kernel_time(C.Structure):
                 ("total_ms", C.c_double)]
 
 
+class ds_tuning(C.Structure):
+    _fields_ = [("search_chunk", C.c_int32), ("search_ctas_per_sm", C.c_int32), ("search_group", C.c_int32),
+                ("search_stage_hits", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ds_tune_entry(C.Structure):
+    _fields_ = [("tuning", ds_tuning), ("ms", C.c_double)]
+
+
 TRACK_DTYPE = np.dtype([("event", "<i4"), ("seed", "<i4"), ("hit", "<i4", 4), ("x", "<f4"), ("y", "<f4"),
                         ("tx", "<f4"), ("ty", "<f4"), ("qop", "<f4"), ("chi2", "<f4"), ("ndof", "<i4"),
                         ("nn", "<f4"), ("flags", "<u4"), ("n_candidates", "<i4")])
@@ -124,6 +136,11 @@ def lib():
             "ds_vertex": ([P, C.POINTER(ds_tracks), C.POINTER(ds_vertices), P], C.c_int),
             "ds_sync_status": ([P, P, C.POINTER(ds_stats)], C.c_int),
             "ds_mlp_eval": ([P, P, C.c_int32, P, C.c_int32, P], C.c_int),
+            "ds_get_tuning": ([P, C.POINTER(ds_tuning)], C.c_int),
+            "ds_set_tuning": ([P, C.POINTER(ds_tuning)], C.c_int),
+            "ds_autotune": ([P, C.POINTER(ds_event_batch), C.POINTER(ds_seeds), C.POINTER(ds_ut_hits),
+                             C.POINTER(ds_tracks), C.c_int32, C.POINTER(ds_tuning), C.POINTER(ds_tune_entry),
+                             C.c_int32, C.POINTER(C.c_int32), P], C.c_int),
             "ds_reconstruct_noalloc": ([C.POINTER(ds_geometry), C.POINTER(ds_params), C.POINTER(ds_nn_weights),
                                         C.POINTER(ds_event_batch), C.POINTER(ds_seeds), C.POINTER(ds_ut_hits),
                                         C.POINTER(ds_tracks), P, P], C.c_int),
@@ -143,7 +160,7 @@ def lib():
 EXPORTED = ("ds_create", "ds_destroy", "ds_status_string", "ds_last_error", "ds_default_params",
             "ds_load_geometry", "ds_load_nn_weights", "ds_set_params", "ds_reserve", "ds_reconstruct",
             "ds_vertex", "ds_sync_status", "ds_process_host", "ds_profile_enable", "ds_profile_read",
-            "ds_reconstruct_noalloc", "ds_mlp_eval")
+            "ds_reconstruct_noalloc", "ds_mlp_eval", "ds_get_tuning", "ds_set_tuning", "ds_autotune")
 
 
 # --------------------------------------------------------------- C names, marshalled
@@ -276,6 +293,33 @@ def ds_mlp_eval(ctx, features, logit, precision: int, stream=None):
         raise ValueError("logit holds fewer than n values")
     _check(ctx, lib().ds_mlp_eval(ctx, _ptr(features), n, _ptr(logit), int(precision), _stream(stream)),
            "ds_mlp_eval")
+
+
+def ds_get_tuning(ctx) -> ds_tuning:
+    t = ds_tuning()
+    _check(ctx, lib().ds_get_tuning(ctx, C.byref(t)), "ds_get_tuning")
+    return t
+
+
+def ds_set_tuning(ctx, t: ds_tuning):
+    return _check(ctx, lib().ds_set_tuning(ctx, C.byref(t)), "ds_set_tuning")
+
+
+def ds_autotune(ctx, dev: dict, out: dict, reps: int = 3, stream=None, max_entries: int = 64):
+    """Autotune the search launch shape on this batch; returns (best, [(tuning dict, ms), ...])."""
+    b = ds_event_batch(dev["n_events"], dev["n_seeds"], dev["n_hits"], 0, _ptr(dev["seed_off"]),
+                       _ptr(dev["hit_off"]))
+    sd = ds_seeds(*[_ptr(dev[k]) for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2")])
+    ht = ds_ut_hits(*[_ptr(dev[k]) for k in ("hit_x0", "hit_ybeg", "hit_yend", "hit_layer")])
+    tr = ds_tracks(_ptr(out["tracks"]), _ptr(out["trk_off"]), _ptr(out["n_tracks"]),
+                   int(out["tracks"].shape[0]), 0)
+    best = ds_tuning()
+    ent = (ds_tune_entry * max_entries)()
+    n = C.c_int32(0)
+    _check(ctx, lib().ds_autotune(ctx, C.byref(b), C.byref(sd), C.byref(ht), C.byref(tr), int(reps), C.byref(best),
+                                  ent, max_entries, C.byref(n), _stream(stream)), "ds_autotune")
+    out["_struct"] = tr
+    return best, [(ent[i].tuning.as_dict(), ent[i].ms) for i in range(min(n.value, max_entries))]
 
 
 def ds_sync_status(ctx, stream=None, raise_on_error: bool = True):

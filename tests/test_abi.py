@@ -45,7 +45,8 @@ def test_library_exports_every_declared_symbol(libpath):
 def test_struct_layout_matches_header(tmp_path):
     structs = {"ds_geometry": ds.ds_geometry, "ds_nn_weights": ds.ds_nn_weights, "ds_params": ds.ds_params,
                "ds_event_batch": ds.ds_event_batch, "ds_seeds": ds.ds_seeds, "ds_ut_hits": ds.ds_ut_hits,
-               "ds_tracks": ds.ds_tracks, "ds_vertices": ds.ds_vertices, "ds_stats": ds.ds_stats}
+               "ds_tracks": ds.ds_tracks, "ds_vertices": ds.ds_vertices, "ds_stats": ds.ds_stats,
+               "ds_kernel_time": ds.ds_kernel_time, "ds_tuning": ds.ds_tuning, "ds_tune_entry": ds.ds_tune_entry}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ds.h"', 'int main(void){']
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')

@@ -1,0 +1,100 @@
+"""Search launch shape (ds_tuning) and the autotuner: outputs must not depend on
+the tuning (bit-identical tracks and vertices), invalid tunings are refused,
+and the autotuner leaves a valid tuning in the context."""
+import numpy as np
+import pytest
+
+from paper_2503_13092_b300 import synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_13092_b300 import build
+    build.build()
+    return torch
+
+
+def mixed_batch():
+    """C2 events and uneven C3 events (up to 30000 hits: staged and unstaged paths)."""
+    b2 = synth.config_batch("c2", seed=4, n_events=40)
+    b3 = synth.config_batch("c3", seed=3, n_events=300)
+    big = np.argsort(np.diff(b3["hit_off"]))[-30:]
+    small = np.arange(20)
+    p3 = parity.sub_batch(b3, np.concatenate([small, np.sort(big)]))
+    p2 = parity.sub_batch(b2, range(40))
+    out = dict(n_events=p2["n_events"] + p3["n_events"], mode="A")
+    out["seed_off"] = np.concatenate([p2["seed_off"], p2["seed_off"][-1] + p3["seed_off"][1:]]).astype(np.int32)
+    out["hit_off"] = np.concatenate([p2["hit_off"], p2["hit_off"][-1] + p3["hit_off"][1:]]).astype(np.int32)
+    for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2", "hit_x0", "hit_ybeg", "hit_yend",
+              "hit_layer"):
+        out[k] = np.concatenate([p2[k], p3[k]])
+    return out
+
+
+def run_with(d, ds, dev, tuning):
+    ds.ds_set_tuning(d.ctx, tuning)
+    out = d.alloc_tracks(dev["n_events"], dev["n_seeds"])
+    d.reconstruct(dev, out)
+    vout = d.alloc_vertices(dev["n_events"], 64 * dev["n_seeds"] + 4096)
+    d.vertex(out, vout)
+    st = d.sync()
+    n_t, n_v = int(out["n_tracks"].cpu()[0]), int(vout["n_vertices"].cpu()[0])
+    return (st, out["tracks"][:n_t].cpu().numpy().tobytes(), out["trk_off"].cpu().numpy().tobytes(),
+            vout["vertices"][:n_v].cpu().numpy().tobytes(), vout["vtx_off"].cpu().numpy().tobytes())
+
+
+def test_outputs_do_not_depend_on_tuning(torch_cuda, weights):
+    from paper_2503_13092_b300 import ds
+    b = mixed_batch()
+    assert np.diff(b["hit_off"]).max() > 2 * 5632      # larger than the default staging buffer
+    d = ds.Downstream(synth.default_config(), weights)
+    dev = d.to_device(b)
+    shapes = [(128, 4, 2, 5632), (32, 1, 1, 0), (64, 3, 8, 32768), (1, 2, 16, 2048), (96, 4, 4, 47104)]
+    ref = None
+    for chunk, ctas, group, stage in shapes:
+        t = ds.ds_tuning(chunk, ctas, group, stage)
+        r = run_with(d, ds, dev, t)
+        assert r[0]["status"] == 0, (t.as_dict(), r[0])
+        assert r[0]["n_tracks"] > 0
+        if ref is None:
+            ref = r
+        else:
+            assert r[1:] == ref[1:], t.as_dict()
+
+
+def test_invalid_tuning_refused(torch_cuda, weights):
+    from paper_2503_13092_b300 import ds
+    d = ds.Downstream(synth.default_config(), weights)
+    before = ds.ds_get_tuning(d.ctx).as_dict()
+    for bad in [(0, 4, 2, 5632), (129, 4, 2, 5632), (128, 0, 2, 5632), (128, 5, 2, 5632), (128, 4, 0, 5632),
+                (128, 4, 17, 5632), (128, 4, 2, -1), (128, 4, 2, 47105)]:
+        with pytest.raises(ds.DSError):
+            ds.ds_set_tuning(d.ctx, ds.ds_tuning(*bad))
+    assert ds.ds_get_tuning(d.ctx).as_dict() == before
+
+
+def test_autotune(torch_cuda, weights):
+    from paper_2503_13092_b300 import ds
+    b = mixed_batch()
+    d = ds.Downstream(synth.default_config(), weights)
+    dev = d.to_device(b)
+    ref = run_with(d, ds, dev, ds.ds_tuning(128, 4, 2, 5632))
+    out = d.alloc_tracks(dev["n_events"], dev["n_seeds"])
+    best, entries = ds.ds_autotune(d.ctx, dev, out, reps=2)
+    d.sync()
+    # coordinate descent from the default: one measurement, then two sweeps over
+    # 7 stage sizes, 4 chunks, 4 CTA counts and 4 groups, each skipping the value
+    # current when it is reached
+    assert 1 + 2 * (6 + 3 + 3 + 3) <= len(entries) <= 1 + 2 * (7 + 4 + 4 + 4)
+    assert all(ms > 0 for _, ms in entries)
+    cur = ds.ds_get_tuning(d.ctx).as_dict()
+    assert cur == best.as_dict()
+    assert min(ms for t, ms in entries if t == cur) == min(ms for _, ms in entries)
+    got = run_with(d, ds, dev, best)
+    assert got[1:] == ref[1:]
