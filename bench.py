@@ -341,6 +341,161 @@ def bench_c3(ds, torch, cfg, w, steps, warmup, dev_index):
     return res
 
 
+def bench_c5(ds, torch, cfg, w, dev_index, n_requests=1000):
+    """Config 5: the serving loop under Poisson arrivals of requests of 1-500
+    events of config-1 occupancy, latency counted from each request's arrival
+    to its results on the host (uploads and downloads included).  The batched
+    form (continuous batching, 4 slots, BF16 tensor-core ghost killer) is set
+    against the plain form (one request at a time, one event per launch,
+    FP32) on the same requests."""
+    from paper_2503_13092_b300 import synth
+    pool = synth.c5_pool(4000, seed=5)
+    for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2", "hit_x0", "hit_ybeg", "hit_yend",
+              "hit_layer"):
+        pool[k] = torch.from_numpy(np.ascontiguousarray(pool[k])).pin_memory().numpy()
+    sizes, starts, gaps = synth.c5_trace(n_requests, 1.0, pool["n_events"], seed=5)
+    reqs = [synth.slice_events(pool, int(a), int(a + k)) for k, a in zip(sizes, starts)]
+    ev = np.array([r["n_events"] for r in reqs])
+
+    def truth(res, r):
+        """(true seeds, found with >= 3 hits of their own track, tracks kept)."""
+        st = r["seed_track"]; ht = r["hit_track"]
+        t = res["tracks"]
+        tid = st[t["seed"]]
+        h = t["hit"]
+        own = (h >= 0) & (ht[np.clip(h, 0, None)] == tid[:, None])
+        good = int(np.sum((tid >= 0) & (own.sum(1) >= 3)))
+        return int(np.sum(st >= 0)), good, len(t)
+
+    max_s = int(max(int(r["seed_off"][-1]) for r in reqs))
+
+    def pinned(n, dtype):
+        t = torch.empty(n * np.dtype(dtype).itemsize, dtype=torch.uint8, pin_memory=True)
+        return t.numpy().view(dtype)
+
+    # output buffers sized for the largest request, recycled as requests complete
+    out_sets = [dict(tracks=pinned(max_s, ds.TRACK_DTYPE), vertices=pinned(2 * max_s + 4096, ds.VERTEX_DTYPE))
+                for _ in range(96)]
+
+    def serve(config, idx, arrivals=None, window=64, accuracy=False):
+        """arrivals None: closed loop, `window` requests outstanding (capacity);
+        else open loop: each request is submitted at its arrival time by a
+        submitter thread."""
+        import threading
+        srv = ds.Server(cfg, w, device=dev_index, **config)
+        ids, got, acc, holding = {}, {}, [], {}
+        free = list(range(len(out_sets)))
+        lock = threading.Lock()
+
+        def submit(i, arrival=0.0):
+            k = free.pop() if free else None
+            if k is None:                      # more outstanding than buffer sets
+                o = srv.alloc_outputs(reqs[i], vtx_capacity=2 * int(reqs[i]["seed_off"][-1]) + 4096)
+            else:
+                o = dict(out_sets[k])
+            E = int(reqs[i]["n_events"])
+            o["trk_off"] = np.zeros(E + 1, np.int32)
+            o["vtx_off"] = np.zeros(E + 1, np.int32)
+            rid = srv.submit(reqs[i], arrival=arrival, out=o)
+            ids[rid] = i
+            holding[rid] = k
+
+        def take(cs):
+            for c in cs:
+                i = ids[c["id"]]
+                if accuracy:
+                    acc.append(truth(c, reqs[i]))
+                c.pop("tracks"); c.pop("vertices")
+                got[c["id"]] = c
+                k = holding.pop(c["id"])
+                if k is not None:
+                    free.append(k)
+
+        t_start = srv.now()
+        if arrivals is None:
+            todo = list(idx)
+            with lock:
+                for i in todo[:window]:
+                    submit(i)
+            todo = todo[window:]
+            while len(got) < len(idx):
+                cs = srv.poll(timeout=1.0)
+                with lock:
+                    take(cs)
+                    for _ in cs:
+                        if todo:
+                            submit(todo.pop(0))
+            t_first = t_start
+        else:
+            t0 = srv.now() + 0.05
+            t_first = t0 + float(arrivals[0])
+
+            def submitter():
+                for i, a in zip(idx, arrivals):
+                    wait = t0 + a - 1e-3 - srv.now()
+                    if wait > 0:
+                        time.sleep(wait)
+                    with lock:
+                        submit(i, arrival=t0 + a)
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            while len(got) < len(idx):
+                cs = srv.poll(timeout=1.0)
+                with lock:
+                    take(cs)
+            th.join()
+        st = srv.stats()
+        srv.close()
+        lat = np.array([got[k]["t_done"] - got[k]["t_arrival"] for k in ids])
+        n_ev = int(sum(ev[i] for i in idx))
+        span = max(c["t_done"] for c in got.values()) - t_first
+        ev_lat = np.repeat(lat, [ev[ids[k]] for k in ids])
+        res = dict(requests=len(idx), events=n_ev, events_per_s=n_ev / span,
+                   p50_ms=1e3 * float(np.percentile(lat, 50)), p99_ms=1e3 * float(np.percentile(lat, 99)),
+                   event_p50_ms=1e3 * float(np.percentile(ev_lat, 50)),
+                   event_p99_ms=1e3 * float(np.percentile(ev_lat, 99)),
+                   batches=st["batches"], peak_inflight=st["peak_inflight"], hbm_peak_mb=st["hbm_peak"] / 2**20,
+                   worker_busy=(st["worker_launch_s"] + st["worker_finish_s"]) / max(st["worker_wall_s"], 1e-9),
+                   status_ok=all(c["status"] == 0 for c in got.values()))
+        if arrivals is None:
+            res["outstanding"] = window
+        if accuracy:
+            tot = np.array(acc).sum(0)
+            res.update(efficiency=tot[1] / max(tot[0], 1), true_track_fraction=tot[1] / max(tot[2], 1))
+        return res
+
+    batched_cfg = dict(n_slots=4, max_batch_events=1024, max_batch_seeds=1024 * 200, max_batch_hits=1024 * 1500,
+                       mlp_precision=ds.DS_MLP_BF16)
+    plain_cfg = dict(n_slots=1, max_batch_events=1, max_batch_seeds=4096, max_batch_hits=65535, events_per_launch=1,
+                     mlp_precision=ds.DS_MLP_FP32)
+    all_idx = np.arange(n_requests)
+    burst = serve(batched_cfg, all_idx, accuracy=True)
+    cap = burst["events_per_s"]
+    mean_ev = float(ev.mean())
+    loads = {}
+    for f in (0.3, 0.6, 0.9):
+        rate = f * cap / mean_ev
+        loads[f"{f:.1f}"] = dict(offered_events_per_s=f * cap, **serve(batched_cfg, all_idx, gaps / rate))
+    n_plain = 24
+    p_idx = all_idx[:n_plain]
+    plain_burst = serve(plain_cfg, p_idx, window=4, accuracy=True)
+    pcap = plain_burst["events_per_s"]
+    mean_p = float(ev[p_idx].mean())
+    plain_loaded = dict(offered_events_per_s=0.6 * pcap,
+                        **serve(plain_cfg, p_idx, gaps[:n_plain] / (0.6 * pcap / mean_p)))
+    batched_same = dict(offered_events_per_s=0.6 * pcap,
+                        **serve(batched_cfg, p_idx, gaps[:n_plain] / (0.6 * pcap / mean_p)))
+    return dict(workload="C5: Poisson arrivals, requests of 1-500 events of config-1 occupancy "
+                         "(200 seeds, ~1500 UT hits per event), pinned host inputs",
+                batched=dict(form="continuous batching, 4 slots, batches <= 1024 events, BF16 tensor-core ghost killer",
+                             capacity=burst, loads=loads, at_plain_load=batched_same),
+                plain=dict(form="one request at a time, one event per launch, FP32",
+                           capacity=plain_burst, load_0_6=plain_loaded),
+                note="latency = results on the host minus the request's arrival; capacity from a closed loop "
+                     "with a fixed number of requests outstanding; loads (open loop, Poisson) as fractions of it")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,6 +509,7 @@ def main():
                     help="profiling run: warmup + steps eager steps on one batch, nothing else")
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--no-c3", action="store_true", help="skip the config-3 (log-normal, 10000 events) leg")
+    ap.add_argument("--no-c5", action="store_true", help="skip the config-5 (serving loop) leg")
     ap.add_argument("--mlp-precision", default="fp32", choices=["fp32", "bf16", "fp8"],
                     help="ghost-killer arithmetic in the --ncu profiling run")
     args = ap.parse_args()
@@ -567,6 +723,10 @@ def main():
     if not args.no_c3:
         c3 = bench_c3(ds, torch, cfg, w, min(args.steps, 10), args.warmup, dev_index)
 
+    c5 = None
+    if not args.no_c5:
+        c5 = bench_c5(ds, torch, cfg, w, dev_index)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(batch, cfg, w)
@@ -581,7 +741,7 @@ def main():
                         l2=f"inputs rotate over {R} replicas ({R * in_bytes / 2**20:.0f} MB > 3x L2)",
                         parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
             roofline=roof, path_roofline=path, kernels=kernels, clocks=clocks, e2e=e2e, mlp_forms=mlp_forms,
-            c3=c3,
+            c3=c3, c5=c5,
             plain_form=dict(value=n_plain / plain_s, unit="events/s",
                             note="one event per ds_reconstruct + ds_vertex call, FP32", events=n_plain),
             eager=dict(value=ws * E * args.steps / eager_s, unit="events/s",

@@ -269,6 +269,11 @@ DS_API ds_status ds_set_params(ds_ctx *ctx, const ds_params *p);
 /* Size the workspaces for batches up to these totals (synchronous allocation).
  * Calls on larger batches grow the workspaces themselves. */
 DS_API ds_status ds_reserve(ds_ctx *ctx, int32_t max_events, int32_t max_seeds, int32_t max_hits);
+/* Size the vertexing workspace for outputs of up to `capacity` vertices
+ * (synchronous allocation).  ds_vertex grows it itself outside stream capture;
+ * call this first to capture ds_vertex in a CUDA graph or to keep allocations
+ * out of a serving loop. */
+DS_API ds_status ds_reserve_vertices(ds_ctx *ctx, int32_t capacity);
 
 /* ----------------------------------------------------------------- compute */
 

@@ -423,6 +423,19 @@ ds_status ds_reserve(ds_ctx *ctx, int32_t E, int32_t S, int32_t H)
     return DS_OK;
 }
 
+ds_status ds_reserve_vertices(ds_ctx *ctx, int32_t capacity)
+{
+    if (!ctx || capacity < 0) return fail(ctx, DS_ERR_ARG, "null context or negative capacity");
+    if (capacity <= ctx->cap_pool) return DS_OK;
+    DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    DS_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    ds_status s;
+    if ((s = grow(ctx, &ctx->pool, (size_t)capacity)) != DS_OK) return s;
+    if ((s = grow(ctx, &ctx->pool_pos, (size_t)capacity)) != DS_OK) return s;
+    ctx->cap_pool = capacity;
+    return DS_OK;
+}
+
 ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *sd, const ds_ut_hits *ht,
                          ds_tracks *out, void *stream)
 {
@@ -633,10 +646,12 @@ ds_status ds_sync_status(ds_ctx *ctx, void *stream, ds_stats *stats)
 {
     if (!ctx) return DS_ERR_ARG;
     DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
-    DS_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+    // stream-ordered: no legacy-stream call that could wait for other streams
+    cudaStream_t st = (cudaStream_t)stream;
     ds::DevCounters c;
-    DS_CUDA(cudaMemcpy(&c, ctx->d_cnt, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
-    DS_CUDA(cudaMemset(ctx->d_cnt, 0, sizeof(c)), "clear counters");
+    DS_CUDA(cudaMemcpyAsync(&c, ctx->d_cnt, sizeof(c), cudaMemcpyDeviceToHost, st), "read counters");
+    DS_CUDA(cudaMemsetAsync(ctx->d_cnt, 0, sizeof(c), st), "clear counters");
+    DS_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     if (stats) {
         stats->n_candidates = (int64_t)c.n_candidates;
         stats->n_pairs = (int64_t)c.n_pairs;

@@ -97,6 +97,34 @@ class ds_tune_entry(C.Structure):
     _fields_ = [("tuning", ds_tuning), ("ms", C.c_double)]
 
 
+class ds_server_config(C.Structure):
+    _fields_ = [("n_slots", C.c_int32), ("max_batch_events", C.c_int32), ("max_batch_seeds", C.c_int32),
+                ("max_batch_hits", C.c_int32), ("events_per_launch", C.c_int32), ("vertices_per_seed", C.c_int32),
+                ("hbm_budget", C.c_int64), ("mlp_precision", C.c_int32), ("reserved0", C.c_int32)]
+
+
+class ds_request(C.Structure):
+    _fields_ = [("n_events", C.c_int32), ("reserved0", C.c_int32), ("seed_off", C.c_void_p),
+                ("hit_off", C.c_void_p)] + \
+               [(k, C.c_void_p) for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2",
+                                          "hit_x0", "hit_ybeg", "hit_yend", "hit_layer", "tracks")] + \
+               [("trk_capacity", C.c_int32), ("vtx_capacity", C.c_int32), ("trk_off", C.c_void_p),
+                ("vertices", C.c_void_p), ("vtx_off", C.c_void_p), ("arrival", C.c_double)]
+
+
+class ds_completion(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("n_tracks", C.c_int32), ("n_vertices", C.c_int32),
+                ("n_batches", C.c_int32), ("t_arrival", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double)]
+
+
+class ds_server_stats(C.Structure):
+    _fields_ = [("requests_done", C.c_int64), ("events_done", C.c_int64), ("batches", C.c_int64),
+                ("hbm_budget", C.c_int64), ("hbm_peak", C.c_int64), ("context_bytes", C.c_int64),
+                ("peak_inflight", C.c_int32), ("queued", C.c_int32), ("worker_launch_s", C.c_double),
+                ("worker_finish_s", C.c_double), ("worker_wall_s", C.c_double)]
+
+
 TRACK_DTYPE = np.dtype([("event", "<i4"), ("seed", "<i4"), ("hit", "<i4", 4), ("x", "<f4"), ("y", "<f4"),
                         ("tx", "<f4"), ("ty", "<f4"), ("qop", "<f4"), ("chi2", "<f4"), ("ndof", "<i4"),
                         ("nn", "<f4"), ("flags", "<u4"), ("n_candidates", "<i4")])
@@ -137,6 +165,16 @@ def lib():
             "ds_sync_status": ([P, P, C.POINTER(ds_stats)], C.c_int),
             "ds_mlp_eval": ([P, P, C.c_int32, P, C.c_int32, P], C.c_int),
             "ds_get_tuning": ([P, C.POINTER(ds_tuning)], C.c_int),
+            "ds_reserve_vertices": ([P, C.c_int32], C.c_int),
+            "ds_server_default_config": ([C.POINTER(ds_server_config)], None),
+            "ds_server_create": ([C.POINTER(P), C.c_int, C.POINTER(ds_geometry), C.POINTER(ds_nn_weights),
+                                  C.POINTER(ds_params), C.POINTER(ds_server_config)], C.c_int),
+            "ds_server_submit": ([P, C.POINTER(ds_request), C.POINTER(C.c_int64)], C.c_int),
+            "ds_server_now": ([P], C.c_double),
+            "ds_server_poll": ([P, C.POINTER(ds_completion), C.c_int32, C.c_double], C.c_int32),
+            "ds_server_drain": ([P], C.c_int),
+            "ds_server_stats_get": ([P, C.POINTER(ds_server_stats)], C.c_int),
+            "ds_server_destroy": ([P], None),
             "ds_set_tuning": ([P, C.POINTER(ds_tuning)], C.c_int),
             "ds_autotune": ([P, C.POINTER(ds_event_batch), C.POINTER(ds_seeds), C.POINTER(ds_ut_hits),
                              C.POINTER(ds_tracks), C.c_int32, C.POINTER(ds_tuning), C.POINTER(ds_tune_entry),
@@ -160,7 +198,9 @@ def lib():
 EXPORTED = ("ds_create", "ds_destroy", "ds_status_string", "ds_last_error", "ds_default_params",
             "ds_load_geometry", "ds_load_nn_weights", "ds_set_params", "ds_reserve", "ds_reconstruct",
             "ds_vertex", "ds_sync_status", "ds_process_host", "ds_profile_enable", "ds_profile_read",
-            "ds_reconstruct_noalloc", "ds_mlp_eval", "ds_get_tuning", "ds_set_tuning", "ds_autotune")
+            "ds_reconstruct_noalloc", "ds_mlp_eval", "ds_get_tuning", "ds_set_tuning", "ds_autotune",
+            "ds_reserve_vertices", "ds_server_default_config", "ds_server_create", "ds_server_submit",
+            "ds_server_now", "ds_server_poll", "ds_server_drain", "ds_server_stats_get", "ds_server_destroy")
 
 
 # --------------------------------------------------------------- C names, marshalled
@@ -320,6 +360,10 @@ def ds_autotune(ctx, dev: dict, out: dict, reps: int = 3, stream=None, max_entri
                                   ent, max_entries, C.byref(n), _stream(stream)), "ds_autotune")
     out["_struct"] = tr
     return best, [(ent[i].tuning.as_dict(), ent[i].ms) for i in range(min(n.value, max_entries))]
+
+
+def ds_reserve_vertices(ctx, capacity: int):
+    return _check(ctx, lib().ds_reserve_vertices(ctx, int(capacity)), "ds_reserve_vertices")
 
 
 def ds_sync_status(ctx, stream=None, raise_on_error: bool = True):
@@ -490,3 +534,120 @@ def decode(out: dict, vout: dict | None = None) -> dict:
         res.update(vertices=vr.view(VERTEX_DTYPE).reshape(-1), vtx_off=vout["vtx_off"].cpu().numpy(),
                    n_vertices=nv)
     return res
+
+
+# --------------------------------------------------------------- serving loop
+
+def ds_server_default_config() -> ds_server_config:
+    c = ds_server_config()
+    lib().ds_server_default_config(C.byref(c))
+    return c
+
+
+class Server:
+    """Continuous-batching request server (include/ds_serve.h) over host numpy
+    requests.  submit() takes one request dict (host arrays of one or more
+    events: seed_off, hit_off, seed_*, hit_* as in Downstream.to_device) and
+    keeps it, and its output arrays, alive until poll() returns it."""
+
+    def __init__(self, cfg: dict, weights: dict, device: int = 0, params: dict | None = None, **config):
+        self.ptr = None
+        c = ds_server_default_config()
+        for k, v in config.items():
+            setattr(c, k, v)
+        self.config = c
+        self._nn = _NN(weights)
+        self._geom = make_geometry(cfg)
+        self._params = make_params(cfg, **(params or {}))
+        p = C.c_void_p()
+        st = lib().ds_server_create(C.byref(p), device, C.byref(self._geom), C.byref(self._nn.s),
+                                    C.byref(self._params), C.byref(c))
+        if st != DS_OK:
+            raise DSError(st, f"ds_server_create: {ds_status_string(st)}")
+        self.ptr = p
+        self._pending = {}
+
+    def now(self) -> float:
+        return lib().ds_server_now(self.ptr)
+
+    def alloc_outputs(self, req: dict, vtx_capacity: int | None = None, pinned: bool = True) -> dict:
+        """Output arrays for one request: tracks (one per seed at most), vertices
+        (vtx_capacity, default 4 per seed + 4096), trk_off, vtx_off.  Pinned
+        (page-locked, through torch's caching host allocator) by default: the
+        server then copies the records into them by DMA."""
+        E, S = int(req["n_events"]), int(req["seed_off"][-1])
+        vcap = vtx_capacity if vtx_capacity is not None else 4 * S + 4096
+
+        def buf(n, dtype):
+            if pinned:
+                import torch
+                t = torch.empty(n * np.dtype(dtype).itemsize, dtype=torch.uint8, pin_memory=True)
+                return t.numpy().view(dtype)
+            return np.zeros(n, dtype)
+
+        return dict(tracks=buf(max(S, 1), TRACK_DTYPE), vertices=buf(max(vcap, 1), VERTEX_DTYPE),
+                    trk_off=np.zeros(E + 1, np.int32), vtx_off=np.zeros(E + 1, np.int32))
+
+    def submit(self, req: dict, arrival: float = 0.0, out: dict | None = None, vtx_capacity: int | None = None) -> int:
+        """Queue one request (host arrays; pinned inputs are uploaded by DMA).
+        out: buffers from alloc_outputs (allocated here when None).  The
+        request's arrays and out stay referenced until poll() returns it."""
+        E = int(req["n_events"])
+        keep = {}
+
+        def arr(k, t):
+            a = np.ascontiguousarray(req[k], t)
+            keep[k] = a
+            return a.ctypes.data
+
+        r = ds_request()
+        r.n_events = E
+        r.seed_off = arr("seed_off", np.int32)
+        r.hit_off = arr("hit_off", np.int32)
+        for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2", "hit_x0", "hit_ybeg", "hit_yend"):
+            setattr(r, k, arr(k, np.float32))
+        r.hit_layer = arr("hit_layer", np.uint8)
+        o = out if out is not None else self.alloc_outputs(req, vtx_capacity)
+        r.tracks, r.trk_capacity, r.trk_off = o["tracks"].ctypes.data, len(o["tracks"]), o["trk_off"].ctypes.data
+        r.vertices, r.vtx_capacity, r.vtx_off = o["vertices"].ctypes.data, len(o["vertices"]), o["vtx_off"].ctypes.data
+        r.arrival = float(arrival)
+        rid = C.c_int64(0)
+        st = lib().ds_server_submit(self.ptr, C.byref(r), C.byref(rid))
+        if st != DS_OK:
+            raise DSError(st, f"ds_server_submit: {ds_status_string(st)}")
+        self._pending[rid.value] = (keep, o["tracks"], o["trk_off"], o["vertices"], o["vtx_off"])
+        return rid.value
+
+    def poll(self, timeout: float = 0.1, max_out: int = 256) -> list:
+        """Completed requests: dicts with the completion fields and the outputs."""
+        buf = (ds_completion * max_out)()
+        n = lib().ds_server_poll(self.ptr, buf, max_out, float(timeout))
+        res = []
+        for i in range(n):
+            c = buf[i]
+            keep, tracks, trk_off, vertices, vtx_off = self._pending.pop(c.id)
+            d = {k: getattr(c, k) for k, _ in ds_completion._fields_}
+            d.update(tracks=tracks[:min(c.n_tracks, len(tracks))], trk_off=trk_off,
+                     vertices=vertices[:min(c.n_vertices, len(vertices))], vtx_off=vtx_off)
+            res.append(d)
+        return res
+
+    def drain(self):
+        lib().ds_server_drain(self.ptr)
+
+    def stats(self) -> dict:
+        s = ds_server_stats()
+        lib().ds_server_stats_get(self.ptr, C.byref(s))
+        return {k: getattr(s, k) for k, _ in ds_server_stats._fields_}
+
+    def close(self):
+        if self.ptr is not None:
+            lib().ds_server_destroy(self.ptr)
+            self.ptr = None
+            self._pending.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

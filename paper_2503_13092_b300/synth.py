@@ -334,6 +334,39 @@ def config_batch(name: str, seed: int | None = None, **kw):
     raise ValueError(name)
 
 
+
+def c5_pool(n_events: int = 4000, seed: int = 5):
+    """Events of config-1 occupancy (50 true tracks + 150 fake seeds, ~1500 UT
+    hits each) from which the serving workload's requests are cut."""
+    return generate(spec_fixed(n_events, 50, 150, 1500), seed)
+
+
+def c5_trace(n_requests: int, rate_hz: float, pool_events: int, seed: int = 5, max_events: int = 500):
+    """Serving workload: request sizes uniform in 1..max_events events, Poisson
+    arrivals at rate_hz (exponential gaps), each request a contiguous run of
+    pool events.  Returns (sizes, first pool event, arrival time in s)."""
+    rng = np.random.Generator(np.random.PCG64(20_000 + seed))
+    sizes = rng.integers(1, max_events + 1, n_requests)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, n_requests))
+    starts = rng.integers(0, pool_events - sizes + 1)
+    return sizes, starts, arrivals
+
+
+def slice_events(b: dict, e0: int, e1: int) -> dict:
+    """Events [e0, e1) of batch b as a batch of their own (views where possible)."""
+    s0, s1 = int(b["seed_off"][e0]), int(b["seed_off"][e1])
+    h0, h1 = int(b["hit_off"][e0]), int(b["hit_off"][e1])
+    out = dict(n_events=e1 - e0, mode=b.get("mode", "A"),
+               seed_off=(b["seed_off"][e0:e1 + 1] - s0).astype(np.int32),
+               hit_off=(b["hit_off"][e0:e1 + 1] - h0).astype(np.int32))
+    for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2", "seed_track"):
+        if k in b:
+            out[k] = b[k][s0:s1]
+    for k in ("hit_x0", "hit_ybeg", "hit_yend", "hit_layer", "hit_track"):
+        if k in b:
+            out[k] = b[k][h0:h1]
+    return out
+
 # --------------------------------------------------------------------------------------
 # ghost-killer weights (inputs to the method; fixed seed, not trained)
 # --------------------------------------------------------------------------------------

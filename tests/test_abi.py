@@ -1,5 +1,5 @@
 """The C ABI library loads and exports every entry point declared in
-include/ds.h; the Python binding's structs match the header's layout
+include/ds.h and include/ds_serve.h; the Python binding's structs match the header's layout
 (compiled with gcc).  No GPU needed: nothing here launches work."""
 import ctypes
 import os
@@ -12,7 +12,7 @@ from paper_2503_13092_b300 import build as ds_build
 from paper_2503_13092_b300 import ds
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "ds.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("ds.h", "ds_serve.h")]
 
 
 @pytest.fixture(scope="module")
@@ -21,7 +21,7 @@ def libpath():
 
 
 def declared_symbols():
-    txt = open(HEADER).read()
+    txt = "".join(open(h).read() for h in HEADERS)
     return sorted(set(re.findall(r"^DS_API [^(]*?\b(ds_\w+)\(", txt, re.M)))
 
 
@@ -29,7 +29,7 @@ def test_header_declares_the_boundary():
     names = declared_symbols()
     for n in ("ds_load_geometry", "ds_load_nn_weights", "ds_reconstruct", "ds_vertex"):
         assert n in names
-    assert sorted(ds.EXPORTED) == [n for n in names if n in ds.EXPORTED]
+    assert sorted(ds.EXPORTED) == names          # the binding wraps every declared call
 
 
 def test_library_exports_every_declared_symbol(libpath):
@@ -46,8 +46,10 @@ def test_struct_layout_matches_header(tmp_path):
     structs = {"ds_geometry": ds.ds_geometry, "ds_nn_weights": ds.ds_nn_weights, "ds_params": ds.ds_params,
                "ds_event_batch": ds.ds_event_batch, "ds_seeds": ds.ds_seeds, "ds_ut_hits": ds.ds_ut_hits,
                "ds_tracks": ds.ds_tracks, "ds_vertices": ds.ds_vertices, "ds_stats": ds.ds_stats,
-               "ds_kernel_time": ds.ds_kernel_time, "ds_tuning": ds.ds_tuning, "ds_tune_entry": ds.ds_tune_entry}
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ds.h"', 'int main(void){']
+               "ds_kernel_time": ds.ds_kernel_time, "ds_tuning": ds.ds_tuning, "ds_tune_entry": ds.ds_tune_entry,
+               "ds_server_config": ds.ds_server_config, "ds_request": ds.ds_request,
+               "ds_completion": ds.ds_completion, "ds_server_stats": ds.ds_server_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ds.h"', '#include "ds_serve.h"', 'int main(void){']
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
         for f, _ in cls._fields_:
