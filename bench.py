@@ -50,6 +50,18 @@ def aggregate(elapsed_s: list, events_per_rank: int, steps: int) -> dict:
     return dict(value=n / t, ms_per_step=1e3 * t / steps, events=n)
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -619,12 +631,7 @@ def main():
     elapsed = t0e.elapsed_time(t1e) / 1e3
     st = d.sync(stream)
     assert st["status"] == 0, st
-    if ws > 1:
-        tt = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        times = [float(tt.item())] * ws
-    else:
-        times = [elapsed]
+    times = [max_over_ranks(elapsed)] * ws
     agg = aggregate(times, E, args.steps)
 
     # ------------------------------------------------- per-kernel roofline
