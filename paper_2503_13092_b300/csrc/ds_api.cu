@@ -308,7 +308,8 @@ ds_status ds_create(ds_ctx **out, int device)
         return DS_ERR_OOM;
     }
     cudaMemset(ctx->d_cnt, 0, sizeof(ds::DevCounters));
-    if (ds::init_vertex_attributes() != cudaSuccess || ds::init_search_attributes() != cudaSuccess) {
+    if (ds::init_vertex_attributes() != cudaSuccess || ds::init_search_attributes() != cudaSuccess ||
+        ds::init_bucket_attributes() != cudaSuccess) {
         cudaFree(ctx->d_cnt);
         delete ctx;
         return DS_ERR_CUDA;

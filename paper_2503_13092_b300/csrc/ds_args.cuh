@@ -159,6 +159,7 @@ const char *fill_dev_nn(const ds_nn_weights *w, DevNN *out, int *n_h2_kernel);
 const char *fill_dev_params(const ds_params *p, DevParams *out);
 
 cudaError_t init_vertex_attributes();
+cudaError_t init_bucket_attributes();
 cudaError_t init_search_attributes();
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st, Prof *prof);
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof);

@@ -32,7 +32,8 @@ constexpr int kSearchCtasPerSm = 4;
 constexpr int kStageHits = 5632;     // event x0 arrays up to this size are staged in shared memory
 constexpr int kStageHitsMax = 47104; // largest staging buffer: 32-sector table + x0 + static arrays < 227 KB
 constexpr int kBucketThreads = 512;
-constexpr int kBucketRegHits = 12;   // hits kept in registers per bucketing thread
+constexpr int kBucketVecRows = 3;    // 16-byte loads (4 hits) per bucketing thread
+constexpr int kBucketStage = 6144;   // events up to this many hits are sorted in shared memory
 constexpr int kMaxVertexTracks = 4096; // tracks per event staged for vertexing
 constexpr unsigned long long kNoKey = ~0ull;
 

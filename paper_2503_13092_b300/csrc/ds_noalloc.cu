@@ -72,7 +72,7 @@ ds_status scratch_address(int device, unsigned char **out)
     if (!g_scratch_dev[device]) {
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) return DS_ERR_CUDA;
-        if (init_search_attributes() != cudaSuccess) return DS_ERR_CUDA;
+        if (init_search_attributes() != cudaSuccess || init_bucket_attributes() != cudaSuccess) return DS_ERR_CUDA;
         g_scratch_dev[device] = static_cast<unsigned char *>(ptr);
     }
     *out = g_scratch_dev[device];

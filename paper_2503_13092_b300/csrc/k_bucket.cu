@@ -7,10 +7,13 @@
 // |x0 - u| < w then maps to one contiguous range of the sorted array per
 // sector, found from two uint16 offsets, with no binary search.
 //
-// One CTA per event.  Pass 1 counts bins with shared-memory atomics (hits
-// stay in registers for events up to 6144 hits), a block scan turns counts into
-// offsets (written out as the event's bin table), pass 2 scatters float4
-// {x0, ybeg, yend, id} records and a compact x0 array in the same order.  The
+// One CTA per event.  Pass 1 reads the hits with 16-byte loads (4 hits per
+// load; events up to 6144 hits stay in registers) and counts bins with
+// shared-memory atomics, a block scan turns counts into offsets (written out
+// as the event's bin table), pass 2 places float4 {x0, ybeg, yend, id} records
+// at their sorted positions in shared memory and writes them, and the compact
+// x0 array, with coalesced stores.  Larger events scatter straight to global
+// memory.  The
 // last CTA also turns per-event seed counts into the search kernel's work
 // items (chunks of at most `chunk` <= 128 seeds of one event).  The order inside a bin comes
 // from atomics and is not deterministic; every consumer ranks hits by
@@ -38,12 +41,15 @@ __device__ __forceinline__ int hit_bin(const DevGeom &g, float x0, float yb, flo
 
 __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_constant__ BucketArgs a)
 {
-    extern __shared__ unsigned int s_cnt[];   // nb + 1 counters, then x0 staging
+    // dynamic shared memory: nb + 1 bin counters (padded to 16 bytes), then the
+    // event's records in sorted order (events up to kBucketStage hits)
+    extern __shared__ __align__(16) unsigned int s_cnt[];
     __shared__ int s_scan[32];
     __shared__ bool s_last;
     const int e = blockIdx.x;
     const DevGeom &g = a.g;
     const int nb = 4 * g.n_sec * kNXB;
+    const int tid = threadIdx.x;
 
     int h0 = __ldg(a.hit_off + e), h1 = __ldg(a.hit_off + e + 1);
     uint16_t *table = a.bins + (size_t)e * g.table_stride;
@@ -51,37 +57,77 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
     if (e == 0 && h0 != 0) bad = true;
     if (e == a.n_events - 1 && h1 != a.n_hits) bad = true;
     if (bad) {
-        if (threadIdx.x == 0) raise_flag(a.cnt, DS_FLAG_BAD_OFFSETS);
+        if (tid == 0) raise_flag(a.cnt, DS_FLAG_BAD_OFFSETS);
         h0 = h1 = 0;
     }
     int n = h1 - h0;
     if (n > kMaxEventHits) {
-        if (threadIdx.x == 0) raise_flag(a.cnt, DS_FLAG_EVENT_TOO_LARGE);
+        if (tid == 0) raise_flag(a.cnt, DS_FLAG_EVENT_TOO_LARGE);
         n = 0;
+        h1 = h0;
     }
 
-    for (int b = threadIdx.x; b <= nb; b += blockDim.x) s_cnt[b] = 0;
+    const int cnt_words = (nb + 1 + 3) & ~3;
+    float4 *s_rec = reinterpret_cast<float4 *>(s_cnt + cnt_words);
+    for (int b = tid; b <= nb; b += blockDim.x) s_cnt[b] = 0;
     __syncthreads();
-    // pass 1: bin of every hit; small events keep their hits in registers
-    const bool in_regs = n <= kBucketRegHits * (int)blockDim.x;
-    int rb[kBucketRegHits];
-    float rx[kBucketRegHits], ryb[kBucketRegHits], rye[kBucketRegHits];
-    if (in_regs) {
+
+    // pass 1: bins.  Events that fit the staging buffer are read with 16-byte
+    // loads (4 hits per load, from the 4-aligned hit below h0) and kept in
+    // registers; the rest with scalar loads.
+    const int a0 = h0 & ~3;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(a.x0) | reinterpret_cast<uintptr_t>(a.ybeg) |
+                           reinterpret_cast<uintptr_t>(a.yend)) & 15) == 0 &&
+                         (reinterpret_cast<uintptr_t>(a.layer) & 3) == 0;
+    const bool vec = aligned && (h1 - a0) <= 4 * kBucketVecRows * (int)blockDim.x;
+    const bool staged = n <= kBucketStage;
+    float4 vx[kBucketVecRows], vyb[kBucketVecRows], vye[kBucketVecRows];
+    int vb[kBucketVecRows][4];
+    if (vec) {
 #pragma unroll
-        for (int k = 0; k < kBucketRegHits; ++k) {
-            const int i = k * blockDim.x + threadIdx.x;
-            rb[k] = -1;
-            if (i < n) {
-                const int h = h0 + i;
-                rx[k] = __ldg(a.x0 + h);
-                ryb[k] = __ldg(a.ybeg + h);
-                rye[k] = __ldg(a.yend + h);
-                rb[k] = hit_bin(g, rx[k], ryb[k], rye[k], __ldg(a.layer + h), nb, a.cnt);
-                atomicAdd(&s_cnt[rb[k]], 1u);
+        for (int r = 0; r < kBucketVecRows; ++r) {
+            const int base = a0 + 4 * (r * (int)blockDim.x + tid);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) vb[r][j] = -1;
+            if (base < h1) {
+                uchar4 ly;
+                if (base + 4 <= a.n_hits) {      // whole group inside the arrays
+                    vx[r] = __ldg(reinterpret_cast<const float4 *>(a.x0 + base));
+                    vyb[r] = __ldg(reinterpret_cast<const float4 *>(a.ybeg + base));
+                    vye[r] = __ldg(reinterpret_cast<const float4 *>(a.yend + base));
+                    ly = __ldg(reinterpret_cast<const uchar4 *>(a.layer + base));
+                } else {                         // the arrays end inside the group
+                    float t[3][4];
+                    unsigned char l4[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const bool in = base + j < a.n_hits;
+                        t[0][j] = in ? __ldg(a.x0 + base + j) : 0.f;
+                        t[1][j] = in ? __ldg(a.ybeg + base + j) : 0.f;
+                        t[2][j] = in ? __ldg(a.yend + base + j) : 0.f;
+                        l4[j] = in ? __ldg(a.layer + base + j) : 0;
+                    }
+                    vx[r] = make_float4(t[0][0], t[0][1], t[0][2], t[0][3]);
+                    vyb[r] = make_float4(t[1][0], t[1][1], t[1][2], t[1][3]);
+                    vye[r] = make_float4(t[2][0], t[2][1], t[2][2], t[2][3]);
+                    ly = make_uchar4(l4[0], l4[1], l4[2], l4[3]);
+                }
+                const float xs[4] = {vx[r].x, vx[r].y, vx[r].z, vx[r].w};
+                const float ybs[4] = {vyb[r].x, vyb[r].y, vyb[r].z, vyb[r].w};
+                const float yes[4] = {vye[r].x, vye[r].y, vye[r].z, vye[r].w};
+                const int ls[4] = {ly.x, ly.y, ly.z, ly.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int h = base + j;
+                    if (h >= h0 && h < h1) {
+                        vb[r][j] = hit_bin(g, xs[j], ybs[j], yes[j], ls[j], nb, a.cnt);
+                        atomicAdd(&s_cnt[vb[r][j]], 1u);
+                    }
+                }
             }
         }
     } else {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int i = tid; i < n; i += blockDim.x) {
             const int h = h0 + i;
             const int b = hit_bin(g, __ldg(a.x0 + h), __ldg(a.ybeg + h), __ldg(a.yend + h), __ldg(a.layer + h),
                                   nb, a.cnt);
@@ -93,7 +139,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
     // exclusive scan over nb + 1 counters: contiguous chunk per thread
     const int total_bins = nb + 1;
     const int per = (total_bins + blockDim.x - 1) / blockDim.x;
-    const int b0 = threadIdx.x * per;
+    const int b0 = tid * per;
     int local = 0;
     for (int k = 0; k < per; ++k)
         if (b0 + k < total_bins) local += s_cnt[b0 + k];
@@ -109,27 +155,48 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
         }
     }
     // remaining table entries (padding) point at the end of the valid hits
-    for (int b = total_bins + threadIdx.x; b < g.table_stride; b += blockDim.x)
-        table[b] = (uint16_t)n;
+    for (int b = total_bins + tid; b < g.table_stride; b += blockDim.x) table[b] = (uint16_t)n;
     __syncthreads();
 
-    // pass 2: scatter float4 records; the compact x0 array is assembled in
-    // shared memory and written out coalesced
-    float *xs = reinterpret_cast<float *>(s_cnt + ((nb + 1 + 3) & ~3));
-    if (in_regs) {
+    // pass 2: records {x0, ybeg, yend, id} in sorted order.  Staged events are
+    // assembled in shared memory and written out with coalesced stores.
+    if (vec && staged) {
 #pragma unroll
-        for (int k = 0; k < kBucketRegHits; ++k) {
-            if (rb[k] >= 0) {
-                const unsigned int slot = atomicAdd(&s_cnt[rb[k]], 1u);
-                a.sorted[h0 + slot] = make_float4(rx[k], ryb[k], rye[k], __int_as_float(h0 + k * (int)blockDim.x +
-                                                                                        (int)threadIdx.x));
-                xs[slot] = rx[k];
-            }
+        for (int r = 0; r < kBucketVecRows; ++r) {
+            const int base = a0 + 4 * (r * (int)blockDim.x + tid);
+            const float xs[4] = {vx[r].x, vx[r].y, vx[r].z, vx[r].w};
+            const float ybs[4] = {vyb[r].x, vyb[r].y, vyb[r].z, vyb[r].w};
+            const float yes[4] = {vye[r].x, vye[r].y, vye[r].z, vye[r].w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (vb[r][j] >= 0) {
+                    const unsigned int slot = atomicAdd(&s_cnt[vb[r][j]], 1u);
+                    s_rec[slot] = make_float4(xs[j], ybs[j], yes[j], __int_as_float(base + j));
+                }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) a.sx0[h0 + i] = xs[i];
+        for (int i = tid; i < n; i += blockDim.x) {
+            const float4 rec = s_rec[i];
+            a.sorted[h0 + i] = rec;
+            a.sx0[h0 + i] = rec.x;
+        }
+    } else if (vec) {
+#pragma unroll
+        for (int r = 0; r < kBucketVecRows; ++r) {
+            const int base = a0 + 4 * (r * (int)blockDim.x + tid);
+            const float xs[4] = {vx[r].x, vx[r].y, vx[r].z, vx[r].w};
+            const float ybs[4] = {vyb[r].x, vyb[r].y, vyb[r].z, vyb[r].w};
+            const float yes[4] = {vye[r].x, vye[r].y, vye[r].z, vye[r].w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (vb[r][j] >= 0) {
+                    const unsigned int slot = atomicAdd(&s_cnt[vb[r][j]], 1u);
+                    a.sorted[h0 + slot] = make_float4(xs[j], ybs[j], yes[j], __int_as_float(base + j));
+                    a.sx0[h0 + slot] = xs[j];
+                }
+        }
     } else {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int i = tid; i < n; i += blockDim.x) {
             const int h = h0 + i;
             const float x0 = __ldg(a.x0 + h), yb = __ldg(a.ybeg + h), ye = __ldg(a.yend + h);
             const int b = hit_bin(g, x0, yb, ye, __ldg(a.layer + h), nb, a.cnt);
@@ -173,16 +240,18 @@ cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st, Prof *prof)
 {
     if (a.n_events <= 0) return cudaSuccess;
     const int nb = 4 * a.g.n_sec * kNXB;
-    const size_t smem = sizeof(unsigned int) * (size_t)((nb + 1 + 3) & ~3) + sizeof(float) * kBucketRegHits * kBucketThreads;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    const size_t smem = sizeof(unsigned int) * (size_t)((nb + 1 + 3) & ~3) + sizeof(float4) * kBucketStage;
     prof->begin("k_bucket", st);
     k_bucket<<<a.n_events, kBucketThreads, smem, st>>>(a);
     prof->end(st);
     return cudaGetLastError();
+}
+
+cudaError_t init_bucket_attributes()
+{
+    const size_t smem = sizeof(unsigned int) * (size_t)((4 * kMaxSectors * kNXB + 1 + 3) & ~3) +
+                        sizeof(float4) * kBucketStage;
+    return cudaFuncSetAttribute(k_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 }  // namespace ds
