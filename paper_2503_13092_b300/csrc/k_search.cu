@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
 
         float d[kK1Max];
         int id[kK1Max], p[kK1Max];
-        const int q = window_scan<kK1Max, 8>(g, X0, H, Tb, 3, u_bx, sc.yl[3], sc.w1, P.dy_tol, d, id, p);
+        const int q = window_scan<kK1Max, 4>(g, X0, H, Tb, 3, u_bx, sc.yl[3], sc.w1, P.dy_tol, d, id, p);
         nbx = min(q, P.k1);
 #pragma unroll
         for (int j = 0; j < kK1Max; ++j) s_bx[j][tid] = (uint16_t)p[j];
@@ -363,14 +363,14 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
         {
             float dd[1]; int ii[1], pp[1];
             const float ul = fmaf(txp, g.z[0] - g.z[3], xh) - g.dxdy[0] * sc.yl[0];
-            const int c = window_scan<1, 4>(g, X0, H, Tb, 0, ul, sc.yl[0], w2, P.dy_tol, dd, ii, pp);
+            const int c = window_scan<1, 3>(g, X0, H, Tb, 0, ul, sc.yl[0], w2, P.dy_tol, dd, ii, pp);
             sel[0] = c > 0 ? pp[0] : -1;
         }
 #pragma unroll
         for (int l = 1; l <= 2; ++l) {
             float dd[2]; int ii[2], pp[2];
             const float ul = fmaf(txp, g.z[l] - g.z[3], xh) - g.dxdy[l] * sc.yl[l];
-            const int c = window_scan<2, 4>(g, X0, H, Tb, l, ul, sc.yl[l], w2, P.dy_tol, dd, ii, pp);
+            const int c = window_scan<2, 3>(g, X0, H, Tb, l, ul, sc.yl[l], w2, P.dy_tol, dd, ii, pp);
             sel[2 * l - 1] = c > 0 ? pp[0] : -1;
             sel[2 * l] = c > 1 ? pp[1] : -1;
         }
