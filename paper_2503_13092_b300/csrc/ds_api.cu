@@ -50,6 +50,7 @@ struct ds_ctx {
     int cand_per_seed = 16;
     int *count_trk = nullptr;
     int *count_vtx = nullptr;
+    int *large_vtx = nullptr;
     ds_vertex_rec *pool = nullptr;
     int *pool_pos = nullptr;
     // host-buffer path: device copies of inputs and outputs
@@ -328,7 +329,7 @@ void ds_destroy(ds_ctx *ctx)
     cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_cnt, ctx->d_tc, ctx->sorted, ctx->sx0, ctx->item_cnt, ctx->item_off, ctx->bins, ctx->cand_feat,
                     ctx->cand_meta, ctx->cand_logit, ctx->seed_cand, ctx->trk_ws, ctx->key_ws, ctx->hit_ws,
-                    ctx->rank_ws, ctx->count_trk, ctx->count_vtx, ctx->pool, ctx->pool_pos,
+                    ctx->rank_ws, ctx->count_trk, ctx->count_vtx, ctx->large_vtx, ctx->pool, ctx->pool_pos,
                     ctx->h.seed_off, ctx->h.hit_off, ctx->h.seed_cols, ctx->h.hit_cols, ctx->h.layer,
                     ctx->h.tracks, ctx->h.trk_off, ctx->h.vtx_off, ctx->h.counts, ctx->h.vertices};
     for (void *q : ptrs)
@@ -395,6 +396,7 @@ ds_status ds_reserve(ds_ctx *ctx, int32_t E, int32_t S, int32_t H)
         if ((st = grow(ctx, &ctx->bins, (size_t)E * ctx->g.table_stride)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->count_trk, (size_t)E)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->count_vtx, (size_t)E)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->large_vtx, (size_t)E)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->item_cnt, (size_t)E)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->item_off, (size_t)E + 1)) != DS_OK) return st;
         ctx->cap_events = E;
@@ -612,9 +614,10 @@ ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tr, ds_vertices *out, void *st
             ctx->cap_pool = out->capacity;
         }
     }
-    static_assert(offsetof(ds::DevCounters, vtx_queue) == offsetof(ds::DevCounters, pool_used) + sizeof(int),
-                  "pool_used and the vertex queues are cleared together");
-    DS_CUDA(cudaMemsetAsync(&ctx->d_cnt->pool_used, 0, 3 * sizeof(int), st), "memset");
+    static_assert(offsetof(ds::DevCounters, vtx_queue) == offsetof(ds::DevCounters, pool_used) + sizeof(int) &&
+                      offsetof(ds::DevCounters, n_large) == offsetof(ds::DevCounters, pool_used) + 3 * sizeof(int),
+                  "pool_used, the vertex queues and n_large are cleared together");
+    DS_CUDA(cudaMemsetAsync(&ctx->d_cnt->pool_used, 0, 4 * sizeof(int), st), "memset");
     ds::VertexArgs va{};
     va.g = ctx->g;
     va.p = ctx->p;
@@ -627,6 +630,7 @@ ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tr, ds_vertices *out, void *st
     va.pool_pos = ctx->pool_pos;
     va.pool_cap = out->capacity;
     va.count_ws = ctx->count_vtx;
+    va.large_list = ctx->large_vtx;
     va.vtx_off = out->vtx_off;
     va.n_vertices = out->n_vertices;
     va.capacity = out->capacity;

@@ -136,6 +136,7 @@ struct VertexArgs {
     int *pool_pos;
     int pool_cap;
     int *count_ws;          // per event
+    int *large_list;        // events with more tracks than the small launch takes
     int32_t *vtx_off;
     int32_t *n_vertices;
     int capacity;

@@ -82,6 +82,7 @@ struct DevCounters {                 // device-side flag word and statistics
     int n_vertices;
     int pool_used;
     int vtx_queue[2];                // event queues of the two vertex launches
+    int n_large;                     // events left to the large-capacity vertex launch
     int cand_used;                   // candidates written this call
     int search_queue;                // next search work item
     unsigned long long n_candidates;

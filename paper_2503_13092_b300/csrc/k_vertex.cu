@@ -26,6 +26,7 @@ namespace ds {
 constexpr int kVtxThreads = 256;
 constexpr int kVtxSmallCap = 512;
 constexpr int kVtxSeg = 8192;          // pairs per two-phase segment
+constexpr int kVtxStore = 1024;        // candidate results kept in shared memory per segment
 
 
 struct Trk {
@@ -236,6 +237,10 @@ __global__ void __launch_bounds__(kVtxThreads, 3) k_vertex(const __grid_constant
     __shared__ unsigned s_mask[kVtxSeg / 32];
     __shared__ unsigned s_keep[kVtxSeg / 32];
     __shared__ int s_wbase[kVtxSeg / 32];
+    __shared__ unsigned s_cmask[kVtxSeg / 32];   // candidates of the segment
+    __shared__ int s_cbase[kVtxSeg / 32];        // their word prefix
+    __shared__ float4 s_res[kVtxStore];           // candidate results: x, y, z, doca
+    __shared__ unsigned s_resf[kVtxStore];        // and flags
     __shared__ bool s_last;
     Trk *s_trk = reinterpret_cast<Trk *>(s_dyn);
     uint16_t *s_pos = reinterpret_cast<uint16_t *>(s_trk + CAP);
@@ -247,8 +252,14 @@ __global__ void __launch_bounds__(kVtxThreads, 3) k_vertex(const __grid_constant
     const DevParams &P = a.p;
     const bool straight = g.gamma0 == 0.f && g.gamma1 == 0.f;
     __shared__ int s_e;
+    // the small-capacity launch pulls every event from its queue and lists the
+    // larger ones; the large-capacity launch pulls from that list only
+    const int n_mine = LARGE ? min(*(volatile const int *)&a.cnt->n_large, a.n_events) : a.n_events;
     for (;;) {
-    if (threadIdx.x == 0) s_e = atomicAdd(&a.cnt->vtx_queue[LARGE ? 1 : 0], 1);
+    if (threadIdx.x == 0) {
+        const int k = atomicAdd(&a.cnt->vtx_queue[LARGE ? 1 : 0], 1);
+        s_e = k < n_mine ? (LARGE ? __ldcg(a.large_list + k) : k) : a.n_events;
+    }
     __syncthreads();
     const int e = s_e;
     __syncthreads();
@@ -259,7 +270,8 @@ __global__ void __launch_bounds__(kVtxThreads, 3) k_vertex(const __grid_constant
     int nt = t1 - t0;
     // the small-capacity launch takes events with nt <= kVtxSmallCap, the
     // large one the rest (clamped to its capacity, flagged)
-    bool mine = LARGE ? nt > kVtxSmallCap : nt <= kVtxSmallCap;
+    const bool mine = LARGE ? nt > kVtxSmallCap : nt <= kVtxSmallCap;
+    if (!LARGE && !mine && threadIdx.x == 0) a.large_list[atomicAdd(&a.cnt->n_large, 1)] = e;
     if (LARGE && nt > CAP) {
         if (threadIdx.x == 0) raise_flag(a.cnt, DS_FLAG_VERTEX_CAPACITY);
         nt = CAP;
@@ -321,45 +333,53 @@ __global__ void __launch_bounds__(kVtxThreads, 3) k_vertex(const __grid_constant
         };
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
         int n64 = 0;
+        bool store = false;
         for (int seg0 = 0; seg0 < npairs; seg0 += kVtxSeg) {
             const int nseg = min(kVtxSeg, npairs - seg0);
             const int nwords = (nseg + 31) >> 5;
-            // phase 1a: every pair of the segment, one per lane: is it a candidate?
-            // With gamma = 0 both trajectories are lines and the solve converges to
-            // their closest approach, whose distance |w.(Di x Dj)| / |Di x Dj| is
-            // exact in closed form: pairs more than 1 um above the cut are not
-            // candidates.  With gamma != 0 every pair is a candidate.
-            for (int w = warp; w < nwords; w += nwarps) {
-                const int p0 = seg0 + (w << 5);
-                int r = 0;
-                if (lane == 0) {
-                    int lo = 0, hi = nt;
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (s_row[mid] <= p0) lo = mid;
-                        else hi = mid;
-                    }
-                    r = lo;
+            // phase 1a: is each pair of the segment a candidate?  With gamma = 0
+            // both trajectories are lines and the solve converges to their
+            // closest approach, whose distance |w.(Di x Dj)| / |Di x Dj| is exact
+            // in closed form: pairs more than 1 um above the cut are not
+            // candidates.  With gamma != 0 every pair is a candidate.  One warp
+            // per row i (track i broadcast), lanes over its partners j.
+            if (!straight) {
+                for (int w = threadIdx.x; w < nwords; w += blockDim.x)
+                    s_mask[w] = (w == nwords - 1 && (nseg & 31)) ? (1u << (nseg & 31)) - 1u : 0xffffffffu;
+            } else {
+                for (int w = threadIdx.x; w < nwords; w += blockDim.x) s_mask[w] = 0u;
+                __syncthreads();
+                int r0 = 0, hi = nt;           // row holding pair seg0
+                while (hi - r0 > 1) {
+                    const int mid = (r0 + hi) >> 1;
+                    if (s_row[mid] <= seg0) r0 = mid;
+                    else hi = mid;
                 }
-                r = __shfl_sync(0xffffffffu, r, 0);
-                const int p = p0 + lane;
-                int cand = 0;
-                if (p < seg0 + nseg) {
-                    cand = 1;
-                    if (straight) {
-                        while (r + 1 < nt && s_row[r + 1] <= p) ++r;
-                        const Trk A = s_trk[r];
-                        const uint16_t *opp = A.q > 0.f ? s_neg : s_pos;
-                        const Trk B = s_trk[opp[s_start[r] + (p - s_row[r])]];
-                        const float dtx = A.tx - B.tx, dty = A.ty - B.ty;
-                        const float cz = fmaf(A.tx, B.ty, -A.ty * B.tx);
-                        const float den = fmaf(dtx, dtx, fmaf(dty, dty, cz * cz));
-                        const float num = fabsf(fmaf(A.x - B.x, dty, -(A.y - B.y) * dtx));
-                        if (den > 1e-12f && num > (P.doca_max + 1e-3f) * sqrtf(den)) cand = 0;
+                const int seg1 = seg0 + nseg;
+                for (int i = r0 + warp; i < nt && s_row[i] < seg1; i += nwarps) {
+                    const Trk A = s_trk[i];
+                    const uint16_t *opp = A.q > 0.f ? s_neg : s_pos;
+                    const int shift = (int)s_start[i] - s_row[i];     // opp[p + shift]: partner of pair p
+                    const int pa = max(s_row[i], seg0), pb = min(s_row[i + 1], seg1);
+                    for (int p0 = pa; p0 < pb; p0 += 32) {
+                        const int p = p0 + lane;
+                        bool cand = false;
+                        if (p < pb) {
+                            const Trk B = s_trk[opp[p + shift]];
+                            const float dtx = A.tx - B.tx, dty = A.ty - B.ty;
+                            const float cz = fmaf(A.tx, B.ty, -A.ty * B.tx);
+                            const float den = fmaf(dtx, dtx, fmaf(dty, dty, cz * cz));
+                            const float num = fabsf(fmaf(A.x - B.x, dty, -(A.y - B.y) * dtx));
+                            cand = !(den > 1e-12f && num > (P.doca_max + 1e-3f) * sqrtf(den));
+                        }
+                        const unsigned m = __ballot_sync(0xffffffffu, cand);
+                        if (lane == 0 && m) {
+                            const int b = p0 - seg0, wd = b >> 5, sh = b & 31;
+                            atomicOr(&s_mask[wd], m << sh);
+                            if (sh && (m >> (32 - sh))) atomicOr(&s_mask[wd + 1], m >> (32 - sh));
+                        }
                     }
                 }
-                const unsigned m = __ballot_sync(0xffffffffu, cand);
-                if (lane == 0) s_mask[w] = m;
             }
             __syncthreads();
             // phase 1b: solve the candidates only, one per thread; keep bits
@@ -370,24 +390,32 @@ __global__ void __launch_bounds__(kVtxThreads, 3) k_vertex(const __grid_constant
                     const int c = w < nwords ? __popc(s_mask[w]) : 0;
                     int t;
                     const int r = block_exclusive_scan(c, s_scan, &t);
-                    if (w < nwords) s_wbase[w] = ctot + r;
+                    if (w < nwords) {
+                        s_cbase[w] = ctot + r;
+                        s_cmask[w] = s_mask[w];
+                    }
                     ctot += t;
                 }
                 __syncthreads();
                 for (int w = threadIdx.x; w < nwords; w += blockDim.x) s_keep[w] = 0u;
                 __syncthreads();
+                store = ctot <= kVtxStore;
                 for (int k = threadIdx.x; k < ctot; k += blockDim.x) {
                     int lo = 0, hi = nwords;
                     while (hi - lo > 1) {
                         const int mid = (lo + hi) >> 1;
-                        if (s_wbase[mid] <= k) lo = mid;
+                        if (s_cbase[mid] <= k) lo = mid;
                         else hi = mid;
                     }
-                    const int bit = __fns(s_mask[lo], 0, k - s_wbase[lo] + 1);
+                    const int bit = __fns(s_cmask[lo], 0, k - s_cbase[lo] + 1);
                     int i, j, f64;
                     pair_of(seg0 + (lo << 5) + bit, i, j);
                     const PairOut o = solve_pair(g, P, s_trk[i], s_trk[j], f64);
                     n64 += f64;
+                    if (store) {
+                        s_res[k] = make_float4(o.x, o.y, o.z, o.doca);
+                        s_resf[k] = o.flags;
+                    }
                     if (o.doca < P.doca_max) atomicOr(&s_keep[lo], 1u << bit);
                 }
                 __syncthreads();
@@ -416,9 +444,18 @@ __global__ void __launch_bounds__(kVtxThreads, 3) k_vertex(const __grid_constant
                 }
                 const int bit = __fns(s_mask[lo], 0, k - s_wbase[lo] + 1);
                 const int p = seg0 + (lo << 5) + bit;
-                int i, j, f64;
+                int i, j;
                 pair_of(p, i, j);
-                const PairOut o = solve_pair(g, P, s_trk[i], s_trk[j], f64);
+                PairOut o;
+                if (store) {           // the candidate's result from phase 1b
+                    const int kc = s_cbase[lo] + __popc(s_cmask[lo] & ((1u << bit) - 1u));
+                    const float4 r4 = s_res[kc];
+                    o.x = r4.x; o.y = r4.y; o.z = r4.z; o.doca = r4.w;
+                    o.flags = s_resf[kc];
+                } else {               // too many candidates to keep: the same solve again
+                    int f64;
+                    o = solve_pair(g, P, s_trk[i], s_trk[j], f64);
+                }
                 const int slot = s_pool_base + k;
                 if (slot < a.pool_cap) {
                     ds_vertex_rec v;
