@@ -314,6 +314,22 @@ DS_API ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tracks, ds_vertices *ou
 DS_API ds_status ds_mlp_eval(ds_ctx *ctx, const float *d_features, int32_t n, float *d_logit,
                              int32_t precision, void *stream);
 
+/* The candidates of the last ds_reconstruct on this context.  In training mode
+ * (fixed 100 / 10 mm windows, clone killing off; Ghost-Killer Neural Network
+ * section) every fitted candidate is a training example for the ghost killer.
+ * Copies on `stream` up to `capacity` candidates into device arrays:
+ * d_features n x 16 FP32 (the network inputs before normalisation), d_seed n
+ * (global seed index), d_hits n x 4 (hit ids in UTaX, UTaU, UTbV, UTbX, -1
+ * absent) and d_logit n (the network output before the sigmoid; may be NULL).
+ * *d_count (device) receives the number of candidates of the call, which may
+ * exceed capacity (the rest are not copied).  A seed's candidates are
+ * contiguous and in enumeration order; the order of the seeds is unspecified.
+ * Call after ds_reconstruct on the same stream and before the next one.
+ * d_features and d_hits 16-byte aligned.  DS_ERR_ARG for null pointers (other
+ * than d_logit), misaligned arrays or capacity < 0. */
+DS_API ds_status ds_candidates(ds_ctx *ctx, float *d_features, int32_t *d_seed, int32_t *d_hits, float *d_logit,
+                               int32_t capacity, int32_t *d_count, void *stream);
+
 /* Synchronise `stream`, read and clear the device flag word and counters.
  * Returns DS_ERR_CAPACITY / DS_ERR_TIMEOUT / DS_ERR_DEVICE_FLAG when the
  * corresponding flags are set, else DS_OK.  stats may be NULL. */

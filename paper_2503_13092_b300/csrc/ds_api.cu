@@ -558,6 +558,25 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     return DS_OK;
 }
 
+ds_status ds_candidates(ds_ctx *ctx, float *d_features, int32_t *d_seed, int32_t *d_hits, float *d_logit,
+                        int32_t capacity, int32_t *d_count, void *stream)
+{
+    if (!ctx || !d_features || !d_seed || !d_hits || !d_count || capacity < 0)
+        return fail(ctx, DS_ERR_ARG, "null pointer or negative capacity");
+    if ((reinterpret_cast<uintptr_t>(d_features) | reinterpret_cast<uintptr_t>(d_hits)) % 16 != 0)
+        return fail(ctx, DS_ERR_ARG, "features and hits must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (ctx->cap_cand == 0) {
+        DS_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int32_t), st), "memset");
+        return DS_OK;
+    }
+    DS_CUDA(ds::launch_export_candidates(ctx->cand_feat, ctx->cand_meta, ctx->cand_logit, ctx->cap_cand, ctx->d_cnt,
+                                         d_features, d_seed, d_hits, d_logit, capacity, d_count, ctx->sm_count, st),
+            "candidate export");
+    return DS_OK;
+}
+
 ds_status ds_mlp_eval(ds_ctx *ctx, const float *d_features, int32_t n, float *d_logit, int32_t precision,
                       void *stream)
 {

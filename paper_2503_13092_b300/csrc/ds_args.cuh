@@ -169,6 +169,10 @@ cudaError_t launch_mlp_pick(const MlpArgs &m, const PickArgs &p, int sm_count, c
 cudaError_t launch_mlp(const MlpArgs &m, int sm_count, int n_bound, cudaStream_t st);
 cudaError_t launch_mlp_tc(const MlpArgs &m, int sm_count, int n_bound, cudaStream_t st);
 void prepare_tc_weights(const DevNN &nn, int n_h2, MlpTcWeights *out);
+// copy the candidate buffer out (features, seed, hits, logit) for training
+cudaError_t launch_export_candidates(const float4 *feat, const CandMeta *meta, const float *logit, int cand_cap,
+                                     const DevCounters *cnt, float *o_feat, int32_t *o_seed, int32_t *o_hits,
+                                     float *o_logit, int capacity, int32_t *o_count, int sm_count, cudaStream_t st);
 cudaError_t launch_clone(const CloneArgs &a, const ScatterTrkArgs &sa, cudaStream_t st, Prof *prof);
 cudaError_t launch_vertex(const VertexArgs &a, const ScatterVtxArgs &sa, int sm_count, cudaStream_t st,
                           Prof *prof);

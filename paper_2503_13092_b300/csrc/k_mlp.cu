@@ -133,6 +133,37 @@ __global__ void __launch_bounds__(256) k_pick(const __grid_constant__ PickArgs a
     }
 }
 
+// The candidate buffer as training examples: features, seed, hits, logit.
+__global__ void __launch_bounds__(256) k_export_candidates(const float4 *__restrict__ feat,
+                                                           const CandMeta *__restrict__ meta,
+                                                           const float *__restrict__ logit, int cand_cap,
+                                                           const DevCounters *cnt, float4 *o_feat, int32_t *o_seed,
+                                                           int4 *o_hits, float *o_logit, int capacity,
+                                                           int32_t *o_count)
+{
+    const int used = min(*(volatile const int *)&cnt->cand_used, cand_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *o_count = used;
+    const int n = min(used, capacity);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o_feat[4 * (size_t)c + q] = feat[4 * (size_t)c + q];
+        const CandMeta m = meta[c];
+        o_seed[c] = m.seed;
+        o_hits[c] = make_int4(m.hit[0], m.hit[1], m.hit[2], m.hit[3]);
+        if (o_logit) o_logit[c] = logit[c];
+    }
+}
+
+cudaError_t launch_export_candidates(const float4 *feat, const CandMeta *meta, const float *logit, int cand_cap,
+                                     const DevCounters *cnt, float *o_feat, int32_t *o_seed, int32_t *o_hits,
+                                     float *o_logit, int capacity, int32_t *o_count, int sm_count, cudaStream_t st)
+{
+    k_export_candidates<<<4 * sm_count, 256, 0, st>>>(feat, meta, logit, cand_cap, cnt,
+                                                      reinterpret_cast<float4 *>(o_feat), o_seed,
+                                                      reinterpret_cast<int4 *>(o_hits), o_logit, capacity, o_count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mlp(const MlpArgs &m, int sm_count, int n_bound, cudaStream_t st)
 {
     if (m.precision != DS_MLP_FP32) return launch_mlp_tc(m, sm_count, n_bound, st);

@@ -166,6 +166,7 @@ def lib():
             "ds_mlp_eval": ([P, P, C.c_int32, P, C.c_int32, P], C.c_int),
             "ds_get_tuning": ([P, C.POINTER(ds_tuning)], C.c_int),
             "ds_reserve_vertices": ([P, C.c_int32], C.c_int),
+            "ds_candidates": ([P, P, P, P, P, C.c_int32, P, P], C.c_int),
             "ds_server_default_config": ([C.POINTER(ds_server_config)], None),
             "ds_server_create": ([C.POINTER(P), C.c_int, C.POINTER(ds_geometry), C.POINTER(ds_nn_weights),
                                   C.POINTER(ds_params), C.POINTER(ds_server_config)], C.c_int),
@@ -199,7 +200,7 @@ EXPORTED = ("ds_create", "ds_destroy", "ds_status_string", "ds_last_error", "ds_
             "ds_load_geometry", "ds_load_nn_weights", "ds_set_params", "ds_reserve", "ds_reconstruct",
             "ds_vertex", "ds_sync_status", "ds_process_host", "ds_profile_enable", "ds_profile_read",
             "ds_reconstruct_noalloc", "ds_mlp_eval", "ds_get_tuning", "ds_set_tuning", "ds_autotune",
-            "ds_reserve_vertices", "ds_server_default_config", "ds_server_create", "ds_server_submit",
+            "ds_reserve_vertices", "ds_candidates", "ds_server_default_config", "ds_server_create", "ds_server_submit",
             "ds_server_now", "ds_server_poll", "ds_server_drain", "ds_server_stats_get", "ds_server_destroy")
 
 
@@ -362,6 +363,16 @@ def ds_autotune(ctx, dev: dict, out: dict, reps: int = 3, stream=None, max_entri
     return best, [(ent[i].tuning.as_dict(), ent[i].ms) for i in range(min(n.value, max_entries))]
 
 
+def ds_candidates(ctx, features, seed, hits, logit, count, stream=None):
+    """Device tensors: features float32 [cap, 16], seed int32 [cap], hits int32 [cap, 4],
+    logit float32 [cap] (or None), count int32 [1] (receives the candidates of the call)."""
+    cap = int(features.shape[0])
+    if seed.numel() < cap or hits.numel() < 4 * cap or (logit is not None and logit.numel() < cap):
+        raise ValueError("output arrays smaller than the capacity")
+    _check(ctx, lib().ds_candidates(ctx, _ptr(features), _ptr(seed), _ptr(hits), _ptr(logit), cap, _ptr(count),
+                                    _stream(stream)), "ds_candidates")
+
+
 def ds_reserve_vertices(ctx, capacity: int):
     return _check(ctx, lib().ds_reserve_vertices(ctx, int(capacity)), "ds_reserve_vertices")
 
@@ -499,6 +510,20 @@ class Downstream:
 
     def sync(self, stream=None, raise_on_error=True):
         return ds_sync_status(self.ctx, stream, raise_on_error)
+
+    def candidates(self, capacity: int, stream=None) -> dict:
+        """The last reconstruct's candidates as host numpy arrays (features, seed, hits, logit)."""
+        t = self.torch
+        dev = f"cuda:{self.device}"
+        f = t.empty((max(capacity, 1), 16), dtype=t.float32, device=dev)
+        sd = t.empty(max(capacity, 1), dtype=t.int32, device=dev)
+        h = t.empty((max(capacity, 1), 4), dtype=t.int32, device=dev)
+        lg = t.empty(max(capacity, 1), dtype=t.float32, device=dev)
+        cnt = t.zeros(1, dtype=t.int32, device=dev)
+        ds_candidates(self.ctx, f, sd, h, lg, cnt, stream)
+        n = min(int(cnt.cpu()[0]), capacity)
+        return dict(n_total=int(cnt.cpu()[0]), features=f[:n].cpu().numpy(), seed=sd[:n].cpu().numpy(),
+                    hits=h[:n].cpu().numpy(), logit=lg[:n].cpu().numpy())
 
     def mlp_eval(self, features, precision: int = 0, stream=None):
         """Network output before the sigmoid for device features [n, 16]."""

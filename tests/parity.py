@@ -6,7 +6,9 @@ is below MARGIN, or whose event holds such a seed sharing a hit with it (a
 flip there can change clone killing here); those excused seeds may be at most
 0.1 % of the tracks.  On identical hits: x, y, tx, ty, q/p within 1e-4
 relative (absolute floor 1e-6), chi2 within 1e-3 relative (absolute floor
-1e-4), network response within 2e-5 absolute.
+1e-4), network response within 2e-5 absolute for the fixed-seed network
+(callers pass a wider bound for a trained one, whose steeper response
+amplifies the FP32 rounding of its inputs).
 
 Vertices: the oracle vertexer is fed the GPU's own FP32 track records; kept
 (i, j) sets must agree except where |DOCA - doca_max| is below MARGIN
@@ -71,9 +73,11 @@ def _close(a, b, rtol, atol):
     return np.abs(a - b) <= np.maximum(rtol * np.maximum(np.abs(a), np.abs(b)), atol)
 
 
-def compare_tracks(batch, orc, gpu, hit_map_gpu=None):
+def compare_tracks(batch, orc, gpu, hit_map_gpu=None, atol_nn=ATOL_NN):
     """orc: oracle.reconstruct(batch); gpu: ds.decode output for the same batch.
-    hit_map_gpu: optional function mapping GPU hit ids to batch hit ids."""
+    hit_map_gpu: optional function mapping GPU hit ids to batch hit ids.
+    atol_nn: response tolerance (a trained network amplifies the FP32 rounding
+    of its inputs more than the fixed-seed one)."""
     S = len(orc["status"])
     E = int(batch["n_events"])
     g = gpu_per_seed(gpu, S)
@@ -112,7 +116,7 @@ def compare_tracks(batch, orc, gpu, hit_map_gpu=None):
         st_o, st_g = orc["state"][same], g["state"][same]
         ok_par = _close(st_o, st_g, RTOL_PAR, ATOL_PAR)
         ok_chi2 = _close(orc["chi2"][same], g["chi2"][same], RTOL_CHI2, ATOL_CHI2)
-        ok_nn = np.abs(orc["nn"][same] - g["nn"][same]) <= ATOL_NN
+        ok_nn = np.abs(orc["nn"][same] - g["nn"][same]) <= atol_nn
         ok_ndof = orc["ndof"][same] == g["ndof"][same]
         rep.update(bad_par=int((~ok_par).sum()), bad_chi2=int((~ok_chi2).sum()), bad_nn=int((~ok_nn).sum()),
                    bad_ndof=int((~ok_ndof).sum()),
