@@ -231,11 +231,25 @@ def bench_reference(args):
     return 0
 
 
+def selection(batch, g):
+    """Truth efficiency (true seeds whose track has >= 3 hits of their own
+    track) and ghost rate (tracks that do not) of one reconstruction."""
+    t = g["tracks"]
+    st = batch["seed_track"][t["seed"]]
+    h = t["hit"]
+    own = ((h >= 0) & (batch["hit_track"][np.clip(h, 0, None)] == st[:, None])).sum(1)
+    good = (st >= 0) & (own >= 3)
+    return dict(efficiency=float(good.sum() / max((batch["seed_track"] >= 0).sum(), 1)),
+                ghost_rate=float(1.0 - good.mean()) if len(t) else 0.0, tracks=int(len(t)))
+
+
 def reduced_precision_forms(d, ds, torch, batch, devs, ref, step, n_prof, stream, kernels, n_cand):
     """The ghost-killer network on the tensor cores (BF16, FP8) against the FP32
-    network on the same batch: k_mlp time, share of seeds whose selected track
-    changes and the response change on tracks both keep.  Also ds_mlp_eval alone
-    on 2^20 feature rows (kernel throughput without the rest of the step)."""
+    network on the same batch (the weights loaded in d): k_mlp time, share of
+    seeds whose selected track changes, the response change on tracks both
+    keep, and the selection's truth efficiency and ghost rate.  Also
+    ds_mlp_eval alone on 2^20 feature rows (kernel throughput without the rest
+    of the step)."""
     S = int(batch["seed_off"][-1])
 
     def per_seed(g):
@@ -269,12 +283,12 @@ def reduced_precision_forms(d, ds, torch, batch, devs, ref, step, n_prof, stream
             flip = (h32 != hl) | (h32 & hl & np.any(k32 != kl, axis=1))
             both = h32 & hl & ~flip
             dn = np.abs(nl[both] - n32[both])
-            f.update(seed_flip_rate=float(flip.mean()), tracks=int(hl.sum()),
+            f.update(seed_flip_rate=float(flip.mean()),
                      response_err_max=float(dn.max()) if dn.size else 0.0,
-                     response_err_mean=float(dn.mean()) if dn.size else 0.0)
+                     response_err_mean=float(dn.mean()) if dn.size else 0.0, **selection(batch, g))
         else:
             f["k_mlp_us"] = kernels["k_mlp"]["avg_us"]
-            f["tracks"] = int(h32.sum())
+            f.update(selection(batch, ref))
         f["k_mlp_candidates_per_s"] = n_cand / (f["k_mlp_us"] * 1e-6)
         for _ in range(3):
             ds.ds_mlp_eval(d.ctx, feats, logit, prec, stream)
@@ -712,7 +726,25 @@ def main():
         roof = dict(kernel=dom, bound="hbm", achieved=kd["gbs"], peak=hbm, unit="GB/s", frac=frac_hbm,
                     peak_source=f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback",
                     traffic=traffic_for(dom))
-    mlp_forms = reduced_precision_forms(d, ds, torch, batch, devs, probe, step, n_prof, stream, kernels, n_cand)
+    # ghost killer trained on separate synthetic events (training mode, BCE +
+    # Adam in FP64); the reduced-precision forms are compared with it loaded
+    from paper_2503_13092_b300 import train
+    t_tr = time.perf_counter()
+    tb = synth.config_batch("c2", seed=21, n_events=80)
+    x_tr, y_tr, _ = train.training_set(cfg, tb, w, device=dev_index)
+    hist = []
+    w_tr = train.train(x_tr, y_tr, epochs=12, seed=0, history=hist)
+    t_tr = time.perf_counter() - t_tr
+    sel_fixed = selection(batch, probe)
+    ds.ds_load_nn_weights(d.ctx, w_tr)
+    probe_tr = d.run(batch, dev=devs[0])
+    mlp_forms = reduced_precision_forms(d, ds, torch, batch, devs, probe_tr, step, n_prof, stream, kernels, n_cand)
+    ds.ds_load_nn_weights(d.ctx, w)
+    trained = dict(events=80, candidates=int(len(y_tr)), ghost_fraction=float(y_tr.mean()), epochs=12,
+                   loss_first=hist[0], loss_last=hist[-1], seconds=t_tr,
+                   selection_fixed_seed_fp32=sel_fixed, selection_trained_fp32=selection(batch, probe_tr),
+                   note="trained on 80 other C2 events in training mode (100/10 mm windows, no clone "
+                        "killing); mlp_forms use these weights; the headline step uses the fixed-seed ones")
 
     path_bytes = 24 * S + 13 * H + 64 * n_t + 32 * n_v
     path = dict(bytes_per_step=path_bytes, gbs=path_bytes * args.steps / max(times) / 1e9,
@@ -781,7 +813,7 @@ def main():
 
     c5 = None
     if not args.no_c5:
-        c5 = bench_c5(ds, torch, cfg, w, dev_index)
+        c5 = bench_c5(ds, torch, cfg, w_tr, dev_index)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -797,7 +829,7 @@ def main():
                         l2=f"inputs rotate over {R} replicas ({R * in_bytes / 2**20:.0f} MB > 3x L2)",
                         parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
             roofline=roof, path_roofline=path, kernels=kernels, clocks=clocks, e2e=e2e, e2e_single_call=e2e_single,
-            mlp_forms=mlp_forms,
+            mlp_forms=mlp_forms, ghost_killer_training=trained,
             c3=c3, c5=c5,
             plain_form=dict(value=n_plain / plain_s, unit="events/s",
                             note="one event per ds_reconstruct + ds_vertex call, FP32", events=n_plain),
