@@ -28,9 +28,9 @@
  *                        Newton-Raphson point of closest approach; opposite charges
  *                        (Expected Physics Impact section)
  *
- * Readings where the paper is silent (window sizes, tie-breaks, fit model, the
- * 16 network inputs, pick key, stopping rule) are those listed in the design doc and
- * are restated at each step below.
+ * Where the paper is silent (window sizes, tie-breaks, fit model, the 16
+ * network inputs, pick key, stopping rule) the reading taken is stated at the
+ * step below.
  *
  * Every decision that could flip under a different rounding (window edges,
  * k-closest boundaries, key comparisons, thresholds) lowers a per-seed "margin":
