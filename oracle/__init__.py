@@ -211,6 +211,35 @@ def vertex(cfg: dict, trk_off, x, y, tx, ty, qop, cap: int | None = None) -> dic
                 iters=it[:k], margin=mg[:k], pairs=pairs.value)
 
 
+def vertex_info(cfg: dict, ti, tj, v) -> np.ndarray:
+    """One vertex's quantities: m_pipi, m_ppi, m_pip, |P|, P_T, ip, 1 - cos, p_pos, p_neg, pt_pos, pt_neg."""
+    out = np.zeros(11)
+    a = lambda t: np.ascontiguousarray(t, np.float64)
+    lib().or_vertex_info(C.byref(make_config(cfg)), _p(a(ti)), _p(a(tj)), _p(a(v)), _p(out))
+    return out
+
+
+def vertex_infos(cfg: dict, tracks: dict, vertices: dict, lines: list) -> dict:
+    """Info, 16 line-network inputs and line responses for every vertex.
+    tracks: arrays x, y, tx, ty, qop, chi2, ndof (output order); vertices: i, j,
+    pos [n, 3] (or x, y, z), doca."""
+    n = len(vertices["i"])
+    f32 = lambda k: np.ascontiguousarray(tracks[k], np.float32)
+    pos = vertices["pos"] if "pos" in vertices else np.stack([vertices["x"], vertices["y"], vertices["z"]], 1)
+    pos = np.ascontiguousarray(pos, np.float64)
+    doca = np.ascontiguousarray(vertices["doca"], np.float64)
+    vi = np.ascontiguousarray(vertices["i"], np.int32)
+    vj = np.ascontiguousarray(vertices["j"], np.int32)
+    ndof = np.ascontiguousarray(tracks["ndof"], np.int32)
+    holders = [_NNHolder(w) for w in lines]
+    arr = (OrNN * max(len(lines), 1))(*[h.s for h in holders])
+    info = np.zeros((n, 11)); feat = np.zeros((n, 16)); score = np.zeros((n, max(len(lines), 1)))
+    cols = [f32(k) for k in ("x", "y", "tx", "ty", "qop", "chi2")]
+    lib().or_vertex_infos(C.byref(make_config(cfg)), C.c_long(n), _p(vi), _p(vj), _p(pos), _p(doca), *[_p(c) for c in cols],
+                          _p(ndof), C.c_int(len(lines)), arr, _p(info), _p(feat), _p(score))
+    return dict(info=info, features=feat, score=score[:, :len(lines)])
+
+
 def seed_prediction(cfg: dict, x, y, tx, ty, qop) -> dict:
     """Magnet point, first-window prediction and window sizes of one seed (FP64)."""
     c = make_config(cfg)

@@ -671,3 +671,99 @@ long or_vertex(const or_config *c, int n_events, const int *trk_off, const float
     if (out_pairs) *out_pairs = pairs;
     return n;
 }
+
+/* ---------------------------------------------------- vertex-level physics */
+
+/* Masses used for the hypotheses (MeV/c^2). */
+#define OR_M_PI 139.57039
+#define OR_M_P 938.27208
+#define OR_M_KS 497.611
+#define OR_M_LAMBDA 1115.683
+
+/* Quantities of one two-track vertex (Expected Physics Impact section: K0S
+ * and Lambda candidates from two opposite-charge downstream tracks; Fig. 18:
+ * their masses once the vertex is known).  Track k = {x, y, tx, ty, q/p} at
+ * z_ref; vertex = {x, y, z}.  Each daughter's momentum at the vertex has
+ * magnitude 1/|q/p| and the direction of its Eq. 4 trajectory there:
+ * slopes (tx + 2 gamma (z_v - z_ref), ty), gamma from Eq. 3.  Masses are the
+ * plain definition M^2 = (E_1 + E_2)^2 - |p_1 + p_2|^2 under three
+ * hypotheses: pi+ pi- (K0S), proton = positive track with pi- (Lambda), pi+
+ * with antiproton = negative track (anti-Lambda).  Parent: P = p_1 + p_2, its
+ * magnitude, transverse momentum, and the distance of closest approach of the
+ * line {V + s P} to the beam line x = y = 0.
+ * out: m_pipi, m_ppi, m_pip, |P|, P_T, ip, 1 - cos(opening), p_pos, p_neg,
+ *      pt_pos, pt_neg.  The first track is taken as the positive one when
+ * q/p > 0, else the second. */
+void or_vertex_info(const or_config *c, const double *ti, const double *tj, const double *v, double *out)
+{
+    const double *tk[2] = {ti, tj};
+    double p3[2][3], pm[2], u[2][3];
+    for (int k = 0; k < 2; ++k) {
+        const double g = or_gamma(c, tk[k][4]);
+        const double txv = tk[k][2] + 2.0 * g * (v[2] - c->z_ref), tyv = tk[k][3];
+        const double n = sqrt(1.0 + txv * txv + tyv * tyv);
+        pm[k] = 1.0 / fabs(tk[k][4]);
+        u[k][0] = txv / n; u[k][1] = tyv / n; u[k][2] = 1.0 / n;
+        for (int a = 0; a < 3; ++a) p3[k][a] = pm[k] * u[k][a];
+    }
+    const int pos = ti[4] > 0.0 ? 0 : 1, neg = 1 - pos;
+    double P[3];
+    for (int a = 0; a < 3; ++a) P[a] = p3[0][a] + p3[1][a];
+    const double P2 = P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
+    const double mpos[3] = {OR_M_PI, OR_M_P, OR_M_PI}, mneg[3] = {OR_M_PI, OR_M_PI, OR_M_P};
+    for (int h = 0; h < 3; ++h) {
+        const double e = sqrt(pm[pos] * pm[pos] + mpos[h] * mpos[h]) + sqrt(pm[neg] * pm[neg] + mneg[h] * mneg[h]);
+        const double m2 = e * e - P2;
+        out[h] = m2 > 0.0 ? sqrt(m2) : 0.0;
+    }
+    out[3] = sqrt(P2);
+    const double pt = sqrt(P[0] * P[0] + P[1] * P[1]);
+    out[4] = pt;
+    out[5] = pt > 0.0 ? fabs(v[0] * P[1] - v[1] * P[0]) / pt : sqrt(v[0] * v[0] + v[1] * v[1]);
+    out[6] = 1.0 - (u[0][0] * u[1][0] + u[0][1] * u[1][1] + u[0][2] * u[1][2]);
+    out[7] = pm[pos];
+    out[8] = pm[neg];
+    out[9] = sqrt(p3[pos][0] * p3[pos][0] + p3[pos][1] * p3[pos][1]);
+    out[10] = sqrt(p3[neg][0] * p3[neg][0] + p3[neg][1] * p3[neg][1]);
+}
+
+/* The 16 inputs of the trigger-line networks (the paper lists track, vertex
+ * and parent-track parameters; this choice and its scales are the library's):
+ * vertex x/100, y/100, z/1000, DOCA; |P|/1e4, P_T/1e3, ip/10;
+ * (m_pipi - m_K0S)/100, (m_ppi - m_Lambda)/100, (m_pip - m_Lambda)/100;
+ * p_pos/1e4, p_neg/1e4, pt_pos/1e3, pt_neg/1e3; 1e3 (1 - cos opening);
+ * mean chi2/ndof of the two tracks. */
+void or_line_features(const double *v, double doca, const double *info, double chi2n_i, double chi2n_j,
+                      double *f)
+{
+    f[0] = v[0] / 100.0; f[1] = v[1] / 100.0; f[2] = v[2] / 1000.0; f[3] = doca;
+    f[4] = info[3] / 1e4; f[5] = info[4] / 1e3; f[6] = info[5] / 10.0;
+    f[7] = (info[0] - OR_M_KS) / 100.0;
+    f[8] = (info[1] - OR_M_LAMBDA) / 100.0;
+    f[9] = (info[2] - OR_M_LAMBDA) / 100.0;
+    f[10] = info[7] / 1e4; f[11] = info[8] / 1e4; f[12] = info[9] / 1e3; f[13] = info[10] / 1e3;
+    f[14] = 1e3 * info[6];
+    f[15] = 0.5 * (chi2n_i + chi2n_j);
+}
+
+/* Every vertex of a vertexer output: info (11 per vertex), features (16) and
+ * the responses of n_lines trigger-line networks (single hidden layer).
+ * Track arrays in output order (chi2, ndof per track); vertices (i, j global
+ * track indices, pos[3], doca). */
+void or_vertex_infos(const or_config *c, long n_vtx, const int *vi, const int *vj, const double *vpos,
+                     const double *vdoca, const float *x, const float *y, const float *tx, const float *ty,
+                     const float *qop, const float *chi2, const int *ndof, int n_lines, const or_nn *lines,
+                     double *out_info, double *out_feat, double *out_score)
+{
+    for (long k = 0; k < n_vtx; ++k) {
+        const int i = vi[k], j = vj[k];
+        double ti[5] = {x[i], y[i], tx[i], ty[i], qop[i]};
+        double tj[5] = {x[j], y[j], tx[j], ty[j], qop[j]};
+        double *info = out_info + 11 * k, *f = out_feat + 16 * k;
+        or_vertex_info(c, ti, tj, vpos + 3 * k, info);
+        const double ci = ndof[i] > 0 ? (double)chi2[i] / ndof[i] : 0.0;
+        const double cj = ndof[j] > 0 ? (double)chi2[j] / ndof[j] : 0.0;
+        or_line_features(vpos + 3 * k, vdoca[k], info, ci, cj, f);
+        for (int l = 0; l < n_lines; ++l) out_score[n_lines * k + l] = or_mlp(&lines[l], f);
+    }
+}

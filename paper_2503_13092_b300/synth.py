@@ -406,6 +406,20 @@ def nn_weights(n_in=16, n_h1=32, n_h2=32, seed=0, out_bias=0.0):
                 b3=b3, mean=mean[:n_in].copy(), scale=scale[:n_in].copy())
 
 
+
+def line_weights(n_lines=4, n_in=16, n_h1=32, seed=100):
+    """Fixed-seed trigger-line networks (Expected Physics Impact section: one
+    hidden layer of 32 nodes, one output): Xavier-uniform from PCG64(seed + k),
+    zero biases, identity normalisation (the 16 vertex inputs are scaled to
+    O(1) by their definition).  Not trained."""
+    nets = []
+    for k in range(n_lines):
+        w = nn_weights(n_in=n_in, n_h1=n_h1, n_h2=0, seed=seed + k)
+        w["mean"] = np.zeros(n_in, np.float32)
+        w["scale"] = np.ones(n_in, np.float32)
+        nets.append(w)
+    return nets
+
 # --------------------------------------------------------------------------------------
 # geometry + method parameters (plain numbers handed to both implementations)
 # --------------------------------------------------------------------------------------
