@@ -197,6 +197,22 @@ typedef struct {
     uint32_t flags;           /* bit0: solved in FP64 (near-parallel pair); bit1: not converged */
 } ds_vertex_rec;
 
+/* Vertex-level quantities, 64 bytes, one per vertex record (same order):
+ * masses under the K0S (pi+ pi-), Lambda (proton = positive track, pi-) and
+ * anti-Lambda (pi+, antiproton = negative track) hypotheses, the parent's
+ * momentum, transverse momentum and impact parameter to the beam line, the
+ * opening angle, the daughters' momenta, and the trigger-line responses. */
+typedef struct {
+    float m_pipi, m_ppi, m_pip; /* MeV/c^2 */
+    float p, pt;              /* parent |P| and P_T (MeV/c) */
+    float ip;                 /* distance of the line {V + s P} to x = y = 0 (mm) */
+    float one_minus_cos;      /* 1 - cos(opening angle) at the vertex */
+    float p_pos, p_neg;       /* daughter momenta (MeV/c) */
+    float pt_pos, pt_neg;     /* daughter transverse momenta at the vertex (MeV/c) */
+    float score[4];           /* trigger-line network responses (0 for unloaded lines) */
+    uint32_t flags;           /* reserved, 0 */
+} ds_vertex_info;
+
 typedef struct {
     ds_vertex_rec *vertices;  /* [capacity], (event, i, j) order */
     int32_t *vtx_off;         /* [n_events + 1] */
@@ -329,6 +345,28 @@ DS_API ds_status ds_mlp_eval(ds_ctx *ctx, const float *d_features, int32_t n, fl
  * than d_logit), misaligned arrays or capacity < 0. */
 DS_API ds_status ds_candidates(ds_ctx *ctx, float *d_features, int32_t *d_seed, int32_t *d_hits, float *d_logit,
                                int32_t capacity, int32_t *d_count, void *stream);
+
+/* Trigger-line networks (Expected Physics Impact section: single hidden
+ * layer of 32 nodes, one output; the paper has four: K0S, Lambda, detached
+ * K0S, detached Lambda).  n_lines <= 4 networks with n_in = 16, n_h1 <= 32,
+ * n_h2 = 0, copied into the context.  Their 16 inputs are listed at
+ * ds_vertex_physics.  DS_ERR_ARG for other shapes. */
+DS_API ds_status ds_load_line_weights(ds_ctx *ctx, const ds_nn_weights *nets, int32_t n_lines);
+
+/* Vertex-level physics for the output of ds_vertex: one ds_vertex_info per
+ * vertex record (Vertexing Two Downstream Tracks and Expected Physics Impact
+ * sections).  Each daughter's momentum at the vertex has magnitude 1/|q/p|
+ * and the direction of its Eq. 4 trajectory there (slopes tx + 2 gamma
+ * (z_v - z_ref), ty); masses use m_pi = 139.57039 and m_p = 938.27208 MeV/c^2.
+ * The line networks see: vertex x/100, y/100, z/1000 (mm), DOCA; |P|/1e4,
+ * P_T/1e3, ip/10; (m_pipi - 497.611)/100, (m_ppi - 1115.683)/100,
+ * (m_pip - 1115.683)/100; p_pos/1e4, p_neg/1e4, pt_pos/1e3, pt_neg/1e3;
+ * 1e3 (1 - cos opening); the mean chi2/ndof of the two tracks; then each
+ * network's own normalisation.  tracks and vertices: device outputs of
+ * ds_reconstruct / ds_vertex; d_info: device [capacity]; records beyond
+ * capacity are not written.  Asynchronous on `stream`. */
+DS_API ds_status ds_vertex_physics(ds_ctx *ctx, const ds_tracks *tracks, const ds_vertices *vertices,
+                                   ds_vertex_info *d_info, int32_t capacity, void *stream);
 
 /* Synchronise `stream`, read and clear the device flag word and counters.
  * Returns DS_ERR_CAPACITY / DS_ERR_TIMEOUT / DS_ERR_DEVICE_FLAG when the

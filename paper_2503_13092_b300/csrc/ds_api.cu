@@ -29,6 +29,7 @@ struct ds_ctx {
     int nn_in = 16, nn_h1 = 32, nn_h2 = 32;
     int mlp_precision = DS_MLP_FP32;
     ds::MlpTcWeights *d_tc = nullptr;    // tensor-core weight tiles (BF16 / FP8 network)
+    ds::DevLines lines{};                // trigger-line networks (none loaded: n_lines = 0)
     ds_tuning tune{kDefaultTuning};
     ds::DevCounters *d_cnt = nullptr;
     // workspaces
@@ -555,6 +556,42 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     xa.out = out->tracks;
     xa.capacity = out->capacity;
     DS_CUDA(ds::launch_clone(ca, xa, st, &ctx->prof), "clone kernel");
+    return DS_OK;
+}
+
+ds_status ds_load_line_weights(ds_ctx *ctx, const ds_nn_weights *nets, int32_t n_lines)
+{
+    if (!ctx) return DS_ERR_ARG;
+    ds::DevLines L;
+    const char *why = ds::fill_dev_lines(nets, n_lines, &L);
+    if (why) return fail(ctx, DS_ERR_ARG, why);
+    ctx->lines = L;
+    return DS_OK;
+}
+
+ds_status ds_vertex_physics(ds_ctx *ctx, const ds_tracks *tr, const ds_vertices *vx, ds_vertex_info *d_info,
+                            int32_t capacity, void *stream)
+{
+    if (!ctx || !tr || !vx || capacity < 0) return fail(ctx, DS_ERR_ARG, "null pointer or negative capacity");
+    if (!ctx->has_geom) return fail(ctx, DS_ERR_NOT_READY, "geometry not loaded");
+    if (capacity == 0 || tr->n_events == 0) return DS_OK;
+    if (!d_info || !tr->tracks || !tr->n_tracks || !vx->vertices || !vx->n_vertices)
+        return fail(ctx, DS_ERR_ARG, "null buffer");
+    if (reinterpret_cast<uintptr_t>(d_info) % 16 != 0) return fail(ctx, DS_ERR_ARG, "d_info must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    ds::VinfoArgs va{};
+    va.g = ctx->g;
+    va.L = ctx->lines;
+    va.tracks = tr->tracks;
+    va.trk_capacity = tr->capacity;
+    va.n_tracks = tr->n_tracks;
+    va.vtx = vx->vertices;
+    va.vtx_capacity = vx->capacity;
+    va.n_vertices = vx->n_vertices;
+    va.out = d_info;
+    va.capacity = capacity;
+    DS_CUDA(ds::launch_vertex_info(va, ctx->sm_count, st, &ctx->prof), "vertex physics kernel");
     return DS_OK;
 }
 

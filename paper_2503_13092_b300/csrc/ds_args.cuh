@@ -154,6 +154,33 @@ struct ScatterVtxArgs {
     const DevCounters *cnt;
 };
 
+// Trigger-line networks: up to 4 of 16 -> n_h1 (<= 32, zero-padded) -> 1.
+struct DevLines {
+    float w1[4][32][16];
+    float b1[4][32];
+    float w3[4][32];
+    float b3[4];
+    float mean[4][16];
+    float scale[4][16];
+    int n_lines;
+};
+
+struct VinfoArgs {
+    DevGeom g;
+    DevLines L;
+    const ds_track *tracks;
+    int trk_capacity;
+    const int32_t *n_tracks;
+    const ds_vertex_rec *vtx;
+    int vtx_capacity;
+    const int32_t *n_vertices;
+    ds_vertex_info *out;
+    int capacity;
+};
+
+cudaError_t launch_vertex_info(const VinfoArgs &a, int sm_count, cudaStream_t st, Prof *prof);
+const char *fill_dev_lines(const ds_nn_weights *nets, int n_lines, DevLines *out);
+
 // Host ABI structs -> device parameter blocks (nullptr = ok, else the reason).
 const char *fill_dev_geom(const ds_geometry *gm, DevGeom *out);
 const char *fill_dev_nn(const ds_nn_weights *w, DevNN *out, int *n_h2_kernel);

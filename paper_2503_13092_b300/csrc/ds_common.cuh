@@ -104,6 +104,7 @@ static_assert(sizeof(CandMeta) == 48, "CandMeta is 48 bytes");
 // Per-seed winner record in the workspace (same 64-byte layout as ds_track).
 static_assert(sizeof(ds_track) == 64, "ds_track must be 64 bytes");
 static_assert(sizeof(ds_vertex_rec) == 32, "ds_vertex_rec must be 32 bytes");
+static_assert(sizeof(ds_vertex_info) == 64, "ds_vertex_info must be 64 bytes");
 
 __device__ __forceinline__ void raise_flag(DevCounters *c, unsigned int bit)
 {

@@ -125,6 +125,11 @@ class ds_server_stats(C.Structure):
                 ("worker_finish_s", C.c_double), ("worker_wall_s", C.c_double)]
 
 
+VINFO_DTYPE = np.dtype([("m_pipi", "<f4"), ("m_ppi", "<f4"), ("m_pip", "<f4"), ("p", "<f4"), ("pt", "<f4"),
+                        ("ip", "<f4"), ("one_minus_cos", "<f4"), ("p_pos", "<f4"), ("p_neg", "<f4"),
+                        ("pt_pos", "<f4"), ("pt_neg", "<f4"), ("score", "<f4", 4), ("flags", "<u4")])
+assert VINFO_DTYPE.itemsize == 64
+
 TRACK_DTYPE = np.dtype([("event", "<i4"), ("seed", "<i4"), ("hit", "<i4", 4), ("x", "<f4"), ("y", "<f4"),
                         ("tx", "<f4"), ("ty", "<f4"), ("qop", "<f4"), ("chi2", "<f4"), ("ndof", "<i4"),
                         ("nn", "<f4"), ("flags", "<u4"), ("n_candidates", "<i4")])
@@ -167,6 +172,8 @@ def lib():
             "ds_get_tuning": ([P, C.POINTER(ds_tuning)], C.c_int),
             "ds_reserve_vertices": ([P, C.c_int32], C.c_int),
             "ds_candidates": ([P, P, P, P, P, C.c_int32, P, P], C.c_int),
+            "ds_load_line_weights": ([P, P, C.c_int32], C.c_int),
+            "ds_vertex_physics": ([P, C.POINTER(ds_tracks), C.POINTER(ds_vertices), P, C.c_int32, P], C.c_int),
             "ds_server_default_config": ([C.POINTER(ds_server_config)], None),
             "ds_server_create": ([C.POINTER(P), C.c_int, C.POINTER(ds_geometry), C.POINTER(ds_nn_weights),
                                   C.POINTER(ds_params), C.POINTER(ds_server_config)], C.c_int),
@@ -200,7 +207,8 @@ EXPORTED = ("ds_create", "ds_destroy", "ds_status_string", "ds_last_error", "ds_
             "ds_load_geometry", "ds_load_nn_weights", "ds_set_params", "ds_reserve", "ds_reconstruct",
             "ds_vertex", "ds_sync_status", "ds_process_host", "ds_profile_enable", "ds_profile_read",
             "ds_reconstruct_noalloc", "ds_mlp_eval", "ds_get_tuning", "ds_set_tuning", "ds_autotune",
-            "ds_reserve_vertices", "ds_candidates", "ds_server_default_config", "ds_server_create", "ds_server_submit",
+            "ds_reserve_vertices", "ds_candidates", "ds_load_line_weights", "ds_vertex_physics",
+            "ds_server_default_config", "ds_server_create", "ds_server_submit",
             "ds_server_now", "ds_server_poll", "ds_server_drain", "ds_server_stats_get", "ds_server_destroy")
 
 
@@ -371,6 +379,22 @@ def ds_candidates(ctx, features, seed, hits, logit, count, stream=None):
         raise ValueError("output arrays smaller than the capacity")
     _check(ctx, lib().ds_candidates(ctx, _ptr(features), _ptr(seed), _ptr(hits), _ptr(logit), cap, _ptr(count),
                                     _stream(stream)), "ds_candidates")
+
+
+def ds_load_line_weights(ctx, nets: list):
+    """Trigger-line networks: list of up to 4 weight dicts (16 -> n_h1 -> 1)."""
+    holders = [_NN(w) for w in nets]
+    arr = (ds_nn_weights * max(len(nets), 1))(*[h.s for h in holders])
+    return _check(ctx, lib().ds_load_line_weights(ctx, arr, len(nets)), "ds_load_line_weights")
+
+
+def ds_vertex_physics(ctx, trk_out: dict, vout: dict, info, stream=None):
+    """info: device uint8 tensor [capacity, 64] (VINFO_DTYPE records)."""
+    tr = trk_out["_struct"]
+    vx = ds_vertices(_ptr(vout["vertices"]), _ptr(vout["vtx_off"]), _ptr(vout["n_vertices"]),
+                     int(vout["vertices"].shape[0]), 0)
+    _check(ctx, lib().ds_vertex_physics(ctx, C.byref(tr), C.byref(vx), _ptr(info), int(info.shape[0]),
+                                        _stream(stream)), "ds_vertex_physics")
 
 
 def ds_reserve_vertices(ctx, capacity: int):

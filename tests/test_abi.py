@@ -49,17 +49,16 @@ def test_struct_layout_matches_header(tmp_path):
                "ds_kernel_time": ds.ds_kernel_time, "ds_tuning": ds.ds_tuning, "ds_tune_entry": ds.ds_tune_entry,
                "ds_server_config": ds.ds_server_config, "ds_request": ds.ds_request,
                "ds_completion": ds.ds_completion, "ds_server_stats": ds.ds_server_stats}
+    dtypes = {"ds_track": ds.TRACK_DTYPE, "ds_vertex_rec": ds.VERTEX_DTYPE, "ds_vertex_info": ds.VINFO_DTYPE}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ds.h"', '#include "ds_serve.h"', 'int main(void){']
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
         for f, _ in cls._fields_:
             lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
-    lines.append('printf("ds_track %zu\\n", sizeof(ds_track));')
-    for f in ds.TRACK_DTYPE.names:
-        lines.append(f'printf("ds_track.{f} %zu\\n", offsetof(ds_track, {f}));')
-    lines.append('printf("ds_vertex_rec %zu\\n", sizeof(ds_vertex_rec));')
-    for f in ds.VERTEX_DTYPE.names:
-        lines.append(f'printf("ds_vertex_rec.{f} %zu\\n", offsetof(ds_vertex_rec, {f}));')
+    for name, dt in dtypes.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f in dt.names:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
     lines.append("return 0;}")
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))
@@ -70,12 +69,10 @@ def test_struct_layout_matches_header(tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for f, _ in cls._fields_:
             assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
-    assert int(got["ds_track"]) == ds.TRACK_DTYPE.itemsize
-    for f in ds.TRACK_DTYPE.names:
-        assert int(got[f"ds_track.{f}"]) == ds.TRACK_DTYPE.fields[f][1], f
-    assert int(got["ds_vertex_rec"]) == ds.VERTEX_DTYPE.itemsize
-    for f in ds.VERTEX_DTYPE.names:
-        assert int(got[f"ds_vertex_rec.{f}"]) == ds.VERTEX_DTYPE.fields[f][1], f
+    for name, dt in dtypes.items():
+        assert int(got[name]) == dt.itemsize, name
+        for f in dt.names:
+            assert int(got[f"{name}.{f}"]) == dt.fields[f][1], (name, f)
 
 
 def test_host_side_errors_without_gpu(libpath):
