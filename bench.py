@@ -568,6 +568,37 @@ def e2e_pipelined(ds, torch, cfg, w, pin, E, S, H, dev_index, n_steps=10, slots=
                      "buffers, uploads, compute and downloads of consecutive steps overlapped")
 
 
+def vertex_physics_leg(d, ds, torch, synth, dv, out, vout, stream, n_v, reps=10):
+    """ds_vertex_physics on one step's vertices (four fixed-seed line networks,
+    FP32 on the CUDA cores and BF16 on the tensor cores): kernel time,
+    vertices/s and the algorithmic bytes rate (vertex record + two track
+    records read, one 64-byte record written)."""
+    ds.ds_load_line_weights(d.ctx, synth.line_weights())
+    d.reconstruct(dv, out, stream)
+    d.vertex(out, vout, stream)
+    info = torch.zeros((max(n_v, 1), 64), dtype=torch.uint8, device="cuda")
+    res = dict(vertices=int(n_v), lines=4,
+               note="per vertex: daughter momenta at the vertex, three mass hypotheses, parent P, P_T, impact "
+                    "parameter, 16 inputs, four 16-32-1 line networks")
+    for name, prec in (("fp32", ds.DS_MLP_FP32), ("bf16_tensor_cores", ds.DS_MLP_BF16)):
+        d.set_params(mlp_precision=prec)
+        for _ in range(3):
+            ds.ds_vertex_physics(d.ctx, out, vout, info, stream)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ds.ds_vertex_physics(d.ctx, out, vout, info, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / reps
+        d.sync(stream)
+        res[name] = dict(us=us, vertices_per_s=n_v / (us * 1e-6), gbs=224.0 * n_v / (us * 1e-6) / 1e9)
+    d.set_params(mlp_precision=ds.DS_MLP_FP32)
+    rec = info.cpu().numpy().view(ds.VINFO_DTYPE).reshape(-1)[:n_v]
+    res["k0s_window_fraction"] = float((np.abs(rec["m_pipi"] - 497.611) < 20.0).mean()) if n_v else 0.0
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -726,6 +757,9 @@ def main():
         roof = dict(kernel=dom, bound="hbm", achieved=kd["gbs"], peak=hbm, unit="GB/s", frac=frac_hbm,
                     peak_source=f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback",
                     traffic=traffic_for(dom))
+    # vertex-level physics + trigger-line networks on the step's vertices
+    vphys = vertex_physics_leg(d, ds, torch, synth, devs[0], out, vout, stream, n_v)
+
     # ghost killer trained on separate synthetic events (training mode, BCE +
     # Adam in FP64); the reduced-precision forms are compared with it loaded
     from paper_2503_13092_b300 import train
@@ -829,7 +863,7 @@ def main():
                         l2=f"inputs rotate over {R} replicas ({R * in_bytes / 2**20:.0f} MB > 3x L2)",
                         parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
             roofline=roof, path_roofline=path, kernels=kernels, clocks=clocks, e2e=e2e, e2e_single_call=e2e_single,
-            mlp_forms=mlp_forms, ghost_killer_training=trained,
+            mlp_forms=mlp_forms, ghost_killer_training=trained, vertex_physics=vphys,
             c3=c3, c5=c5,
             plain_form=dict(value=n_plain / plain_s, unit="events/s",
                             note="one event per ds_reconstruct + ds_vertex call, FP32", events=n_plain),

@@ -362,7 +362,11 @@ DS_API ds_status ds_load_line_weights(ds_ctx *ctx, const ds_nn_weights *nets, in
  * P_T/1e3, ip/10; (m_pipi - 497.611)/100, (m_ppi - 1115.683)/100,
  * (m_pip - 1115.683)/100; p_pos/1e4, p_neg/1e4, pt_pos/1e3, pt_neg/1e3;
  * 1e3 (1 - cos opening); the mean chi2/ndof of the two tracks; then each
- * network's own normalisation.  tracks and vertices: device outputs of
+ * network's own normalisation.  With mlp_precision FP32 the networks run on
+ * the CUDA cores in FP32; with BF16 or FP8 all four run as one BF16
+ * tensor-core product per 128 vertices (inputs and first-layer weights, with
+ * the normalisation folded in, rounded to BF16; FP32 accumulation, bias,
+ * ReLU and output node).  tracks and vertices: device outputs of
  * ds_reconstruct / ds_vertex; d_info: device [capacity]; records beyond
  * capacity are not written.  Asynchronous on `stream`. */
 DS_API ds_status ds_vertex_physics(ds_ctx *ctx, const ds_tracks *tracks, const ds_vertices *vertices,

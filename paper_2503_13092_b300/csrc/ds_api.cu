@@ -30,6 +30,7 @@ struct ds_ctx {
     int mlp_precision = DS_MLP_FP32;
     ds::MlpTcWeights *d_tc = nullptr;    // tensor-core weight tiles (BF16 / FP8 network)
     ds::DevLines lines{};                // trigger-line networks (none loaded: n_lines = 0)
+    ds::LineTcWeights *d_lines_tc = nullptr;   // their tensor-core operand
     ds_tuning tune{kDefaultTuning};
     ds::DevCounters *d_cnt = nullptr;
     // workspaces
@@ -328,7 +329,7 @@ void ds_destroy(ds_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    void *ptrs[] = {ctx->d_cnt, ctx->d_tc, ctx->sorted, ctx->sx0, ctx->item_cnt, ctx->item_off, ctx->bins, ctx->cand_feat,
+    void *ptrs[] = {ctx->d_cnt, ctx->d_tc, ctx->d_lines_tc, ctx->sorted, ctx->sx0, ctx->item_cnt, ctx->item_off, ctx->bins, ctx->cand_feat,
                     ctx->cand_meta, ctx->cand_logit, ctx->seed_cand, ctx->trk_ws, ctx->key_ws, ctx->hit_ws,
                     ctx->rank_ws, ctx->count_trk, ctx->count_vtx, ctx->large_vtx, ctx->pool, ctx->pool_pos,
                     ctx->h.seed_off, ctx->h.hit_off, ctx->h.seed_cols, ctx->h.hit_cols, ctx->h.layer,
@@ -565,6 +566,18 @@ ds_status ds_load_line_weights(ds_ctx *ctx, const ds_nn_weights *nets, int32_t n
     ds::DevLines L;
     const char *why = ds::fill_dev_lines(nets, n_lines, &L);
     if (why) return fail(ctx, DS_ERR_ARG, why);
+    ds::LineTcWeights tcw;
+    ds::prepare_line_tc(L, &tcw);
+    DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (!ctx->d_lines_tc) {
+        cudaError_t e = cudaMalloc((void **)&ctx->d_lines_tc, sizeof(tcw));
+        if (e != cudaSuccess) {
+            ctx->d_lines_tc = nullptr;
+            return fail(ctx, DS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+    }
+    DS_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    DS_CUDA(cudaMemcpy(ctx->d_lines_tc, &tcw, sizeof(tcw), cudaMemcpyHostToDevice), "line weight upload");
     ctx->lines = L;
     return DS_OK;
 }
@@ -591,7 +604,10 @@ ds_status ds_vertex_physics(ds_ctx *ctx, const ds_tracks *tr, const ds_vertices 
     va.n_vertices = vx->n_vertices;
     va.out = d_info;
     va.capacity = capacity;
-    DS_CUDA(ds::launch_vertex_info(va, ctx->sm_count, st, &ctx->prof), "vertex physics kernel");
+    va.tcw = ctx->d_lines_tc;
+    va.cnt = ctx->d_cnt;
+    const bool tensor_cores = ctx->mlp_precision != DS_MLP_FP32 && ctx->d_lines_tc != nullptr;
+    DS_CUDA(ds::launch_vertex_info(va, tensor_cores, ctx->sm_count, st, &ctx->prof), "vertex physics kernel");
     return DS_OK;
 }
 

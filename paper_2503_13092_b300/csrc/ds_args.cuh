@@ -165,9 +165,21 @@ struct DevLines {
     int n_lines;
 };
 
+// The line networks for the tensor-core kernel: first layers of all four as
+// one 128 x 16 BF16 operand (K-major core matrices), normalisation folded in.
+struct LineTcWeights {
+    uint8_t b_bf16[4096];
+    float b1[128];
+    float w3[128];
+    float b3[4];
+    int n_lines;
+};
+
 struct VinfoArgs {
     DevGeom g;
     DevLines L;
+    const LineTcWeights *tcw;   // device copy (tensor-core kernel)
+    DevCounters *cnt;
     const ds_track *tracks;
     int trk_capacity;
     const int32_t *n_tracks;
@@ -178,7 +190,8 @@ struct VinfoArgs {
     int capacity;
 };
 
-cudaError_t launch_vertex_info(const VinfoArgs &a, int sm_count, cudaStream_t st, Prof *prof);
+cudaError_t launch_vertex_info(const VinfoArgs &a, bool tensor_cores, int sm_count, cudaStream_t st, Prof *prof);
+void prepare_line_tc(const DevLines &L, LineTcWeights *out);
 const char *fill_dev_lines(const ds_nn_weights *nets, int n_lines, DevLines *out);
 
 // Host ABI structs -> device parameter blocks (nullptr = ok, else the reason).

@@ -110,3 +110,62 @@ def test_boosted_decays_give_their_mass(torch_cuda):
     assert np.all(got["score"] == 0)
     part = physics(t, d, out, vout, cap=7)
     assert len(part) == 7 and np.array_equal(part.view(np.uint8), got[:7].view(np.uint8))
+
+
+def _bf16(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
+
+
+def test_tensor_core_lines_match_their_specified_arithmetic(torch_cuda, weights):
+    """BF16 line networks (one N = 128 tcgen05 product per 128 vertices)
+    against the same arithmetic restated on the CPU from the kernel's own FP32
+    vertex quantities; and close to the FP32 networks."""
+    from paper_2503_13092_b300 import ds
+    t = torch_cuda
+    cfg = synth.default_config()
+    b = synth.config_batch("c2", seed=33, n_events=40)
+    nets = synth.line_weights()
+    for k, w in enumerate(nets):        # non-trivial normalisation, folded into the weights on the GPU
+        w["mean"] = np.linspace(-0.5, 0.5, 16).astype(np.float32) * (k + 1)
+        w["scale"] = np.linspace(0.5, 2.0, 16).astype(np.float32)
+        w["b1"] = np.linspace(-0.2, 0.2, 32).astype(np.float32)
+    d = ds.Downstream(cfg, weights)
+    ds.ds_load_line_weights(d.ctx, nets)
+    dev = d.to_device(b)
+    out = d.alloc_tracks(dev["n_events"], dev["n_seeds"])
+    d.reconstruct(dev, out)
+    vout = d.alloc_vertices(dev["n_events"], 16 * dev["n_seeds"] + 4096)
+    d.vertex(out, vout)
+    fp32 = physics(t, d, out, vout)
+    d.set_params(mlp_precision=ds.DS_MLP_BF16)
+    tc = physics(t, d, out, vout)
+    g = ds.decode(out, vout)
+    tr, v = g["tracks"], g["vertices"]
+    n = len(v)
+    assert n > 300 and len(tc) == n
+    names = ("m_pipi", "m_ppi", "m_pip", "p", "pt", "ip", "one_minus_cos", "p_pos", "p_neg", "pt_pos", "pt_neg")
+    for k in names:                      # the physics is the same code in both kernels
+        assert np.array_equal(tc[k], fp32[k]), k
+    f32 = np.float32
+    ca = tr["chi2"][v["i"]] / tr["ndof"][v["i"]].astype(f32)
+    cb = tr["chi2"][v["j"]] / tr["ndof"][v["j"]].astype(f32)
+    F = np.stack([v["x"] / f32(100), v["y"] / f32(100), v["z"] / f32(1000), v["doca"], tc["p"] / f32(1e4),
+                  tc["pt"] / f32(1e3), tc["ip"] / f32(10), (tc["m_pipi"] - f32(497.611)) / f32(100),
+                  (tc["m_ppi"] - f32(1115.683)) / f32(100), (tc["m_pip"] - f32(1115.683)) / f32(100),
+                  tc["p_pos"] / f32(1e4), tc["p_neg"] / f32(1e4), tc["pt_pos"] / f32(1e3), tc["pt_neg"] / f32(1e3),
+                  f32(1e3) * tc["one_minus_cos"], f32(0.5) * (ca + cb)], 1).astype(np.float32)
+    Fq = _bf16(t, F).astype(np.float64)
+    for k, w in enumerate(nets):
+        W = w["w1"].astype(np.float64).reshape(32, 16) * w["scale"].astype(np.float64)
+        b1 = (w["b1"].astype(np.float64) - W @ w["mean"].astype(np.float64)).astype(np.float32).astype(np.float64)
+        Wq = _bf16(t, W.astype(np.float32)).astype(np.float64)
+        acc = Fq @ Wq.T
+        h = np.maximum(acc + b1, 0.0)
+        terms = h * w["w3"].astype(np.float64)
+        z = float(w["b3"]) + terms.sum(1)
+        want = 1 / (1 + np.exp(-z))
+        bound = 0.25 * (1e-5 * (np.abs(terms).sum(1) + np.abs(acc) @ np.abs(w["w3"].astype(np.float64))) + 1e-6)
+        err = np.abs(tc["score"][:, k] - want)
+        assert np.all(err <= bound + 2e-7), (k, err.max())
+        # and the BF16 networks stay close to the FP32 ones
+        assert np.max(np.abs(tc["score"][:, k] - fp32["score"][:, k])) < 0.05
