@@ -42,7 +42,8 @@ class OrConfig(C.Structure):
                 ("dy_tol", C.c_double), ("nn_threshold", C.c_double), ("doca_max", C.c_double),
                 ("nr_tol", C.c_double), ("k1", C.c_int), ("first_window_origin", C.c_int),
                 ("pick_chi2", C.c_int), ("clone_kill", C.c_int), ("training", C.c_int),
-                ("nr_max_iter", C.c_int)]
+                ("nr_max_iter", C.c_int), ("variant", C.c_int), ("dv1_dtx_max", C.c_double),
+                ("dv1_w_tri", C.c_double)]
 
 
 class OrNN(C.Structure):
@@ -80,6 +81,9 @@ def make_config(cfg: dict) -> OrConfig:
         setattr(c, k, float(cfg[k]))
     for k in ("k1", "first_window_origin", "pick_chi2", "clone_kill", "training", "nr_max_iter"):
         setattr(c, k, int(cfg[k]))
+    c.variant = int(cfg.get("variant", 0))
+    c.dv1_dtx_max = float(cfg.get("dv1_dtx_max", 0.8))
+    c.dv1_w_tri = float(cfg.get("dv1_w_tri", 1.0))
     return c
 
 

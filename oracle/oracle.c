@@ -67,6 +67,9 @@ typedef struct {
     int clone_kill;
     int training;       /* fixed windows 100/10 mm, clone killing off */
     int nr_max_iter;
+    int variant;        /* 0: Dv0; 1: Dv1 (triplet search in UTaX x UTbX) */
+    double dv1_dtx_max; /* Dv1: largest kink |tx_UT - tx_seed| a UTbX hit may imply */
+    double dv1_w_tri;   /* Dv1: UTaX hit within this distance of the magnet-point line */
 } or_config;
 
 typedef struct {
@@ -300,6 +303,54 @@ void or_seed_prediction(const or_config *c, double x_s, double y_s, double tx_s,
     out[10] = tx_ut;
 }
 
+/* Dv1 (Algorithm Design section): triplets (magnet point, UTaX hit, UTbX hit)
+ * in the axial layers, with no momentum-dependent first window.  Every UTbX
+ * hit whose strip spans y and whose implied kink is physical,
+ * |tx' - tx_s| < dtx_max with tx' = (x_h - x_m)/(z_bX - z_m) (a window of
+ * half-width dtx_max (z_m - z_bX) around the straight extrapolation of the
+ * seed), is joined to the magnet point; the closest UTaX hit (by (|dx|, id))
+ * within w_tri of that line at z_aX completes the triplet, whose residual is
+ * that distance.  Triplets are ranked by (residual, UTbX hit id) and the first
+ * `keep` are kept: bx (UTbX), ax (UTaX) local indices, d (residual). */
+static int triplet_search(const or_config *c, const or_event_hits *ev, double xm, double zm, double tx_s,
+                          const double *yl, int keep, int *bx, int *ax, double *d, double *m, double sxs,
+                          double sys)
+{
+    const double w_b = c->dv1_dtx_max * (zm - c->z[3]);
+    const double u0 = xm + tx_s * (c->z[3] - zm) - c->dxdy[3] * yl[3];
+    int *cand = (int *)malloc(sizeof(int) * (size_t)(ev->n > 0 ? ev->n : 1));
+    double *cd = (double *)malloc(sizeof(double) * (size_t)(ev->n > 0 ? ev->n : 1));
+    const int nb = window_search(c, ev, 3, u0, yl[3], w_b, ev->n > 0 ? ev->n : 1, cand, cd, m, sxs, sys);
+    or_ranked *q = (or_ranked *)malloc(sizeof(or_ranked) * (size_t)(nb > 0 ? nb : 1));
+    int *qa = (int *)malloc(sizeof(int) * (size_t)(nb > 0 ? nb : 1));
+    int nq = 0;
+    for (int k = 0; k < nb; ++k) {
+        const int hb = cand[k];
+        const double x_h = (double)ev->x0[hb] + c->dxdy[3] * yl[3];
+        const double txp = (x_h - xm) / (c->z[3] - zm);
+        const double ua = x_h + txp * (c->z[0] - c->z[3]) - c->dxdy[0] * yl[0];
+        int a;
+        double da;
+        if (window_search(c, ev, 0, ua, yl[0], c->dv1_w_tri, 1, &a, &da, m, sxs, sys) == 0) continue;
+        q[nq].d = da;
+        q[nq].id = ev->id0 + hb;
+        q[nq].idx = nq;
+        qa[nq] = a;
+        cand[nq] = hb;      /* compact in place: k >= nq */
+        ++nq;
+    }
+    qsort(q, (size_t)nq, sizeof(or_ranked), cmp_ranked);
+    if (nq > keep) upd_margin(m, q[keep - 1].d, q[keep].d, c->dv1_w_tri);
+    const int n = nq < keep ? nq : keep;
+    for (int i = 0; i < n; ++i) {
+        bx[i] = cand[q[i].idx];
+        ax[i] = qa[q[i].idx];
+        d[i] = q[i].d;
+    }
+    free(q); free(qa); free(cand); free(cd);
+    return n;
+}
+
 /* Full per-seed method.  Returns the number of candidates; the winner (if any)
  * goes to *best and *has_best is set.  cands/max_c optionally receive every
  * candidate (for tests and for training-sample dumps). */
@@ -320,10 +371,14 @@ static int process_seed(const or_config *c, const or_nn *nn, const or_event_hits
     const double sxs = fmax(fmax(fabs(x_s), fabs(tx_s * (zm - c->z_seed))), fmax(fabs(xm), 1.0));
     const double sys = fmax(fmax(fabs(y_s), fabs(ty_s * (zm - c->z_seed))), fmax(fabs(ym), 1.0));
 
-    int bx[OR_MAX_K1];
+    int bx[OR_MAX_K1], ax[OR_MAX_K1];
     double bx_d[OR_MAX_K1];
     const int k1 = c->k1 < OR_MAX_K1 ? c->k1 : OR_MAX_K1;
-    int nbx = window_search(c, ev, 3, u_bx, yl[3], w1, k1, bx, bx_d, &m, sxs, sys);
+    int nbx;
+    if (c->variant == 1)
+        nbx = triplet_search(c, ev, xm, zm, tx_s, yl, k1, bx, ax, bx_d, &m, sxs, sys);
+    else
+        nbx = window_search(c, ev, 3, u_bx, yl[3], w1, k1, bx, bx_d, &m, sxs, sys);
     if (n_bx_out) *n_bx_out = nbx;
 
     int ncand = 0;
@@ -340,6 +395,11 @@ static int process_seed(const or_config *c, const or_nn *nn, const or_event_hits
         int sel[3][2], nsel[3];
         const int keep[3] = {1, 2, 2};
         for (int l = 0; l < 3; ++l) {
+            if (l == 0 && c->variant == 1) {   /* Dv1: the triplet's UTaX hit */
+                sel[0][0] = ax[j];
+                nsel[0] = 1;
+                continue;
+            }
             double xl = x_h + txp * (c->z[l] - c->z[3]);
             double ul = xl - c->dxdy[l] * yl[l];
             nsel[l] = window_search(c, ev, l, ul, yl[l], w2, keep[l], sel[l], NULL, &m, sxs, sys);
@@ -383,7 +443,7 @@ static int process_seed(const or_config *c, const or_nn *nn, const or_event_hits
                     p[6] = 1000.0 * qop_s; p[7] = chi2_s;
                     for (int l = 0; l < 4; ++l) p[8 + l] = res[l] / c->sigma_hit;
                     p[12] = nh / 4.0;
-                    p[13] = bx_d[j] / w1;
+                    p[13] = c->variant == 1 ? bx_d[j] / c->dv1_w_tri : bx_d[j] / w1;
                     p[14] = tx_s; p[15] = ty_s;
                     /* candidates are ranked by the network output before the
                      * sigmoid: the same order as the response, without the

@@ -444,6 +444,7 @@ def default_config(world: World = WORLD, mode: str = "A", **overrides):
         w1a=3.0, w1b=1.7e5, w2=2.0, dy_tol=2.0, k1=10,
         first_window_origin=0, pick_chi2=0, clone_kill=1, training=0,
         nn_threshold=0.5, doca_max=2.0, nr_tol=1e-6, nr_max_iter=10,
+        variant=0, dv1_dtx_max=0.8, dv1_w_tri=1.0,
     )
     for k, v in overrides.items():
         if k not in cfg:

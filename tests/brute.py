@@ -49,12 +49,17 @@ def seed_best(batch, cfg, w, s):
     w1 = cfg["w1a"] + cfg["w1b"] * abs(qop)
     per_layer = [[h for h in range(h0, h1) if batch["hit_layer"][h] == l] for l in range(4)]
     opts = [(p if p else [-1]) for p in per_layer[:3]]
+    dv1 = int(cfg.get("variant", 0)) == 1
+    if dv1:                                  # Dv1: the UTaX hit is part of every triplet
+        assert len(per_layer[0]) == 1
     cands = []
     for hb in per_layer[3]:
         for combo in itertools.product(*opts):
             hits = list(combo) + [hb]
             present = [l for l in range(4) if hits[l] >= 0]
             if len(present) < 3 or (hits[0] < 0 and hits[1] < 0):
+                continue
+            if dv1 and hits[0] < 0:
                 continue
             rows_z = [z[l] - cfg["z_ref"] for l in present] + [zm - cfg["z_ref"]]
             meas = [float(batch["hit_x0"][hits[l]]) + dxdy[l] * yl[l] for l in present] + [xm]
@@ -71,9 +76,14 @@ def seed_best(batch, cfg, w, s):
                 res[l] = float(batch["hit_x0"][hits[l]]) + dxdy[l] * yl[l] - (xr + t * (z[l] - cfg["z_ref"]))
             yr = ym + ty * (cfg["z_ref"] - zm)
             q = cfg["mp"] * (t - tx) / cfg["kappa"] / np.sqrt(1 + t * t + ty * ty) if cfg["kappa"] != 0 else qop
+            if dv1:
+                x_h = float(batch["hit_x0"][hb]) + dxdy[3] * yl[3]
+                u_a = x_h + (x_h - xm) / (z[3] - zm) * (z[0] - z[3]) - dxdy[0] * yl[0]
+                p13 = abs(float(batch["hit_x0"][hits[0]]) - u_a) / cfg["dv1_w_tri"]
+            else:
+                p13 = abs(float(batch["hit_x0"][hb]) - u_bx) / w1
             phi = np.array([xr / 1e3, yr / 1e3, t, ty, 1e3 * q, chi2 / ndof, 1e3 * qop, chi2s,
-                            *(res / cfg["sigma_hit"]), len(present) / 4,
-                            abs(float(batch["hit_x0"][hb]) - u_bx) / w1, tx, ty])
+                            *(res / cfg["sigma_hit"]), len(present) / 4, p13, tx, ty])
             cands.append(dict(hits=[h if h >= 0 else -1 for h in hits], state=[xr, yr, t, ty, q],
                               chi2=chi2, ndof=ndof, phi=phi))
     if not cands:
