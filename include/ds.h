@@ -136,7 +136,13 @@ typedef struct {
     int32_t cand_per_seed; /* candidate buffer size per seed on average (default 16, max
                               40 = 10 x 1 x 2 x 2; training mode always uses 40); exceeding
                               it raises DS_FLAG_CAND_CAPACITY */
-    int32_t reserved1;
+    int32_t variant;       /* 0: Dv0 (default).  1: Dv1 (Algorithm Design section): every
+                              UTbX hit whose implied kink |tx' - tx_seed| < dv1_dtx_max is
+                              joined to the magnet point; the closest UTaX hit within
+                              dv1_w_tri of that line completes a triplet; the k1 triplets
+                              with the smallest residual go on to the stereo windows */
+    double dv1_dtx_max;    /* Dv1 kink bound (default 0.8: p above ~1.5 GeV/c) */
+    double dv1_w_tri;      /* Dv1 UTaX collinearity tolerance, mm (default 1) */
 } ds_params;
 
 /* One event batch (CSR over events).  Device pointers. */

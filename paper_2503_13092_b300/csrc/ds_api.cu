@@ -227,6 +227,8 @@ const char *fill_dev_params(const ds_params *p, DevParams *out)
     if (p->mlp_precision != DS_MLP_FP32 && p->mlp_precision != DS_MLP_BF16 && p->mlp_precision != DS_MLP_FP8)
         return "unknown mlp_precision";
     if (p->cand_per_seed < 1 || p->cand_per_seed > 40) return "cand_per_seed outside 1..40";
+    if (p->variant != 0 && p->variant != 1) return "variant must be 0 (Dv0) or 1 (Dv1)";
+    if (p->variant == 1 && (!(p->dv1_dtx_max > 0) || !(p->dv1_w_tri > 0))) return "Dv1 bounds must be positive";
     DevParams &d = *out;
     d.w1a = (float)p->w1a;
     d.w1b = (float)p->w1b;
@@ -249,6 +251,9 @@ const char *fill_dev_params(const ds_params *p, DevParams *out)
     d.training = p->training ? 1 : 0;
     d.nr_max_iter = p->nr_max_iter;
     d.fault_inject = p->fault_inject;
+    d.variant = p->variant;
+    d.dv1_dtx = (float)p->dv1_dtx_max;
+    d.dv1_w_tri = (float)p->dv1_w_tri;
     return nullptr;
 }
 
@@ -293,6 +298,9 @@ ds_status ds_default_params(ds_params *p)
     p->nr_max_iter = 10;
     p->mlp_precision = DS_MLP_FP32;
     p->cand_per_seed = 16;
+    p->variant = 0;
+    p->dv1_dtx_max = 0.8;
+    p->dv1_w_tri = 1.0;
     return DS_OK;
 }
 

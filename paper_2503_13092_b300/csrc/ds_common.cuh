@@ -58,6 +58,8 @@ struct DevParams {
     float thr_logit;                 // ln(T / (1 - T)): response < T <=> logit < thr_logit
     int k1, origin, pick_chi2, clone_kill, training, nr_max_iter;
     int fault_inject;                // tests only: bit 0 stalls the staging barrier
+    int variant;                     // 0: Dv0, 1: Dv1 (triplet search)
+    float dv1_dtx, dv1_w_tri;        // Dv1 kink bound and UTaX tolerance
 };
 
 // Ghost-killer weights padded to the largest supported shape 16-32-32-1.

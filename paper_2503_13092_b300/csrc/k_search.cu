@@ -224,6 +224,17 @@ __device__ __forceinline__ CandFit fit_candidate(const DevGeom &g, const SeedCtx
     return f;
 }
 
+// Dv1: the UTaX strip coordinate predicted by the line through the magnet
+// point and the UTbX hit at sorted position ib.
+__device__ __forceinline__ float dv1_ua(const DevGeom &g, const SeedCtx &sc, const float *X0, int ib)
+{
+    const float x_h = fmaf(g.dxdy[3], sc.yl[3], X0[ib]);
+    const float txp = (x_h - sc.xm) / (g.z[3] - sc.zm);
+    return fmaf(txp, g.z[0] - g.z[3], x_h) - g.dxdy[0] * sc.yl[0];
+}
+
+// V = 0: Dv0.  V = 1: Dv1, whose first stage is the triplet search.
+template <int V>
 __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char s_dyn[];   // bin table, then staged x0
@@ -333,10 +344,50 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
 
         float d[kK1Max];
         int id[kK1Max], p[kK1Max];
-        const int q = window_scan<kK1Max, 4>(g, X0, H, Tb, 3, u_bx, sc.yl[3], sc.w1, P.dy_tol, d, id, p);
-        nbx = min(q, P.k1);
+        if (V == 0) {
+            const int q = window_scan<kK1Max, 4>(g, X0, H, Tb, 3, u_bx, sc.yl[3], sc.w1, P.dy_tol, d, id, p);
+            nbx = min(q, P.k1);
 #pragma unroll
-        for (int j = 0; j < kK1Max; ++j) s_bx[j][tid] = (uint16_t)p[j];
+            for (int j = 0; j < kK1Max; ++j) s_bx[j][tid] = (uint16_t)p[j];
+        } else {
+            // Dv1 triplets: every UTbX hit with a physical kink (a window of
+            // half-width dtx_max (z_m - z_bX) around the seed's straight
+            // extrapolation) whose magnet-point line meets a UTaX hit within
+            // w_tri; ranked by (residual, UTbX id).  p packs (UTbX, UTaX) positions.
+#pragma unroll
+            for (int k = 0; k < kK1Max; ++k) {
+                d[k] = __int_as_float(0x7f800000);
+                id[k] = 0x7fffffff;
+                p[k] = -1;
+            }
+            const float w_b = P.dv1_dtx * (sc.zm - g.z[3]);
+            const float u0 = fmaf(sc.tx, g.z[3] - sc.zm, sc.xm) - g.dxdy[3] * sc.yl[3];
+            const float y3 = sc.yl[3], dy = P.dy_tol;
+            const int s_lo = sector_of(g, y3 - dy - 0.01f), s_hi = sector_of(g, y3 + dy + 0.01f);
+            const int b0 = xbin_of(g, u0 - w_b - 1e-3f), b1 = xbin_of(g, u0 + w_b + 1e-3f);
+            int n_tri = 0;
+            for (int sct = s_lo; sct <= s_hi; ++sct) {
+                const int row = (3 * g.n_sec + sct) * kNXB;
+                const int i0 = Tb[row + b0], i1 = Tb[row + b1 + 1];
+                for (int i = i0; i < i1; ++i) {
+                    if (!(fabsf(X0[i] - u0) < w_b)) continue;
+                    const float4 hb = __ldg(H + i);
+                    if (!(hb.y - dy <= y3 && y3 <= hb.z + dy)) continue;
+                    float dd[1];
+                    int ii[1], pp[1];
+                    const float ua = dv1_ua(g, sc, X0, i);
+                    if (window_scan<1, 3>(g, X0, H, Tb, 0, ua, sc.yl[0], P.dv1_w_tri, dy, dd, ii, pp) == 0) continue;
+                    topn_insert<kK1Max>(d, id, p, dd[0], __float_as_int(hb.w), i | (pp[0] << 16));
+                    ++n_tri;
+                }
+            }
+            nbx = min(n_tri, P.k1);
+#pragma unroll
+            for (int j = 0; j < kK1Max; ++j) {
+                s_bx[j][tid] = (uint16_t)(p[j] & 0xffff);
+                s_sel[j][0][tid] = j < nbx ? (uint16_t)((unsigned)p[j] >> 16) : kNone;   // the triplet's UTaX hit
+            }
+        }
     }
     int total_j;
     const int jbase = block_exclusive_scan(nbx, s_scan, &total_j);
@@ -360,7 +411,9 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
         const float xh = x0b + g.dxdy[3] * sc.yl[3];
         const float txp = (xh - sc.xm) / (g.z[3] - sc.zm);
         int sel[5];
-        {
+        if (V == 1) {
+            sel[0] = s_sel[j][0][o];            // Dv1: the triplet's UTaX hit
+        } else {
             float dd[1]; int ii[1], pp[1];
             const float ul = fmaf(txp, g.z[0] - g.z[3], xh) - g.dxdy[0] * sc.yl[0];
             const int c = window_scan<1, 3>(g, X0, H, Tb, 0, ul, sc.yl[0], w2, P.dy_tol, dd, ii, pp);
@@ -441,7 +494,8 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
 #pragma unroll
         for (int l = 0; l < 4; ++l) phi[8 + l] = f.res[l] * g.inv_sigma_hit;
         phi[12] = 0.25f * (float)f.nh;
-        phi[13] = fabsf(X0[loc[3]] - sc.u_bx) / sc.w1;
+        phi[13] = V == 1 ? fabsf(X0[loc[0]] - dv1_ua(g, sc, X0, loc[3])) / P.dv1_w_tri
+                         : fabsf(X0[loc[3]] - sc.u_bx) / sc.w1;
         phi[14] = sc.tx;
         phi[15] = sc.ty;
         const int slot = cand0 + c;
@@ -470,13 +524,18 @@ cudaError_t init_search_attributes()
     const int smem = (int)(sizeof(uint16_t) * (((4 * kMaxSectors * kNXB + 1) + 7) & ~7) + sizeof(float) * (kStageHitsMax + 4));
     cudaFuncAttributes fa;
     int dev = 0, optin = 0;
-    cudaError_t e = cudaFuncGetAttributes(&fa, k_search);
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_search<0>);
+    cudaFuncAttributes fa1;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa1, k_search<1>);
+    if (e == cudaSuccess && fa1.sharedSizeBytes > fa.sharedSizeBytes) fa = fa1;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     if ((size_t)smem + fa.sharedSizeBytes > (size_t)optin) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(k_search, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    for (auto fn : {k_search<0>, k_search<1>}) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
     return e;
 }
 
@@ -491,7 +550,8 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
     if (grid > items_max) grid = items_max;
     const size_t smem = sizeof(uint16_t) * a.g.table_stride + sizeof(float) * (a.stage_hits + 4);
     prof->begin("k_search", st);
-    k_search<<<grid, T, smem, st>>>(a);
+    if (a.p.variant == 1) k_search<1><<<grid, T, smem, st>>>(a);
+    else k_search<0><<<grid, T, smem, st>>>(a);
     prof->end(st);
     return cudaGetLastError();
 }

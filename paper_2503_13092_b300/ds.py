@@ -48,7 +48,8 @@ class ds_params(C.Structure):
                 ("eps_parallel", C.c_double), ("k1", C.c_int32), ("first_window_origin", C.c_int32),
                 ("pick_chi2", C.c_int32), ("clone_kill", C.c_int32), ("training", C.c_int32),
                 ("nr_max_iter", C.c_int32), ("mlp_precision", C.c_int32), ("fault_inject", C.c_int32),
-                ("cand_per_seed", C.c_int32), ("reserved1", C.c_int32)]
+                ("cand_per_seed", C.c_int32), ("variant", C.c_int32), ("dv1_dtx_max", C.c_double),
+                ("dv1_w_tri", C.c_double)]
 
 
 class ds_event_batch(C.Structure):
@@ -264,6 +265,9 @@ def make_params(cfg: dict, **over) -> ds_params:
         setattr(p, k, float(cfg[k]))
     for k in ("k1", "first_window_origin", "pick_chi2", "clone_kill", "training", "nr_max_iter"):
         setattr(p, k, int(cfg[k]))
+    p.variant = int(cfg.get("variant", 0))
+    p.dv1_dtx_max = float(cfg.get("dv1_dtx_max", 0.8))
+    p.dv1_w_tri = float(cfg.get("dv1_w_tri", 1.0))
     for k, v in over.items():
         setattr(p, k, v)
     return p
