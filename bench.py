@@ -599,6 +599,37 @@ def vertex_physics_leg(d, ds, torch, synth, dv, out, vout, stream, n_v, reps=10)
     return res
 
 
+def dv1_leg(ds, torch, cfg, w, batch, dv, dev_index, reps=10):
+    """The paper's two variants on the step's batch: Dv0 (momentum window in
+    UTbX) and Dv1 (triplet search in UTaX x UTbX), with Dv0's origin-pointing
+    window (the paper's first version) beside them; device time of
+    ds_reconstruct + ds_vertex and the chi2-pick selection against truth."""
+    res = {}
+    for name, over in (("dv0_kick", dict(variant=0)), ("dv0_origin", dict(variant=0, first_window_origin=1)),
+                       ("dv1", dict(variant=1))):
+        c = dict(cfg, pick_chi2=1, nn_threshold=2.0, **over)
+        d = ds.Downstream(c, w, device=dev_index)
+        g = d.run(batch, dev=dv)
+        out = d.alloc_tracks(dv["n_events"], dv["n_seeds"])
+        vout = d.alloc_vertices(dv["n_events"], 2 * int(g["n_vertices"]) + 4096)
+        st = torch.cuda.current_stream()
+        for _ in range(3):
+            d.reconstruct(dv, out, st); d.vertex(out, vout, st)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            d.reconstruct(dv, out, st); d.vertex(out, vout, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        d.sync(st)
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = dict(ms_per_step=ms, events_per_s=dv["n_events"] / (ms * 1e-3), **selection(batch, g))
+        d.close()
+    res["note"] = ("chi2 pick (the paper's distance score) so that the variants are compared without a trained "
+                   "network; eager launches")
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -614,7 +645,9 @@ def main():
     ap.add_argument("--no-c3", action="store_true", help="skip the config-3 (log-normal, 10000 events) leg")
     ap.add_argument("--no-c5", action="store_true", help="skip the config-5 (serving loop) leg")
     ap.add_argument("--mlp-precision", default="fp32", choices=["fp32", "bf16", "fp8"],
-                    help="ghost-killer arithmetic in the --ncu profiling run")
+                    help="network arithmetic (ghost killer and trigger lines) in the --ncu profiling run")
+    ap.add_argument("--physics", action="store_true", help="--ncu run: add ds_vertex_physics to every step")
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1], help="--ncu run: 1 = Dv1 triplet search")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -641,12 +674,20 @@ def main():
     if args.ncu:
         d.set_params(mlp_precision={"fp32": ds.DS_MLP_FP32, "bf16": ds.DS_MLP_BF16, "fp8": ds.DS_MLP_FP8}[
             args.mlp_precision])
+        if args.variant:
+            d.set_params(variant=1)
         dv = d.to_device(batch)
         out = d.alloc_tracks(E, S)
         vout = d.alloc_vertices(E, 16 * S + 4096)
+        info = None
+        if args.physics:
+            ds.ds_load_line_weights(d.ctx, synth.line_weights())
+            info = torch.zeros((16 * S + 4096, 64), dtype=torch.uint8, device="cuda")
         for _ in range(args.warmup + args.steps):
             d.reconstruct(dv, out)
             d.vertex(out, vout)
+            if info is not None:
+                ds.ds_vertex_physics(d.ctx, out, vout, info)
         st = d.sync()
         print(json.dumps(dict(ncu_run=True, steps=args.warmup + args.steps, status=st["status"],
                               tracks=st["n_tracks"], vertices=st["n_vertices"])), flush=True)
@@ -757,6 +798,8 @@ def main():
         roof = dict(kernel=dom, bound="hbm", achieved=kd["gbs"], peak=hbm, unit="GB/s", frac=frac_hbm,
                     peak_source=f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback",
                     traffic=traffic_for(dom))
+    variants = dv1_leg(ds, torch, cfg, w, batch, devs[0], dev_index)
+
     # vertex-level physics + trigger-line networks on the step's vertices
     vphys = vertex_physics_leg(d, ds, torch, synth, devs[0], out, vout, stream, n_v)
 
@@ -863,7 +906,7 @@ def main():
                         l2=f"inputs rotate over {R} replicas ({R * in_bytes / 2**20:.0f} MB > 3x L2)",
                         parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
             roofline=roof, path_roofline=path, kernels=kernels, clocks=clocks, e2e=e2e, e2e_single_call=e2e_single,
-            mlp_forms=mlp_forms, ghost_killer_training=trained, vertex_physics=vphys,
+            mlp_forms=mlp_forms, ghost_killer_training=trained, vertex_physics=vphys, variants=variants,
             c3=c3, c5=c5,
             plain_form=dict(value=n_plain / plain_s, unit="events/s",
                             note="one event per ds_reconstruct + ds_vertex call, FP32", events=n_plain),

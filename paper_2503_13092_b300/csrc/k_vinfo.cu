@@ -109,12 +109,14 @@ __global__ void __launch_bounds__(256) k_vertex_info(const __grid_constant__ Vin
         if (vertex_quantities(a, nt, v, q11, f)) {
 #pragma unroll
             for (int q = 0; q < 11; ++q) r[q] = q11[q];
-            for (int l = 0; l < L.n_lines; ++l) {
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {        // compile-time weight indices (parameter bank operands)
+                if (l >= L.n_lines) break;
                 float x[16];
 #pragma unroll
                 for (int q = 0; q < 16; ++q) x[q] = (f[q] - L.mean[l][q]) * L.scale[l][q];
                 float out = L.b3[l];
-#pragma unroll 4
+#pragma unroll
                 for (int o = 0; o < 32; ++o) {
                     float h = L.b1[l][o];
 #pragma unroll
