@@ -345,10 +345,61 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
         float d[kK1Max];
         int id[kK1Max], p[kK1Max];
         if (V == 0) {
-            const int q = window_scan<kK1Max, 4>(g, X0, H, Tb, 3, u_bx, sc.yl[3], sc.w1, P.dy_tol, d, id, p);
-            nbx = min(q, P.k1);
+            // UTbX window: x-passing positions collected in this thread's
+            // column of s_sel (free until the refined windows), their records
+            // loaded together for the strip test, the survivors insertion-sorted
+            // by (|dx|, id) in place (ids loaded only on exact distance ties)
+            uint16_t *col = &s_sel[0][0][0] + tid;
+            constexpr int kCap = kK1Max * 5;
+            const float u = u_bx, w = sc.w1, y3 = sc.yl[3], dy = P.dy_tol;
+            const int s_lo = sector_of(g, y3 - dy - 0.01f), s_hi = sector_of(g, y3 + dy + 0.01f);
+            const int b0 = xbin_of(g, u - w - 1e-3f), b1 = xbin_of(g, u + w + 1e-3f);
+            int nq = 0;
+            for (int sct = s_lo; sct <= s_hi; ++sct) {
+                const int row = (3 * g.n_sec + sct) * kNXB;
+                const int i0 = Tb[row + b0], i1 = Tb[row + b1 + 1];
+                for (int i = i0; i < i1; ++i)
+                    if (fabsf(X0[i] - u) < w) {
+                        if (nq < kCap) col[nq * T] = (uint16_t)i;
+                        ++nq;
+                    }
+            }
+            if (nq > kCap) {
+                const int q = window_scan<kK1Max, 4>(g, X0, H, Tb, 3, u_bx, sc.yl[3], sc.w1, P.dy_tol, d, id, p);
+                nbx = min(q, P.k1);
 #pragma unroll
-            for (int j = 0; j < kK1Max; ++j) s_bx[j][tid] = (uint16_t)p[j];
+                for (int j = 0; j < kK1Max; ++j) s_bx[j][tid] = (uint16_t)p[j];
+            } else {
+                int nok = 0;
+                for (int k0 = 0; k0 < nq; k0 += 4) {
+                    float4 h[4];
+                    int ii[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        ii[k] = k0 + k < nq ? col[(k0 + k) * T] : -1;
+                        if (ii[k] >= 0) h[k] = __ldg(H + ii[k]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (ii[k] >= 0 && h[k].y - dy <= y3 && y3 <= h[k].z + dy) col[(nok++) * T] = (uint16_t)ii[k];
+                }
+                for (int a2 = 1; a2 < nok; ++a2) {
+                    const int v = col[a2 * T];
+                    const float dv = fabsf(X0[v] - u);
+                    int j = a2 - 1;
+                    while (j >= 0) {
+                        const int c = col[j * T];
+                        const float dc = fabsf(X0[c] - u);
+                        const bool before = dv < dc || (dv == dc && __float_as_int(__ldg(&H[v].w)) < __float_as_int(__ldg(&H[c].w)));
+                        if (!before) break;
+                        col[(j + 1) * T] = (uint16_t)c;
+                        --j;
+                    }
+                    col[(j + 1) * T] = (uint16_t)v;
+                }
+                nbx = min(nok, P.k1);
+                for (int j = 0; j < kK1Max; ++j) s_bx[j][tid] = j < nbx ? col[j * T] : (uint16_t)0xFFFF;
+            }
         } else {
             // Dv1 triplets: every UTbX hit with a physical kink (a window of
             // half-width dtx_max (z_m - z_bX) around the seed's straight
