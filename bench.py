@@ -774,7 +774,8 @@ def main():
     prof = ds.ds_profile_read(d.ctx)
     ds.ds_profile_enable(d.ctx, False)
     d.sync(stream)
-    table_stride = ((4 * cfg["n_sectors"] * 64 + 1) + 7) & ~7
+    # per-event table: offsets padded to 8 entries + one float4 extent per (layer, sector)
+    table_stride = (((4 * cfg["n_sectors"] * 64 + 1) + 7) & ~7) + 32 * cfg["n_sectors"]
     alg = algorithmic(E, S, H, n_t, n_v, n_cand, n_pairs, table_stride)
     kernels = {k: dict(launches=v[0], avg_us=1e3 * v[1] / max(v[0], 1)) for k, v in prof.items()}
     step_us = sum(v["avg_us"] * v["launches"] for v in kernels.values()) / n_prof

@@ -173,8 +173,8 @@ const char *fill_dev_geom(const ds_geometry *gm, DevGeom *out)
     g.w_hit = (float)(1.0 / (gm->sigma_hit * gm->sigma_hit));
     g.w_mag = (float)(1.0 / (gm->sigma_mag * gm->sigma_mag));
     g.inv_sigma_hit = (float)(1.0 / gm->sigma_hit);
-    const int nb = 4 * g.n_sec * kNXB + 1;
-    g.table_stride = (nb + 7) & ~7;
+    g.ext_off = table_ext_offset(g.n_sec);
+    g.table_stride = table_stride_for(g.n_sec);
     return nullptr;
 }
 

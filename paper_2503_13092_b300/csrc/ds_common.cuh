@@ -9,8 +9,11 @@
 //   sx0       the same order, x0 only (4 bytes per hit): staged per event in
 //             shared memory for the window scans
 //   items     search work items: (event, chunk of <= 128 of its seeds)
-//   bins      uint16 offsets per event: (layer, sector, xbin) -> first sorted
-//             hit, relative to the event's first hit (<= 65535 hits per event)
+//   bins      per event: uint16 offsets (layer, sector, xbin) -> first sorted
+//             hit, relative to the event's first hit (<= 65535 hits per event),
+//             then one bit per (layer, sector): set when one of its strips does
+//             not cover the whole sector (otherwise a window decides the strip
+//             test of the whole sector at once)
 //   trk_ws    one 64-byte candidate-winner record per seed + its clone key
 #pragma once
 
@@ -37,6 +40,11 @@ constexpr int kBucketStage = 6144;   // events up to this many hits are sorted i
 constexpr int kMaxVertexTracks = 4096; // tracks per event staged for vertexing
 constexpr unsigned long long kNoKey = ~0ull;
 
+// Per-event table: nb + 1 = 4 n_sec kNXB + 1 uint16 offsets padded to 8
+// entries, then 16 bytes of flags, one bit per (layer, sector) row (<= 128).
+__host__ __device__ constexpr int table_ext_offset(int n_sec) { return ((4 * n_sec * kNXB + 1) + 7) & ~7; }
+__host__ __device__ constexpr int table_stride_for(int n_sec) { return table_ext_offset(n_sec) + 8; }
+
 struct DevGeom {
     float z[4];
     float dxdy[4];
@@ -49,7 +57,8 @@ struct DevGeom {
     float gamma0, gamma1, z_ref;
     float w_hit, w_mag;              // 1 / sigma^2
     float inv_sigma_hit;
-    int table_stride;                // uint16 entries per event bin table
+    int table_stride;                // uint16 entries per event bin table (offsets + row bits)
+    int ext_off;                     // uint16 entry where the partial-strip row bits start
 };
 
 struct DevParams {
@@ -119,6 +128,23 @@ __device__ __forceinline__ int sector_of(const DevGeom &g, float y)
     return min(max(k, 0), g.n_sec - 1);
 }
 
+// Y extent of sector k, rounded the same way wherever it is used.
+__device__ __forceinline__ float sector_lo(const DevGeom &g, int k) { return __fmaf_rn((float)k, g.sector_h, g.y_min); }
+__device__ __forceinline__ float sector_hi(const DevGeom &g, int k) { return __fadd_rn(sector_lo(g, k), g.sector_h); }
+
+// Strip test (ybeg - dy <= y && y <= yend + dy) for every hit of one (layer,
+// sector) row at once.  A row whose flag bit is clear has only strips that
+// cover the whole sector (ybeg <= lo, yend >= hi), so y in [lo - dy, hi + dy]
+// passes for all of them (float rounding is monotonic).  Returns 1 when every
+// hit of the row passes, 2 when the hits must be tested one by one.
+__device__ __forceinline__ int sector_strip_class(const DevGeom &g, const uint32_t *part, int layer, int k,
+                                                  float y, float dy)
+{
+    const int row = layer * g.n_sec + k;
+    if ((part[row >> 5] >> (row & 31)) & 1u) return 2;
+    return (__fsub_rn(sector_lo(g, k), dy) <= y && y <= __fadd_rn(sector_hi(g, k), dy)) ? 1 : 2;
+}
+
 __device__ __forceinline__ int xbin_of(const DevGeom &g, float x)
 {
     int b = __float2int_rd((x + g.x_half) * g.inv_xbin);
@@ -135,6 +161,24 @@ __device__ __forceinline__ int find_segment(const int32_t *__restrict__ off, int
         else hi = mid;
     }
     return lo;
+}
+
+// find_segment by one warp (all 32 lanes call it): 32 probes per round, so
+// two or three dependent loads instead of log2(n).
+__device__ __forceinline__ int warp_find_segment(const int32_t *__restrict__ off, int n, int s)
+{
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = n;          // invariant: off[lo] <= s, answer in [lo, hi)
+    while (hi - lo > 32) {
+        const int step = (hi - lo + 31) >> 5;
+        const int idx = lo + lane * step;
+        const unsigned m = __ballot_sync(0xffffffffu, idx < hi && __ldg(off + idx) <= s);
+        const int k = 31 - __clz(m);   // lane 0 always qualifies
+        lo += k * step;
+        hi = min(hi, lo + step);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, lo + lane < hi && __ldg(off + lo + lane) <= s);
+    return lo + 31 - __clz(m);
 }
 
 // Order-preserving float -> uint32 map (negative values included) and back.

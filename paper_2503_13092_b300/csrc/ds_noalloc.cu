@@ -33,7 +33,7 @@ constexpr int kNASeeds = 16384;
 constexpr int kNAHits = 327680;
 constexpr int kNACandPerSeed = 8;
 constexpr int kNACand = kNASeeds * kNACandPerSeed;
-constexpr int kNATableStride = ((4 * kMaxSectors * kNXB + 1) + 7) & ~7;
+constexpr int kNATableStride = table_stride_for(kMaxSectors);
 
 constexpr size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 constexpr size_t kOffCounters = 0;

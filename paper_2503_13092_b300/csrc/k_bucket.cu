@@ -13,9 +13,12 @@
 // as the event's bin table), pass 2 places float4 {x0, ybeg, yend, id} records
 // at their sorted positions in shared memory and writes them, and the compact
 // x0 array, with coalesced stores.  Larger events scatter straight to global
-// memory.  The
-// last CTA also turns per-event seed counts into the search kernel's work
-// items (chunks of at most `chunk` <= 128 seeds of one event).  The order inside a bin comes
+// memory.  Pass 1 also marks the (layer, sector) rows holding a strip
+// shorter than its sector (one bit per row, written beside the bin table);
+// the search decides the strip test of an unmarked row from the sector's
+// bounds.  The last CTA also turns
+// per-event seed counts into the search kernel's work items (chunks of at
+// most `chunk` <= 128 seeds of one event).  The order inside a bin comes
 // from atomics and is not deterministic; every consumer ranks hits by
 // (|dx|, id), which does not depend on it.
 #include "ds_args.cuh"
@@ -24,7 +27,7 @@ namespace ds {
 
 
 __device__ __forceinline__ int hit_bin(const DevGeom &g, float x0, float yb, float ye, int lay,
-                                       int nb, DevCounters *cnt)
+                                       int nb, DevCounters *cnt, uint32_t *part)
 {
     // strips must lie in one Y sector; the sector is the one of the midpoint
     if (lay > 3 || !(x0 == x0) || !(yb == yb) || !(ye == ye) || fabsf(x0) > 1e30f) {
@@ -33,10 +36,12 @@ __device__ __forceinline__ int hit_bin(const DevGeom &g, float x0, float yb, flo
     }
     const float ym = 0.5f * (yb + ye);
     const int k = sector_of(g, ym);
-    const float lo = g.y_min + k * g.sector_h, hi = lo + g.sector_h;
+    const float lo = sector_lo(g, k), hi = sector_hi(g, k);
     const float tol = 5e-3f;
     if (yb < lo - tol || ye > hi + tol) raise_flag(cnt, DS_FLAG_STRIP_SECTOR);
-    return (lay * g.n_sec + k) * kNXB + xbin_of(g, x0);
+    const int row = lay * g.n_sec + k;
+    if (yb > lo || ye < hi) atomicOr(part + (row >> 5), 1u << (row & 31));   // strip shorter than its sector
+    return row * kNXB + xbin_of(g, x0);
 }
 
 __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_constant__ BucketArgs a)
@@ -44,6 +49,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
     // dynamic shared memory: nb + 1 bin counters (padded to 16 bytes), then the
     // event's records in sorted order (events up to kBucketStage hits)
     extern __shared__ __align__(16) unsigned int s_cnt[];
+    __shared__ uint32_t s_part[4];                // rows with a strip shorter than its sector
     __shared__ int s_scan[32];
     __shared__ bool s_last;
     const int e = blockIdx.x;
@@ -70,6 +76,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
     const int cnt_words = (nb + 1 + 3) & ~3;
     float4 *s_rec = reinterpret_cast<float4 *>(s_cnt + cnt_words);
     for (int b = tid; b <= nb; b += blockDim.x) s_cnt[b] = 0;
+    if (tid < 4) s_part[tid] = 0u;
     __syncthreads();
 
     // pass 1: bins.  Events that fit the staging buffer are read with 16-byte
@@ -120,7 +127,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
                 for (int j = 0; j < 4; ++j) {
                     const int h = base + j;
                     if (h >= h0 && h < h1) {
-                        vb[r][j] = hit_bin(g, xs[j], ybs[j], yes[j], ls[j], nb, a.cnt);
+                        vb[r][j] = hit_bin(g, xs[j], ybs[j], yes[j], ls[j], nb, a.cnt, s_part);
                         atomicAdd(&s_cnt[vb[r][j]], 1u);
                     }
                 }
@@ -130,7 +137,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
         for (int i = tid; i < n; i += blockDim.x) {
             const int h = h0 + i;
             const int b = hit_bin(g, __ldg(a.x0 + h), __ldg(a.ybeg + h), __ldg(a.yend + h), __ldg(a.layer + h),
-                                  nb, a.cnt);
+                                  nb, a.cnt, s_part);
             atomicAdd(&s_cnt[b], 1u);
         }
     }
@@ -154,8 +161,10 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
             run += c;
         }
     }
-    // remaining table entries (padding) point at the end of the valid hits
-    for (int b = total_bins + tid; b < g.table_stride; b += blockDim.x) table[b] = (uint16_t)n;
+    // remaining offset entries (padding) point at the end of the valid hits
+    for (int b = total_bins + tid; b < g.ext_off; b += blockDim.x) table[b] = (uint16_t)n;
+    // partial-strip row bits after the offsets
+    if (tid < 4) reinterpret_cast<uint32_t *>(table + g.ext_off)[tid] = s_part[tid];
     __syncthreads();
 
     // pass 2: records {x0, ybeg, yend, id} in sorted order.  Staged events are
@@ -199,7 +208,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
         for (int i = tid; i < n; i += blockDim.x) {
             const int h = h0 + i;
             const float x0 = __ldg(a.x0 + h), yb = __ldg(a.ybeg + h), ye = __ldg(a.yend + h);
-            const int b = hit_bin(g, x0, yb, ye, __ldg(a.layer + h), nb, a.cnt);
+            const int b = hit_bin(g, x0, yb, ye, __ldg(a.layer + h), nb, a.cnt, s_part);
             const unsigned int slot = atomicAdd(&s_cnt[b], 1u);
             a.sorted[h0 + slot] = make_float4(x0, yb, ye, __int_as_float(h));
             a.sx0[h0 + slot] = x0;
@@ -251,7 +260,10 @@ cudaError_t init_bucket_attributes()
 {
     const size_t smem = sizeof(unsigned int) * (size_t)((4 * kMaxSectors * kNXB + 1 + 3) & ~3) +
                         sizeof(float4) * kBucketStage;
-    return cudaFuncSetAttribute(k_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // two CTAs per SM need nearly all of its shared memory: ask for the largest carveout
+    cudaError_t e = cudaFuncSetAttribute(k_bucket, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
 }
 
 }  // namespace ds

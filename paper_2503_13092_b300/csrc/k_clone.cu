@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(kCloneThreads) k_clone(const __grid_constant__
         const int b = c0 + threadIdx.x;
         int alive = 0;
         if (b < ns) {
-            const unsigned long long kb = in_smem ? s_key[b] : K[b];
+            // the keys are staged in shared memory only when clone killing is on
+            const unsigned long long kb = (in_smem && a.clone_kill) ? s_key[b] : K[b];
             if (kb != kNoKey) {
                 alive = 1;
                 if (a.clone_kill) {

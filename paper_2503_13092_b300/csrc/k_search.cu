@@ -13,9 +13,11 @@
 //   best pick run in k_mlp.cu over all candidates of the batch.
 //
 // Work decomposition (B300): one CTA per work item = up to 128 seeds of one
-// event.  The event's bin table and compact x0 array are staged in shared
-// memory by two bulk copies (TMA) on an mbarrier; every x test of every window
-// reads shared memory, and only hits passing it load their 16-byte record.
+// event.  The event's bin table (with its partial-strip row bits) and
+// compact x0 array are staged in shared memory by two bulk copies (TMA) on an
+// mbarrier; every x test of every window reads shared memory, and a hit
+// passing it loads its 16-byte record only when its sector holds a strip
+// shorter than the sector or its distance ties with another hit's.
 // Three flattened phases keep lanes busy whatever the hits per seed: UTbX
 // window (thread per seed), refined windows (thread per (seed, UTbX hit)),
 // fit + features (thread per candidate).  Candidates are written to a compact
@@ -56,15 +58,18 @@ __device__ __forceinline__ bool key_less(float da, int ia, float db, int ib)
 // Hits of `layer` with |x0 - u| < w whose strip extent (+- dy) contains y,
 // ranked by (|dx|, id); the N best are kept.  Returns how many qualified.
 // The x test reads the staged x0 array (shared memory for events that fit).
-// Up to B hits passing it are collected during the scan; after the scan (one
-// uniform point for the whole warp) their 16-byte records are loaded together
-// for the y test and id, and the survivors are ordered by a compare-exchange
-// network.  A window with more than B x-passing hits (rare) is rescanned with
-// one insertion per hit.
+// Sectors whose strips all cover the whole sector pass the strip test as a
+// whole (sector_strip_class).  Up to B hits passing the x test are collected
+// during the scan; after it (one uniform point for the whole warp) their
+// 16-byte records are loaded together for the per-hit strip test and the
+// ids, but only when a sector needs the per-hit test or two
+// collected distances are equal (the id breaks the tie); the survivors are
+// ordered by a compare-exchange network.  A window with more than B
+// x-passing hits (rare) is rescanned with one insertion per hit.
 template <int N, int B>
 __device__ __forceinline__ int window_scan(const DevGeom &g, const float *X0, const float4 *__restrict__ H,
-                                           const uint16_t *Tb, int layer, float u, float y, float w, float dy,
-                                           float (&d)[N], int (&id)[N], int (&p)[N])
+                                           const uint16_t *Tb, const uint32_t *Part, int layer, float u, float y,
+                                           float w, float dy, float (&d)[N], int (&id)[N], int (&p)[N])
 {
     const int s_lo = sector_of(g, y - dy - 0.01f), s_hi = sector_of(g, y + dy + 0.01f);
     const float eps = 1e-3f;
@@ -72,7 +77,9 @@ __device__ __forceinline__ int window_scan(const DevGeom &g, const float *X0, co
     int qi[B];
     float qd[B];
     int nq = 0;
+    bool per_hit = false;
     for (int s = s_lo; s <= s_hi; ++s) {
+        per_hit |= sector_strip_class(g, Part, layer, s, y, dy) == 2;
         const int row = (layer * g.n_sec + s) * kNXB;
         const int i0 = Tb[row + b0], i1 = Tb[row + b1 + 1];
         for (int i = i0; i < i1; ++i) {
@@ -96,18 +103,39 @@ __device__ __forceinline__ int window_scan(const DevGeom &g, const float *X0, co
     }
     int cnt = 0;
     if (nq <= B) {
-        // records of the collected hits, all loads in flight together
-        float4 h[B];
+        bool tie = false;
 #pragma unroll
         for (int k = 0; k < B; ++k)
-            if (k < nq) h[k] = __ldg(H + qi[k]);
-        int hid[B];
 #pragma unroll
-        for (int k = 0; k < B; ++k) {
-            const bool ok = k < nq && h[k].y - dy <= y && y <= h[k].z + dy;
-            hid[k] = ok ? __float_as_int(h[k].w) : 0x7fffffff;
-            if (!ok) qd[k] = __int_as_float(0x7f800000);
-            cnt += ok;
+            for (int k2 = k + 1; k2 < B; ++k2)
+                tie |= k2 < nq && qd[k] == qd[k2];
+        int hid[B];
+        if (per_hit || tie) {
+            // records of the collected hits, all loads in flight together
+            float4 h[B];
+#pragma unroll
+            for (int k = 0; k < B; ++k)
+                if (k < nq) h[k] = __ldg(H + qi[k]);
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                const bool ok = k < nq && h[k].y - dy <= y && y <= h[k].z + dy;
+                hid[k] = ok ? __float_as_int(h[k].w) : 0x7fffffff;
+                if (!ok) qd[k] = __int_as_float(0x7f800000);
+                cnt += ok;
+            }
+        } else {
+            // every collected hit passes the strip test and the distances are
+            // distinct: the order is by distance alone
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                const bool ok = k < nq;
+                hid[k] = 0;
+                if (!ok) {
+                    qd[k] = __int_as_float(0x7f800000);
+                    hid[k] = 0x7fffffff;
+                }
+                cnt += ok;
+            }
         }
         // odd-even transposition sort of (dx, id) over the B slots
 #pragma unroll
@@ -246,6 +274,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     __shared__ int s_cand0;
     __shared__ int s_scan[32];
     __shared__ int s_item[4];
+    __shared__ int s_hits[3];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ int s_jbase[T + 1];
 
@@ -257,6 +286,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     // the event's data is staged again only when the event changes
     const int n_items = __ldg(a.item_off + a.n_events);
     uint16_t *Tb = reinterpret_cast<uint16_t *>(s_dyn);
+    const uint32_t *Part = reinterpret_cast<const uint32_t *>(Tb + g.ext_off);
     float *xs = reinterpret_cast<float *>(s_dyn + sizeof(uint16_t) * g.table_stride);
     if (tid == 0) {
         mbar_init(&s_bar, 1);
@@ -272,41 +302,62 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     __syncthreads();
     if (b_first >= n_items) break;
     for (int bi = b_first; bi < b_first + a.group && bi < n_items; ++bi) {
-    // work item: chunk k of event e's seeds (sizes differ by at most one)
-    if (tid == 0) {
-        const int e = find_segment(a.item_off, a.n_events, bi);
-        const int k = bi - __ldg(a.item_off + e), nc = __ldg(a.item_off + e + 1) - __ldg(a.item_off + e);
-        const int s0 = __ldg(a.seed_off + e), ns = __ldg(a.seed_off + e + 1) - s0;
-        s_item[0] = e;
-        s_item[1] = s0 + (int)(((long long)k * ns) / nc);
-        s_item[2] = s0 + (int)(((long long)(k + 1) * ns) / nc);
+    // work item: chunk k of event e's seeds (sizes differ by at most one).
+    // Warp 0 finds the event; lane 0 reads its offsets and, when the event
+    // changes, starts the staging copies before the block meets.
+    if (tid < 32) {
+        const int e = warp_find_segment(a.item_off, a.n_events, bi);
+        if (tid == 0) {
+            const int i0 = __ldg(a.item_off + e), i1 = __ldg(a.item_off + e + 1);
+            const int s0 = __ldg(a.seed_off + e), ns = __ldg(a.seed_off + e + 1) - s0;
+            int h0 = __ldg(a.hit_off + e), h1 = __ldg(a.hit_off + e + 1);
+            if (h0 < 0 || h1 < h0 || h1 > a.n_hits || h1 - h0 > kMaxEventHits) h1 = h0 = 0;
+            const int k = bi - i0, nc = i1 - i0;
+            s_item[0] = e;
+            s_item[1] = s0 + (int)(((long long)k * ns) / nc);
+            s_item[2] = s0 + (int)(((long long)(k + 1) * ns) / nc);
+            s_hits[0] = h0;
+            s_hits[1] = h1;
+            const bool restage = s_item[3] != e;
+            s_hits[2] = restage;
+            if (restage) {
+                // the event's bin table and (if it fits) its x0 array, by two
+                // bulk copies (TMA); the x0 copy starts at the 16-byte
+                // boundary below h0.  The previous item's readers are done
+                // (the block met at the end of it).
+                const int nh = h1 - h0, lead = h0 & 3;
+                const uint32_t tb_bytes = sizeof(uint16_t) * g.table_stride;
+                const uint32_t x_bytes = nh <= a.stage_hits ? (uint32_t)(((lead + nh) * 4 + 15) & ~15) : 0u;
+                // fault injection (tests): expect 16 bytes that never arrive
+                mbar_expect_tx(&s_bar, tb_bytes + x_bytes + ((P.fault_inject & 1) ? 16u : 0u));
+                bulk_copy_g2s(Tb, a.bins + (size_t)e * g.table_stride, tb_bytes, &s_bar);
+                if (x_bytes) bulk_copy_g2s(xs, a.sx0 + (h0 - lead), x_bytes, &s_bar);
+                s_item[3] = e;
+            }
+        }
     }
     __syncthreads();
     const int e = s_item[0];
     const int s = s_item[1] + tid;
     const bool active = s < s_item[2];
-    int h0 = __ldg(a.hit_off + e), h1 = __ldg(a.hit_off + e + 1);
-    if (h0 < 0 || h1 < h0 || h1 > a.n_hits || h1 - h0 > kMaxEventHits) h1 = h0 = 0;
+    const int h0 = s_hits[0], h1 = s_hits[1];
+    const bool restage = s_hits[2] != 0;
     const int nh = h1 - h0;
     const float4 *H = a.sorted + h0;
-
-    // stage the event's bin table and (if it fits) its x0 array with two bulk
-    // copies (TMA); the x0 copy starts at the 16-byte boundary below h0
     const bool staged = nh <= a.stage_hits;
-    const int lead = h0 & 3;
-    const float *X0 = staged ? xs + lead : a.sx0 + h0;
-    const bool restage = s_item[3] != e;
-    if (restage) {
-        if (tid == 0) {
-            const uint32_t tb_bytes = sizeof(uint16_t) * g.table_stride;
-            const uint32_t x_bytes = staged ? (uint32_t)(((lead + nh) * 4 + 15) & ~15) : 0u;
-            // fault injection (tests): expect 16 bytes that never arrive
-            mbar_expect_tx(&s_bar, tb_bytes + x_bytes + ((P.fault_inject & 1) ? 16u : 0u));
-            bulk_copy_g2s(Tb, a.bins + (size_t)e * g.table_stride, tb_bytes, &s_bar);
-            if (x_bytes) bulk_copy_g2s(xs, a.sx0 + (h0 - lead), x_bytes, &s_bar);
-        }
+    const float *X0 = staged ? xs + (h0 & 3) : a.sx0 + h0;
+
+    // the seed's state is loaded while the staging copies are in flight
+    float sd_x = 0.f, sd_y = 0.f, sd_tx = 0.f, sd_ty = 0.f, sd_qop = 0.f, sd_chi2 = 0.f;
+    if (active) {
+        sd_x = __ldg(a.sx + s);
+        sd_y = __ldg(a.sy + s);
+        sd_tx = __ldg(a.stx + s);
+        sd_ty = __ldg(a.sty + s);
+        sd_qop = __ldg(a.sqop + s);
+        sd_chi2 = __ldg(a.schi2 + s);
+        a.rank_ws[s] = -1;     // the clone kernel ranks this call's winners
     }
-    if (active) a.rank_ws[s] = -1;     // the clone kernel ranks this call's winners
     if (restage) {
         // bounded wait; the decision to go on is taken by the whole block
         if (!__syncthreads_and(mbar_wait_bounded(&s_bar, phase, limit))) {
@@ -314,7 +365,6 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
             return;
         }
         phase ^= 1u;
-        if (tid == 0) s_item[3] = e;
     }
 
     // ---------------------------------------------------------------- search
@@ -322,11 +372,11 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     int nbx = 0;
     if (active) {
         SeedCtx sc;
-        const float x = __ldg(a.sx + s), y = __ldg(a.sy + s);
-        sc.tx = __ldg(a.stx + s);
-        sc.ty = __ldg(a.sty + s);
-        sc.qop = __ldg(a.sqop + s);
-        sc.chi2 = __ldg(a.schi2 + s);
+        const float x = sd_x, y = sd_y;
+        sc.tx = sd_tx;
+        sc.ty = sd_ty;
+        sc.qop = sd_qop;
+        sc.chi2 = sd_chi2;
         const float aq = fabsf(sc.qop);
         // magnet point (Eq. 1 kink model): parameterised z, straight-line x, y
         sc.zm = g.zmag[0] + g.zmag[1] * sc.tx * sc.tx + g.zmag[2] * sc.ty * sc.ty + g.zmag[3] * aq;
@@ -346,16 +396,20 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
         int id[kK1Max], p[kK1Max];
         if (V == 0) {
             // UTbX window: x-passing positions collected in this thread's
-            // column of s_sel (free until the refined windows), their records
-            // loaded together for the strip test, the survivors insertion-sorted
-            // by (|dx|, id) in place (ids loaded only on exact distance ties)
+            // column of s_sel (free until the refined windows); the hits of
+            // sectors whose strips all cover the sector pass the strip test as
+            // a whole, otherwise the records are loaded together for it;
+            // the survivors are insertion-sorted by (|dx|, id) in place (ids
+            // loaded only on exact distance ties)
             uint16_t *col = &s_sel[0][0][0] + tid;
             constexpr int kCap = kK1Max * 5;
             const float u = u_bx, w = sc.w1, y3 = sc.yl[3], dy = P.dy_tol;
             const int s_lo = sector_of(g, y3 - dy - 0.01f), s_hi = sector_of(g, y3 + dy + 0.01f);
             const int b0 = xbin_of(g, u - w - 1e-3f), b1 = xbin_of(g, u + w + 1e-3f);
             int nq = 0;
+            bool per_hit = false;     // a sector whose strips must be tested hit by hit
             for (int sct = s_lo; sct <= s_hi; ++sct) {
+                per_hit |= sector_strip_class(g, Part, 3, sct, y3, dy) == 2;
                 const int row = (3 * g.n_sec + sct) * kNXB;
                 const int i0 = Tb[row + b0], i1 = Tb[row + b1 + 1];
                 for (int i = i0; i < i1; ++i)
@@ -365,13 +419,13 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
                     }
             }
             if (nq > kCap) {
-                const int q = window_scan<kK1Max, 4>(g, X0, H, Tb, 3, u_bx, sc.yl[3], sc.w1, P.dy_tol, d, id, p);
+                const int q = window_scan<kK1Max, 4>(g, X0, H, Tb, Part, 3, u_bx, sc.yl[3], sc.w1, P.dy_tol, d, id, p);
                 nbx = min(q, P.k1);
 #pragma unroll
                 for (int j = 0; j < kK1Max; ++j) s_bx[j][tid] = (uint16_t)p[j];
             } else {
-                int nok = 0;
-                for (int k0 = 0; k0 < nq; k0 += 4) {
+                int nok = per_hit ? 0 : nq;   // otherwise every collected hit passes the strip test
+                for (int k0 = 0; per_hit && k0 < nq; k0 += 4) {
                     float4 h[4];
                     int ii[4];
 #pragma unroll
@@ -427,7 +481,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
                     float dd[1];
                     int ii[1], pp[1];
                     const float ua = dv1_ua(g, sc, X0, i);
-                    if (window_scan<1, 3>(g, X0, H, Tb, 0, ua, sc.yl[0], P.dv1_w_tri, dy, dd, ii, pp) == 0) continue;
+                    if (window_scan<1, 3>(g, X0, H, Tb, Part, 0, ua, sc.yl[0], P.dv1_w_tri, dy, dd, ii, pp) == 0) continue;
                     topn_insert<kK1Max>(d, id, p, dd[0], __float_as_int(hb.w), i | (pp[0] << 16));
                     ++n_tri;
                 }
@@ -467,14 +521,14 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
         } else {
             float dd[1]; int ii[1], pp[1];
             const float ul = fmaf(txp, g.z[0] - g.z[3], xh) - g.dxdy[0] * sc.yl[0];
-            const int c = window_scan<1, 3>(g, X0, H, Tb, 0, ul, sc.yl[0], w2, P.dy_tol, dd, ii, pp);
+            const int c = window_scan<1, 3>(g, X0, H, Tb, Part, 0, ul, sc.yl[0], w2, P.dy_tol, dd, ii, pp);
             sel[0] = c > 0 ? pp[0] : -1;
         }
 #pragma unroll
         for (int l = 1; l <= 2; ++l) {
             float dd[2]; int ii[2], pp[2];
             const float ul = fmaf(txp, g.z[l] - g.z[3], xh) - g.dxdy[l] * sc.yl[l];
-            const int c = window_scan<2, 3>(g, X0, H, Tb, l, ul, sc.yl[l], w2, P.dy_tol, dd, ii, pp);
+            const int c = window_scan<2, 3>(g, X0, H, Tb, Part, l, ul, sc.yl[l], w2, P.dy_tol, dd, ii, pp);
             sel[2 * l - 1] = c > 0 ? pp[0] : -1;
             sel[2 * l] = c > 1 ? pp[1] : -1;
         }
@@ -572,7 +626,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
 cudaError_t init_search_attributes()
 {
     // shared memory, not L1, limits residency: ask for the largest carveout
-    const int smem = (int)(sizeof(uint16_t) * (((4 * kMaxSectors * kNXB + 1) + 7) & ~7) + sizeof(float) * (kStageHitsMax + 4));
+    const int smem = (int)(sizeof(uint16_t) * table_stride_for(kMaxSectors) + sizeof(float) * (kStageHitsMax + 4));
     cudaFuncAttributes fa;
     int dev = 0, optin = 0;
     cudaError_t e = cudaFuncGetAttributes(&fa, k_search<0>);

@@ -87,6 +87,31 @@ def test_c2_sample_parity(torch_cuda, weights):
     parity.assert_vertices_match(vrep)
 
 
+@pytest.mark.parametrize("training", [0, 1])
+def test_partial_strips(torch_cuda, weights, training):
+    """Strips shorter than their Y sector (in the even sectors only, half of
+    their hits shortened by up to 40 mm at each end, midpoint kept inside): the
+    per-hit strip test decides there, while rows whose strips all span the
+    sector are decided as a whole.  Both must agree with the oracle."""
+    b = synth.config_batch("c2", n_events=16)
+    rng = np.random.default_rng(11)
+    yb, ye = b["hit_ybeg"].astype(np.float64), b["hit_yend"].astype(np.float64)
+    sector = np.floor((0.5 * (yb + ye) + 700.0) / 100.0).astype(int)
+    cut = (sector % 2 == 0) & (rng.random(yb.size) < 0.5)
+    b = dict(b)
+    b["hit_ybeg"] = np.where(cut, yb + rng.uniform(0.0, 40.0, yb.size), yb).astype(np.float32)
+    b["hit_yend"] = np.where(cut, ye - rng.uniform(0.0, 40.0, ye.size), ye).astype(np.float32)
+    cfg = synth.default_config(training=training)
+    d = make(torch_cuda, cfg, weights)
+    g, o, rep, vrep = run_both(d, b, cfg, weights)
+    assert rep["n_tracks_oracle"] > 500
+    parity.assert_tracks_match(rep)
+    parity.assert_vertices_match(vrep)
+    # the shortened strips lost hits: fewer candidates than with full strips
+    full = synth.config_batch("c2", n_events=16)
+    assert g["stats"]["n_candidates"] < d.run(full)["stats"]["n_candidates"]
+
+
 @pytest.mark.parametrize("name,n_events,n_sample", [("c2", 1000, 24), ("c3", 2000, 16)])
 def test_full_size_sampled(torch_cuda, weights, name, n_events, n_sample):
     """The benchmark's launch (whole batch in one call); the oracle recomputes
