@@ -38,7 +38,6 @@ struct ds_ctx {
     float4 *sorted = nullptr;
     float *sx0 = nullptr;
     uint16_t *bins = nullptr;
-    int *item_cnt = nullptr;
     int *item_off = nullptr;
     ds_track *trk_ws = nullptr;
     unsigned long long *key_ws = nullptr;
@@ -337,7 +336,7 @@ void ds_destroy(ds_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    void *ptrs[] = {ctx->d_cnt, ctx->d_tc, ctx->d_lines_tc, ctx->sorted, ctx->sx0, ctx->item_cnt, ctx->item_off, ctx->bins, ctx->cand_feat,
+    void *ptrs[] = {ctx->d_cnt, ctx->d_tc, ctx->d_lines_tc, ctx->sorted, ctx->sx0, ctx->item_off, ctx->bins, ctx->cand_feat,
                     ctx->cand_meta, ctx->cand_logit, ctx->seed_cand, ctx->trk_ws, ctx->key_ws, ctx->hit_ws,
                     ctx->rank_ws, ctx->count_trk, ctx->count_vtx, ctx->large_vtx, ctx->pool, ctx->pool_pos,
                     ctx->h.seed_off, ctx->h.hit_off, ctx->h.seed_cols, ctx->h.hit_cols, ctx->h.layer,
@@ -407,7 +406,6 @@ ds_status ds_reserve(ds_ctx *ctx, int32_t E, int32_t S, int32_t H)
         if ((st = grow(ctx, &ctx->count_trk, (size_t)E)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->count_vtx, (size_t)E)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->large_vtx, (size_t)E)) != DS_OK) return st;
-        if ((st = grow(ctx, &ctx->item_cnt, (size_t)E)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->item_off, (size_t)E + 1)) != DS_OK) return st;
         ctx->cap_events = E;
     }
@@ -487,7 +485,6 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     ba.sorted = ctx->sorted;
     ba.sx0 = ctx->sx0;
     ba.bins = ctx->bins;
-    ba.item_cnt = ctx->item_cnt;
     ba.item_off = ctx->item_off;
     ba.chunk = ctx->tune.search_chunk;
     ba.cnt = ctx->d_cnt;

@@ -32,7 +32,6 @@ struct BucketArgs {
     float4 *sorted;
     float *sx0;
     uint16_t *bins;
-    int *item_cnt;         // per event: search chunks
     int *item_off;         // [n_events + 1]
     int chunk;             // max seeds per search work item (<= kSearchThreads)
     DevCounters *cnt;

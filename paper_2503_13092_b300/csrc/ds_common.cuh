@@ -88,7 +88,6 @@ struct DevCounters {                 // device-side flag word and statistics
     unsigned int flags;
     unsigned int done_trk;           // last-block-done tickets
     unsigned int done_vtx;
-    unsigned int done_bkt;
     int n_tracks;
     int n_vertices;
     int pool_used;
@@ -274,6 +273,52 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *scratch, int *to
     *total = scratch[nwarps - 1];
     __syncthreads();
     return base + x - v;
+}
+
+// Exclusive prefix sums of n counts written by other CTAs (read from L2):
+// off[i] = cnt[0] + ... + cnt[i - 1] for i < n; returns the total to every
+// thread.  One contiguous chunk per thread, all of its loads issued before
+// the one block scan (a single round trip instead of one per blockDim.x
+// counts).  All threads call.
+// count(i) gives the i-th count (block_offsets: a load).
+template <class Count>
+__device__ __forceinline__ int block_offsets_f(Count count, int n, int *off, int *scratch)
+{
+    const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int i0 = min((int)threadIdx.x * per, n), i1 = min(i0 + per, n);
+    constexpr int R = 8;
+    int v[R];
+    int local = 0;
+    if (per <= R) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            v[k] = i0 + k < i1 ? count(i0 + k) : 0;
+            local += v[k];
+        }
+    } else {
+        for (int i = i0; i < i1; ++i) local += count(i);
+    }
+    int total;
+    int run = block_exclusive_scan(local, scratch, &total);
+    if (per <= R) {
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            if (i0 + k < i1) {
+                off[i0 + k] = run;
+                run += v[k];
+            }
+    } else {
+        for (int i = i0; i < i1; ++i) {
+            off[i] = run;
+            run += count(i);
+        }
+    }
+    return total;
+}
+
+__device__ __forceinline__ int block_offsets(const int *cnt, int n, int *off, int *scratch)
+{
+    return block_offsets_f([cnt](int i) { return __ldcg(cnt + i); }, n, off, scratch);
 }
 
 }  // namespace ds

@@ -46,8 +46,7 @@ constexpr size_t kOffHit = kOffKey + align256(sizeof(unsigned long long) * (size
 constexpr size_t kOffRank = kOffHit + align256(sizeof(int4) * (size_t)kNASeeds);
 constexpr size_t kOffSeedCand = kOffRank + align256(sizeof(int) * (size_t)kNASeeds);
 constexpr size_t kOffCount = kOffSeedCand + align256(sizeof(int4) * (size_t)kNASeeds);
-constexpr size_t kOffItemCnt = kOffCount + align256(sizeof(int) * (size_t)kNAEvents);
-constexpr size_t kOffItemOff = kOffItemCnt + align256(sizeof(int) * (size_t)kNAEvents);
+constexpr size_t kOffItemOff = kOffCount + align256(sizeof(int) * (size_t)kNAEvents);
 constexpr size_t kOffCandFeat = kOffItemOff + align256(sizeof(int) * (size_t)(kNAEvents + 1));
 constexpr size_t kOffCandMeta = kOffCandFeat + align256(sizeof(float4) * 4 * (size_t)kNACand);
 constexpr size_t kOffCandLogit = kOffCandMeta + align256(sizeof(CandMeta) * (size_t)kNACand);
@@ -130,7 +129,6 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         ba.sorted = reinterpret_cast<float4 *>(base + kOffSorted);
         ba.sx0 = reinterpret_cast<float *>(base + kOffSx0);
         ba.bins = reinterpret_cast<uint16_t *>(base + kOffBins);
-        ba.item_cnt = reinterpret_cast<int *>(base + kOffItemCnt);
         ba.item_off = reinterpret_cast<int *>(base + kOffItemOff);
         ba.chunk = kSearchThreads;
         ba.cnt = cnt;

@@ -16,11 +16,10 @@
 // memory.  Pass 1 also marks the (layer, sector) rows holding a strip
 // shorter than its sector (one bit per row, written beside the bin table);
 // the search decides the strip test of an unmarked row from the sector's
-// bounds.  The last CTA also turns
-// per-event seed counts into the search kernel's work items (chunks of at
-// most `chunk` <= 128 seeds of one event).  The order inside a bin comes
-// from atomics and is not deterministic; every consumer ranks hits by
-// (|dx|, id), which does not depend on it.
+// bounds.  Block 0 also turns the per-event seed counts into the search
+// kernel's work items (chunks of at most `chunk` <= 128 seeds of one event).
+// The order inside a bin comes from atomics and is not deterministic; every
+// consumer ranks hits by (|dx|, id), which does not depend on it.
 #include "ds_args.cuh"
 
 namespace ds {
@@ -51,7 +50,6 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
     extern __shared__ __align__(16) unsigned int s_cnt[];
     __shared__ uint32_t s_part[4];                // rows with a strip shorter than its sector
     __shared__ int s_scan[32];
-    __shared__ bool s_last;
     const int e = blockIdx.x;
     const DevGeom &g = a.g;
     const int nb = 4 * g.n_sec * kNXB;
@@ -71,6 +69,23 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
         if (tid == 0) raise_flag(a.cnt, DS_FLAG_EVENT_TOO_LARGE);
         n = 0;
         h1 = h0;
+    }
+
+    // search work items: chunks of at most a.chunk seeds of one event.  They
+    // depend on the seed offsets only, so block 0 lays them out first.
+    if (e == 0) {
+        const int32_t *so = a.seed_off;
+        const int n_items = block_offsets_f(
+            [so, &a](int k) {
+                const int s0 = __ldg(so + k), s1 = __ldg(so + k + 1);
+                const int ns = (s0 < 0 || s1 < s0 || s1 > a.n_seeds) ? 0 : s1 - s0;
+                return (ns + a.chunk - 1) / a.chunk;
+            },
+            a.n_events, a.item_off, s_scan);
+        if (tid == 0) {
+            a.item_off[a.n_events] = n_items;
+            if (__ldg(so) != 0 || __ldg(so + a.n_events) != a.n_seeds) raise_flag(a.cnt, DS_FLAG_BAD_OFFSETS);
+        }
     }
 
     const int cnt_words = (nb + 1 + 3) & ~3;
@@ -215,34 +230,6 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
         }
     }
 
-    // search work items of this event: chunks of at most a.chunk seeds;
-    // the last CTA to finish scans them into item_off
-    if (threadIdx.x == 0) {
-        const int s0 = __ldg(a.seed_off + e), s1 = __ldg(a.seed_off + e + 1);
-        const int ns = (s0 < 0 || s1 < s0 || s1 > a.n_seeds) ? 0 : s1 - s0;
-        a.item_cnt[e] = (ns + a.chunk - 1) / a.chunk;
-        __threadfence();
-        const unsigned int t = atomicAdd(&a.cnt->done_bkt, 1u);
-        s_last = t == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    int acc = 0;
-    for (int c0 = 0; c0 < a.n_events; c0 += blockDim.x) {
-        const int i = c0 + threadIdx.x;
-        const int v = i < a.n_events ? __ldcg(a.item_cnt + i) : 0;
-        int t;
-        const int r = block_exclusive_scan(v, s_scan, &t);
-        if (i < a.n_events) a.item_off[i] = acc + r;
-        acc += t;
-    }
-    if (threadIdx.x == 0) {
-        a.item_off[a.n_events] = acc;
-        if (__ldg(a.seed_off) != 0 || __ldg(a.seed_off + a.n_events) != a.n_seeds)
-            raise_flag(a.cnt, DS_FLAG_BAD_OFFSETS);
-        a.cnt->done_bkt = 0;
-    }
 }
 
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st, Prof *prof)

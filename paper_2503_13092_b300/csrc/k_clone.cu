@@ -108,15 +108,7 @@ __global__ void __launch_bounds__(kCloneThreads) k_clone(const __grid_constant__
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    int run = 0;
-    for (int c0 = 0; c0 < a.n_events; c0 += blockDim.x) {
-        const int i = c0 + threadIdx.x;
-        const int v = i < a.n_events ? __ldcg(a.count_ws + i) : 0;
-        int tot;
-        const int r = block_exclusive_scan(v, s_scan, &tot);
-        if (i < a.n_events) a.trk_off[i] = run + r;
-        run += tot;
-    }
+    const int run = block_offsets(a.count_ws, a.n_events, a.trk_off, s_scan);
     if (threadIdx.x == 0) {
         a.trk_off[a.n_events] = run;
         *a.n_tracks = run;
