@@ -25,6 +25,7 @@ namespace ds {
 
 constexpr int kVtxThreads = 256;
 constexpr int kVtxSmallCap = 512;
+constexpr int kVtxCtasPerSm = 4;      // resident CTAs of the small-capacity launch per SM
 constexpr int kVtxSeg = 8192;          // pairs per two-phase segment
 constexpr int kVtxStore = 1024;        // candidate results kept in shared memory per segment
 
@@ -229,7 +230,7 @@ __device__ __forceinline__ int lower_bound_u16(const uint16_t *list, int n, int 
 }
 
 template <int CAP, bool LARGE>
-__global__ void __launch_bounds__(kVtxThreads, 3) k_vertex(const __grid_constant__ VertexArgs a)
+__global__ void __launch_bounds__(kVtxThreads, kVtxCtasPerSm) k_vertex(const __grid_constant__ VertexArgs a)
 {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ int s_scan[32];
@@ -528,7 +529,7 @@ cudaError_t launch_vertex(const VertexArgs &a0, const ScatterVtxArgs &sa, int sm
     if (a0.n_events <= 0) return cudaSuccess;
     VertexArgs a = a0;
     const size_t sm_small = vtx_smem(kVtxSmallCap), sm_large = vtx_smem(kMaxVertexTracks);
-    const int g_small = a.n_events < 4 * sm_count ? a.n_events : 4 * sm_count;
+    const int g_small = a.n_events < kVtxCtasPerSm * sm_count ? a.n_events : kVtxCtasPerSm * sm_count;
     const int g_large = a.n_events < sm_count ? a.n_events : sm_count;
     a.n_tickets = g_small + g_large;
     prof->begin("k_vertex_small", st);
