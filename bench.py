@@ -125,11 +125,11 @@ def algorithmic(E, S, H, n_t, n_v, n_cand, n_pairs, table_stride):
     tb = 2 * table_stride * E                    # per-event bin tables
     mlp_flop = MLP_FLOP
     return {
-        # hits in (13 B) -> float4 records (16 B) + compact x0 (4 B) + tables
-        "k_bucket": dict(bytes=13 * H + 20 * H + tb),
-        # seeds (24 B), staged x0 + records (20 B/hit), tables -> candidates
+        # hits in (13 B) -> sorted x0 (4 B) + index inside the event (2 B) + tables
+        "k_bucket": dict(bytes=13 * H + 6 * H + tb),
+        # seeds (24 B), staged x0 + index map (6 B/hit), tables -> candidates
         # (64 B inputs + 48 B fit) + per-seed range and rank (20 B)
-        "k_search": dict(bytes=24 * S + 20 * H + tb + 112 * n_cand + 20 * S),
+        "k_search": dict(bytes=24 * S + 6 * H + tb + 112 * n_cand + 20 * S),
         "k_mlp": dict(bytes=68 * n_cand, flop=mlp_flop * n_cand),
         "k_pick": dict(bytes=16 * S + 20 * n_cand + 48 * n_t + 88 * S),
         "k_clone": dict(bytes=28 * S + 8 * E),

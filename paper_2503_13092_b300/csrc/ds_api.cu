@@ -35,7 +35,7 @@ struct ds_ctx {
     ds::DevCounters *d_cnt = nullptr;
     // workspaces
     int cap_events = 0, cap_seeds = 0, cap_hits = 0, cap_pool = 0;
-    float4 *sorted = nullptr;
+    uint16_t *sperm = nullptr;
     float *sx0 = nullptr;
     uint16_t *bins = nullptr;
     int *item_off = nullptr;
@@ -336,7 +336,7 @@ void ds_destroy(ds_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    void *ptrs[] = {ctx->d_cnt, ctx->d_tc, ctx->d_lines_tc, ctx->sorted, ctx->sx0, ctx->item_off, ctx->bins, ctx->cand_feat,
+    void *ptrs[] = {ctx->d_cnt, ctx->d_tc, ctx->d_lines_tc, ctx->sperm, ctx->sx0, ctx->item_off, ctx->bins, ctx->cand_feat,
                     ctx->cand_meta, ctx->cand_logit, ctx->seed_cand, ctx->trk_ws, ctx->key_ws, ctx->hit_ws,
                     ctx->rank_ws, ctx->count_trk, ctx->count_vtx, ctx->large_vtx, ctx->pool, ctx->pool_pos,
                     ctx->h.seed_off, ctx->h.hit_off, ctx->h.seed_cols, ctx->h.hit_cols, ctx->h.layer,
@@ -427,7 +427,7 @@ ds_status ds_reserve(ds_ctx *ctx, int32_t E, int32_t S, int32_t H)
         ctx->cap_seeds = S;
     }
     if (H > ctx->cap_hits) {
-        if ((st = grow(ctx, &ctx->sorted, (size_t)H)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->sperm, (size_t)H)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->sx0, (size_t)H + 4)) != DS_OK) return st;   // bulk-copy tail
         ctx->cap_hits = H;
     }
@@ -482,8 +482,8 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     ba.ybeg = ht->ybeg;
     ba.yend = ht->yend;
     ba.layer = ht->layer;
-    ba.sorted = ctx->sorted;
     ba.sx0 = ctx->sx0;
+    ba.sperm = ctx->sperm;
     ba.bins = ctx->bins;
     ba.item_off = ctx->item_off;
     ba.chunk = ctx->tune.search_chunk;
@@ -499,8 +499,10 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     sa.seed_off = b->seed_off;
     sa.hit_off = b->hit_off;
     sa.sx = sd->x; sa.sy = sd->y; sa.stx = sd->tx; sa.sty = sd->ty; sa.sqop = sd->qop; sa.schi2 = sd->chi2;
-    sa.sorted = ctx->sorted;
+    sa.ybeg = ht->ybeg;
+    sa.yend = ht->yend;
     sa.sx0 = ctx->sx0;
+    sa.sperm = ctx->sperm;
     sa.bins = ctx->bins;
     sa.item_off = ctx->item_off;
     sa.cand_feat = ctx->cand_feat;

@@ -29,8 +29,8 @@ struct BucketArgs {
     const int32_t *seed_off;
     const float *x0, *ybeg, *yend;
     const uint8_t *layer;
-    float4 *sorted;
     float *sx0;
+    uint16_t *sperm;
     uint16_t *bins;
     int *item_off;         // [n_events + 1]
     int chunk;             // max seeds per search work item (<= kSearchThreads)
@@ -45,8 +45,9 @@ struct SearchArgs {
     int n_hits;
     const int32_t *seed_off, *hit_off;
     const float *sx, *sy, *stx, *sty, *sqop, *schi2;
-    const float4 *sorted;
+    const float *ybeg, *yend;   // the caller's hit arrays (strip extents)
     const float *sx0;
+    const uint16_t *sperm;
     const uint16_t *bins;
     const int *item_off;
     float4 *cand_feat;     // [cand_cap][4]: the 16 network inputs

@@ -3,11 +3,12 @@
 // Data layout in HBM (per batch):
 //   seeds     caller's SoA float32 (x, y, tx, ty, qop, chi2), CSR over events
 //   hits      caller's SoA (x0, ybeg, yend float32, layer u8), CSR over events
-//   sorted    float4 per hit {x0, ybeg, yend, id-bits}, grouped by event, then
-//             by (layer, Y sector, x bin): one 16-byte load per hit that passes
-//             a window's x test
-//   sx0       the same order, x0 only (4 bytes per hit): staged per event in
-//             shared memory for the window scans
+//   sx0       x0 per hit, grouped by event, then by (layer, Y sector, x bin)
+//             (4 bytes per hit): staged per event in shared memory for the
+//             window scans
+//   sperm     the same order: uint16 index of the hit inside its event (2
+//             bytes per hit), giving its id and, through the caller's arrays,
+//             its strip extent when a window needs them
 //   items     search work items: (event, chunk of <= 128 of its seeds)
 //   bins      per event: uint16 offsets (layer, sector, xbin) -> first sorted
 //             hit, relative to the event's first hit (<= 65535 hits per event),

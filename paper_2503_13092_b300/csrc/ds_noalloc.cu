@@ -37,8 +37,8 @@ constexpr int kNATableStride = table_stride_for(kMaxSectors);
 
 constexpr size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 constexpr size_t kOffCounters = 0;
-constexpr size_t kOffSorted = align256(sizeof(DevCounters));
-constexpr size_t kOffSx0 = kOffSorted + align256(sizeof(float4) * (size_t)kNAHits);
+constexpr size_t kOffPerm = align256(sizeof(DevCounters));
+constexpr size_t kOffSx0 = kOffPerm + align256(sizeof(uint16_t) * (size_t)kNAHits);
 constexpr size_t kOffBins = kOffSx0 + align256(sizeof(float) * ((size_t)kNAHits + 4));
 constexpr size_t kOffTrk = kOffBins + align256(sizeof(uint16_t) * (size_t)kNATableStride * kNAEvents);
 constexpr size_t kOffKey = kOffTrk + align256(sizeof(ds_track) * (size_t)kNASeeds);
@@ -126,8 +126,8 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         ba.hit_off = b->hit_off;
         ba.seed_off = b->seed_off;
         ba.x0 = ht->x0; ba.ybeg = ht->ybeg; ba.yend = ht->yend; ba.layer = ht->layer;
-        ba.sorted = reinterpret_cast<float4 *>(base + kOffSorted);
         ba.sx0 = reinterpret_cast<float *>(base + kOffSx0);
+        ba.sperm = reinterpret_cast<uint16_t *>(base + kOffPerm);
         ba.bins = reinterpret_cast<uint16_t *>(base + kOffBins);
         ba.item_off = reinterpret_cast<int *>(base + kOffItemOff);
         ba.chunk = kSearchThreads;
@@ -143,8 +143,10 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         sa.seed_off = b->seed_off;
         sa.hit_off = b->hit_off;
         sa.sx = sd->x; sa.sy = sd->y; sa.stx = sd->tx; sa.sty = sd->ty; sa.sqop = sd->qop; sa.schi2 = sd->chi2;
-        sa.sorted = ba.sorted;
+        sa.ybeg = ht->ybeg;
+        sa.yend = ht->yend;
         sa.sx0 = ba.sx0;
+        sa.sperm = ba.sperm;
         sa.bins = ba.bins;
         sa.item_off = ba.item_off;
         sa.cand_feat = reinterpret_cast<float4 *>(base + kOffCandFeat);

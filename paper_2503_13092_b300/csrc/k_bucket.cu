@@ -10,9 +10,9 @@
 // One CTA per event.  Pass 1 reads the hits with 16-byte loads (4 hits per
 // load; events up to 6144 hits stay in registers) and counts bins with
 // shared-memory atomics, a block scan turns counts into offsets (written out
-// as the event's bin table), pass 2 places float4 {x0, ybeg, yend, id} records
-// at their sorted positions in shared memory and writes them, and the compact
-// x0 array, with coalesced stores.  Larger events scatter straight to global
+// as the event's bin table), pass 2 places each hit's x0 and its index inside
+// the event at its sorted position in shared memory, and both arrays are
+// written with coalesced stores.  Larger events scatter straight to global
 // memory.  Pass 1 also marks the (layer, sector) rows holding a strip
 // shorter than its sector (one bit per row, written beside the bin table);
 // the search decides the strip test of an unmarked row from the sector's
@@ -46,7 +46,7 @@ __device__ __forceinline__ int hit_bin(const DevGeom &g, float x0, float yb, flo
 __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_constant__ BucketArgs a)
 {
     // dynamic shared memory: nb + 1 bin counters (padded to 16 bytes), then the
-    // event's records in sorted order (events up to kBucketStage hits)
+    // event's x0 and hit indices in sorted order (events up to kBucketStage hits)
     extern __shared__ __align__(16) unsigned int s_cnt[];
     __shared__ uint32_t s_part[4];                // rows with a strip shorter than its sector
     __shared__ int s_scan[32];
@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
     }
 
     const int cnt_words = (nb + 1 + 3) & ~3;
-    float4 *s_rec = reinterpret_cast<float4 *>(s_cnt + cnt_words);
+    float *s_x = reinterpret_cast<float *>(s_cnt + cnt_words);
+    uint16_t *s_pm = reinterpret_cast<uint16_t *>(s_x + kBucketStage);
     for (int b = tid; b <= nb; b += blockDim.x) s_cnt[b] = 0;
     if (tid < 4) s_part[tid] = 0u;
     __syncthreads();
@@ -182,51 +183,41 @@ __global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_const
     if (tid < 4) reinterpret_cast<uint32_t *>(table + g.ext_off)[tid] = s_part[tid];
     __syncthreads();
 
-    // pass 2: records {x0, ybeg, yend, id} in sorted order.  Staged events are
-    // assembled in shared memory and written out with coalesced stores.
-    if (vec && staged) {
+    // pass 2: x0 and the index inside the event, in sorted order.  Staged
+    // events are assembled in shared memory and written with coalesced stores.
+    if (vec) {
 #pragma unroll
         for (int r = 0; r < kBucketVecRows; ++r) {
             const int base = a0 + 4 * (r * (int)blockDim.x + tid);
             const float xs[4] = {vx[r].x, vx[r].y, vx[r].z, vx[r].w};
-            const float ybs[4] = {vyb[r].x, vyb[r].y, vyb[r].z, vyb[r].w};
-            const float yes[4] = {vye[r].x, vye[r].y, vye[r].z, vye[r].w};
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 if (vb[r][j] >= 0) {
                     const unsigned int slot = atomicAdd(&s_cnt[vb[r][j]], 1u);
-                    s_rec[slot] = make_float4(xs[j], ybs[j], yes[j], __int_as_float(base + j));
+                    if (staged) {
+                        s_x[slot] = xs[j];
+                        s_pm[slot] = (uint16_t)(base + j - h0);
+                    } else {
+                        a.sx0[h0 + slot] = xs[j];
+                        a.sperm[h0 + slot] = (uint16_t)(base + j - h0);
+                    }
                 }
         }
-        __syncthreads();
-        for (int i = tid; i < n; i += blockDim.x) {
-            const float4 rec = s_rec[i];
-            a.sorted[h0 + i] = rec;
-            a.sx0[h0 + i] = rec.x;
-        }
-    } else if (vec) {
-#pragma unroll
-        for (int r = 0; r < kBucketVecRows; ++r) {
-            const int base = a0 + 4 * (r * (int)blockDim.x + tid);
-            const float xs[4] = {vx[r].x, vx[r].y, vx[r].z, vx[r].w};
-            const float ybs[4] = {vyb[r].x, vyb[r].y, vyb[r].z, vyb[r].w};
-            const float yes[4] = {vye[r].x, vye[r].y, vye[r].z, vye[r].w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (vb[r][j] >= 0) {
-                    const unsigned int slot = atomicAdd(&s_cnt[vb[r][j]], 1u);
-                    a.sorted[h0 + slot] = make_float4(xs[j], ybs[j], yes[j], __int_as_float(base + j));
-                    a.sx0[h0 + slot] = xs[j];
-                }
+        if (staged) {
+            __syncthreads();
+            for (int i = tid; i < n; i += blockDim.x) {
+                a.sx0[h0 + i] = s_x[i];
+                a.sperm[h0 + i] = s_pm[i];
+            }
         }
     } else {
         for (int i = tid; i < n; i += blockDim.x) {
             const int h = h0 + i;
-            const float x0 = __ldg(a.x0 + h), yb = __ldg(a.ybeg + h), ye = __ldg(a.yend + h);
-            const int b = hit_bin(g, x0, yb, ye, __ldg(a.layer + h), nb, a.cnt, s_part);
+            const float x0 = __ldg(a.x0 + h);
+            const int b = hit_bin(g, x0, __ldg(a.ybeg + h), __ldg(a.yend + h), __ldg(a.layer + h), nb, a.cnt, s_part);
             const unsigned int slot = atomicAdd(&s_cnt[b], 1u);
-            a.sorted[h0 + slot] = make_float4(x0, yb, ye, __int_as_float(h));
             a.sx0[h0 + slot] = x0;
+            a.sperm[h0 + slot] = (uint16_t)i;
         }
     }
 
@@ -236,7 +227,7 @@ cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st, Prof *prof)
 {
     if (a.n_events <= 0) return cudaSuccess;
     const int nb = 4 * a.g.n_sec * kNXB;
-    const size_t smem = sizeof(unsigned int) * (size_t)((nb + 1 + 3) & ~3) + sizeof(float4) * kBucketStage;
+    const size_t smem = sizeof(unsigned int) * (size_t)((nb + 1 + 3) & ~3) + (sizeof(float) + sizeof(uint16_t)) * kBucketStage;
     prof->begin("k_bucket", st);
     k_bucket<<<a.n_events, kBucketThreads, smem, st>>>(a);
     prof->end(st);
@@ -246,7 +237,7 @@ cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st, Prof *prof)
 cudaError_t init_bucket_attributes()
 {
     const size_t smem = sizeof(unsigned int) * (size_t)((4 * kMaxSectors * kNXB + 1 + 3) & ~3) +
-                        sizeof(float4) * kBucketStage;
+                        (sizeof(float) + sizeof(uint16_t)) * kBucketStage;
     // two CTAs per SM need nearly all of its shared memory: ask for the largest carveout
     cudaError_t e = cudaFuncSetAttribute(k_bucket, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

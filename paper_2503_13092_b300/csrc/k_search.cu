@@ -16,8 +16,10 @@
 // event.  The event's bin table (with its partial-strip row bits) and
 // compact x0 array are staged in shared memory by two bulk copies (TMA) on an
 // mbarrier; every x test of every window reads shared memory, and a hit
-// passing it loads its 16-byte record only when its sector holds a strip
-// shorter than the sector or its distance ties with another hit's.
+// passing it looks up its strip extent and id (through the sorted index map
+// and the caller's arrays) only when its sector holds a strip shorter than
+// the sector or its distance ties with another hit's; the ids of a
+// candidate's hits are looked up when it is written.
 // Three flattened phases keep lanes busy whatever the hits per seed: UTbX
 // window (thread per seed), refined windows (thread per (seed, UTbX hit)),
 // fit + features (thread per candidate).  Candidates are written to a compact
@@ -29,6 +31,23 @@ namespace ds {
 
 constexpr uint16_t kNone = 0xFFFFu;
 constexpr int T = kSearchThreads;
+
+// The sorted hits of one event: x0 is staged separately; the index inside the
+// event (sperm) gives a hit's id and, through the caller's arrays, its strip.
+struct EvHits {
+    const uint16_t *perm;       // sorted position -> index inside the event
+    const float *ybeg, *yend;   // caller's arrays from the event's first hit
+    int h0;                     // the event's first hit (ids are h0 + index)
+};
+
+// {unused, ybeg, yend, id bits} of the hit at sorted position pos
+__device__ __forceinline__ float4 hit_record(const EvHits &E, int pos)
+{
+    const int k = __ldg(E.perm + pos);
+    return make_float4(0.f, __ldg(E.ybeg + k), __ldg(E.yend + k), __int_as_float(E.h0 + k));
+}
+
+__device__ __forceinline__ int hit_id(const EvHits &E, int pos) { return E.h0 + __ldg(E.perm + pos); }
 
 template <int N>
 __device__ __forceinline__ void topn_insert(float (&d)[N], int (&id)[N], int (&p)[N], float dn,
@@ -61,13 +80,13 @@ __device__ __forceinline__ bool key_less(float da, int ia, float db, int ib)
 // Sectors whose strips all cover the whole sector pass the strip test as a
 // whole (sector_strip_class).  Up to B hits passing the x test are collected
 // during the scan; after it (one uniform point for the whole warp) their
-// 16-byte records are loaded together for the per-hit strip test and the
-// ids, but only when a sector needs the per-hit test or two
+// strip extents and ids are looked up together for the per-hit strip test,
+// but only when a sector needs the per-hit test or two
 // collected distances are equal (the id breaks the tie); the survivors are
 // ordered by a compare-exchange network.  A window with more than B
 // x-passing hits (rare) is rescanned with one insertion per hit.
 template <int N, int B>
-__device__ __forceinline__ int window_scan(const DevGeom &g, const float *X0, const float4 *__restrict__ H,
+__device__ __forceinline__ int window_scan(const DevGeom &g, const float *X0, const EvHits &H,
                                            const uint16_t *Tb, const uint32_t *Part, int layer, float u, float y,
                                            float w, float dy, float (&d)[N], int (&id)[N], int (&p)[N])
 {
@@ -111,11 +130,11 @@ __device__ __forceinline__ int window_scan(const DevGeom &g, const float *X0, co
                 tie |= k2 < nq && qd[k] == qd[k2];
         int hid[B];
         if (per_hit || tie) {
-            // records of the collected hits, all loads in flight together
+            // strips and ids of the collected hits, all loads in flight together
             float4 h[B];
 #pragma unroll
             for (int k = 0; k < B; ++k)
-                if (k < nq) h[k] = __ldg(H + qi[k]);
+                if (k < nq) h[k] = hit_record(H, qi[k]);
 #pragma unroll
             for (int k = 0; k < B; ++k) {
                 const bool ok = k < nq && h[k].y - dy <= y && y <= h[k].z + dy;
@@ -165,7 +184,7 @@ __device__ __forceinline__ int window_scan(const DevGeom &g, const float *X0, co
         for (int i = i0; i < i1; ++i) {
             const float dx = fabsf(X0[i] - u);
             if (dx < w) {
-                const float4 hh = __ldg(H + i);
+                const float4 hh = hit_record(H, i);
                 if (hh.y - dy <= y && y <= hh.z + dy) {
                     topn_insert<N>(d, id, p, dx, __float_as_int(hh.w), i);
                     ++cnt;
@@ -250,6 +269,22 @@ __device__ __forceinline__ CandFit fit_candidate(const DevGeom &g, const SeedCtx
         f.qop = sc.qop;
     }
     return f;
+}
+
+// First window with more x-passing hits than the collection column holds
+// (rare): exact rescan with insertion into the k1 best, kept out of line so
+// its arrays do not weigh on the kernel's registers.  Writes the kept sorted
+// positions to out[j * T], returns how many were kept.
+__device__ __noinline__ int wide_first_window(const DevGeom &g, const float *X0, const EvHits &H,
+                                              const uint16_t *Tb, const uint32_t *Part, float u, float y, float w,
+                                              float dy, int k1, uint16_t *out)
+{
+    float d[kK1Max];
+    int id[kK1Max], p[kK1Max];
+    const int q = window_scan<kK1Max, 4>(g, X0, H, Tb, Part, 3, u, y, w, dy, d, id, p);
+#pragma unroll
+    for (int j = 0; j < kK1Max; ++j) out[j * T] = (uint16_t)p[j];
+    return min(q, k1);
 }
 
 // Dv1: the UTaX strip coordinate predicted by the line through the magnet
@@ -343,7 +378,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     const int h0 = s_hits[0], h1 = s_hits[1];
     const bool restage = s_hits[2] != 0;
     const int nh = h1 - h0;
-    const float4 *H = a.sorted + h0;
+    const EvHits H{a.sperm + h0, a.ybeg + h0, a.yend + h0, h0};
     const bool staged = nh <= a.stage_hits;
     const float *X0 = staged ? xs + (h0 & 3) : a.sx0 + h0;
 
@@ -419,10 +454,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
                     }
             }
             if (nq > kCap) {
-                const int q = window_scan<kK1Max, 4>(g, X0, H, Tb, Part, 3, u_bx, sc.yl[3], sc.w1, P.dy_tol, d, id, p);
-                nbx = min(q, P.k1);
-#pragma unroll
-                for (int j = 0; j < kK1Max; ++j) s_bx[j][tid] = (uint16_t)p[j];
+                nbx = wide_first_window(g, X0, H, Tb, Part, u_bx, sc.yl[3], sc.w1, P.dy_tol, P.k1, &s_bx[0][tid]);
             } else {
                 int nok = per_hit ? 0 : nq;   // otherwise every collected hit passes the strip test
                 for (int k0 = 0; per_hit && k0 < nq; k0 += 4) {
@@ -431,7 +463,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         ii[k] = k0 + k < nq ? col[(k0 + k) * T] : -1;
-                        if (ii[k] >= 0) h[k] = __ldg(H + ii[k]);
+                        if (ii[k] >= 0) h[k] = hit_record(H, ii[k]);
                     }
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
@@ -444,7 +476,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
                     while (j >= 0) {
                         const int c = col[j * T];
                         const float dc = fabsf(X0[c] - u);
-                        const bool before = dv < dc || (dv == dc && __float_as_int(__ldg(&H[v].w)) < __float_as_int(__ldg(&H[c].w)));
+                        const bool before = dv < dc || (dv == dc && hit_id(H, v) < hit_id(H, c));
                         if (!before) break;
                         col[(j + 1) * T] = (uint16_t)c;
                         --j;
@@ -476,7 +508,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
                 const int i0 = Tb[row + b0], i1 = Tb[row + b1 + 1];
                 for (int i = i0; i < i1; ++i) {
                     if (!(fabsf(X0[i] - u0) < w_b)) continue;
-                    const float4 hb = __ldg(H + i);
+                    const float4 hb = hit_record(H, i);
                     if (!(hb.y - dy <= y3 && y3 <= hb.z + dy)) continue;
                     float dd[1];
                     int ii[1], pp[1];
@@ -614,7 +646,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
         m.seed = s_item[1] + o;
         m.ty = sc.ty;
 #pragma unroll
-        for (int l = 0; l < 4; ++l) m.hit[l] = loc[l] >= 0 ? __float_as_int(__ldg(H + loc[l]).w) : -1;
+        for (int l = 0; l < 4; ++l) m.hit[l] = loc[l] >= 0 ? hit_id(H, loc[l]) : -1;
         a.cand_meta[slot] = m;
     }
     }
