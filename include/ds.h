@@ -345,7 +345,10 @@ DS_API ds_status ds_mlp_eval(ds_ctx *ctx, const float *d_features, int32_t n, fl
  * absent) and d_logit n (the network output before the sigmoid; may be NULL).
  * *d_count (device) receives the number of candidates of the call, which may
  * exceed capacity (the rest are not copied).  A seed's candidates are
- * contiguous and in enumeration order; the order of the seeds is unspecified.
+ * contiguous; in training mode they are in enumeration order (its UTbX hits
+ * by (|dx|, id), then the UTaU and UTbV options), otherwise grouped by UTbX
+ * hit in an unspecified order of those hits.  The order of the seeds is
+ * unspecified.
  * Call after ds_reconstruct on the same stream and before the next one.
  * d_features and d_hits 16-byte aligned.  DS_ERR_ARG for null pointers (other
  * than d_logit), misaligned arrays or capacity < 0. */

@@ -43,7 +43,7 @@ __device__ __forceinline__ int hit_bin(const DevGeom &g, float x0, float yb, flo
     return row * kNXB + xbin_of(g, x0);
 }
 
-__global__ void __launch_bounds__(kBucketThreads, 2) k_bucket(const __grid_constant__ BucketArgs a)
+__global__ void __launch_bounds__(kBucketThreads, 3) k_bucket(const __grid_constant__ BucketArgs a)
 {
     // dynamic shared memory: nb + 1 bin counters (padded to 16 bytes), then the
     // event's x0 and hit indices in sorted order (events up to kBucketStage hits)
@@ -238,7 +238,7 @@ cudaError_t init_bucket_attributes()
 {
     const size_t smem = sizeof(unsigned int) * (size_t)((4 * kMaxSectors * kNXB + 1 + 3) & ~3) +
                         (sizeof(float) + sizeof(uint16_t)) * kBucketStage;
-    // two CTAs per SM need nearly all of its shared memory: ask for the largest carveout
+    // three CTAs per SM (about 52 KB each): ask for the largest shared-memory carveout
     cudaError_t e = cudaFuncSetAttribute(k_bucket, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return e;

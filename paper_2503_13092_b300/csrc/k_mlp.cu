@@ -5,7 +5,7 @@
 // section: NN Response < 0.5).  The best candidate of each seed is the one with
 // the lowest network output before the sigmoid (same order as the response,
 // no saturation) among those under the threshold; chi2 then breaks ties, then
-// the enumeration order.  In chi2 mode the lowest chi2/ndof wins and the cut
+// the hit ids in layer order (absent last).  In chi2 mode the lowest chi2/ndof wins and the cut
 // is applied to the winner (Algorithm Design section: score from the distance
 // between expected and real hit positions).
 //
@@ -65,6 +65,18 @@ __global__ void __launch_bounds__(256) k_mlp_fp32(const __grid_constant__ MlpArg
 
 __device__ __forceinline__ float sigmoid_fast(float z) { return 1.f / (1.f + __expf(-z)); }
 
+// Last part of the pick key: hit ids in layer order, absent (-1) last.
+__device__ __forceinline__ bool hits_less(const CandMeta *x, const CandMeta *y)
+{
+    const int4 hx = __ldg(reinterpret_cast<const int4 *>(x) + 2), hy = __ldg(reinterpret_cast<const int4 *>(y) + 2);
+    const unsigned ax[4] = {(unsigned)hx.x, (unsigned)hx.y, (unsigned)hx.z, (unsigned)hx.w};
+    const unsigned ay[4] = {(unsigned)hy.x, (unsigned)hy.y, (unsigned)hy.z, (unsigned)hy.w};
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+        if (ax[l] != ay[l]) return ax[l] < ay[l];
+    return false;
+}
+
 __global__ void __launch_bounds__(256) k_pick(const __grid_constant__ PickArgs a)
 {
     // each warp stages its 32 winner records in shared memory and writes them
@@ -92,7 +104,7 @@ __global__ void __launch_bounds__(256) k_pick(const __grid_constant__ PickArgs a
             unsigned long long key = kNoKey;
             if (P.pick_chi2) key = pack_key(chi2 / (float)ndof, lg);
             else if (lg < thr) key = pack_key(lg, chi2);
-            if (key < best) {
+            if (key < best || (key == best && key != kNoKey && hits_less(a.meta + c, a.meta + bi))) {
                 best = key;
                 bi = c;
             }

@@ -405,6 +405,10 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     // ---------------------------------------------------------------- search
     int n_cand = 0;
     int nbx = 0;
+    // first window (Dv0): 0 keep the survivors as collected, 1 select the k1
+    // closest (warp), 2 exact sort (training mode or a distance tie), 3 done
+    int sel_state = 0, sel_n = 0;
+    float sel_u = 0.f;
     if (active) {
         SeedCtx sc;
         const float x = sd_x, y = sd_y;
@@ -433,9 +437,10 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
             // UTbX window: x-passing positions collected in this thread's
             // column of s_sel (free until the refined windows); the hits of
             // sectors whose strips all cover the sector pass the strip test as
-            // a whole, otherwise the records are loaded together for it;
-            // the survivors are insertion-sorted by (|dx|, id) in place (ids
-            // loaded only on exact distance ties)
+            // a whole, otherwise their strips are looked up together.  The
+            // kept hits are the k1 closest by (|dx|, id); their order matters
+            // only for the candidate export, so they are sorted in training
+            // mode only (the pick breaks exact key ties by hit ids)
             uint16_t *col = &s_sel[0][0][0] + tid;
             constexpr int kCap = kK1Max * 5;
             const float u = u_bx, w = sc.w1, y3 = sc.yl[3], dy = P.dy_tol;
@@ -455,6 +460,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
             }
             if (nq > kCap) {
                 nbx = wide_first_window(g, X0, H, Tb, Part, u_bx, sc.yl[3], sc.w1, P.dy_tol, P.k1, &s_bx[0][tid]);
+                sel_state = 3;
             } else {
                 int nok = per_hit ? 0 : nq;   // otherwise every collected hit passes the strip test
                 for (int k0 = 0; per_hit && k0 < nq; k0 += 4) {
@@ -469,22 +475,13 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
                     for (int k = 0; k < 4; ++k)
                         if (ii[k] >= 0 && h[k].y - dy <= y3 && y3 <= h[k].z + dy) col[(nok++) * T] = (uint16_t)ii[k];
                 }
-                for (int a2 = 1; a2 < nok; ++a2) {
-                    const int v = col[a2 * T];
-                    const float dv = fabsf(X0[v] - u);
-                    int j = a2 - 1;
-                    while (j >= 0) {
-                        const int c = col[j * T];
-                        const float dc = fabsf(X0[c] - u);
-                        const bool before = dv < dc || (dv == dc && hit_id(H, v) < hit_id(H, c));
-                        if (!before) break;
-                        col[(j + 1) * T] = (uint16_t)c;
-                        --j;
-                    }
-                    col[(j + 1) * T] = (uint16_t)v;
-                }
-                nbx = min(nok, P.k1);
-                for (int j = 0; j < kK1Max; ++j) s_bx[j][tid] = j < nbx ? col[j * T] : (uint16_t)0xFFFF;
+                // the order of the kept hits matters only for the candidate
+                // export (training mode: exact sort below); otherwise only the
+                // k1 closest are needed, and a window with more survivors has
+                // them selected by its warp below
+                sel_n = nok;
+                sel_u = u;
+                sel_state = P.training ? 2 : (nok > P.k1 ? 1 : 0);
             }
         } else {
             // Dv1 triplets: every UTbX hit with a physical kink (a window of
@@ -524,6 +521,65 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
                 s_bx[j][tid] = (uint16_t)(p[j] & 0xffff);
                 s_sel[j][0][tid] = j < nbx ? (uint16_t)((unsigned)p[j] >> 16) : kNone;   // the triplet's UTaX hit
             }
+        }
+    }
+    if (V == 0) {
+        // first windows with more than k1 survivors (outside training): the
+        // warp ranks each one's hits by (|dx|, position), one or two hits per
+        // lane, and the k1 first take the first k1 slots of its column.  A
+        // shared distance that could change the kept set (the order is then
+        // by id) sends the seed to the exact sort.
+        const int lane = tid & 31;
+        const float inf = __int_as_float(0x7f800000);
+        unsigned wm = __ballot_sync(0xffffffffu, sel_state == 1);
+        while (wm) {
+            const int src = __ffs(wm) - 1;
+            wm &= wm - 1;
+            const int n = __shfl_sync(0xffffffffu, sel_n, src);         // <= kCap < 64
+            const float uu = __shfl_sync(0xffffffffu, sel_u, src);
+            uint16_t *cc = &s_sel[0][0][0] + (tid - lane + src);
+            const int p0 = lane < n ? cc[lane * T] : 0, p1 = lane + 32 < n ? cc[(lane + 32) * T] : 0;
+            const float d0 = lane < n ? fabsf(X0[p0] - uu) : inf, d1 = lane + 32 < n ? fabsf(X0[p1] - uu) : inf;
+            int r0 = 0, r1 = 0;
+            bool t0 = false, t1 = false;
+            for (int k = 0; k < n; ++k) {
+                const float dk = __shfl_sync(0xffffffffu, k < 32 ? d0 : d1, k & 31);
+                const int pk = __shfl_sync(0xffffffffu, k < 32 ? p0 : p1, k & 31);
+                r0 += dk < d0 || (dk == d0 && pk < p0);
+                r1 += dk < d1 || (dk == d1 && pk < p1);
+                t0 |= dk == d0 && pk != p0;
+                t1 |= dk == d1 && pk != p1;
+            }
+            const bool tie = __any_sync(0xffffffffu, (lane < n && t0 && r0 <= P.k1) ||
+                                                         (lane + 32 < n && t1 && r1 <= P.k1));
+            __syncwarp();
+            if (!tie) {
+                if (lane < n && r0 < P.k1) cc[r0 * T] = (uint16_t)p0;
+                if (lane + 32 < n && r1 < P.k1) cc[r1 * T] = (uint16_t)p1;
+            } else if (lane == src) {
+                sel_state = 2;
+            }
+            __syncwarp();
+        }
+        if (active && sel_state != 3) {
+            uint16_t *col = &s_sel[0][0][0] + tid;
+            // exact insertion sort by (|dx|, id), ids looked up only on ties
+            for (int a2 = 1; sel_state == 2 && a2 < sel_n; ++a2) {
+                const int v = col[a2 * T];
+                const float dv = fabsf(X0[v] - sel_u);
+                int j = a2 - 1;
+                while (j >= 0) {
+                    const int c = col[j * T];
+                    const float dc = fabsf(X0[c] - sel_u);
+                    const bool before = dv < dc || (dv == dc && hit_id(H, v) < hit_id(H, c));
+                    if (!before) break;
+                    col[(j + 1) * T] = (uint16_t)c;
+                    --j;
+                }
+                col[(j + 1) * T] = (uint16_t)v;
+            }
+            nbx = min(sel_n, P.k1);
+            for (int j = 0; j < kK1Max; ++j) s_bx[j][tid] = j < nbx ? col[j * T] : (uint16_t)0xFFFF;
         }
     }
     int total_j;
