@@ -393,7 +393,7 @@ DS_API ds_status ds_sync_status(ds_ctx *ctx, void *stream, ds_stats *stats);
  * deployment variant of the same computation.  Runs the same kernels as
  * ds_reconstruct on the CURRENT device and stream, taking geometry, parameters
  * and weights as host structs, with every scratch buffer inside one static
- * device array of about 28 MB that each GPU loading the library holds until
+ * device array of about 22 MB that each GPU loading the library holds until
  * process exit.  It calls no cudaMalloc/cudaFree.  Limits per call: at most
  * 256 events, 16384 seeds and 327680 hits (DS_ERR_CAPACITY beyond, nothing
  * launched) and 8 candidates per seed on average (DS_FLAG_CAND_CAPACITY).  The first call on a device looks up the array's device address
