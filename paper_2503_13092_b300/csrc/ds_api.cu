@@ -50,6 +50,7 @@ struct ds_ctx {
     int cap_cand = 0;
     int cand_per_seed = 16;
     int *count_trk = nullptr;
+    int *clone_next = nullptr;
     int *count_vtx = nullptr;
     int *large_vtx = nullptr;
     ds_vertex_rec *pool = nullptr;
@@ -338,7 +339,7 @@ void ds_destroy(ds_ctx *ctx)
     cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_cnt, ctx->d_tc, ctx->d_lines_tc, ctx->sperm, ctx->sx0, ctx->item_off, ctx->bins, ctx->cand_feat,
                     ctx->cand_meta, ctx->cand_logit, ctx->seed_cand, ctx->trk_ws, ctx->key_ws, ctx->hit_ws,
-                    ctx->rank_ws, ctx->count_trk, ctx->count_vtx, ctx->large_vtx, ctx->pool, ctx->pool_pos,
+                    ctx->rank_ws, ctx->clone_next, ctx->count_trk, ctx->count_vtx, ctx->large_vtx, ctx->pool, ctx->pool_pos,
                     ctx->h.seed_off, ctx->h.hit_off, ctx->h.seed_cols, ctx->h.hit_cols, ctx->h.layer,
                     ctx->h.tracks, ctx->h.trk_off, ctx->h.vtx_off, ctx->h.counts, ctx->h.vertices};
     for (void *q : ptrs)
@@ -424,6 +425,7 @@ ds_status ds_reserve(ds_ctx *ctx, int32_t E, int32_t S, int32_t H)
         if ((st = grow(ctx, &ctx->key_ws, (size_t)S)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->hit_ws, (size_t)S)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->rank_ws, (size_t)S)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->clone_next, 2 * (size_t)S)) != DS_OK) return st;
         ctx->cap_seeds = S;
     }
     if (H > ctx->cap_hits) {
@@ -549,6 +551,7 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     ca.key_ws = ctx->key_ws;
     ca.hit_ws = ctx->hit_ws;
     ca.rank_ws = ctx->rank_ws;
+    ca.next_ws = ctx->clone_next;
     ca.count_ws = ctx->count_trk;
     ca.trk_off = out->trk_off;
     ca.n_tracks = out->n_tracks;

@@ -106,6 +106,7 @@ struct CloneArgs {
     const unsigned long long *key_ws;
     const int4 *hit_ws;
     int *rank_ws;         // per seed: rank inside its event, -1 = not output
+    int *next_ws;         // 2 ints per seed: clone chains of events larger than shared memory holds
     int *count_ws;        // per event
     int32_t *trk_off;     // [n_events + 1] (caller's)
     int32_t *n_tracks;    // caller's device scalar

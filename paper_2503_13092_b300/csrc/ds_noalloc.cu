@@ -44,7 +44,8 @@ constexpr size_t kOffTrk = kOffBins + align256(sizeof(uint16_t) * (size_t)kNATab
 constexpr size_t kOffKey = kOffTrk + align256(sizeof(ds_track) * (size_t)kNASeeds);
 constexpr size_t kOffHit = kOffKey + align256(sizeof(unsigned long long) * (size_t)kNASeeds);
 constexpr size_t kOffRank = kOffHit + align256(sizeof(int4) * (size_t)kNASeeds);
-constexpr size_t kOffSeedCand = kOffRank + align256(sizeof(int) * (size_t)kNASeeds);
+constexpr size_t kOffCloneNext = kOffRank + align256(sizeof(int) * (size_t)kNASeeds);
+constexpr size_t kOffSeedCand = kOffCloneNext + align256(2 * sizeof(int) * (size_t)kNASeeds);
 constexpr size_t kOffCount = kOffSeedCand + align256(sizeof(int4) * (size_t)kNASeeds);
 constexpr size_t kOffItemOff = kOffCount + align256(sizeof(int) * (size_t)kNAEvents);
 constexpr size_t kOffCandFeat = kOffItemOff + align256(sizeof(int) * (size_t)(kNAEvents + 1));
@@ -192,6 +193,7 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         ca.key_ws = pa.key_ws;
         ca.hit_ws = pa.hit_ws;
         ca.rank_ws = sa.rank_ws;
+        ca.next_ws = reinterpret_cast<int *>(base + kOffCloneNext);
         ca.count_ws = reinterpret_cast<int *>(base + kOffCount);
         ca.trk_off = out->trk_off;
         ca.n_tracks = out->n_tracks;

@@ -6,10 +6,12 @@
 // ties by seed order).  Every decision is taken against the full set before
 // killing, so the result does not depend on the order pairs are visited.
 //
-// One CTA per event: winners' hits and keys are staged in shared memory (up
-// to kCloneSmem seeds; larger events read them from the workspace), each thread
-// owns a seed and compares it with every other winner, then alive seeds get
-// their rank in seed order by a chunked block scan.  The last CTA to finish
+// One CTA per event: winners are chained by their UTbX and UTaU hits (hash
+// heads in shared memory; hits, keys and chain links staged in shared memory
+// for events up to kCloneSmem seeds, read from and kept in the workspace for
+// larger ones), each thread owns a seed and compares it with the winners on
+// its two chains, then alive seeds get their rank in seed order by a chunked
+// block scan.  The last CTA to finish
 // turns the per-event counts into trk_off with one scan; a second kernel
 // scatters the surviving records to the packed output in (event, seed) order.
 #include "ds_args.cuh"
@@ -46,7 +48,8 @@ __global__ void __launch_bounds__(kCloneThreads) k_clone(const __grid_constant__
     const bool in_smem = ns <= kCloneSmem;
     const unsigned long long *K = a.key_ws + s0;
     const int4 *Hh = a.hit_ws + s0;
-    if (in_smem && a.clone_kill) {
+    int *g_next_bx = a.next_ws + 2 * (size_t)s0, *g_next_au = g_next_bx + ns;   // chains of larger events
+    if (a.clone_kill) {
         // two winners sharing more than two of their hits share the UTbX hit or
         // the UTaU hit: chain the winners by those two hits
         for (int i = threadIdx.x; i < (1 << kCloneHashBits); i += blockDim.x) s_head_bx[i] = s_head_au[i] = -1;
@@ -54,11 +57,20 @@ __global__ void __launch_bounds__(kCloneThreads) k_clone(const __grid_constant__
         for (int i = threadIdx.x; i < ns; i += blockDim.x) {
             const unsigned long long k = K[i];
             const int4 h = Hh[i];
-            s_key[i] = k;
-            s_hit[i] = h;
+            if (in_smem) {
+                s_key[i] = k;
+                s_hit[i] = h;
+            }
             if (k != kNoKey) {
-                s_next_bx[i] = atomicExch(&s_head_bx[clone_hash(h.w)], i);
-                s_next_au[i] = h.y >= 0 ? atomicExch(&s_head_au[clone_hash(h.y)], i) : -1;
+                const int nb = atomicExch(&s_head_bx[clone_hash(h.w)], i);
+                const int na = h.y >= 0 ? atomicExch(&s_head_au[clone_hash(h.y)], i) : -1;
+                if (in_smem) {
+                    s_next_bx[i] = nb;
+                    s_next_au[i] = na;
+                } else {
+                    g_next_bx[i] = nb;
+                    g_next_au[i] = na;
+                }
             }
         }
         __syncthreads();
@@ -83,11 +95,17 @@ __global__ void __launch_bounds__(kCloneThreads) k_clone(const __grid_constant__
                                 if (o != b && s_hit[o].y == hb.y && kills(s_key[o], o, kb, b, s_hit[o], hb))
                                     alive = 0;
                     } else {
+                        // the same chains, links in the workspace (written by this block)
                         const int4 hb = Hh[b];
-                        for (int o = 0; o < ns && alive; ++o) {
-                            const unsigned long long ko = K[o];
-                            if (o != b && ko != kNoKey && kills(ko, o, kb, b, Hh[o], hb)) alive = 0;
+                        for (int o = s_head_bx[clone_hash(hb.w)]; o >= 0 && alive; o = g_next_bx[o]) {
+                            const int4 ho = Hh[o];
+                            if (o != b && ho.w == hb.w && kills(K[o], o, kb, b, ho, hb)) alive = 0;
                         }
+                        if (hb.y >= 0)
+                            for (int o = s_head_au[clone_hash(hb.y)]; o >= 0 && alive; o = g_next_au[o]) {
+                                const int4 ho = Hh[o];
+                                if (o != b && ho.y == hb.y && kills(K[o], o, kb, b, ho, hb)) alive = 0;
+                            }
                     }
                 }
             }

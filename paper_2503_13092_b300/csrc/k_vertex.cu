@@ -24,6 +24,7 @@
 namespace ds {
 
 constexpr int kVtxThreads = 256;
+constexpr int kVtxLargeThreads = 1024;  // the large-capacity launch: one CTA per SM, all of its warps
 constexpr int kVtxSmallCap = 512;
 constexpr int kVtxCtasPerSm = 4;      // resident CTAs of the small-capacity launch per SM
 constexpr int kVtxSeg = 8192;          // pairs per two-phase segment
@@ -230,7 +231,8 @@ __device__ __forceinline__ int lower_bound_u16(const uint16_t *list, int n, int 
 }
 
 template <int CAP, bool LARGE>
-__global__ void __launch_bounds__(kVtxThreads, kVtxCtasPerSm) k_vertex(const __grid_constant__ VertexArgs a)
+__global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE ? 1 : kVtxCtasPerSm)
+    k_vertex(const __grid_constant__ VertexArgs a)
 {
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ int s_scan[32];
@@ -538,7 +540,7 @@ cudaError_t launch_vertex(const VertexArgs &a0, const ScatterVtxArgs &sa, int sm
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     prof->begin("k_vertex_large", st);
-    k_vertex<kMaxVertexTracks, true><<<g_large, kVtxThreads, sm_large, st>>>(a);
+    k_vertex<kMaxVertexTracks, true><<<g_large, kVtxLargeThreads, sm_large, st>>>(a);
     prof->end(st);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
