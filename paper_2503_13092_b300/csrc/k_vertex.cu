@@ -218,6 +218,12 @@ __device__ __noinline__ PairOut solve_pair(const DevGeom &g, const DevParams &P,
     return o;
 }
 
+__device__ __forceinline__ Trk trk_of(const float4 *tr, const float *q, int i)
+{
+    const float4 v = tr[i];
+    return Trk{v.x, v.y, v.z, v.w, q[i]};
+}
+
 // First index k in [0, n) with list[k] >= v (list ascending).
 __device__ __forceinline__ int lower_bound_u16(const uint16_t *list, int n, int v)
 {
@@ -245,8 +251,9 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
     __shared__ float4 s_res[kVtxStore];           // candidate results: x, y, z, doca
     __shared__ unsigned s_resf[kVtxStore];        // and flags
     __shared__ bool s_last;
-    Trk *s_trk = reinterpret_cast<Trk *>(s_dyn);
-    uint16_t *s_pos = reinterpret_cast<uint16_t *>(s_trk + CAP);
+    float4 *s_tr = reinterpret_cast<float4 *>(s_dyn);          // x, y, tx, ty
+    float *s_q = reinterpret_cast<float *>(s_tr + CAP);         // q/p
+    uint16_t *s_pos = reinterpret_cast<uint16_t *>(s_q + CAP);
     uint16_t *s_neg = s_pos + CAP;
     uint16_t *s_start = s_neg + CAP;
     int *s_row = reinterpret_cast<int *>(s_start + CAP + (CAP & 1));  // CAP + 1 entries
@@ -283,14 +290,15 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
     if (mine && nt >= 2) {
         for (int i = threadIdx.x; i < nt; i += blockDim.x) {
             const ds_track &r = a.tracks[t0 + i];
-            s_trk[i] = Trk{r.x, r.y, r.tx, r.ty, r.qop};
+            s_tr[i] = make_float4(r.x, r.y, r.tx, r.ty);
+            s_q[i] = r.qop;
         }
         __syncthreads();
         // opposite-charge partner lists, in track order
         int npos = 0, nneg = 0;
         for (int c0 = 0; c0 < nt; c0 += blockDim.x) {
             const int i = c0 + threadIdx.x;
-            const float q = i < nt ? s_trk[i].q : 0.f;
+            const float q = i < nt ? s_q[i] : 0.f;
             int tp, tn;
             const int rp = block_exclusive_scan(q > 0.f, s_scan, &tp);
             const int rn = block_exclusive_scan(q < 0.f, s_scan, &tn);
@@ -306,7 +314,7 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
             const int i = c0 + threadIdx.x;
             int cnt = 0;
             if (i < nt) {
-                const float q = s_trk[i].q;
+                const float q = s_q[i];
                 const uint16_t *opp = q > 0.f ? s_neg : s_pos;
                 const int nopp = q > 0.f ? nneg : (q < 0.f ? npos : 0);
                 const int st = lower_bound_u16(opp, nopp, i + 1);
@@ -331,7 +339,7 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
                 else hi = mid;
             }
             i = lo;
-            const uint16_t *opp = s_trk[i].q > 0.f ? s_neg : s_pos;
+            const uint16_t *opp = s_q[i] > 0.f ? s_neg : s_pos;
             j = opp[s_start[i] + (p - s_row[i])];
         };
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -359,21 +367,23 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
                     else hi = mid;
                 }
                 const int seg1 = seg0 + nseg;
+                // (|num| > lim sqrt(den)) squared; the 1 um margin dwarfs the rounding
+                const float lim2 = (P.doca_max + 1e-3f) * (P.doca_max + 1e-3f);
                 for (int i = r0 + warp; i < nt && s_row[i] < seg1; i += nwarps) {
-                    const Trk A = s_trk[i];
-                    const uint16_t *opp = A.q > 0.f ? s_neg : s_pos;
+                    const float4 A = s_tr[i];
+                    const uint16_t *opp = s_q[i] > 0.f ? s_neg : s_pos;
                     const int shift = (int)s_start[i] - s_row[i];     // opp[p + shift]: partner of pair p
                     const int pa = max(s_row[i], seg0), pb = min(s_row[i + 1], seg1);
                     for (int p0 = pa; p0 < pb; p0 += 32) {
                         const int p = p0 + lane;
                         bool cand = false;
                         if (p < pb) {
-                            const Trk B = s_trk[opp[p + shift]];
-                            const float dtx = A.tx - B.tx, dty = A.ty - B.ty;
-                            const float cz = fmaf(A.tx, B.ty, -A.ty * B.tx);
+                            const float4 B = s_tr[opp[p + shift]];   // x, y, tx, ty
+                            const float dtx = A.z - B.z, dty = A.w - B.w;
+                            const float cz = fmaf(A.z, B.w, -A.w * B.z);
                             const float den = fmaf(dtx, dtx, fmaf(dty, dty, cz * cz));
-                            const float num = fabsf(fmaf(A.x - B.x, dty, -(A.y - B.y) * dtx));
-                            cand = !(den > 1e-12f && num > (P.doca_max + 1e-3f) * sqrtf(den));
+                            const float num = fmaf(A.x - B.x, dty, -(A.y - B.y) * dtx);
+                            cand = !(den > 1e-12f && num * num > lim2 * den);
                         }
                         const unsigned m = __ballot_sync(0xffffffffu, cand);
                         if (lane == 0 && m) {
@@ -413,7 +423,7 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
                     const int bit = __fns(s_cmask[lo], 0, k - s_cbase[lo] + 1);
                     int i, j, f64;
                     pair_of(seg0 + (lo << 5) + bit, i, j);
-                    const PairOut o = solve_pair(g, P, s_trk[i], s_trk[j], f64);
+                    const PairOut o = solve_pair(g, P, trk_of(s_tr, s_q, i), trk_of(s_tr, s_q, j), f64);
                     n64 += f64;
                     if (store) {
                         s_res[k] = make_float4(o.x, o.y, o.z, o.doca);
@@ -457,7 +467,7 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
                     o.flags = s_resf[kc];
                 } else {               // too many candidates to keep: the same solve again
                     int f64;
-                    o = solve_pair(g, P, s_trk[i], s_trk[j], f64);
+                    o = solve_pair(g, P, trk_of(s_tr, s_q, i), trk_of(s_tr, s_q, j), f64);
                 }
                 const int slot = s_pool_base + k;
                 if (slot < a.pool_cap) {
@@ -522,7 +532,7 @@ cudaError_t init_vertex_attributes()
 
 static size_t vtx_smem(int cap)
 {
-    return sizeof(Trk) * cap + sizeof(uint16_t) * (3 * cap + (cap & 1)) + sizeof(int) * (cap + 1);
+    return (sizeof(float4) + sizeof(float)) * cap + sizeof(uint16_t) * (3 * cap + (cap & 1)) + sizeof(int) * (cap + 1);
 }
 
 cudaError_t launch_vertex(const VertexArgs &a0, const ScatterVtxArgs &sa, int sm_count, cudaStream_t st,
