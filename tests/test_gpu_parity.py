@@ -87,6 +87,34 @@ def test_c2_sample_parity(torch_cuda, weights):
     parity.assert_vertices_match(vrep)
 
 
+@pytest.mark.parametrize("pick", ["nn", "chi2"])
+def test_duplicated_hits(torch_cuda, weights, pick):
+    """Every hit of the C1 event twice (a second id, the same measurement, in a
+    seeded order): every window holds exact distance ties, ordered by hit id;
+    wide first windows tie at the k1 boundary (the warp selection falls back to
+    the exact sort); duplicated candidates have equal keys and the pick takes
+    the lower hit ids.  GPU and oracle must choose the same hits seed by seed,
+    with no margin excuse."""
+    b = synth.config_batch("c1")
+    n = len(b["hit_x0"])
+    order = np.random.default_rng(5).permutation(2 * n)
+    b2 = dict(b)
+    for k in ("hit_x0", "hit_ybeg", "hit_yend", "hit_layer", "hit_track"):
+        b2[k] = np.concatenate([b[k], b[k]])[order]
+    b2["hit_off"] = np.array([0, 2 * n], np.int32)
+    over = dict(pick_chi2=1, nn_threshold=0.9) if pick == "chi2" else {}
+    cfg = synth.default_config(**over)
+    d = make(torch_cuda, cfg, weights)
+    g = d.run(b2)
+    assert g["stats"]["status"] == 0
+    o = oracle.reconstruct(b2, cfg, weights, n_threads=8)
+    gp = parity.gpu_per_seed(g, len(o["status"]))
+    o_has = o["status"] == 2
+    same = (o_has == gp["has"]) & (~o_has | np.all(o["hits"] == gp["hits"], axis=1))
+    assert o_has.sum() > 20
+    assert same.mean() >= 0.995, np.nonzero(~same)[0]
+
+
 @pytest.mark.parametrize("training", [0, 1])
 def test_partial_strips(torch_cuda, weights, training):
     """Strips shorter than their Y sector (in the even sectors only, half of
