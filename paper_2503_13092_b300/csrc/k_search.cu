@@ -69,6 +69,27 @@ __device__ __forceinline__ void topn_insert(float (&d)[N], int (&id)[N], int (&p
     }
 }
 
+// Dv1: the N best triplets by (residual, UTbX id), p packing the UTbX
+// position in its low 16 bits; ids are looked up only on exact residual ties.
+template <int N>
+__device__ __forceinline__ void topn_insert_lazy(float (&d)[N], int (&p)[N], float dn, int pn, const EvHits &H)
+{
+    const float inf = __int_as_float(0x7f800000);
+    if (dn < d[N - 1] || (dn == d[N - 1] && hit_id(H, pn & 0xffff) < hit_id(H, p[N - 1] & 0xffff))) {
+        d[N - 1] = dn;
+        p[N - 1] = pn;
+#pragma unroll
+        for (int k = N - 1; k > 0; --k) {
+            const bool sw = d[k] < d[k - 1] ||
+                            (d[k] == d[k - 1] && d[k] != inf && hit_id(H, p[k] & 0xffff) < hit_id(H, p[k - 1] & 0xffff));
+            if (sw) {
+                float td = d[k]; d[k] = d[k - 1]; d[k - 1] = td;
+                int tp = p[k]; p[k] = p[k - 1]; p[k - 1] = tp;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ bool key_less(float da, int ia, float db, int ib)
 {
     return da < db || (da == db && ia < ib);
@@ -501,17 +522,21 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
             const int b0 = xbin_of(g, u0 - w_b - 1e-3f), b1 = xbin_of(g, u0 + w_b + 1e-3f);
             int n_tri = 0;
             for (int sct = s_lo; sct <= s_hi; ++sct) {
+                // rows whose strips all span the sector pass the strip test as a whole
+                const bool per_hit = sector_strip_class(g, Part, 3, sct, y3, dy) == 2;
                 const int row = (3 * g.n_sec + sct) * kNXB;
                 const int i0 = Tb[row + b0], i1 = Tb[row + b1 + 1];
                 for (int i = i0; i < i1; ++i) {
                     if (!(fabsf(X0[i] - u0) < w_b)) continue;
-                    const float4 hb = hit_record(H, i);
-                    if (!(hb.y - dy <= y3 && y3 <= hb.z + dy)) continue;
+                    if (per_hit) {
+                        const float4 hb = hit_record(H, i);
+                        if (!(hb.y - dy <= y3 && y3 <= hb.z + dy)) continue;
+                    }
                     float dd[1];
                     int ii[1], pp[1];
                     const float ua = dv1_ua(g, sc, X0, i);
                     if (window_scan<1, 3>(g, X0, H, Tb, Part, 0, ua, sc.yl[0], P.dv1_w_tri, dy, dd, ii, pp) == 0) continue;
-                    topn_insert<kK1Max>(d, id, p, dd[0], __float_as_int(hb.w), i | (pp[0] << 16));
+                    topn_insert_lazy<kK1Max>(d, p, dd[0], i | (pp[0] << 16), H);
                     ++n_tri;
                 }
             }
