@@ -141,7 +141,6 @@ struct VertexArgs {
     int32_t *vtx_off;
     int32_t *n_vertices;
     int capacity;
-    int n_tickets;          // CTAs of both vertex launches together
     DevCounters *cnt;
 };
 

@@ -88,7 +88,8 @@ struct DevNN {
 struct DevCounters {                 // device-side flag word and statistics
     unsigned int flags;
     unsigned int done_trk;           // last-block-done tickets
-    unsigned int done_vtx;
+    unsigned int done_vtx;           // small-capacity vertex launch
+    unsigned int done_vtx_large;     // large-capacity vertex launch
     int n_tracks;
     int n_vertices;
     int pool_used;

@@ -265,6 +265,8 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
     // the small-capacity launch pulls every event from its queue and lists the
     // larger ones; the large-capacity launch pulls from that list only
     const int n_mine = LARGE ? min(*(volatile const int *)&a.cnt->n_large, a.n_events) : a.n_events;
+    // no large event: the small-capacity launch has laid out the offsets already
+    if (LARGE && n_mine == 0) return;
     for (;;) {
     if (threadIdx.x == 0) {
         const int k = atomicAdd(&a.cnt->vtx_queue[LARGE ? 1 : 0], 1);
@@ -493,10 +495,16 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
     if (threadIdx.x == 0 && mine) a.count_ws[e] = ev_count;
     }   // event loop
 
+    // the last CTA of the launch that finishes the batch turns the per-event
+    // counts into offsets: the small-capacity launch when it listed no large
+    // event, otherwise the large-capacity one
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned int t = atomicAdd(&a.cnt->done_vtx, 1u);
-        s_last = t == (unsigned)a.n_tickets - 1;
+        unsigned int *done = LARGE ? &a.cnt->done_vtx_large : &a.cnt->done_vtx;
+        const unsigned int t = atomicAdd(done, 1u);
+        s_last = t == gridDim.x - 1;
+        if (s_last) *done = 0;
+        if (!LARGE && s_last) s_last = *(volatile const int *)&a.cnt->n_large == 0;
     }
     __syncthreads();
     if (!s_last) return;
@@ -507,7 +515,6 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
         *a.n_vertices = run;
         a.cnt->n_vertices = run;
         if (run > a.capacity) raise_flag(a.cnt, DS_FLAG_VERTEX_CAPACITY);
-        a.cnt->done_vtx = 0;
     }
 }
 
@@ -543,7 +550,6 @@ cudaError_t launch_vertex(const VertexArgs &a0, const ScatterVtxArgs &sa, int sm
     const size_t sm_small = vtx_smem(kVtxSmallCap), sm_large = vtx_smem(kMaxVertexTracks);
     const int g_small = a.n_events < kVtxCtasPerSm * sm_count ? a.n_events : kVtxCtasPerSm * sm_count;
     const int g_large = a.n_events < sm_count ? a.n_events : sm_count;
-    a.n_tickets = g_small + g_large;
     prof->begin("k_vertex_small", st);
     k_vertex<kVtxSmallCap, false><<<g_small, kVtxThreads, sm_small, st>>>(a);
     prof->end(st);
