@@ -328,8 +328,8 @@ DS_API ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tracks, ds_vertices *ou
  * rounded to BF16, weights to BF16, products accumulated in FP32 on the
  * tensor cores (tcgen05), biases, ReLU and the output layer in FP32;
  * DS_MLP_FP8 - as BF16 with E4M3 (saturating at +-448) in place of BF16 and
- * each weight layer scaled by 448 / max|W| before rounding (the scale undone
- * in FP32).  The paper's network runs in FP32; the reduced forms are this
+ * each output neuron's weights scaled by the power of two that brings its
+ * largest weight into (224, 448] before rounding (the scale undone in FP32).  The paper's network runs in FP32; the reduced forms are this
  * library's.  DS_ERR_NOT_READY without weights, DS_ERR_ARG for n < 0, null
  * or misaligned pointers or an unknown precision.  Asynchronous on `stream`;
  * a tensor-core wait that runs out raises DS_FLAG_TIMEOUT (ds_sync_status). */

@@ -65,14 +65,15 @@ struct SearchArgs {
 // Ghost-killer weights for the tensor-core kernels, in the K-major no-swizzle
 // core-matrix layout of tcgen05 operands (8 rows x 16 bytes per core matrix,
 // core matrices 128 bytes apart along K).  W1 is 32 x 16 (E4M3: padded to K =
-// 32 with zeros), W2 32 x 32.  FP8 weights are stored times 448 / max|W| of
-// their layer; inv_s1, inv_s2 undo that in the epilogue.
+// 32 with zeros), W2 32 x 32.  FP8 weights are stored times a power of two
+// per output neuron (row) bringing its largest weight into (224, 448];
+// inv_s1, inv_s2 undo that per accumulator column in the epilogue.
 struct MlpTcWeights {
     uint8_t b1_bf16[1024];
     uint8_t b2_bf16[2048];
     uint8_t b1_fp8[1024];
     uint8_t b2_fp8[1024];
-    float inv_s1, inv_s2;
+    float inv_s1[32], inv_s2[32];
 };
 
 struct MlpArgs {

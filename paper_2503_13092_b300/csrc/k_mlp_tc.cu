@@ -9,9 +9,11 @@
 // accumulators in tensor memory (TMEM columns 0-31 and 32-63).  Each warp
 // reads its 32 accumulator rows back with tcgen05.ld; bias, ReLU and the
 // down-conversion for the next layer run there, and the 32 -> 1 output layer
-// is 32 FMAs per row on the CUDA cores.  FP8 uses a per-layer weight scale
-// (448 / max|W|) undone in the epilogue; inputs and hidden activations are
-// converted with saturation at +-448.
+// is 32 FMAs per row on the CUDA cores.  FP8 scales each output neuron's
+// weights by a power of two bringing its largest weight into (224, 448] (each
+// row uses the upper E4M3 range), undone exactly per accumulator column in the
+// epilogue; inputs and hidden activations are converted with saturation at
+// +-448.
 //
 // Persistent CTAs of 4 warps (one per TMEM sub-partition); every mbarrier wait
 // is bounded: on time-out the kernel raises DS_FLAG_TIMEOUT, releases its TMEM
@@ -48,6 +50,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __grid_constant__ MlpArgs 
     __shared__ __align__(128) uint8_t sB2[FP8 ? 1024 : 2048];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tmem;
+    __shared__ float s_is1[32], s_is2[32];     // FP8: per-neuron inverse weight scales
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const MlpTcWeights &W = *a.tc;
@@ -56,6 +59,10 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __grid_constant__ MlpArgs 
         const uint4 *s2 = reinterpret_cast<const uint4 *>(FP8 ? W.b2_fp8 : W.b2_bf16);
         for (int i = tid; i < (int)sizeof(sB1) / 16; i += 128) reinterpret_cast<uint4 *>(sB1)[i] = __ldg(s1 + i);
         for (int i = tid; i < (int)sizeof(sB2) / 16; i += 128) reinterpret_cast<uint4 *>(sB2)[i] = __ldg(s2 + i);
+        if (tid < 32) {
+            s_is1[tid] = FP8 ? __ldg(W.inv_s1 + tid) : 1.f;
+            s_is2[tid] = FP8 ? __ldg(W.inv_s2 + tid) : 1.f;
+        }
     }
     if (tid == 0) mbar_init(&s_bar, 1);
     if (warp == 0) {
@@ -70,7 +77,6 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __grid_constant__ MlpArgs 
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const uint64_t dA1 = smem_desc(sA1, 128, kSboA1), dB1 = smem_desc(sB1, 128, 256);
     const uint64_t dA2 = smem_desc(sA2, 128, kSboA2), dB2 = smem_desc(sB2, 128, FP8 ? 256 : 512);
-    const float is1 = FP8 ? W.inv_s1 : 1.f, is2 = FP8 ? W.inv_s2 : 1.f;
     const int n = a.n_host >= 0 ? a.n_host : min(*(volatile const int *)&a.cnt->cand_used, a.cand_cap);
     const int ntiles = (n + 127) >> 7;
     const int limit = kWaitLimit;
@@ -135,7 +141,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __grid_constant__ MlpArgs 
         float v[32];
         tmem_ld32(tmem + lane_base, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = fmaxf(fmaf(v[j], is1, a.nn.b1[j]), 0.f);
+        for (int j = 0; j < 32; ++j) v[j] = fmaxf(fmaf(v[j], FP8 ? s_is1[j] : 1.f, a.nn.b1[j]), 0.f);
         if (FP8) {
 #pragma unroll
             for (int kc = 0; kc < 2; ++kc)
@@ -173,7 +179,7 @@ __global__ void __launch_bounds__(128) k_mlp_tc(const __grid_constant__ MlpArgs 
         tmem_ld32(tmem + lane_base + 32, v);
         float out = a.nn.b3;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) out = fmaf(a.nn.w3[j], fmaxf(fmaf(v[j], is2, a.nn.b2[j]), 0.f), out);
+        for (int j = 0; j < 32; ++j) out = fmaf(a.nn.w3[j], fmaxf(fmaf(v[j], FP8 ? s_is2[j] : 1.f, a.nn.b2[j]), 0.f), out);
         if (c < n) a.logit[c] = out;
         tc_fence_before();
         __syncthreads();     // TMEM and the A tiles are rewritten by the next tile
@@ -203,15 +209,23 @@ void prepare_tc_weights(const DevNN &nn, int n_h2, MlpTcWeights *out)
     float w2[32][32];
     for (int o = 0; o < 32; ++o)
         for (int i = 0; i < 32; ++i) w2[o][i] = n_h2 > 0 ? nn.w2[o][i] : (o == i ? 1.f : 0.f);
-    float m1 = 0.f, m2 = 0.f;
+    // FP8: each neuron's weights scaled by the largest power of two 2^k with
+    // 2^k max|W| <= 448 (its largest weight lands in (224, 448]); undoing a
+    // power of two is exact
+    auto pow2_scale = [](float m) {
+        if (!(m > 0.f)) return 1.f;
+        float s = std::ldexp(1.f, (int)std::floor(std::log2(448.f / m)));
+        while (m * s > 448.f) s *= 0.5f;
+        while (m * s * 2.f <= 448.f) s *= 2.f;
+        return s;
+    };
     for (int o = 0; o < 32; ++o) {
+        float m1 = 0.f, m2 = 0.f;
         for (int i = 0; i < 16; ++i) m1 = std::fmax(m1, std::fabs(nn.w1[o][i]));
         for (int i = 0; i < 32; ++i) m2 = std::fmax(m2, std::fabs(w2[o][i]));
-    }
-    const float s1 = m1 > 0.f ? 448.f / m1 : 1.f, s2 = m2 > 0.f ? 448.f / m2 : 1.f;
-    out->inv_s1 = 1.f / s1;
-    out->inv_s2 = 1.f / s2;
-    for (int o = 0; o < 32; ++o) {
+        const float s1 = pow2_scale(m1), s2 = pow2_scale(m2);
+        out->inv_s1[o] = 1.f / s1;
+        out->inv_s2[o] = 1.f / s2;
         for (int i = 0; i < 16; ++i) {
             const __nv_bfloat16 h = __float2bfloat16_rn(nn.w1[o][i]);
             std::memcpy(out->b1_bf16 + kmajor_offset(o, i, 2, 256), &h, 2);

@@ -67,10 +67,17 @@ def emulate(torch, w, phi, prec):
         W1q, W2q, is1, is2 = q(W1), q(W2), np.float32(1), np.float32(1)
     else:
         q = lambda a: _e4m3(torch, a)
-        s1 = np.float32(448.0) / np.float32(np.abs(W1).max())
-        s2 = np.float32(448.0) / np.float32(np.abs(W2).max())
-        W1q, W2q = q(W1 * s1), q(W2 * s2)
-        is1, is2 = np.float32(1) / s1, np.float32(1) / s2
+        # each output neuron's weights scaled by the power of two that brings
+        # its largest weight into (224, 448]
+        def row_scale(W):
+            m = np.abs(W).max(axis=1).astype(np.float64)
+            k = np.floor(np.log2(448.0 / np.where(m > 0, m, 1.0)))
+            k = np.where(m * 2.0 ** k > 448.0, k - 1, k)
+            k = np.where(m * 2.0 ** (k + 1) <= 448.0, k + 1, k)
+            return np.where(m > 0, 2.0 ** k, 1.0).astype(np.float32)
+        s1, s2 = row_scale(W1), row_scale(W2)
+        W1q, W2q = q(W1 * s1[:, None]), q(W2 * s2[:, None])
+        is1, is2 = (np.float32(1) / s1).astype(np.float32), (np.float32(1) / s2).astype(np.float32)
     a1 = q(x).astype(np.float64) @ W1q.T.astype(np.float64)
     h1 = np.maximum((a1 * np.float64(is1) + b1).astype(np.float32), 0)
     h1q = q(h1)
@@ -88,7 +95,8 @@ def gpu_logits(torch, dsx, phi, prec):
 
 
 def dyadic_net(rng, with_big):
-    """Weights in {0, +-1/2, +-1} (one 1.75 when with_big, so that 448 / max|W| = 256)."""
+    """Weights in {0, +-1/2, +-1} (one 1.75 when with_big): a neuron's power-of-two
+    scale is 256 or 512, and every scaled weight is an E4M3 number."""
     vals = np.array([-1.0, -0.5, 0.0, 0.5, 1.0], np.float32)
     w1 = rng.choice(vals, (32, 16)); w2 = rng.choice(vals, (32, 32)); w3 = rng.choice(vals, 32)
     if with_big:
