@@ -27,8 +27,13 @@ constexpr int kVtxThreads = 256;
 constexpr int kVtxLargeThreads = 1024;  // the large-capacity launch: one CTA per SM, all of its warps
 constexpr int kVtxSmallCap = 512;
 constexpr int kVtxCtasPerSm = 4;      // resident CTAs of the small-capacity launch per SM
-constexpr int kVtxSeg = 8192;          // pairs per two-phase segment
-constexpr int kVtxStore = 1024;        // candidate results kept in shared memory per segment
+// pairs per two-phase segment and candidate results kept in shared memory per
+// segment: larger for the large-capacity launch (one CTA per SM), whose
+// events have up to millions of pairs
+template <bool LARGE> struct VtxSeg {
+    static constexpr int seg = LARGE ? 65536 : 8192;
+    static constexpr int store = LARGE ? 2048 : 1024;
+};
 
 
 struct Trk {
@@ -240,18 +245,20 @@ template <int CAP, bool LARGE>
 __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE ? 1 : kVtxCtasPerSm)
     k_vertex(const __grid_constant__ VertexArgs a)
 {
+    constexpr int kVtxSeg = VtxSeg<LARGE>::seg, kVtxStore = VtxSeg<LARGE>::store;
+    // dynamic: candidate results, segment masks, then the event's tracks
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ int s_scan[32];
     __shared__ int s_pool_base;
-    __shared__ unsigned s_mask[kVtxSeg / 32];
-    __shared__ unsigned s_keep[kVtxSeg / 32];
-    __shared__ int s_wbase[kVtxSeg / 32];
-    __shared__ unsigned s_cmask[kVtxSeg / 32];   // candidates of the segment
-    __shared__ int s_cbase[kVtxSeg / 32];        // their word prefix
-    __shared__ float4 s_res[kVtxStore];           // candidate results: x, y, z, doca
-    __shared__ unsigned s_resf[kVtxStore];        // and flags
     __shared__ bool s_last;
-    float4 *s_tr = reinterpret_cast<float4 *>(s_dyn);          // x, y, tx, ty
+    float4 *s_res = reinterpret_cast<float4 *>(s_dyn);          // candidate results: x, y, z, doca
+    unsigned *s_resf = reinterpret_cast<unsigned *>(s_res + kVtxStore);   // and flags
+    unsigned *s_mask = s_resf + kVtxStore;
+    unsigned *s_keep = s_mask + kVtxSeg / 32;
+    int *s_wbase = reinterpret_cast<int *>(s_keep + kVtxSeg / 32);
+    unsigned *s_cmask = reinterpret_cast<unsigned *>(s_wbase + kVtxSeg / 32);   // candidates of the segment
+    int *s_cbase = reinterpret_cast<int *>(s_cmask + kVtxSeg / 32);            // their word prefix
+    float4 *s_tr = reinterpret_cast<float4 *>(s_cbase + kVtxSeg / 32);         // x, y, tx, ty
     float *s_q = reinterpret_cast<float *>(s_tr + CAP);         // q/p
     uint16_t *s_pos = reinterpret_cast<uint16_t *>(s_q + CAP);
     uint16_t *s_neg = s_pos + CAP;
@@ -529,17 +536,18 @@ __global__ void __launch_bounds__(256) k_scatter_vertices(const __grid_constant_
     }
 }
 
-static size_t vtx_smem(int cap);
+template <bool LARGE>
+static size_t vtx_smem(int cap)
+{
+    constexpr int seg = VtxSeg<LARGE>::seg, store = VtxSeg<LARGE>::store;
+    return (sizeof(float4) + sizeof(unsigned)) * store + 5 * sizeof(unsigned) * (seg / 32) +
+           (sizeof(float4) + sizeof(float)) * cap + sizeof(uint16_t) * (3 * cap + (cap & 1)) + sizeof(int) * (cap + 1);
+}
 
 cudaError_t init_vertex_attributes()
 {
     return cudaFuncSetAttribute(k_vertex<kMaxVertexTracks, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)vtx_smem(kMaxVertexTracks));
-}
-
-static size_t vtx_smem(int cap)
-{
-    return (sizeof(float4) + sizeof(float)) * cap + sizeof(uint16_t) * (3 * cap + (cap & 1)) + sizeof(int) * (cap + 1);
+                                (int)vtx_smem<true>(kMaxVertexTracks));
 }
 
 cudaError_t launch_vertex(const VertexArgs &a0, const ScatterVtxArgs &sa, int sm_count, cudaStream_t st,
@@ -547,7 +555,7 @@ cudaError_t launch_vertex(const VertexArgs &a0, const ScatterVtxArgs &sa, int sm
 {
     if (a0.n_events <= 0) return cudaSuccess;
     VertexArgs a = a0;
-    const size_t sm_small = vtx_smem(kVtxSmallCap), sm_large = vtx_smem(kMaxVertexTracks);
+    const size_t sm_small = vtx_smem<false>(kVtxSmallCap), sm_large = vtx_smem<true>(kMaxVertexTracks);
     const int g_small = a.n_events < kVtxCtasPerSm * sm_count ? a.n_events : kVtxCtasPerSm * sm_count;
     const int g_large = a.n_events < sm_count ? a.n_events : sm_count;
     prof->begin("k_vertex_small", st);
