@@ -216,6 +216,81 @@ __device__ __forceinline__ int window_scan(const DevGeom &g, const float *X0, co
     return cnt;
 }
 
+// Result of a refined-window search: how many hits qualified, the best
+// distance and the sorted positions of the (up to) two best.
+struct WinBest {
+    int cnt;
+    float d0;
+    int p0, p1;
+};
+
+// window_scan kept out of line for the rare windows window_best hands over.
+template <int N>
+__device__ __noinline__ WinBest window_best_exact(const DevGeom &g, const float *X0, const EvHits &H,
+                                                  const uint16_t *Tb, const uint32_t *Part, int layer, float u,
+                                                  float y, float w, float dy)
+{
+    float d[N];
+    int id[N], p[N];
+    WinBest r;
+    r.cnt = window_scan<N, 3>(g, X0, H, Tb, Part, layer, u, y, w, dy, d, id, p);
+    r.d0 = d[0];
+    r.p0 = p[0];
+    r.p1 = N > 1 ? p[1] : -1;
+    return r;
+}
+
+// The N (1 or 2) best hits of a window by (|dx|, id), as window_scan ranks
+// them, from one pass that keeps the running N smallest distances.  Ids are
+// needed only when two x-passing distances are equal, and strips only in
+// sectors with partial strips; both cases (rare) go to window_scan.  A
+// distance equal to a kept one is the only tie that can change the kept set:
+// a hit dropped from it is farther than every later kept hit.
+template <int N>
+__device__ __forceinline__ WinBest window_best(const DevGeom &g, const float *X0, const EvHits &H,
+                                               const uint16_t *Tb, const uint32_t *Part, int layer, float u, float y,
+                                               float w, float dy)
+{
+    static_assert(N == 1 || N == 2, "one or two kept hits");
+    const int s_lo = sector_of(g, y - dy - 0.01f), s_hi = sector_of(g, y + dy + 0.01f);
+    const float eps = 1e-3f;
+    const int b0 = xbin_of(g, u - w - eps), b1 = xbin_of(g, u + w + eps);
+    const float inf = __int_as_float(0x7f800000);
+    WinBest r{0, inf, -1, -1};
+    float d1 = inf;
+    bool slow = false;
+    for (int s = s_lo; s <= s_hi; ++s) {
+        slow |= sector_strip_class(g, Part, layer, s, y, dy) == 2;
+        const int row = (layer * g.n_sec + s) * kNXB;
+        const int i0 = Tb[row + b0], i1 = Tb[row + b1 + 1];
+        for (int i = i0; i < i1; ++i) {
+            const float dx = fabsf(X0[i] - u);
+            if (dx < w) {
+                ++r.cnt;
+                slow |= dx == r.d0 || (N > 1 && dx == d1);
+                if (N == 1) {
+                    if (dx < r.d0) {
+                        r.d0 = dx;
+                        r.p0 = i;
+                    }
+                } else if (dx < d1) {
+                    if (dx < r.d0) {
+                        d1 = r.d0;
+                        r.p1 = r.p0;
+                        r.d0 = dx;
+                        r.p0 = i;
+                    } else {
+                        d1 = dx;
+                        r.p1 = i;
+                    }
+                }
+            }
+        }
+    }
+    if (slow) return window_best_exact<N>(g, X0, H, Tb, Part, layer, u, y, w, dy);
+    return r;
+}
+
 struct SeedCtx {     // per-seed quantities reused by candidate scoring
     float zm, xm, ym, tx, ty, qop, chi2, w1, u_bx;
     float yl[4];
@@ -326,13 +401,17 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     __shared__ uint16_t s_sel[kK1Max][5][T];
     __shared__ uint8_t s_nc[kK1Max][T];
     __shared__ SeedCtx s_sc[T];
-    __shared__ int s_base[T + 1];
+    // (seed, UTbX rank) of each refined-window pair, then the candidate offsets
+    __shared__ union {
+        uint16_t pair[kK1Max * T];
+        int base[T + 1];
+    } s_pb;
+    int *s_base = s_pb.base;
     __shared__ int s_cand0;
     __shared__ int s_scan[32];
     __shared__ int s_item[4];
     __shared__ int s_hits[3];
     __shared__ __align__(8) uint64_t s_bar;
-    __shared__ int s_jbase[T + 1];
 
     const DevGeom &g = a.g;
     const DevParams &P = a.p;
@@ -532,11 +611,10 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
                         const float4 hb = hit_record(H, i);
                         if (!(hb.y - dy <= y3 && y3 <= hb.z + dy)) continue;
                     }
-                    float dd[1];
-                    int ii[1], pp[1];
                     const float ua = dv1_ua(g, sc, X0, i);
-                    if (window_scan<1, 3>(g, X0, H, Tb, Part, 0, ua, sc.yl[0], P.dv1_w_tri, dy, dd, ii, pp) == 0) continue;
-                    topn_insert_lazy<kK1Max>(d, p, dd[0], i | (pp[0] << 16), H);
+                    const WinBest wa = window_best<1>(g, X0, H, Tb, Part, 0, ua, sc.yl[0], P.dv1_w_tri, dy);
+                    if (wa.cnt == 0) continue;
+                    topn_insert_lazy<kK1Max>(d, p, wa.d0, i | (wa.p0 << 16), H);
                     ++n_tri;
                 }
             }
@@ -609,20 +687,13 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     }
     int total_j;
     const int jbase = block_exclusive_scan(nbx, s_scan, &total_j);
-    s_jbase[tid] = jbase;
-    if (tid == T - 1) s_jbase[T] = jbase + nbx;
+    for (int j = 0; j < nbx; ++j) s_pb.pair[jbase + j] = (uint16_t)((tid << 4) | j);
     __syncthreads();
 
     // refined windows, one (seed, UTbX hit) pair per thread: every lane does
     // the same three window searches whatever the hits per seed
     for (int t = tid; t < total_j; t += T) {
-        int lo = 0, hi = T;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_jbase[mid] <= t) lo = mid;
-            else hi = mid;
-        }
-        const int o = lo, j = t - s_jbase[o];
+        const int o = s_pb.pair[t] >> 4, j = s_pb.pair[t] & 15;
         const SeedCtx sc = s_sc[o];
         const float w2 = P.training ? 10.f : P.w2;
         const float x0b = X0[s_bx[j][o]];
@@ -632,18 +703,15 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
         if (V == 1) {
             sel[0] = s_sel[j][0][o];            // Dv1: the triplet's UTaX hit
         } else {
-            float dd[1]; int ii[1], pp[1];
             const float ul = fmaf(txp, g.z[0] - g.z[3], xh) - g.dxdy[0] * sc.yl[0];
-            const int c = window_scan<1, 3>(g, X0, H, Tb, Part, 0, ul, sc.yl[0], w2, P.dy_tol, dd, ii, pp);
-            sel[0] = c > 0 ? pp[0] : -1;
+            sel[0] = window_best<1>(g, X0, H, Tb, Part, 0, ul, sc.yl[0], w2, P.dy_tol).p0;
         }
 #pragma unroll
         for (int l = 1; l <= 2; ++l) {
-            float dd[2]; int ii[2], pp[2];
             const float ul = fmaf(txp, g.z[l] - g.z[3], xh) - g.dxdy[l] * sc.yl[l];
-            const int c = window_scan<2, 3>(g, X0, H, Tb, Part, l, ul, sc.yl[l], w2, P.dy_tol, dd, ii, pp);
-            sel[2 * l - 1] = c > 0 ? pp[0] : -1;
-            sel[2 * l] = c > 1 ? pp[1] : -1;
+            const WinBest wb = window_best<2>(g, X0, H, Tb, Part, l, ul, sc.yl[l], w2, P.dy_tol);
+            sel[2 * l - 1] = wb.p0;
+            sel[2 * l] = wb.p1;
         }
 #pragma unroll
         for (int k = 0; k < 5; ++k) s_sel[j][k][o] = sel[k] >= 0 ? (uint16_t)sel[k] : kNone;
