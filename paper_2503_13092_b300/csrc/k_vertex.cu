@@ -258,7 +258,8 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
     int *s_wbase = reinterpret_cast<int *>(s_keep + kVtxSeg / 32);
     unsigned *s_cmask = reinterpret_cast<unsigned *>(s_wbase + kVtxSeg / 32);   // candidates of the segment
     int *s_cbase = reinterpret_cast<int *>(s_cmask + kVtxSeg / 32);            // their word prefix
-    float4 *s_tr = reinterpret_cast<float4 *>(s_cbase + kVtxSeg / 32);         // x, y, tx, ty
+    int *s_wrow = s_cbase + kVtxSeg / 32;              // row holding each mask word's first pair
+    float4 *s_tr = reinterpret_cast<float4 *>(s_wrow + kVtxSeg / 32);          // x, y, tx, ty
     float *s_q = reinterpret_cast<float *>(s_tr + CAP);         // q/p
     uint16_t *s_pos = reinterpret_cast<uint16_t *>(s_q + CAP);
     uint16_t *s_neg = s_pos + CAP;
@@ -339,15 +340,12 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
         __syncthreads();
         const int npairs = run;
         if (threadIdx.x == 0 && npairs > 0) atomicAdd(&a.cnt->n_pairs, (unsigned long long)npairs);
-        // pair p of the event -> (i, j), i < j, opposite charges, (i, j) order
-        auto pair_of = [&](int p, int &i, int &j) {
-            int lo = 0, hi = nt;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (s_row[mid] <= p) lo = mid;
-                else hi = mid;
-            }
-            i = lo;
+        // pair p of the current segment (first pair seg0) -> (i, j), i < j,
+        // opposite charges, (i, j) order: from the row of p's mask word, a
+        // short walk over the rows starting inside the word
+        auto pair_of = [&](int p, int seg0, int &i, int &j) {
+            i = s_wrow[(p - seg0) >> 5];
+            while (s_row[i + 1] <= p) ++i;
             const uint16_t *opp = s_q[i] > 0.f ? s_neg : s_pos;
             j = opp[s_start[i] + (p - s_row[i])];
         };
@@ -357,50 +355,40 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
         for (int seg0 = 0; seg0 < npairs; seg0 += kVtxSeg) {
             const int nseg = min(kVtxSeg, npairs - seg0);
             const int nwords = (nseg + 31) >> 5;
+            const int seg1 = seg0 + nseg;
+            // each row records the mask words whose first pair it holds
+            for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+                const int lo = max(s_row[i], seg0), hi = min(s_row[i + 1], seg1);
+                for (int w = (lo - seg0 + 31) >> 5; seg0 + (w << 5) < hi; ++w) s_wrow[w] = i;
+            }
+            __syncthreads();
             // phase 1a: is each pair of the segment a candidate?  With gamma = 0
             // both trajectories are lines and the solve converges to their
             // closest approach, whose distance |w.(Di x Dj)| / |Di x Dj| is exact
             // in closed form: pairs more than 1 um above the cut are not
             // candidates.  With gamma != 0 every pair is a candidate.  One warp
-            // per row i (track i broadcast), lanes over its partners j.
+            // per mask word, one pair per lane.
             if (!straight) {
                 for (int w = threadIdx.x; w < nwords; w += blockDim.x)
                     s_mask[w] = (w == nwords - 1 && (nseg & 31)) ? (1u << (nseg & 31)) - 1u : 0xffffffffu;
             } else {
-                for (int w = threadIdx.x; w < nwords; w += blockDim.x) s_mask[w] = 0u;
-                __syncthreads();
-                int r0 = 0, hi = nt;           // row holding pair seg0
-                while (hi - r0 > 1) {
-                    const int mid = (r0 + hi) >> 1;
-                    if (s_row[mid] <= seg0) r0 = mid;
-                    else hi = mid;
-                }
-                const int seg1 = seg0 + nseg;
                 // (|num| > lim sqrt(den)) squared; the 1 um margin dwarfs the rounding
                 const float lim2 = (P.doca_max + 1e-3f) * (P.doca_max + 1e-3f);
-                for (int i = r0 + warp; i < nt && s_row[i] < seg1; i += nwarps) {
-                    const float4 A = s_tr[i];
-                    const uint16_t *opp = s_q[i] > 0.f ? s_neg : s_pos;
-                    const int shift = (int)s_start[i] - s_row[i];     // opp[p + shift]: partner of pair p
-                    const int pa = max(s_row[i], seg0), pb = min(s_row[i + 1], seg1);
-                    for (int p0 = pa; p0 < pb; p0 += 32) {
-                        const int p = p0 + lane;
-                        bool cand = false;
-                        if (p < pb) {
-                            const float4 B = s_tr[opp[p + shift]];   // x, y, tx, ty
-                            const float dtx = A.z - B.z, dty = A.w - B.w;
-                            const float cz = fmaf(A.z, B.w, -A.w * B.z);
-                            const float den = fmaf(dtx, dtx, fmaf(dty, dty, cz * cz));
-                            const float num = fmaf(A.x - B.x, dty, -(A.y - B.y) * dtx);
-                            cand = !(den > 1e-12f && num * num > lim2 * den);
-                        }
-                        const unsigned m = __ballot_sync(0xffffffffu, cand);
-                        if (lane == 0 && m) {
-                            const int b = p0 - seg0, wd = b >> 5, sh = b & 31;
-                            atomicOr(&s_mask[wd], m << sh);
-                            if (sh && (m >> (32 - sh))) atomicOr(&s_mask[wd + 1], m >> (32 - sh));
-                        }
+                for (int w = warp; w < nwords; w += nwarps) {
+                    const int p = seg0 + (w << 5) + lane;
+                    bool cand = false;
+                    if (p < seg1) {
+                        int i, j;
+                        pair_of(p, seg0, i, j);
+                        const float4 A = s_tr[i], B = s_tr[j];   // x, y, tx, ty
+                        const float dtx = A.z - B.z, dty = A.w - B.w;
+                        const float cz = fmaf(A.z, B.w, -A.w * B.z);
+                        const float den = fmaf(dtx, dtx, fmaf(dty, dty, cz * cz));
+                        const float num = fmaf(A.x - B.x, dty, -(A.y - B.y) * dtx);
+                        cand = !(den > 1e-12f && num * num > lim2 * den);
                     }
+                    const unsigned m = __ballot_sync(0xffffffffu, cand);
+                    if (lane == 0) s_mask[w] = m;
                 }
             }
             __syncthreads();
@@ -431,7 +419,7 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
                     }
                     const int bit = __fns(s_cmask[lo], 0, k - s_cbase[lo] + 1);
                     int i, j, f64;
-                    pair_of(seg0 + (lo << 5) + bit, i, j);
+                    pair_of(seg0 + (lo << 5) + bit, seg0, i, j);
                     const PairOut o = solve_pair(g, P, trk_of(s_tr, s_q, i), trk_of(s_tr, s_q, j), f64);
                     n64 += f64;
                     if (store) {
@@ -467,7 +455,7 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
                 const int bit = __fns(s_mask[lo], 0, k - s_wbase[lo] + 1);
                 const int p = seg0 + (lo << 5) + bit;
                 int i, j;
-                pair_of(p, i, j);
+                pair_of(p, seg0, i, j);
                 PairOut o;
                 if (store) {           // the candidate's result from phase 1b
                     const int kc = s_cbase[lo] + __popc(s_cmask[lo] & ((1u << bit) - 1u));
@@ -540,7 +528,7 @@ template <bool LARGE>
 static size_t vtx_smem(int cap)
 {
     constexpr int seg = VtxSeg<LARGE>::seg, store = VtxSeg<LARGE>::store;
-    return (sizeof(float4) + sizeof(unsigned)) * store + 5 * sizeof(unsigned) * (seg / 32) +
+    return (sizeof(float4) + sizeof(unsigned)) * store + 6 * sizeof(unsigned) * (seg / 32) +
            (sizeof(float4) + sizeof(float)) * cap + sizeof(uint16_t) * (3 * cap + (cap & 1)) + sizeof(int) * (cap + 1);
 }
 
