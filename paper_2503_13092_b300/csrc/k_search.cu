@@ -240,27 +240,39 @@ __device__ __noinline__ WinBest window_best_exact(const DevGeom &g, const float 
     return r;
 }
 
+// The sectors a seed's window in `layer` visits (those of y -+ (dy + 0.01),
+// as window_scan takes them) and whether one of them needs the per-hit strip
+// test, packed as lo | hi << 5 | per_hit << 10.  They depend on the seed
+// only, not on the UTbX hit a refined window starts from.
+__device__ __forceinline__ int window_sectors(const DevGeom &g, const uint32_t *Part, int layer, float y, float dy)
+{
+    const int s_lo = sector_of(g, y - dy - 0.01f), s_hi = sector_of(g, y + dy + 0.01f);
+    int per_hit = 0;
+    for (int s = s_lo; s <= s_hi; ++s) per_hit |= sector_strip_class(g, Part, layer, s, y, dy) == 2;
+    return s_lo | (s_hi << 5) | (per_hit << 10);
+}
+
 // The N (1 or 2) best hits of a window by (|dx|, id), as window_scan ranks
 // them, from one pass that keeps the running N smallest distances.  Ids are
 // needed only when two x-passing distances are equal, and strips only in
 // sectors with partial strips; both cases (rare) go to window_scan.  A
 // distance equal to a kept one is the only tie that can change the kept set:
-// a hit dropped from it is farther than every later kept hit.
+// a hit dropped from it is farther than every later kept hit.  sinfo is
+// window_sectors(g, Part, layer, y, dy).
 template <int N>
 __device__ __forceinline__ WinBest window_best(const DevGeom &g, const float *X0, const EvHits &H,
                                                const uint16_t *Tb, const uint32_t *Part, int layer, float u, float y,
-                                               float w, float dy)
+                                               float w, float dy, int sinfo)
 {
     static_assert(N == 1 || N == 2, "one or two kept hits");
-    const int s_lo = sector_of(g, y - dy - 0.01f), s_hi = sector_of(g, y + dy + 0.01f);
+    const int s_lo = sinfo & 31, s_hi = (sinfo >> 5) & 31;
     const float eps = 1e-3f;
     const int b0 = xbin_of(g, u - w - eps), b1 = xbin_of(g, u + w + eps);
     const float inf = __int_as_float(0x7f800000);
     WinBest r{0, inf, -1, -1};
     float d1 = inf;
-    bool slow = false;
+    bool slow = (sinfo >> 10) & 1;
     for (int s = s_lo; s <= s_hi; ++s) {
-        slow |= sector_strip_class(g, Part, layer, s, y, dy) == 2;
         const int row = (layer * g.n_sec + s) * kNXB;
         const int i0 = Tb[row + b0], i1 = Tb[row + b1 + 1];
         for (int i = i0; i < i1; ++i) {
@@ -401,6 +413,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     __shared__ uint16_t s_sel[kK1Max][5][T];
     __shared__ uint8_t s_nc[kK1Max][T];
     __shared__ SeedCtx s_sc[T];
+    __shared__ uint16_t s_wsec[3][T];   // window_sectors of the refined windows (layers 0-2)
     // (seed, UTbX rank) of each refined-window pair, then the candidate offsets
     __shared__ union {
         uint16_t pair[kK1Max * T];
@@ -530,6 +543,8 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
         sc.w1 = P.training ? 100.f : fmaf(P.w1b, aq, P.w1a);
         sc.u_bx = u_bx;
         s_sc[tid] = sc;
+#pragma unroll
+        for (int l = 0; l < 3; ++l) s_wsec[l][tid] = (uint16_t)window_sectors(g, Part, l, sc.yl[l], P.dy_tol);
 
         float d[kK1Max];
         int id[kK1Max], p[kK1Max];
@@ -612,7 +627,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
                         if (!(hb.y - dy <= y3 && y3 <= hb.z + dy)) continue;
                     }
                     const float ua = dv1_ua(g, sc, X0, i);
-                    const WinBest wa = window_best<1>(g, X0, H, Tb, Part, 0, ua, sc.yl[0], P.dv1_w_tri, dy);
+                    const WinBest wa = window_best<1>(g, X0, H, Tb, Part, 0, ua, sc.yl[0], P.dv1_w_tri, dy, s_wsec[0][tid]);
                     if (wa.cnt == 0) continue;
                     topn_insert_lazy<kK1Max>(d, p, wa.d0, i | (wa.p0 << 16), H);
                     ++n_tri;
@@ -704,12 +719,12 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
             sel[0] = s_sel[j][0][o];            // Dv1: the triplet's UTaX hit
         } else {
             const float ul = fmaf(txp, g.z[0] - g.z[3], xh) - g.dxdy[0] * sc.yl[0];
-            sel[0] = window_best<1>(g, X0, H, Tb, Part, 0, ul, sc.yl[0], w2, P.dy_tol).p0;
+            sel[0] = window_best<1>(g, X0, H, Tb, Part, 0, ul, sc.yl[0], w2, P.dy_tol, s_wsec[0][o]).p0;
         }
 #pragma unroll
         for (int l = 1; l <= 2; ++l) {
             const float ul = fmaf(txp, g.z[l] - g.z[3], xh) - g.dxdy[l] * sc.yl[l];
-            const WinBest wb = window_best<2>(g, X0, H, Tb, Part, l, ul, sc.yl[l], w2, P.dy_tol);
+            const WinBest wb = window_best<2>(g, X0, H, Tb, Part, l, ul, sc.yl[l], w2, P.dy_tol, s_wsec[l][o]);
             sel[2 * l - 1] = wb.p0;
             sel[2 * l] = wb.p1;
         }
