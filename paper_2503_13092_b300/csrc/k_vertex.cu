@@ -229,18 +229,6 @@ __device__ __forceinline__ Trk trk_of(const float4 *tr, const float *q, int i)
     return Trk{v.x, v.y, v.z, v.w, q[i]};
 }
 
-// First index k in [0, n) with list[k] >= v (list ascending).
-__device__ __forceinline__ int lower_bound_u16(const uint16_t *list, int n, int v)
-{
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((int)list[mid] < v) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
 template <int CAP, bool LARGE>
 __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE ? 1 : kVtxCtasPerSm)
     k_vertex(const __grid_constant__ VertexArgs a)
@@ -304,20 +292,22 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
             s_q[i] = r.qop;
         }
         __syncthreads();
-        // opposite-charge partner lists, in track order
+        // opposite-charge partner lists, in track order, from one scan of
+        // packed (positive, negative) counts: a track's place in its own list
+        // and, in the other list, the first partner after it
         int npos = 0, nneg = 0;
         for (int c0 = 0; c0 < nt; c0 += blockDim.x) {
             const int i = c0 + threadIdx.x;
             const float q = i < nt ? s_q[i] : 0.f;
-            int tp, tn;
-            const int rp = block_exclusive_scan(q > 0.f, s_scan, &tp);
-            const int rn = block_exclusive_scan(q < 0.f, s_scan, &tn);
-            if (q > 0.f) s_pos[npos + rp] = (uint16_t)i;
-            if (q < 0.f) s_neg[nneg + rn] = (uint16_t)i;
-            npos += tp;
-            nneg += tn;
+            int tot;
+            const int r = block_exclusive_scan((q > 0.f ? 1 : 0) | (q < 0.f ? 0x10000 : 0), s_scan, &tot);
+            const int pb = npos + (r & 0xffff), nb = nneg + (r >> 16);
+            if (q > 0.f) s_pos[pb] = (uint16_t)i;
+            if (q < 0.f) s_neg[nb] = (uint16_t)i;
+            if (i < nt) s_start[i] = (uint16_t)(q > 0.f ? nb : pb);
+            npos += tot & 0xffff;
+            nneg += tot >> 16;
         }
-        __syncthreads();
         // row i holds partners j > i of opposite charge
         int run = 0;
         for (int c0 = 0; c0 < nt; c0 += blockDim.x) {
@@ -325,11 +315,7 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
             int cnt = 0;
             if (i < nt) {
                 const float q = s_q[i];
-                const uint16_t *opp = q > 0.f ? s_neg : s_pos;
-                const int nopp = q > 0.f ? nneg : (q < 0.f ? npos : 0);
-                const int st = lower_bound_u16(opp, nopp, i + 1);
-                s_start[i] = (uint16_t)st;
-                cnt = nopp - st;
+                cnt = q > 0.f ? nneg - s_start[i] : (q < 0.f ? npos - s_start[i] : 0);
             }
             int tot;
             const int r = block_exclusive_scan(cnt, s_scan, &tot);
