@@ -183,7 +183,8 @@ typedef struct {
 } ds_track;
 
 /* Track output buffers (device).  Tracks are packed in (event, seed) order;
- * trk_off[e]..trk_off[e+1] are event e's tracks. */
+ * trk_off[e]..trk_off[e+1] are event e's tracks.  `tracks` must be 16-byte
+ * aligned (DS_ERR_ARG otherwise): records are written as 16-byte chunks. */
 typedef struct {
     ds_track *tracks;         /* [capacity] */
     int32_t *trk_off;         /* [n_events + 1] */
@@ -219,6 +220,8 @@ typedef struct {
     uint32_t flags;           /* reserved, 0 */
 } ds_vertex_info;
 
+/* Vertex output buffers (device).  `vertices` must be 16-byte aligned
+ * (DS_ERR_ARG otherwise). */
 typedef struct {
     ds_vertex_rec *vertices;  /* [capacity], (event, i, j) order */
     int32_t *vtx_off;         /* [n_events + 1] */

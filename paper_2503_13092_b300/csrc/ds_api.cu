@@ -463,6 +463,8 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     if (b->n_hits > 0 && (!ht->x0 || !ht->ybeg || !ht->yend || !ht->layer))
         return fail(ctx, DS_ERR_ARG, "null hit column");
     if (out->capacity > 0 && !out->tracks) return fail(ctx, DS_ERR_ARG, "null track buffer");
+    if (reinterpret_cast<uintptr_t>(out->tracks) % 16 != 0)
+        return fail(ctx, DS_ERR_ARG, "track buffer must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     ds_status s = ensure_workspace(ctx, b->n_events, b->n_seeds, b->n_hits, st);
@@ -682,6 +684,8 @@ ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tr, ds_vertices *out, void *st
         return fail(ctx, DS_ERR_ARG, "null offsets");
     if (tr->capacity > 0 && !tr->tracks) return fail(ctx, DS_ERR_ARG, "null track buffer");
     if (out->capacity > 0 && !out->vertices) return fail(ctx, DS_ERR_ARG, "null vertex buffer");
+    if (reinterpret_cast<uintptr_t>(out->vertices) % 16 != 0)
+        return fail(ctx, DS_ERR_ARG, "vertex buffer must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
     DS_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     const int E = tr->n_events;

@@ -96,6 +96,7 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
     if (b->n_seeds > 0 && (!sd->x || !sd->y || !sd->tx || !sd->ty || !sd->qop || !sd->chi2)) return DS_ERR_ARG;
     if (b->n_hits > 0 && (!ht->x0 || !ht->ybeg || !ht->yend || !ht->layer)) return DS_ERR_ARG;
     if (out->capacity > 0 && !out->tracks) return DS_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(out->tracks) % 16 != 0) return DS_ERR_ARG;
     if (params->mlp_precision != DS_MLP_FP32) return DS_ERR_ARG;
 
     DevGeom g;

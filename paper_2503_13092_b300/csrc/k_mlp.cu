@@ -77,6 +77,8 @@ __device__ __forceinline__ bool hits_less(const CandMeta *x, const CandMeta *y)
     return false;
 }
 
+constexpr int kPickBatch = 8;
+
 __global__ void __launch_bounds__(256) k_pick(const __grid_constant__ PickArgs a)
 {
     // each warp stages its 32 winner records in shared memory and writes them
@@ -95,19 +97,33 @@ __global__ void __launch_bounds__(256) k_pick(const __grid_constant__ PickArgs a
         const int4 sc = a.seed_cand[s];        // first candidate, count, event
         const float thr = P.thr_logit;
         int bi = -1;
-        for (int k = 0; k < sc.y; ++k) {
-            const int c = sc.x + k;
-            const float lg = __ldg(a.logit + c);
-            const float4 q = __ldg(reinterpret_cast<const float4 *>(a.meta + c) + 1);   // chi2, ndof, seed, ty
-            const float chi2 = q.x;
-            const int ndof = __float_as_int(q.y);
-            unsigned long long key = kNoKey;
-            if (P.pick_chi2) key = pack_key(chi2 / (float)ndof, lg);
-            else if (lg < thr) key = pack_key(lg, chi2);
-            if (key < best || (key == best && key != kNoKey && hits_less(a.meta + c, a.meta + bi))) {
-                best = key;
-                bi = c;
-            }
+        // candidates in rounds of kPickBatch whose loads are all in flight
+        // together: a seed with many candidates waits for a few round trips,
+        // not one per candidate
+        for (int k0 = 0; k0 < sc.y; k0 += kPickBatch) {
+            float lg[kPickBatch];
+            float2 q[kPickBatch];   // chi2, ndof
+#pragma unroll
+            for (int k = 0; k < kPickBatch; ++k)
+                if (k0 + k < sc.y) {
+                    const int c = sc.x + k0 + k;
+                    lg[k] = __ldg(a.logit + c);
+                    q[k] = __ldg(reinterpret_cast<const float2 *>(a.meta + c) + 2);
+                }
+#pragma unroll
+            for (int k = 0; k < kPickBatch; ++k)
+                if (k0 + k < sc.y) {
+                    const int c = sc.x + k0 + k;
+                    const float chi2 = q[k].x;
+                    const int ndof = __float_as_int(q[k].y);
+                    unsigned long long key = kNoKey;
+                    if (P.pick_chi2) key = pack_key(chi2 / (float)ndof, lg[k]);
+                    else if (lg[k] < thr) key = pack_key(lg[k], chi2);
+                    if (key < best || (key == best && key != kNoKey && hits_less(a.meta + c, a.meta + bi))) {
+                        best = key;
+                        bi = c;
+                    }
+                }
         }
         bool have = bi >= 0;
         float lg_best = 0.f;

@@ -454,14 +454,10 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
                 }
                 const int slot = s_pool_base + k;
                 if (slot < a.pool_cap) {
-                    ds_vertex_rec v;
-                    v.event = e;
-                    v.i = t0 + i;
-                    v.j = t0 + j;
-                    v.x = o.x; v.y = o.y; v.z = o.z;
-                    v.doca = o.doca;
-                    v.flags = o.flags;
-                    a.pool[slot] = v;
+                    // the 32-byte record as two 16-byte stores (the pool is 16-byte aligned)
+                    int4 *dst = reinterpret_cast<int4 *>(a.pool + slot);
+                    dst[0] = make_int4(e, t0 + i, t0 + j, __float_as_int(o.x));
+                    dst[1] = make_int4(__float_as_int(o.y), __float_as_int(o.z), __float_as_int(o.doca), (int)o.flags);
                     a.pool_pos[slot] = ev_count + k;
                 } else {
                     raise_flag(a.cnt, DS_FLAG_VERTEX_CAPACITY);
@@ -502,11 +498,17 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
 
 __global__ void __launch_bounds__(256) k_scatter_vertices(const __grid_constant__ ScatterVtxArgs a)
 {
+    // records move as two 16-byte chunks (pool and output are 16-byte aligned)
     const int used = min(*(volatile const int *)&a.cnt->pool_used, a.pool_cap);
+    const int4 *src = reinterpret_cast<const int4 *>(a.pool);
+    int4 *dst = reinterpret_cast<int4 *>(a.out);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < used; k += gridDim.x * blockDim.x) {
-        const ds_vertex_rec v = a.pool[k];
-        const int pos = __ldg(a.vtx_off + v.event) + __ldg(a.pool_pos + k);
-        if (pos < a.capacity) a.out[pos] = v;
+        const int4 lo = __ldcs(src + 2 * k), hi = __ldcs(src + 2 * k + 1);
+        const int pos = __ldg(a.vtx_off + lo.x) + __ldcs(a.pool_pos + k);
+        if (pos < a.capacity) {
+            dst[2 * pos] = lo;
+            dst[2 * pos + 1] = hi;
+        }
     }
 }
 

@@ -291,6 +291,34 @@ def test_malformed_input_is_flagged(torch_cuda, weights):
     assert g["stats"]["status"] == 0
 
 
+def test_misaligned_outputs_are_refused(torch_cuda, weights):
+    """Track and vertex records are written as 16-byte chunks: output buffers
+    that are not 16-byte aligned are refused with DS_ERR_ARG before any launch,
+    and the context stays usable."""
+    from paper_2503_13092_b300 import ds
+    torch = torch_cuda
+    b = synth.config_batch("c2", n_events=2)
+    d = make(torch_cuda, synth.default_config(), weights)
+    dev = d.to_device(b)
+    S = int(b["seed_off"][-1])
+    out = d.alloc_tracks(2, S)
+    raw = torch.zeros(S * 64 + 16, dtype=torch.uint8, device="cuda")
+    bad = dict(out, tracks=raw[4:4 + S * 64].view(S, 64))
+    with pytest.raises(ds.DSError) as ei:
+        d.reconstruct(dev, bad)
+    assert ei.value.status == ds.DS_ERR_ARG
+    d.reconstruct(dev, out)
+    vout = d.alloc_vertices(2, 4096)
+    rawv = torch.zeros(4096 * 32 + 16, dtype=torch.uint8, device="cuda")
+    badv = dict(vout, vertices=rawv[8:8 + 4096 * 32].view(4096, 32))
+    with pytest.raises(ds.DSError) as ei:
+        d.vertex(out, badv)
+    assert ei.value.status == ds.DS_ERR_ARG
+    d.vertex(out, vout)
+    st = d.sync()
+    assert st["status"] == 0 and st["n_tracks"] > 0
+
+
 def test_bounded_wait_reports_timeout(torch_cuda, weights):
     """Failure detection without a GPU fault: the staging wait is made to run
     out (its barrier expects bytes nothing sends); the kernel gives up after a
