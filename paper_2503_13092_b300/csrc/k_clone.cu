@@ -18,8 +18,11 @@
 
 namespace ds {
 
-constexpr int kCloneThreads = 256;
-constexpr int kCloneSmem = 1024;
+// 192 threads, 24 KB of shared memory and at most 40 registers: 8 CTAs per
+// SM, so a batch of up to 8 x (number of SMs) events runs in one wave
+constexpr int kCloneThreads = 192;
+constexpr int kCloneCtasPerSm = 8;
+constexpr int kCloneSmem = 512;
 constexpr int kCloneHashBits = 10;
 
 
@@ -33,7 +36,7 @@ __device__ __forceinline__ bool kills(unsigned long long ko, int o, unsigned lon
     return shared > 2;
 }
 
-__global__ void __launch_bounds__(kCloneThreads) k_clone(const __grid_constant__ CloneArgs a)
+__global__ void __launch_bounds__(kCloneThreads, kCloneCtasPerSm) k_clone(const __grid_constant__ CloneArgs a)
 {
     __shared__ unsigned long long s_key[kCloneSmem];
     __shared__ int4 s_hit[kCloneSmem];
