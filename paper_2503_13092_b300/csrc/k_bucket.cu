@@ -24,6 +24,13 @@
 
 namespace ds {
 
+// Bin counters per CTA: every thread scans a run of `per` consecutive
+// counters, a multiple of 4 (16-byte shared loads, 8-byte table stores).
+__host__ __device__ constexpr int bucket_counters_per_thread(int n_sec)
+{
+    return ((4 * n_sec * kNXB + 1 + kBucketThreads - 1) / kBucketThreads + 3) & ~3;
+}
+__host__ __device__ constexpr int bucket_cnt_words(int n_sec) { return bucket_counters_per_thread(n_sec) * kBucketThreads; }
 
 __device__ __forceinline__ int hit_bin(const DevGeom &g, float x0, float yb, float ye, int lay,
                                        int nb, DevCounters *cnt, uint32_t *part)
@@ -88,10 +95,11 @@ __global__ void __launch_bounds__(kBucketThreads, 3) k_bucket(const __grid_const
         }
     }
 
-    const int cnt_words = (nb + 1 + 3) & ~3;
+    const int per = bucket_counters_per_thread(g.n_sec);
+    const int cnt_words = per * kBucketThreads;
     float *s_x = reinterpret_cast<float *>(s_cnt + cnt_words);
     uint16_t *s_pm = reinterpret_cast<uint16_t *>(s_x + kBucketStage);
-    for (int b = tid; b <= nb; b += blockDim.x) s_cnt[b] = 0;
+    for (int w = tid; w < cnt_words / 4; w += blockDim.x) reinterpret_cast<uint4 *>(s_cnt)[w] = make_uint4(0, 0, 0, 0);
     if (tid < 4) s_part[tid] = 0u;
     __syncthreads();
 
@@ -159,26 +167,32 @@ __global__ void __launch_bounds__(kBucketThreads, 3) k_bucket(const __grid_const
     }
     __syncthreads();
 
-    // exclusive scan over nb + 1 counters: contiguous chunk per thread
-    const int total_bins = nb + 1;
-    const int per = (total_bins + blockDim.x - 1) / blockDim.x;
-    const int b0 = tid * per;
-    int local = 0;
-    for (int k = 0; k < per; ++k)
-        if (b0 + k < total_bins) local += s_cnt[b0 + k];
-    int tot;
-    int run = block_exclusive_scan(local, s_scan, &tot);
-    for (int k = 0; k < per; ++k) {
-        const int b = b0 + k;
-        if (b < total_bins) {
-            const unsigned int c = s_cnt[b];
-            s_cnt[b] = run;
-            table[b] = (uint16_t)run;
-            run += c;
+    // exclusive scan over the counters (nb + 1 used, the rest zero): a run of
+    // `per` consecutive counters per thread, read and written 4 at a time.
+    // Every table entry below ext_off is written; those past the last bin get
+    // the hit count (the padding points at the end of the valid hits).
+    {
+        uint4 *c4 = reinterpret_cast<uint4 *>(s_cnt + tid * per);
+        int local = 0;
+        for (int q = 0; q < per / 4; ++q) {
+            const uint4 v = c4[q];
+            local += (int)(v.x + v.y + v.z + v.w);
+        }
+        int tot;
+        unsigned run = (unsigned)block_exclusive_scan(local, s_scan, &tot);
+        for (int q = 0; q < per / 4; ++q) {
+            const uint4 v = c4[q];
+            uint4 o;
+            o.x = run; run += v.x;
+            o.y = run; run += v.y;
+            o.z = run; run += v.z;
+            o.w = run; run += v.w;
+            c4[q] = o;
+            const int b = tid * per + 4 * q;
+            if (b < g.ext_off)
+                *reinterpret_cast<uint2 *>(table + b) = make_uint2(o.x | (o.y << 16), o.z | (o.w << 16));
         }
     }
-    // remaining offset entries (padding) point at the end of the valid hits
-    for (int b = total_bins + tid; b < g.ext_off; b += blockDim.x) table[b] = (uint16_t)n;
     // partial-strip row bits after the offsets
     if (tid < 4) reinterpret_cast<uint32_t *>(table + g.ext_off)[tid] = s_part[tid];
     __syncthreads();
@@ -227,7 +241,8 @@ cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st, Prof *prof)
 {
     if (a.n_events <= 0) return cudaSuccess;
     const int nb = 4 * a.g.n_sec * kNXB;
-    const size_t smem = sizeof(unsigned int) * (size_t)((nb + 1 + 3) & ~3) + (sizeof(float) + sizeof(uint16_t)) * kBucketStage;
+    const size_t smem = sizeof(unsigned int) * (size_t)bucket_cnt_words(a.g.n_sec) +
+                        (sizeof(float) + sizeof(uint16_t)) * kBucketStage;
     prof->begin("k_bucket", st);
     k_bucket<<<a.n_events, kBucketThreads, smem, st>>>(a);
     prof->end(st);
@@ -236,7 +251,7 @@ cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st, Prof *prof)
 
 cudaError_t init_bucket_attributes()
 {
-    const size_t smem = sizeof(unsigned int) * (size_t)((4 * kMaxSectors * kNXB + 1 + 3) & ~3) +
+    const size_t smem = sizeof(unsigned int) * (size_t)bucket_cnt_words(kMaxSectors) +
                         (sizeof(float) + sizeof(uint16_t)) * kBucketStage;
     // three CTAs per SM (about 52 KB each): ask for the largest shared-memory carveout
     cudaError_t e = cudaFuncSetAttribute(k_bucket, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
