@@ -240,7 +240,6 @@ __global__ void __launch_bounds__(kBucketThreads, 3) k_bucket(const __grid_const
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st, Prof *prof)
 {
     if (a.n_events <= 0) return cudaSuccess;
-    const int nb = 4 * a.g.n_sec * kNXB;
     const size_t smem = sizeof(unsigned int) * (size_t)bucket_cnt_words(a.g.n_sec) +
                         (sizeof(float) + sizeof(uint16_t)) * kBucketStage;
     prof->begin("k_bucket", st);

@@ -26,6 +26,7 @@ namespace ds {
 constexpr int kVtxThreads = 256;
 constexpr int kVtxLargeThreads = 1024;  // the large-capacity launch: one CTA per SM, all of its warps
 constexpr int kVtxSmallCap = 512;
+constexpr int kVtxOrderMax = 4096;    // large events ordered largest first, up to this many
 constexpr int kVtxCtasPerSm = 4;      // resident CTAs of the small-capacity launch per SM
 // pairs per two-phase segment and candidate results kept in shared memory per
 // segment: larger for the large-capacity launch (one CTA per SM), whose
@@ -263,10 +264,35 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
     const int n_mine = LARGE ? min(*(volatile const int *)&a.cnt->n_large, a.n_events) : a.n_events;
     // no large event: the small-capacity launch has laid out the offsets already
     if (LARGE && n_mine == 0) return;
+    // the large-capacity launch takes its events largest first (track count,
+    // then list position), so that the biggest ones do not start last: every
+    // CTA ranks the listed events the same way (up to kVtxOrderMax of them;
+    // beyond that, list order)
+    __shared__ uint16_t s_order[LARGE ? kVtxOrderMax : 1];
+    if (LARGE && n_mine <= kVtxOrderMax) {
+        int *s_nt = reinterpret_cast<int *>(s_dyn);   // free until the first event
+        const int tcap0 = min(__ldg(a.n_tracks), a.trk_capacity);
+        for (int j = threadIdx.x; j < n_mine; j += blockDim.x) {
+            const int ej = __ldcg(a.large_list + j);
+            s_nt[j] = min(__ldg(a.trk_off + ej + 1), tcap0) - min(__ldg(a.trk_off + ej), tcap0);
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < n_mine; j += blockDim.x) {
+            const int nj = s_nt[j];
+            int rank = 0;
+            for (int m = 0; m < n_mine; ++m) {
+                const int nm = s_nt[m];
+                rank += nm > nj || (nm == nj && m < j);
+            }
+            s_order[rank] = (uint16_t)j;
+        }
+        __syncthreads();
+    }
     for (;;) {
     if (threadIdx.x == 0) {
         const int k = atomicAdd(&a.cnt->vtx_queue[LARGE ? 1 : 0], 1);
-        s_e = k < n_mine ? (LARGE ? __ldcg(a.large_list + k) : k) : a.n_events;
+        s_e = k < n_mine ? (LARGE ? __ldcg(a.large_list + (n_mine <= kVtxOrderMax ? (int)s_order[k] : k)) : k)
+                         : a.n_events;
     }
     __syncthreads();
     const int e = s_e;
