@@ -7,7 +7,10 @@ shaped like the paper's minimum-bias workload (Poisson(300) SciFi seeds, 40 %
 true, 5000 UT hits per event, 16-32-32-1 ghost killer in FP32, opposite-charge
 vertexing with DOCA < 2 mm), inputs resident in HBM.  Inputs rotate over
 replicas totalling more than three times the L2, so every step reads cold
-inputs.  Prints one JSON line (rank 0).
+inputs.  Steps are issued round-robin on STREAMS CUDA streams, each with its
+own library context (workspaces and outputs), so consecutive batches overlap
+(the whole-job throughput a production loop gets); the same steps on one
+stream are reported as `single_stream`.  Prints one JSON line (rank 0).
 
 Under torchrun each rank processes its own batch (weak scaling, no
 collective on the data path); value = all events / max-over-ranks time.
@@ -34,6 +37,7 @@ N_EVENTS = 1000
 WORKLOAD = ("c2: 1000 events/step, Poisson(300) SciFi seeds (40% true), 5000 UT hits/event, "
             "16-32-32-1 ghost killer FP32, opposite-charge vertexing DOCA<2mm")
 KERNELS_PER_STEP = 9
+STREAMS = 3             # concurrent batches in the headline measurement
 
 
 def dist_info():
@@ -695,6 +699,7 @@ def main():
         return 0
     in_bytes = 24 * S + 13 * H + 8 * (E + 1)
     R = max(2, math.ceil(3 * L2_BYTES / in_bytes))
+    R = STREAMS * math.ceil(R / STREAMS)     # replica k % R belongs to stream k % STREAMS
     devs = [d.to_device(batch) for _ in range(R)]
     out = d.alloc_tracks(E, S)
     # size the vertex output from one run
@@ -743,6 +748,48 @@ def main():
     def step_graph(k):
         graphs[k % R].replay()
 
+    # one stream, one context: the same steps in sequence
+    torch.cuda.synchronize()
+    s0e = torch.cuda.Event(enable_timing=True)
+    s1e = torch.cuda.Event(enable_timing=True)
+    s0e.record(stream)
+    for k in range(args.steps):
+        step_graph(k)
+    s1e.record(stream)
+    torch.cuda.synchronize()
+    single_s = s0e.elapsed_time(s1e) / 1e3
+    st = d.sync(stream)
+    assert st["status"] == 0, st
+
+    # STREAMS lanes (context + outputs + stream); lane l replays the graphs of
+    # replicas l, l + STREAMS, ...  The lanes' buffers stay referenced here for
+    # as long as their graphs exist.
+    lanes = [dict(d=d, out=out, vout=vout, stream=torch.cuda.Stream(), graphs={})]
+    for _ in range(1, STREAMS):
+        dl = ds.Downstream(cfg, w, device=dev_index)
+        ds.ds_reserve(dl.ctx, E, S, H)
+        dl.run(batch, dev=devs[0])            # sizes its vertex workspace
+        lanes.append(dict(d=dl, out=dl.alloc_tracks(E, S), vout=dl.alloc_vertices(E, vcap),
+                          stream=torch.cuda.Stream(), graphs={}))
+    for r in range(R):
+        ln = lanes[r % STREAMS]
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap_stream):
+            cs = torch.cuda.current_stream()
+            ln["d"].reconstruct(devs[r], ln["out"], cs)
+            ln["d"].vertex(ln["out"], ln["vout"], cs)
+        ln["graphs"][r] = g
+
+    def steps_lanes(k0, n):
+        for k in range(k0, k0 + n):
+            ln = lanes[k % STREAMS]
+            with torch.cuda.stream(ln["stream"]):
+                ln["graphs"][k % R].replay()
+
+    torch.cuda.synchronize()
+    steps_lanes(0, max(args.warmup, STREAMS))
+    torch.cuda.synchronize()
+
     # ------------------------------------------------------------- timed
     if ws > 1:
         import torch.distributed as dist
@@ -753,18 +800,31 @@ def main():
     t0e = torch.cuda.Event(enable_timing=True)
     t1e = torch.cuda.Event(enable_timing=True)
     t0e.record(stream)
-    for k in range(args.steps):
-        step_graph(k)
+    for ln in lanes:
+        ln["stream"].wait_event(t0e)
+    steps_lanes(0, args.steps)
+    for ln in lanes:
+        ev = torch.cuda.Event()
+        ev.record(ln["stream"])
+        stream.wait_event(ev)
     t1e.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
     if ws > 1:
         dist.barrier()
     elapsed = t0e.elapsed_time(t1e) / 1e3
-    st = d.sync(stream)
-    assert st["status"] == 0, st
+    for ln in lanes:
+        st = ln["d"].sync(ln["stream"])
+        assert st["status"] == 0, st
+    for ln in lanes[1:]:                  # graphs first, then the contexts they point into
+        ln["graphs"].clear()
+        ln["d"].close()
+    lanes[0]["graphs"].clear()
     times = [max_over_ranks(elapsed)] * ws
     agg = aggregate(times, E, args.steps)
+    single = dict(value=ws * E * args.steps / max_over_ranks(single_s), unit="events/s",
+                  ms_per_step=1e3 * max_over_ranks(single_s) / args.steps,
+                  note="the same graph steps on one stream and one context, in sequence")
 
     # ------------------------------------------------- per-kernel roofline
     ds.ds_profile_enable(d.ctx, True)
@@ -905,7 +965,9 @@ def main():
             config=dict(workload=WORKLOAD, n_events=E, n_seeds=S, n_hits=H, tracks=n_t, vertices=n_v,
                         candidates=n_cand, pairs=n_pairs, pairs_fp64=n_fp64, mlp="fp32",
                         l2=f"inputs rotate over {R} replicas ({R * in_bytes / 2**20:.0f} MB > 3x L2)",
+                        streams=STREAMS,
                         parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
+            single_stream=single,
             roofline=roof, path_roofline=path, kernels=kernels, clocks=clocks, e2e=e2e, e2e_single_call=e2e_single,
             mlp_forms=mlp_forms, ghost_killer_training=trained, vertex_physics=vphys, variants=variants,
             c3=c3, c5=c5,
