@@ -37,7 +37,7 @@ N_EVENTS = 1000
 WORKLOAD = ("c2: 1000 events/step, Poisson(300) SciFi seeds (40% true), 5000 UT hits/event, "
             "16-32-32-1 ghost killer FP32, opposite-charge vertexing DOCA<2mm")
 KERNELS_PER_STEP = 9
-STREAMS = 3             # concurrent batches in the headline measurement
+STREAMS = 4             # concurrent batches in the headline measurement
 
 
 def dist_info():
@@ -637,7 +637,7 @@ def dv1_leg(ds, torch, cfg, w, batch, dv, dev_index, reps=10):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
