@@ -31,7 +31,7 @@ constexpr int kK1Max = 10;           // UTbX hits kept per seed (paper: up to 10
 constexpr int kMaxEventHits = 65535; // uint16 offsets
 constexpr int kSearchThreads = 128;  // threads per CTA in the search kernel (max seeds per work item)
 // run-time search shape (ds_tuning): defaults and limits
-constexpr int kSearchGroup = 2;      // consecutive work items per queue pull
+constexpr int kSearchGroup = 1;      // consecutive work items per queue pull
 constexpr int kSearchCtasPerSm = 4;
 constexpr int kStageHits = 5632;     // event x0 arrays up to this size are staged in shared memory
 constexpr int kStageHitsMax = 47104; // largest staging buffer: 32-sector table + x0 + static arrays < 227 KB
