@@ -184,6 +184,51 @@ def test_full_size_sampled(torch_cuda, weights, name, n_events, n_sample):
     parity.assert_vertices_match(vrep)
 
 
+def test_concurrent_contexts_match_single(torch_cuda, weights):
+    """The bench's launch configuration: four contexts, each with its own
+    stream, outputs and CUDA graph of the full c2 batch, replayed at the same
+    time.  Every context's tracks and vertices equal one context alone, byte
+    for byte (that result is checked against the oracle in
+    test_full_size_sampled)."""
+    from paper_2503_13092_b300 import ds
+    torch = torch_cuda
+    b = synth.config_batch("c2", n_events=1000)
+    cfg = synth.default_config()
+    ref = make(torch_cuda, cfg, weights).run(b)
+    assert ref["stats"]["status"] == 0
+    E, S, H = b["n_events"], int(b["seed_off"][-1]), int(b["hit_off"][-1])
+    lanes = []     # every buffer a graph points at stays referenced here
+    for _ in range(4):
+        d = make(torch_cuda, cfg, weights)
+        ds.ds_reserve(d.ctx, E, S, H)
+        dev = d.to_device(b)
+        d.run(b, dev=dev)                       # sizes the vertex workspace
+        out = d.alloc_tracks(E, S)
+        vout = d.alloc_vertices(E, 2 * ref["n_vertices"] + 4096)
+        st = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            cs = torch.cuda.current_stream()
+            d.reconstruct(dev, out, cs)
+            d.vertex(out, vout, cs)
+        lanes.append(dict(d=d, dev=dev, out=out, vout=vout, st=st, g=g))
+    torch.cuda.synchronize()
+    for _ in range(3):
+        for ln in lanes:
+            with torch.cuda.stream(ln["st"]):
+                ln["g"].replay()
+    torch.cuda.synchronize()
+    for ln in lanes:
+        assert ln["d"].sync(ln["st"])["status"] == 0
+        r = ds.decode(ln["out"], ln["vout"])
+        assert r["n_tracks"] == ref["n_tracks"] and r["n_vertices"] == ref["n_vertices"]
+        assert r["tracks"].tobytes() == ref["tracks"].tobytes()
+        assert r["vertices"].tobytes() == ref["vertices"].tobytes()
+        assert np.array_equal(r["trk_off"], ref["trk_off"]) and np.array_equal(r["vtx_off"], ref["vtx_off"])
+    for ln in lanes:
+        del ln["g"]                              # graphs go before the buffers they point at
+
+
 def test_edge_cases(torch_cuda, weights):
     from paper_2503_13092_b300 import ds
     cfg = synth.default_config()
