@@ -147,6 +147,10 @@ __global__ void __launch_bounds__(256) k_pick(const __grid_constant__ PickArgs a
         a.key_ws[s] = best;
         a.hit_ws[s] = hits;
     }
+    // only winners' records are read later (the clone kernel ranks winners
+    // alone, the scatter copies ranked seeds): the others are not written
+    const unsigned win = __ballot_sync(0xffffffffu, best != kNoKey);
+    if (win == 0) return;
     int4 *sr = s_rec[warp];
     sr[lane * 4 + 0] = r0;
     sr[lane * 4 + 1] = r1;
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(256) k_pick(const __grid_constant__ PickArgs a
     for (int k = lane; k < 128; k += 32) {
         const int rec = k >> 2;
         const int sg = warp_s0 + rec;
-        if (sg < a.n_seeds && sg >= 0) dst[k] = sr[k];
+        if (((win >> rec) & 1u) && sg < a.n_seeds && sg >= 0) dst[k] = sr[k];
     }
 }
 
