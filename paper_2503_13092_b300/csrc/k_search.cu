@@ -422,74 +422,84 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     int *s_base = s_pb.base;
     __shared__ int s_cand0;
     __shared__ int s_scan[32];
-    __shared__ int s_item[4];
-    __shared__ int s_hits[3];
+    __shared__ int s_nx[6];     // next work item: index, event, seed begin, seed end, h0, h1
     __shared__ __align__(8) uint64_t s_bar;
 
     const DevGeom &g = a.g;
     const DevParams &P = a.p;
     const int tid = threadIdx.x;
 
-    // persistent CTA: pairs of consecutive work items from a device queue;
-    // the event's data is staged again only when the event changes
+    // persistent CTA: work items from a device queue (a.group consecutive
+    // items per pull).  The last warp resolves the next item (queue pull,
+    // event lookup, offsets) into s_nx while the block works on the current
+    // one, after the refined windows, where that warp has the fewest pairs;
+    // the event's data is staged again only when the event changes.
     const int n_items = __ldg(a.item_off + a.n_events);
     uint16_t *Tb = reinterpret_cast<uint16_t *>(s_dyn);
     const uint32_t *Part = reinterpret_cast<const uint32_t *>(Tb + g.ext_off);
     float *xs = reinterpret_cast<float *>(s_dyn + sizeof(uint16_t) * g.table_stride);
-    if (tid == 0) {
-        mbar_init(&s_bar, 1);
-        s_item[3] = -1;               // staged event
-    }
-    __syncthreads();
-    uint32_t phase = 0;
-    const int limit = P.fault_inject ? 1024 : kWaitLimit;
-    for (;;) {
-    if (tid == 0) s_item[0] = atomicAdd(&a.cnt->search_queue, a.group);
-    __syncthreads();
-    const int b_first = s_item[0];
-    __syncthreads();
-    if (b_first >= n_items) break;
-    for (int bi = b_first; bi < b_first + a.group && bi < n_items; ++bi) {
-    // work item: chunk k of event e's seeds (sizes differ by at most one).
-    // Warp 0 finds the event; lane 0 reads its offsets and, when the event
-    // changes, starts the staging copies before the block meets.
-    if (tid < 32) {
+    constexpr int kNextWarp = T / 32 - 1;
+    const bool next_warp = (tid >> 5) == kNextWarp;
+    int q_next = 0, q_end = 0;     // lane 0 of the next-item warp: rest of its queue group
+    // work item bi: chunk k of event e's seeds (sizes differ by at most one)
+    auto resolve_next = [&]() {    // the next-item warp, all 32 lanes
+        int bi = 0;
+        if ((tid & 31) == 0) {
+            if (q_next >= q_end) {
+                q_next = atomicAdd(&a.cnt->search_queue, a.group);
+                q_end = q_next + a.group;
+            }
+            bi = q_next++;
+        }
+        bi = __shfl_sync(0xffffffffu, bi, 0);
+        if (bi >= n_items) {
+            if ((tid & 31) == 0) s_nx[0] = n_items;
+            return;
+        }
         const int e = warp_find_segment(a.item_off, a.n_events, bi);
-        if (tid == 0) {
+        if ((tid & 31) == 0) {
             const int i0 = __ldg(a.item_off + e), i1 = __ldg(a.item_off + e + 1);
             const int s0 = __ldg(a.seed_off + e), ns = __ldg(a.seed_off + e + 1) - s0;
             int h0 = __ldg(a.hit_off + e), h1 = __ldg(a.hit_off + e + 1);
             if (h0 < 0 || h1 < h0 || h1 > a.n_hits || h1 - h0 > kMaxEventHits) h1 = h0 = 0;
             const int k = bi - i0, nc = i1 - i0;
-            s_item[0] = e;
-            s_item[1] = s0 + (int)(((long long)k * ns) / nc);
-            s_item[2] = s0 + (int)(((long long)(k + 1) * ns) / nc);
-            s_hits[0] = h0;
-            s_hits[1] = h1;
-            const bool restage = s_item[3] != e;
-            s_hits[2] = restage;
-            if (restage) {
-                // the event's bin table and (if it fits) its x0 array, by two
-                // bulk copies (TMA); the x0 copy starts at the 16-byte
-                // boundary below h0.  The previous item's readers are done
-                // (the block met at the end of it).
-                const int nh = h1 - h0, lead = h0 & 3;
-                const uint32_t tb_bytes = sizeof(uint16_t) * g.table_stride;
-                const uint32_t x_bytes = nh <= a.stage_hits ? (uint32_t)(((lead + nh) * 4 + 15) & ~15) : 0u;
-                // fault injection (tests): expect 16 bytes that never arrive
-                mbar_expect_tx(&s_bar, tb_bytes + x_bytes + ((P.fault_inject & 1) ? 16u : 0u));
-                bulk_copy_g2s(Tb, a.bins + (size_t)e * g.table_stride, tb_bytes, &s_bar);
-                if (x_bytes) bulk_copy_g2s(xs, a.sx0 + (h0 - lead), x_bytes, &s_bar);
-                s_item[3] = e;
-            }
+            s_nx[0] = bi;
+            s_nx[1] = e;
+            s_nx[2] = s0 + (int)(((long long)k * ns) / nc);
+            s_nx[3] = s0 + (int)(((long long)(k + 1) * ns) / nc);
+            s_nx[4] = h0;
+            s_nx[5] = h1;
         }
-    }
+    };
+    if (tid == 0) mbar_init(&s_bar, 1);
+    if (next_warp) resolve_next();
     __syncthreads();
-    const int e = s_item[0];
-    const int s = s_item[1] + tid;
-    const bool active = s < s_item[2];
-    const int h0 = s_hits[0], h1 = s_hits[1];
-    const bool restage = s_hits[2] != 0;
+    uint32_t phase = 0;
+    const int limit = P.fault_inject ? 1024 : kWaitLimit;
+    int staged_e = -1;             // the event in the staging buffers (same in every thread)
+    for (;;) {
+    // s_nx is read by every thread here and rewritten by the next-item warp
+    // only after the block has met again (first-window scan)
+    if (s_nx[0] >= n_items) break;
+    const int e = s_nx[1];
+    const int s_begin = s_nx[2], s_end = s_nx[3];
+    const int h0 = s_nx[4], h1 = s_nx[5];
+    const bool restage = e != staged_e;
+    staged_e = e;
+    if (tid == 0 && restage) {
+        // the event's bin table and (if it fits) its x0 array, by two bulk
+        // copies (TMA); the x0 copy starts at the 16-byte boundary below h0.
+        // The previous item's readers are done (the block met at the end of it).
+        const int nh = h1 - h0, lead = h0 & 3;
+        const uint32_t tb_bytes = sizeof(uint16_t) * g.table_stride;
+        const uint32_t x_bytes = nh <= a.stage_hits ? (uint32_t)(((lead + nh) * 4 + 15) & ~15) : 0u;
+        // fault injection (tests): expect 16 bytes that never arrive
+        mbar_expect_tx(&s_bar, tb_bytes + x_bytes + ((P.fault_inject & 1) ? 16u : 0u));
+        bulk_copy_g2s(Tb, a.bins + (size_t)e * g.table_stride, tb_bytes, &s_bar);
+        if (x_bytes) bulk_copy_g2s(xs, a.sx0 + (h0 - lead), x_bytes, &s_bar);
+    }
+    const int s = s_begin + tid;
+    const bool active = s < s_end;
     const int nh = h1 - h0;
     const EvHits H{a.sperm + h0, a.ybeg + h0, a.yend + h0, h0};
     const bool staged = nh <= a.stage_hits;
@@ -735,6 +745,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
         const int valid = (1 + pa + pu + pv >= 3) && (pa || pu);
         s_nc[j][o] = (uint8_t)(valid ? nu * nv : 0);
     }
+    if (next_warp) resolve_next();
     __syncthreads();
     for (int j = 0; j < nbx; ++j) n_cand += s_nc[j][tid];
     for (int j = nbx; j < kK1Max; ++j) s_nc[j][tid] = 0;
@@ -807,16 +818,15 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
         m.xr = f.xr; m.yr = f.yr; m.t = f.t; m.qop = f.qop;
         m.chi2 = f.chi2;
         m.ndof = f.ndof;
-        m.seed = s_item[1] + o;
+        m.seed = s_begin + o;
         m.ty = sc.ty;
 #pragma unroll
         for (int l = 0; l < 4; ++l) m.hit[l] = loc[l] >= 0 ? hit_id(H, loc[l]) : -1;
         a.cand_meta[slot] = m;
     }
     }
-    __syncthreads();   // shared state is reused by the next item
-    }   // items of the group
-    }   // queue
+    __syncthreads();   // shared state is reused by the next item; s_nx is visible
+    }   // work items
 }
 
 cudaError_t init_search_attributes()
