@@ -12,8 +12,9 @@
 //   magnet point) and its 16 network inputs are formed.  The network and the
 //   best pick run in k_mlp.cu over all candidates of the batch.
 //
-// Work decomposition (B300): one CTA per work item = up to 128 seeds of one
-// event.  The event's bin table (with its partial-strip row bits) and
+// Work decomposition (B300): persistent CTAs, 4 per SM, take work items (up
+// to 128 seeds of one event) from a device queue; the last warp resolves the
+// next item while the block finishes the current one.  The event's bin table (with its partial-strip row bits) and
 // compact x0 array are staged in shared memory by two bulk copies (TMA) on an
 // mbarrier; every x test of every window reads shared memory, and a hit
 // passing it looks up its strip extent and id (through the sorted index map
