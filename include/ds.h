@@ -399,8 +399,13 @@ DS_API ds_status ds_sync_status(ds_ctx *ctx, void *stream, ds_stats *stats);
  * device array of about 22 MB that each GPU loading the library holds until
  * process exit.  It calls no cudaMalloc/cudaFree.  Limits per call: at most
  * 256 events, 16384 seeds and 327680 hits (DS_ERR_CAPACITY beyond, nothing
- * launched) and 8 candidates per seed on average (DS_FLAG_CAND_CAPACITY).  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * launched) and 8 candidates per seed on average whatever params->cand_per_seed
+ * says (beyond that DS_FLAG_CAND_CAPACITY is set in *d_flags and the seeds
+ * left over stay empty, so pass d_flags to see it).  Only the FP32 network
+ * and non-training parameters are accepted (DS_ERR_ARG otherwise: training
+ * mode gives up to 40 candidates per seed).  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.
  * All calls share the array: calls that overlap on the GPU race and must be
  * serialised by the caller.  Outputs as ds_reconstruct; if d_flags (device
  * pointer, may be NULL) is given, the call's device flag word (DS_FLAG_*) is

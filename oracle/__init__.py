@@ -43,7 +43,7 @@ class OrConfig(C.Structure):
                 ("nr_tol", C.c_double), ("k1", C.c_int), ("first_window_origin", C.c_int),
                 ("pick_chi2", C.c_int), ("clone_kill", C.c_int), ("training", C.c_int),
                 ("nr_max_iter", C.c_int), ("variant", C.c_int), ("dv1_dtx_max", C.c_double),
-                ("dv1_w_tri", C.c_double)]
+                ("dv1_w_tri", C.c_double), ("chi2_margin_scale", C.c_double)]
 
 
 class OrNN(C.Structure):
@@ -84,6 +84,9 @@ def make_config(cfg: dict) -> OrConfig:
     c.variant = int(cfg.get("variant", 0))
     c.dv1_dtx_max = float(cfg.get("dv1_dtx_max", 0.8))
     c.dv1_w_tri = float(cfg.get("dv1_w_tri", 1.0))
+    # margin of a chi2 key comparison per unit of its relative gap (decision
+    # margins are compared with 1e-5 by the parity rules)
+    c.chi2_margin_scale = float(cfg.get("chi2_margin_scale", 1e-2))
     return c
 
 
@@ -261,5 +264,5 @@ def clone_kill(hits, k1, k2, enabled: bool = True, has=None) -> np.ndarray:
     k1 = np.ascontiguousarray(k1, np.float64); k2 = np.ascontiguousarray(k2, np.float64)
     st = np.zeros(n, np.int32)
     lib().or_clone_kill(C.c_int(n), _p(has), _p(hits), _p(k1), _p(k2), C.c_int(int(enabled)),
-                        C.c_int(0), _p(st), None)
+                        C.c_int(0), C.c_double(1e-2), _p(st), None)
     return st

@@ -70,6 +70,7 @@ typedef struct {
     int variant;        /* 0: Dv0; 1: Dv1 (triplet search in UTaX x UTbX) */
     double dv1_dtx_max; /* Dv1: largest kink |tx_UT - tx_seed| a UTbX hit may imply */
     double dv1_w_tri;   /* Dv1: UTaX hit within this distance of the magnet-point line */
+    double chi2_margin_scale; /* margin of a chi2 comparison per unit of relative gap */
 } or_config;
 
 typedef struct {
@@ -90,12 +91,13 @@ static void upd_margin(double *m, double a, double b, double s)
 }
 
 /* Key comparisons: a network response is compared on an absolute scale; a
- * chi2 (or chi2/ndof) comparison counts in units of the chi2 tolerance, 1e-3
- * relative, so a 1e-3 relative gap maps to a margin of 1e-5. */
-static void upd_key_margin(double *m, int is_chi2, double a, double b)
+ * chi2 (or chi2/ndof) comparison's relative gap is multiplied by
+ * chi2_scale.  With 1e-2 the gap counts in units of the chi2 tolerance (1e-3
+ * relative), so a 1e-3 relative gap maps to a margin of 1e-5. */
+static void upd_key_margin(double *m, int is_chi2, double a, double b, double chi2_scale)
 {
     if (is_chi2) {
-        double r = fabs(a - b) / fmax(fmax(fabs(a), fabs(b)), 1e-300) * 1e-2;
+        double r = fabs(a - b) / fmax(fmax(fabs(a), fabs(b)), 1e-300) * chi2_scale;
         if (r < *m) *m = r;
     } else {
         upd_margin(m, a, b, 1.0);
@@ -473,8 +475,8 @@ static int process_seed(const or_config *c, const or_nn *nn, const or_event_hits
             if (i == wi) continue;
             int elig = c->pick_chi2 || all[i].f < T;
             if (elig) {
-                if (all[i].k1 != win.k1) upd_key_margin(&m, c->pick_chi2, all[i].k1, win.k1);
-                else upd_key_margin(&m, !c->pick_chi2, all[i].k2, win.k2);
+                if (all[i].k1 != win.k1) upd_key_margin(&m, c->pick_chi2, all[i].k1, win.k1, c->chi2_margin_scale);
+                else upd_key_margin(&m, !c->pick_chi2, all[i].k2, win.k2, c->chi2_margin_scale);
             } else if (key_less(&all[i], &win)) {
                 upd_margin(&m, all[i].f, T, 1.0);
             }
@@ -498,7 +500,7 @@ static int process_seed(const or_config *c, const or_nn *nn, const or_event_hits
  * against the full set before killing, so the result does not depend on the
  * order of the pairs.  status: 0 no winner, 1 killed, 2 kept. */
 void or_clone_kill(int n, const int *has, const int *hits, const double *k1, const double *k2,
-                   int enabled, int k1_is_chi2, int *status, double *margin)
+                   int enabled, int k1_is_chi2, double chi2_scale, int *status, double *margin)
 {
     for (int b = 0; b < n; ++b) {
         if (!has[b]) {
@@ -512,8 +514,8 @@ void or_clone_kill(int n, const int *has, const int *hits, const double *k1, con
             for (int l = 0; l < 4; ++l) shared += hits[4 * a + l] >= 0 && hits[4 * a + l] == hits[4 * b + l];
             if (shared <= 2) continue;
             if (margin) {
-                if (k1[a] != k1[b]) upd_key_margin(&margin[b], k1_is_chi2, k1[a], k1[b]);
-                else upd_key_margin(&margin[b], !k1_is_chi2, k2[a], k2[b]);
+                if (k1[a] != k1[b]) upd_key_margin(&margin[b], k1_is_chi2, k1[a], k1[b], chi2_scale);
+                else upd_key_margin(&margin[b], !k1_is_chi2, k2[a], k2[b], chi2_scale);
             }
             int a_better = (k1[a] < k1[b]) || (k1[a] == k1[b] && k2[a] < k2[b]) ||
                            (k1[a] == k1[b] && k2[a] == k2[b] && a < b);
@@ -568,8 +570,8 @@ void or_reconstruct(const or_config *c, const or_nn *nn, int n_events, const int
             k1[b] = win[b].k1;
             k2[b] = win[b].k2;
         }
-        or_clone_kill(ns, has, wh, k1, k2, c->clone_kill && !c->training, c->pick_chi2, st,
-                      margin + s0);
+        or_clone_kill(ns, has, wh, k1, k2, c->clone_kill && !c->training, c->pick_chi2, c->chi2_margin_scale,
+                      st, margin + s0);
         for (int b = 0; b < ns; ++b) {
             int s = s0 + b;
             status[s] = st[b];

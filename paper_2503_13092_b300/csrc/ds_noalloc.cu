@@ -98,6 +98,9 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
     if (out->capacity > 0 && !out->tracks) return DS_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(out->tracks) % 16 != 0) return DS_ERR_ARG;
     if (params->mlp_precision != DS_MLP_FP32) return DS_ERR_ARG;
+    // training mode can give every seed 40 candidates, five times what the
+    // static candidate buffer holds per seed on average
+    if (params->training) return DS_ERR_ARG;
 
     DevGeom g;
     DevParams p;
@@ -108,7 +111,8 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
 
     int device = 0, sm_count = 148;
     if (cudaGetDevice(&device) != cudaSuccess) return DS_ERR_CUDA;
-    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sm_count < 1)
+        return DS_ERR_CUDA;
     unsigned char *base = nullptr;
     ds_status st = scratch_address(device, &base);
     if (st != DS_OK) return st;

@@ -14,7 +14,8 @@
 // allocation or device-wide synchronisation happens while serving) and a
 // non-blocking stream; batches in different slots overlap on the device.
 // Results are renumbered into each request's own event, seed, hit and track
-// indices on the host when its last segment completes.
+// indices on the GPU (k_renumber, on the slot's stream after ds_vertex) and
+// copied straight into the caller's output buffers.
 #include <algorithm>
 #include <atomic>
 #include <chrono>

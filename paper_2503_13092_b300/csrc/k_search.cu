@@ -425,6 +425,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     __shared__ int s_scan[32];
     __shared__ int s_nx[6];     // next work item: index, event, seed begin, seed end, h0, h1
     __shared__ __align__(8) uint64_t s_bar;
+    __shared__ __align__(8) uint64_t s_bar_fi;   // fault injection only: a barrier no copy targets
 
     const DevGeom &g = a.g;
     const DevParams &P = a.p;
@@ -472,11 +473,18 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
             s_nx[5] = h1;
         }
     };
-    if (tid == 0) mbar_init(&s_bar, 1);
+    if (tid == 0) {
+        mbar_init(&s_bar, 1);
+        if (P.fault_inject & 1) {
+            // tests: a barrier that expects 16 bytes nothing sends; the
+            // staging wait below also waits on it and runs out
+            mbar_init(&s_bar_fi, 1);
+            mbar_expect_tx(&s_bar_fi, 16u);
+        }
+    }
     if (next_warp) resolve_next();
     __syncthreads();
     uint32_t phase = 0;
-    const int limit = P.fault_inject ? 1024 : kWaitLimit;
     int staged_e = -1;             // the event in the staging buffers (same in every thread)
     for (;;) {
     // s_nx is read by every thread here and rewritten by the next-item warp
@@ -494,8 +502,7 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
         const int nh = h1 - h0, lead = h0 & 3;
         const uint32_t tb_bytes = sizeof(uint16_t) * g.table_stride;
         const uint32_t x_bytes = nh <= a.stage_hits ? (uint32_t)(((lead + nh) * 4 + 15) & ~15) : 0u;
-        // fault injection (tests): expect 16 bytes that never arrive
-        mbar_expect_tx(&s_bar, tb_bytes + x_bytes + ((P.fault_inject & 1) ? 16u : 0u));
+        mbar_expect_tx(&s_bar, tb_bytes + x_bytes);
         bulk_copy_g2s(Tb, a.bins + (size_t)e * g.table_stride, tb_bytes, &s_bar);
         if (x_bytes) bulk_copy_g2s(xs, a.sx0 + (h0 - lead), x_bytes, &s_bar);
     }
@@ -519,8 +526,16 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     }
     if (restage) {
         // bounded wait; the decision to go on is taken by the whole block
-        if (!__syncthreads_and(mbar_wait_bounded(&s_bar, phase, limit))) {
+        bool ok = mbar_wait_bounded(&s_bar, phase, kWaitLimit);
+        if (P.fault_inject & 1) ok = ok && mbar_wait_bounded(&s_bar_fi, 0, 1024);
+        if (!__syncthreads_and(ok)) {
             if (tid == 0) raise_flag(a.cnt, DS_FLAG_TIMEOUT);
+            // the block must not leave while bulk copies still write into its
+            // shared memory: wait (bounded again) for the staging copies.  With
+            // fault injection they have already landed; after a real time-out
+            // they may still be in flight if this wait runs out too.
+            mbar_wait_bounded(&s_bar, phase, kWaitLimit);
+            __syncthreads();
             return;
         }
         phase ^= 1u;

@@ -16,6 +16,9 @@ Vertices: the oracle vertexer is fed the GPU's own FP32 track records; kept
 largest float32 coordinate where that is coarser (vertices beyond 8 m, whose
 float32 coordinates cannot hold 1 um); DOCA within 1e-4 mm.
 """
+import json
+import os
+
 import numpy as np
 
 import oracle
@@ -118,13 +121,29 @@ def compare_tracks(batch, orc, gpu, hit_map_gpu=None, atol_nn=ATOL_NN):
         ok_chi2 = _close(orc["chi2"][same], g["chi2"][same], RTOL_CHI2, ATOL_CHI2)
         ok_nn = np.abs(orc["nn"][same] - g["nn"][same]) <= atol_nn
         ok_ndof = orc["ndof"][same] == g["ndof"][same]
+        rel_chi2 = np.abs(orc["chi2"][same] - g["chi2"][same]) / np.maximum(orc["chi2"][same], ATOL_CHI2 / RTOL_CHI2)
         rep.update(bad_par=int((~ok_par).sum()), bad_chi2=int((~ok_chi2).sum()), bad_nn=int((~ok_nn).sum()),
                    bad_ndof=int((~ok_ndof).sum()),
                    max_rel_par=float(np.max(np.abs(st_o - st_g) / np.maximum(np.abs(st_o), ATOL_PAR / RTOL_PAR))),
-                   max_rel_chi2=float(np.max(np.abs(orc["chi2"][same] - g["chi2"][same]) /
-                                            np.maximum(orc["chi2"][same], ATOL_CHI2 / RTOL_CHI2))),
+                   max_rel_chi2=float(np.max(rel_chi2)),
+                   rel_chi2_q=[float(np.quantile(rel_chi2, q)) for q in (0.5, 0.99, 0.999)],
                    max_abs_nn=float(np.max(np.abs(orc["nn"][same] - g["nn"][same]))))
+    log_report("tracks", rep)
     return rep
+
+
+def log_report(kind, rep):
+    """Append a parity report to the JSON-lines file named by DS_PARITY_LOG
+    (if set), tagged with the running test, and print a one-line summary."""
+    test = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+    keys = ("n_tracks_oracle", "n_same", "n_diff", "n_excused", "max_rel_chi2", "n_oracle", "n_gpu",
+            "n_unexcused", "max_pos_err")
+    print(f"parity[{kind}] {test}: " + ", ".join(f"{k}={rep[k]}" for k in keys if k in rep))
+    path = os.environ.get("DS_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(dict(kind=kind, test=test, **{k: v for k, v in rep.items()
+                                                               if k not in ("unexcused", "bad_pos_pairs")})) + "\n")
 
 
 def assert_tracks_match(rep):
@@ -175,6 +194,7 @@ def compare_vertices(cfg, gpu):
                    max_pos_err_within_8m=float(dpos[big < 8192].max()) if np.any(big < 8192) else 0.0,
                    max_doca_err=float(np.max(np.abs(gv["doca"][gi] - ov["doca"][oi]))),
                    bad_pos_pairs=[both[k] for k in np.nonzero(bad)[0][:10]])
+    log_report("vertices", rep)
     return rep
 
 

@@ -32,9 +32,15 @@ def test_noalloc_matches_reconstruct():
     for call in range(2):
         out = d.alloc_tracks(E, S)
         flags = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         st = ds.ds_reconstruct_noalloc(geom, params, w, dev, out, d_flags=flags)
         assert st == ds.DS_OK, ds.ds_status_string(st)
         torch.cuda.synchronize()
+        if call == 1:
+            # the defining property: the call itself takes no device memory
+            # (the first call may load the library's module on the device)
+            assert torch.cuda.mem_get_info()[0] == free0
         assert int(flags.item()) == 0
         got = ds.decode(out)
         assert got["n_tracks"] == ref["n_tracks"]
@@ -51,4 +57,6 @@ def test_noalloc_matches_reconstruct():
     big["n_events"] = 257
     out = d.alloc_tracks(E, S)
     assert ds.ds_reconstruct_noalloc(geom, params, w, big, out) == ds.DS_ERR_CAPACITY
+    # training mode (up to 40 candidates per seed) does not fit the static buffer
+    assert ds.ds_reconstruct_noalloc(geom, ds.make_params(cfg, training=1), w, dev, out) == ds.DS_ERR_ARG
     d.close()
