@@ -36,7 +36,6 @@ L2_BYTES = 126 * 2 ** 20
 N_EVENTS = 1000
 WORKLOAD = ("c2: 1000 events/step, Poisson(300) SciFi seeds (40% true), 5000 UT hits/event, "
             "16-32-32-1 ghost killer FP32, opposite-charge vertexing DOCA<2mm")
-KERNELS_PER_STEP = 9
 STREAMS = 4             # concurrent batches in the headline measurement
 
 
@@ -122,18 +121,20 @@ class Clocks:
 MLP_FLOP = 2 * (16 * 32 + 32 * 32 + 32)          # 16-32-32-1 network: multiply-adds x 2
 
 
-def algorithmic(E, S, H, n_t, n_v, n_cand, n_pairs, table_stride):
-    """Algorithmic bytes (each input read once, each output written once) and
-    FLOPs per launch of every kernel of a step.  C = candidates, T = tracks,
-    V = vertices, P = opposite-charge pairs."""
+def algorithmic(E, S, H, n_t, n_v, n_cand, n_pairs, table_stride, fused=True):
+    """Bytes each kernel of a step moves through HBM, this design's
+    workspaces included (each read once, each write once), and FLOPs.  C =
+    candidates, T = tracks, V = vertices, P = opposite-charge pairs."""
     tb = 2 * table_stride * E                    # per-event bin tables
     mlp_flop = MLP_FLOP
+    # seeds (24 B), staged x0 + index map (6 B/hit), tables; fused: the pick
+    # key + hit ids (24 B) and rank (4 B) per seed and one record per track;
+    # unfused: candidates (64 B inputs + 48 B fit) + per-seed range and rank
+    search = (24 * S + 6 * H + tb + 28 * S + 64 * n_t) if fused else (24 * S + 6 * H + tb + 112 * n_cand + 20 * S)
     return {
         # hits in (13 B) -> sorted x0 (4 B) + index inside the event (2 B) + tables
         "k_bucket": dict(bytes=13 * H + 6 * H + tb),
-        # seeds (24 B), staged x0 + index map (6 B/hit), tables -> candidates
-        # (64 B inputs + 48 B fit) + per-seed range and rank (20 B)
-        "k_search": dict(bytes=24 * S + 6 * H + tb + 112 * n_cand + 20 * S),
+        "k_search": dict(bytes=search, flop=mlp_flop * n_cand if fused else 0),
         "k_mlp": dict(bytes=68 * n_cand, flop=mlp_flop * n_cand),
         "k_pick": dict(bytes=16 * S + 20 * n_cand + 48 * n_t + 88 * S),
         "k_clone": dict(bytes=28 * S + 8 * E),
@@ -195,33 +196,38 @@ def step_traffic():
 
 
 def h2d_ceiling(torch, nbytes, reps=5):
-    """Pinned host -> device copy rate of one buffer of nbytes: one
-    cudaMemcpyAsync on one stream, and the same bytes split over two streams."""
+    """Pinned host -> device copy rate for nbytes per step, issued as plain
+    cudaMemcpyAsync calls: one copy on one stream, the same bytes as two
+    copies on two streams, and as four copies on one and on two streams."""
+    from cuda.bindings import runtime as rt
     src = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
     dst = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    s0, s1 = torch.cuda.Stream(), torch.cuda.Stream()
-    half = nbytes // 2
-    res = {}
-    for name in ("one_stream", "two_streams"):
-        for it in range(2 + reps):
-            if it == 2:
-                torch.cuda.synchronize()
-                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(s0)
-            if name == "one_stream":
-                with torch.cuda.stream(s0):
-                    dst.copy_(src, non_blocking=True)
-            else:
-                s1.wait_stream(s0)
-                with torch.cuda.stream(s0):
-                    dst[:half].copy_(src[:half], non_blocking=True)
-                with torch.cuda.stream(s1):
-                    dst[half:].copy_(src[half:], non_blocking=True)
-                s0.wait_stream(s1)
-        e1.record(s0)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    h2d = rt.cudaMemcpyKind.cudaMemcpyHostToDevice
+
+    def issue(n_chunks, n_streams):
+        step = (nbytes + n_chunks - 1) // n_chunks
+        for c in range(n_chunks):
+            off = c * step
+            n = min(step, nbytes - off)
+            st = streams[c % n_streams]
+            err, = rt.cudaMemcpyAsync(dst.data_ptr() + off, src.data_ptr() + off, n, h2d, st.cuda_stream)
+            assert err == rt.cudaError_t.cudaSuccess, err
+
+    res = dict(bytes=nbytes)
+    for name, nc, ns in (("one_copy", 1, 1), ("two_copies_two_streams", 2, 2), ("four_copies_one_stream", 4, 1),
+                         ("four_copies_two_streams", 4, 2)):
+        issue(nc, ns)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(streams[0])
+        streams[1].wait_stream(streams[0])
+        for _ in range(reps):
+            issue(nc, ns)
+        streams[0].wait_stream(streams[1])
+        e1.record(streams[0])
         torch.cuda.synchronize()
         res[name + "_gbs"] = nbytes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
-    res["bytes"] = nbytes
     return res
 
 
@@ -354,10 +360,16 @@ def reduced_precision_forms(d, ds, torch, batch, devs, ref, step, n_prof, stream
             f.update(seed_flip_rate=float(flip.mean()),
                      response_err_max=float(dn.max()) if dn.size else 0.0,
                      response_err_mean=float(dn.mean()) if dn.size else 0.0, **selection(batch, g))
-        else:
+        elif "k_mlp" in kernels:
             f["k_mlp_us"] = kernels["k_mlp"]["avg_us"]
             f.update(selection(batch, ref))
-        f["k_mlp_candidates_per_s"] = n_cand / (f["k_mlp_us"] * 1e-6)
+        else:       # the FP32 network runs inside k_search (no separate launch)
+            f["k_mlp_us"] = None
+            f["network"] = "fused into k_search"
+            f["k_search_us"] = kernels["k_search"]["avg_us"]
+            f.update(selection(batch, ref))
+        if f["k_mlp_us"]:
+            f["k_mlp_candidates_per_s"] = n_cand / (f["k_mlp_us"] * 1e-6)
         for _ in range(3):
             ds.ds_mlp_eval(d.ctx, feats, logit, prec, stream)
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
@@ -420,6 +432,15 @@ def bench_c3(ds, torch, cfg, w, steps, warmup, dev_index):
         return dict(value=E / (ms * 1e-3), ms_per_step=ms, tuning=ds.ds_get_tuning(d.ctx).as_dict())
 
     default = timed("default")
+    # per-kernel CUDA-event times of one profiled (eager) step
+    d.sync(stream)
+    ds.ds_profile_enable(d.ctx, True)
+    for _ in range(2):
+        d.reconstruct(dv, out, stream); d.vertex(out, vout, stream)
+    pr = ds.ds_profile_read(d.ctx)
+    ds.ds_profile_enable(d.ctx, False)
+    d.sync(stream)
+    c3_kernels = {k: dict(launches=v[0], avg_us=1e3 * v[1] / max(v[0], 1)) for k, v in pr.items()}
     t_tune = time.perf_counter()
     best, entries = ds.ds_autotune(d.ctx, dv, out, reps=2)
     t_tune = time.perf_counter() - t_tune
@@ -429,8 +450,9 @@ def bench_c3(ds, torch, cfg, w, steps, warmup, dev_index):
                unit="events/s", n_events=E, n_seeds=S, n_hits=H, tracks=n_t, vertices=n_v,
                seeds_per_event=[int(seeds.min()), int(seeds.max())], hits_per_event=[int(hits.min()), int(hits.max())],
                default=default, autotuned=tuned, autotune_s=t_tune, autotune_configs=len(entries),
+               kernels=c3_kernels,
                generate_s=t_gen, inputs_mb=(24 * S + 13 * H) / 2**20,
-               step="one CUDA graph replay: ds_reconstruct + ds_vertex over all 10000 events (9 kernels)")
+               step="one CUDA graph replay: ds_reconstruct + ds_vertex over all 10000 events")
     d.close()
     return res
 
@@ -898,20 +920,38 @@ def main():
     prof = ds.ds_profile_read(d.ctx)
     ds.ds_profile_enable(d.ctx, False)
     d.sync(stream)
-    # per-event table: offsets padded to 8 entries + one float4 extent per (layer, sector)
-    table_stride = (((4 * cfg["n_sectors"] * 64 + 1) + 7) & ~7) + 32 * cfg["n_sectors"]
-    alg = algorithmic(E, S, H, n_t, n_v, n_cand, n_pairs, table_stride)
+    # per-event table (uint16 entries): offsets padded to 8 entries, then 16 bytes of row flags
+    table_stride = (((4 * cfg["n_sectors"] * 64 + 1) + 7) & ~7) + 8
+    alg = algorithmic(E, S, H, n_t, n_v, n_cand, n_pairs, table_stride, fused="k_mlp" not in prof)
     kernels = {k: dict(launches=v[0], avg_us=1e3 * v[1] / max(v[0], 1)) for k, v in prof.items()}
+    launches_per_step = sum(v["launches"] for v in kernels.values()) / n_prof
     step_us = sum(v["avg_us"] * v["launches"] for v in kernels.values()) / n_prof
     for k, v in kernels.items():
         v["share"] = v["avg_us"] * v["launches"] / n_prof / step_us
         a = alg.get(k, {})
         v["gbs"] = a.get("bytes", 0) / (v["avg_us"] * 1e-6) / 1e9 if v["avg_us"] > 0 else 0.0
-        if "flop" in a:
+        if a.get("flop"):
             v["tflops"] = a["flop"] / (v["avg_us"] * 1e-6) / 1e12
     mb = method_bytes(S, H, n_t, n_v)
     for k, v in kernels.items():
         v["method_gbs"] = mb.get(k, 0) / (v["avg_us"] * 1e-6) / 1e9 if v["avg_us"] > 0 else 0.0
+    # the network scored inside the search kernel instead (fuse_network = 1)
+    d.set_params(fuse_network=1)
+    for k in range(3):
+        step(k)
+    d.sync(stream)
+    ds.ds_profile_enable(d.ctx, True)
+    for k in range(n_prof):
+        step(k)
+    prf = ds.ds_profile_read(d.ctx)
+    ds.ds_profile_enable(d.ctx, False)
+    d.set_params(fuse_network=0)
+    d.sync(stream)
+    fused_form = {k: 1e3 * v[1] / max(v[0], 1) for k, v in prf.items()}
+    fused_form = dict(kernels_us=fused_form, step_us=sum(1e3 * v[1] for v in prf.values()) / n_prof,
+                      separate_step_us=step_us,
+                      note="network + pick inside k_search (fuse_network = 1) against the separate k_mlp and "
+                           "k_pick (default), CUDA-event time per kernel, same steps")
     dom = max(kernels, key=lambda k: kernels[k]["share"])
     hbm, sm_mhz, src = peaks()
     kd = kernels[dom]
@@ -983,7 +1023,7 @@ def main():
     e2e = e2e_pipelined(ds, torch, cfg, w, pin, E, S, H, dev_index, n_steps=max(args.steps, 10))
     e2e["value"] *= ws
     ceil = h2d_ceiling(torch, e2e["h2d_bytes_per_step"])
-    best = max(ceil["one_stream_gbs"], ceil["two_streams_gbs"])
+    best = max(v for k, v in ceil.items() if k.endswith("_gbs"))
     e2e["h2d_ceiling_gbs"] = best
     e2e["h2d_ceiling"] = ceil
     # the rate the upload alone allows, and e2e as a fraction of it
@@ -1044,13 +1084,13 @@ def main():
                         parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
             single_stream=single,
             roofline=roof, path_roofline=path, kernels=kernels, clocks=clocks, e2e=e2e, e2e_single_call=e2e_single,
-            mlp_forms=mlp_forms, ghost_killer_training=trained, vertex_physics=vphys, variants=variants,
+            mlp_forms=mlp_forms, network_in_search=fused_form, ghost_killer_training=trained, vertex_physics=vphys, variants=variants,
             c3=c3, c5=c5,
             plain_form=dict(value=n_plain / plain_s, unit="events/s",
                             note="one event per ds_reconstruct + ds_vertex call, FP32", events=n_plain),
             eager=dict(value=ws * E * args.steps / eager_s, unit="events/s",
                        note="same steps launched from Python without CUDA graphs"),
-            gpu_launches=KERNELS_PER_STEP * args.steps,
+            gpu_launches=int(round(launches_per_step * args.steps)), kernels_per_step=launches_per_step,
             cpu_baseline=cpu)
         print(json.dumps(line), flush=True)
     if ws > 1:

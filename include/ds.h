@@ -135,7 +135,8 @@ typedef struct {
                               produces no tracks; no GPU fault is involved. */
     int32_t cand_per_seed; /* candidate buffer size per seed on average (default 16, max
                               40 = 10 x 1 x 2 x 2; training mode always uses 40); exceeding
-                              it raises DS_FLAG_CAND_CAPACITY */
+                              it raises DS_FLAG_CAND_CAPACITY.  Used only when candidates
+                              go through the buffer (see fuse_network) */
     int32_t variant;       /* 0: Dv0 (default).  1: Dv1 (Algorithm Design section): every
                               UTbX hit whose implied kink |tx' - tx_seed| < dv1_dtx_max is
                               joined to the magnet point; the closest UTaX hit within
@@ -143,6 +144,16 @@ typedef struct {
                               with the smallest residual go on to the stereo windows */
     double dv1_dtx_max;    /* Dv1 kink bound (default 0.8: p above ~1.5 GeV/c) */
     double dv1_w_tri;      /* Dv1 UTaX collinearity tolerance, mm (default 1) */
+    int32_t fuse_network;  /* 0 (default): candidates are written to the candidate buffer and
+                              scored and picked by separate kernels (ds_candidates can export
+                              them).  1: with the FP32 two-hidden-layer network outside
+                              training mode, every candidate is scored inside the search
+                              kernel and only each seed's winner leaves it (no candidate
+                              buffer; measured slower on B300: the network then runs at the
+                              search kernel's occupancy).  Training mode, the BF16 / FP8
+                              network and single-hidden-layer networks always use the
+                              buffer.  Results are identical either way. */
+    int32_t reserved2;
 } ds_params;
 
 /* One event batch (CSR over events).  Device pointers. */
@@ -258,7 +269,7 @@ typedef struct {
     int32_t search_ctas_per_sm; /* persistent search CTAs per SM, 1..4 (default 4) */
     int32_t search_group;       /* consecutive work items per queue pull, 1..16 (default 1) */
     int32_t search_stage_hits;  /* events with at most this many hits have their x0 array
-                                   staged in shared memory, 0..47104 (default 5632);
+                                   staged in shared memory, 0..46080 (default 5120);
                                    larger events read it from global memory */
 } ds_tuning;
 

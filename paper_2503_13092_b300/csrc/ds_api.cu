@@ -28,6 +28,7 @@ struct ds_ctx {
     ds::DevNN nn{};
     int nn_in = 16, nn_h1 = 32, nn_h2 = 32;
     int mlp_precision = DS_MLP_FP32;
+    int fuse_network = 0;
     ds::MlpTcWeights *d_tc = nullptr;    // tensor-core weight tiles (BF16 / FP8 network)
     ds::DevLines lines{};                // trigger-line networks (none loaded: n_lines = 0)
     ds::LineTcWeights *d_lines_tc = nullptr;   // their tensor-core operand
@@ -53,8 +54,11 @@ struct ds_ctx {
     int *clone_next = nullptr;
     int *count_vtx = nullptr;
     int *large_vtx = nullptr;
+    int *large_aux = nullptr;      // per listed event: pair count [E], first work item [E + 1]
+    int *vtx_items = nullptr;      // per work item: kept count, offset inside its event
     ds_vertex_rec *pool = nullptr;
     int *pool_pos = nullptr;
+    int *pool_item = nullptr;
     // host-buffer path: device copies of inputs and outputs
     struct {
         int cap_events = 0, cap_seeds = 0, cap_hits = 0, cap_trk = 0, cap_vtx = 0;
@@ -229,6 +233,7 @@ const char *fill_dev_params(const ds_params *p, DevParams *out)
     if (p->cand_per_seed < 1 || p->cand_per_seed > 40) return "cand_per_seed outside 1..40";
     if (p->variant != 0 && p->variant != 1) return "variant must be 0 (Dv0) or 1 (Dv1)";
     if (p->variant == 1 && (!(p->dv1_dtx_max > 0) || !(p->dv1_w_tri > 0))) return "Dv1 bounds must be positive";
+    if (p->fuse_network != 0 && p->fuse_network != 1) return "fuse_network must be 0 or 1";
     DevParams &d = *out;
     d.w1a = (float)p->w1a;
     d.w1b = (float)p->w1b;
@@ -339,7 +344,7 @@ void ds_destroy(ds_ctx *ctx)
     cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_cnt, ctx->d_tc, ctx->d_lines_tc, ctx->sperm, ctx->sx0, ctx->item_off, ctx->bins, ctx->cand_feat,
                     ctx->cand_meta, ctx->cand_logit, ctx->seed_cand, ctx->trk_ws, ctx->key_ws, ctx->hit_ws,
-                    ctx->rank_ws, ctx->clone_next, ctx->count_trk, ctx->count_vtx, ctx->large_vtx, ctx->pool, ctx->pool_pos,
+                    ctx->rank_ws, ctx->clone_next, ctx->count_trk, ctx->count_vtx, ctx->large_vtx, ctx->large_aux, ctx->vtx_items, ctx->pool, ctx->pool_pos, ctx->pool_item,
                     ctx->h.seed_off, ctx->h.hit_off, ctx->h.seed_cols, ctx->h.hit_cols, ctx->h.layer,
                     ctx->h.tracks, ctx->h.trk_off, ctx->h.vtx_off, ctx->h.counts, ctx->h.vertices};
     for (void *q : ptrs)
@@ -389,6 +394,7 @@ ds_status ds_set_params(ds_ctx *ctx, const ds_params *p)
     const char *why = ds::fill_dev_params(p, &ctx->p);
     if (why) return fail(ctx, DS_ERR_ARG, why);
     ctx->mlp_precision = p->mlp_precision;
+    ctx->fuse_network = p->fuse_network;
     // training mode (100/10 mm windows) can give every seed the maximum of 10 x 1 x 2 x 2
     ctx->cand_per_seed = p->training ? 40 : p->cand_per_seed;
     return DS_OK;
@@ -407,6 +413,8 @@ ds_status ds_reserve(ds_ctx *ctx, int32_t E, int32_t S, int32_t H)
         if ((st = grow(ctx, &ctx->count_trk, (size_t)E)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->count_vtx, (size_t)E)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->large_vtx, (size_t)E)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->large_aux, 2 * (size_t)E + 2)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->vtx_items, 2 * (size_t)ds::kVtxItemsPerEvent * E)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->item_off, (size_t)E + 1)) != DS_OK) return st;
         ctx->cap_events = E;
     }
@@ -445,6 +453,7 @@ ds_status ds_reserve_vertices(ds_ctx *ctx, int32_t capacity)
     ds_status s;
     if ((s = grow(ctx, &ctx->pool, (size_t)capacity)) != DS_OK) return s;
     if ((s = grow(ctx, &ctx->pool_pos, (size_t)capacity)) != DS_OK) return s;
+    if ((s = grow(ctx, &ctx->pool_item, (size_t)capacity)) != DS_OK) return s;
     ctx->cap_pool = capacity;
     return DS_OK;
 }
@@ -519,6 +528,15 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     sa.group = ctx->tune.search_group;
     sa.stage_hits = ctx->tune.search_stage_hits;
     sa.cnt = ctx->d_cnt;
+    // the network scored inside the search (on request): FP32, the
+    // two-hidden-layer kernel shape, outside training mode
+    sa.fused = ctx->fuse_network && ctx->mlp_precision == DS_MLP_FP32 && !ctx->p.training && ctx->nn_h2 == 32;
+    if (sa.fused) {
+        sa.nn = ctx->nn;
+        sa.trk_ws = ctx->trk_ws;
+        sa.key_ws = ctx->key_ws;
+        sa.hit_ws = ctx->hit_ws;
+    }
     DS_CUDA(ds::launch_search(sa, st, &ctx->prof), "search kernel");
 
     ds::MlpArgs ma{};
@@ -543,7 +561,7 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     pa.trk_ws = ctx->trk_ws;
     pa.key_ws = ctx->key_ws;
     pa.hit_ws = ctx->hit_ws;
-    DS_CUDA(ds::launch_mlp_pick(ma, pa, ctx->sm_count, st, &ctx->prof), "network kernel");
+    if (!sa.fused) DS_CUDA(ds::launch_mlp_pick(ma, pa, ctx->sm_count, st, &ctx->prof), "network kernel");
 
     ds::CloneArgs ca{};
     ca.n_events = b->n_events;
@@ -697,6 +715,7 @@ ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tr, ds_vertices *out, void *st
         if (ctx->cap_pool < out->capacity) {
             if ((s = grow(ctx, &ctx->pool, (size_t)out->capacity)) != DS_OK) return s;
             if ((s = grow(ctx, &ctx->pool_pos, (size_t)out->capacity)) != DS_OK) return s;
+            if ((s = grow(ctx, &ctx->pool_item, (size_t)out->capacity)) != DS_OK) return s;
             ctx->cap_pool = out->capacity;
         }
     }
@@ -714,9 +733,15 @@ ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tr, ds_vertices *out, void *st
     va.n_tracks = tr->n_tracks;
     va.pool = ctx->pool;
     va.pool_pos = ctx->pool_pos;
+    va.pool_item = ctx->pool_item;
     va.pool_cap = out->capacity;
     va.count_ws = ctx->count_vtx;
     va.large_list = ctx->large_vtx;
+    va.large_pairs = ctx->large_aux;
+    va.large_item_off = ctx->large_aux + ctx->cap_events;
+    va.item_count = ctx->vtx_items;
+    va.item_base = ctx->vtx_items + (size_t)ds::kVtxItemsPerEvent * ctx->cap_events;
+    va.max_items = ds::kVtxItemsPerEvent * ctx->cap_events;
     va.vtx_off = out->vtx_off;
     va.n_vertices = out->n_vertices;
     va.capacity = out->capacity;
@@ -724,6 +749,8 @@ ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tr, ds_vertices *out, void *st
     ds::ScatterVtxArgs xa{};
     xa.pool = ctx->pool;
     xa.pool_pos = ctx->pool_pos;
+    xa.pool_item = ctx->pool_item;
+    xa.item_base = va.item_base;
     xa.pool_cap = out->capacity;
     xa.vtx_off = out->vtx_off;
     xa.out = out->vertices;
@@ -815,7 +842,7 @@ ds_status ds_autotune(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *sd, 
     ds_tuning cur = ctx->tune;
     double cur_ms = 0.0;
     rs = measure(cur, &cur_ms);
-    static const int stage_opts[] = {2048, 5632, 8192, 12288, 16384, 24576, 32768};
+    static const int stage_opts[] = {2048, 5120, 8192, 12288, 16384, 24576, 32768};
     static const int chunk_opts[] = {32, 64, 96, 128};
     static const int ctas_opts[] = {1, 2, 3, 4};
     static const int group_opts[] = {1, 2, 4, 8};

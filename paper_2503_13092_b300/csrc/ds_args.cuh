@@ -55,6 +55,14 @@ struct SearchArgs {
     int cand_cap;
     int4 *seed_cand;       // per seed: first candidate, count, event
     int *rank_ws;
+    // fused form (fused = 1): every candidate is scored by the FP32 network
+    // (16-32-32-1) inside the search and only each seed's winner leaves it,
+    // as k_pick would write it: record, pick key and hit ids per seed
+    int fused;
+    DevNN nn;
+    ds_track *trk_ws;
+    unsigned long long *key_ws;
+    int4 *hit_ws;
     int sm_count;
     int ctas_per_sm;       // persistent CTAs per SM
     int group;             // work items per queue pull
@@ -135,10 +143,16 @@ struct VertexArgs {
     const int32_t *trk_off;
     const int32_t *n_tracks;
     ds_vertex_rec *pool;
-    int *pool_pos;
+    int *pool_pos;          // slot -> rank inside its event (small launch) or work item (large)
+    int *pool_item;         // slot -> work item of the large-capacity launch
     int pool_cap;
     int *count_ws;          // per event
     int *large_list;        // events with more tracks than the small launch takes
+    int *large_pairs;       // per listed event: opposite-charge pairs
+    int *large_item_off;    // per listed event: first work item (pair segment); [n_large] = total
+    int *item_count;        // per work item: vertices kept
+    int *item_base;         // per work item: vertices of the event's earlier items
+    int max_items;
     int32_t *vtx_off;
     int32_t *n_vertices;
     int capacity;
@@ -148,6 +162,8 @@ struct VertexArgs {
 struct ScatterVtxArgs {
     const ds_vertex_rec *pool;
     const int *pool_pos;
+    const int *pool_item;
+    const int *item_base;
     int pool_cap;
     const int32_t *vtx_off;
     ds_vertex_rec *out;

@@ -33,12 +33,15 @@ constexpr int kSearchThreads = 128;  // threads per CTA in the search kernel (ma
 // run-time search shape (ds_tuning): defaults and limits
 constexpr int kSearchGroup = 1;      // consecutive work items per queue pull
 constexpr int kSearchCtasPerSm = 4;
-constexpr int kStageHits = 5632;     // event x0 arrays up to this size are staged in shared memory
-constexpr int kStageHitsMax = 47104; // largest staging buffer: 32-sector table + x0 + static arrays < 227 KB
+constexpr int kStageHits = 5120;     // event x0 arrays up to this size are staged in shared memory (4 fused search CTAs per SM fit)
+constexpr int kStageHitsMax = 46080; // largest staging buffer: 32-sector table + x0 + static arrays (fused form) < 227 KB
 constexpr int kBucketThreads = 512;
 constexpr int kBucketVecRows = 3;    // 16-byte loads (4 hits) per bucketing thread
 constexpr int kBucketStage = 6144;   // events up to this many hits are sorted in shared memory
 constexpr int kMaxVertexTracks = 4096; // tracks per event staged for vertexing
+constexpr int kVtxLargeSeg = 65536;  // pairs per work item of the large-capacity vertex launch
+// items of one event: its opposite-charge pairs, at most (4096 / 2)^2, in segments
+constexpr int kVtxItemsPerEvent = (kMaxVertexTracks / 2) * (kMaxVertexTracks / 2) / kVtxLargeSeg;
 constexpr unsigned long long kNoKey = ~0ull;
 
 // Per-event table: nb + 1 = 4 n_sec kNXB + 1 uint16 offsets padded to 8
@@ -95,6 +98,7 @@ struct DevCounters {                 // device-side flag word and statistics
     int pool_used;
     int vtx_queue[2];                // event queues of the two vertex launches
     int n_large;                     // events left to the large-capacity vertex launch
+    int pool_small;                  // vertex pool slots filled by the small-capacity launch
     int cand_used;                   // candidates written this call
     int search_queue;                // next search work item
     unsigned long long n_candidates;
@@ -181,6 +185,42 @@ __device__ __forceinline__ int warp_find_segment(const int32_t *__restrict__ off
     const unsigned m = __ballot_sync(0xffffffffu, lo + lane < hi && __ldg(off + lo + lane) <= s);
     return lo + 31 - __clz(m);
 }
+
+// Ghost-killer network (Ghost-Killer Neural Network section) in FP32, inputs
+// normalised, ReLU hidden layer(s), output before the sigmoid.  Weights come
+// from a kernel parameter block with compile-time indices (every lane reads
+// the same weight: constant-bank operands of the FMAs).
+template <int NIN, int NH1, int NH2>
+__device__ __forceinline__ float mlp_logit_fp32(const DevNN &nn, const float (&phi)[16])
+{
+    float x[NIN];
+#pragma unroll
+    for (int i = 0; i < NIN; ++i) x[i] = (phi[i] - nn.mean[i]) * nn.scale[i];
+    float h1[NH1];
+#pragma unroll
+    for (int o = 0; o < NH1; ++o) {
+        float acc = nn.b1[o];
+#pragma unroll
+        for (int i = 0; i < NIN; ++i) acc = fmaf(nn.w1[o][i], x[i], acc);
+        h1[o] = fmaxf(acc, 0.f);
+    }
+    float out = nn.b3;
+    if (NH2 > 0) {
+#pragma unroll
+        for (int o = 0; o < NH2; ++o) {
+            float acc = nn.b2[o];
+#pragma unroll
+            for (int i = 0; i < NH1; ++i) acc = fmaf(nn.w2[o][i], h1[i], acc);
+            out = fmaf(nn.w3[o], fmaxf(acc, 0.f), out);
+        }
+    } else {
+#pragma unroll
+        for (int o = 0; o < NH1; ++o) out = fmaf(nn.w3[o], h1[o], out);
+    }
+    return out;
+}
+
+__device__ __forceinline__ float sigmoid_fast(float z) { return 1.f / (1.f + __expf(-z)); }
 
 // Order-preserving float -> uint32 map (negative values included) and back.
 __device__ __forceinline__ unsigned int ord_f32(float x)

@@ -18,36 +18,6 @@
 namespace ds {
 
 template <int NIN, int NH1, int NH2>
-__device__ __forceinline__ float mlp_logit_fp32(const DevNN &nn, const float (&phi)[16])
-{
-    float x[NIN];
-#pragma unroll
-    for (int i = 0; i < NIN; ++i) x[i] = (phi[i] - nn.mean[i]) * nn.scale[i];
-    float h1[NH1];
-#pragma unroll
-    for (int o = 0; o < NH1; ++o) {
-        float acc = nn.b1[o];
-#pragma unroll
-        for (int i = 0; i < NIN; ++i) acc = fmaf(nn.w1[o][i], x[i], acc);
-        h1[o] = fmaxf(acc, 0.f);
-    }
-    float out = nn.b3;
-    if (NH2 > 0) {
-#pragma unroll
-        for (int o = 0; o < NH2; ++o) {
-            float acc = nn.b2[o];
-#pragma unroll
-            for (int i = 0; i < NH1; ++i) acc = fmaf(nn.w2[o][i], h1[i], acc);
-            out = fmaf(nn.w3[o], fmaxf(acc, 0.f), out);
-        }
-    } else {
-#pragma unroll
-        for (int o = 0; o < NH1; ++o) out = fmaf(nn.w3[o], h1[o], out);
-    }
-    return out;
-}
-
-template <int NIN, int NH1, int NH2>
 __global__ void __launch_bounds__(256) k_mlp_fp32(const __grid_constant__ MlpArgs a)
 {
     const int n = a.n_host >= 0 ? a.n_host : min(*(volatile const int *)&a.cnt->cand_used, a.cand_cap);
@@ -62,8 +32,6 @@ __global__ void __launch_bounds__(256) k_mlp_fp32(const __grid_constant__ MlpArg
         a.logit[c] = mlp_logit_fp32<NIN, NH1, NH2>(a.nn, phi);
     }
 }
-
-__device__ __forceinline__ float sigmoid_fast(float z) { return 1.f / (1.f + __expf(-z)); }
 
 // Last part of the pick key: hit ids in layer order, absent (-1) last.
 __device__ __forceinline__ bool hits_less(const CandMeta *x, const CandMeta *y)

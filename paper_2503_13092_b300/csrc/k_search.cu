@@ -23,8 +23,15 @@
 // candidate's hits are looked up when it is written.
 // Three flattened phases keep lanes busy whatever the hits per seed: UTbX
 // window (thread per seed), refined windows (thread per (seed, UTbX hit)),
-// fit + features (thread per candidate).  Candidates are written to a compact
-// buffer reserved with one atomicAdd per CTA, seed by seed.
+// fit + features (thread per candidate).  Unfused form: candidates are
+// written to a compact buffer reserved with one atomicAdd per CTA, seed by
+// seed, for k_mlp / k_pick.  Fused form (FP32 network): each candidate's
+// thread also evaluates the network (Ghost-Killer Neural Network section: the
+// network runs inside the tracking, weights in the parameter bank) and merges
+// its pick key with the hit ids of its layers into its seed's running minimum
+// in shared memory (a 128-bit compare-and-swap); the fit of the current
+// minimum is kept beside it, and after the last candidate each seed's thread
+// writes the winner record, key and hit ids as k_pick does.
 #include "ds_args.cuh"
 
 namespace ds {
@@ -32,6 +39,10 @@ namespace ds {
 
 constexpr uint16_t kNone = 0xFFFFu;
 constexpr int T = kSearchThreads;
+#ifndef DS_FUSED_CTAS
+#define DS_FUSED_CTAS 4
+#endif
+constexpr int kSearchFusedCtas = DS_FUSED_CTAS;   // resident CTAs per SM the fused form is compiled for
 
 // The sorted hits of one event: x0 is staged separately; the index inside the
 // event (sperm) gives a hit's id and, through the caller's arrays, its strip.
@@ -304,6 +315,31 @@ __device__ __forceinline__ WinBest window_best(const DevGeom &g, const float *X0
     return r;
 }
 
+// A seed's best candidate so far in the fused form: the pick key (as k_pick
+// packs it) and the hits' indices inside the event in layer order (16 bits
+// each, 0xFFFF = absent): as one 128-bit integer the order is the pick order,
+// hit ids breaking key ties with absent last.
+struct __align__(16) KeyIds {
+    unsigned long long key, ids;
+};
+
+__device__ __forceinline__ bool keyids_less(const KeyIds &x, const KeyIds &y)
+{
+    return x.key < y.key || (x.key == y.key && x.ids < y.ids);
+}
+
+// *dst = min(*dst, v) in shared memory (compare-and-swap on all 128 bits; the
+// loop ends when v is no longer smaller or the swap went through)
+__device__ __forceinline__ void keyids_min(KeyIds *dst, const KeyIds &v)
+{
+    KeyIds old = *dst;
+    while (keyids_less(v, old)) {
+        const KeyIds prev = atomicCAS(dst, old, v);
+        if (prev.key == old.key && prev.ids == old.ids) break;
+        old = prev;
+    }
+}
+
 struct SeedCtx {     // per-seed quantities reused by candidate scoring
     float zm, xm, ym, tx, ty, qop, chi2, w1, u_bx;
     float yl[4];
@@ -381,19 +417,47 @@ __device__ __forceinline__ CandFit fit_candidate(const DevGeom &g, const SeedCtx
 }
 
 // First window with more x-passing hits than the collection column holds
-// (rare): exact rescan with insertion into the k1 best, kept out of line so
-// its arrays do not weigh on the kernel's registers.  Writes the kept sorted
-// positions to out[j * T], returns how many were kept.
+// (rare): the k1 closest by (|dx|, id) are found by k1 passes over the
+// window, pass r keeping the smallest (|dx|, id) above the one pass r - 1
+// kept; only the running minimum lives in registers.  A hit's strip and id
+// are looked up only when its distance could still win the pass.  Writes the
+// kept sorted positions to out[r * T] in order, returns how many were kept.
 __device__ __noinline__ int wide_first_window(const DevGeom &g, const float *X0, const EvHits &H,
                                               const uint16_t *Tb, const uint32_t *Part, float u, float y, float w,
                                               float dy, int k1, uint16_t *out)
 {
-    float d[kK1Max];
-    int id[kK1Max], p[kK1Max];
-    const int q = window_scan<kK1Max, 4>(g, X0, H, Tb, Part, 3, u, y, w, dy, d, id, p);
-#pragma unroll
-    for (int j = 0; j < kK1Max; ++j) out[j * T] = (uint16_t)p[j];
-    return min(q, k1);
+    const int s_lo = sector_of(g, y - dy - 0.01f), s_hi = sector_of(g, y + dy + 0.01f);
+    const int b0 = xbin_of(g, u - w - 1e-3f), b1 = xbin_of(g, u + w + 1e-3f);
+    const float inf = __int_as_float(0x7f800000);
+    float dp = -1.f;          // the last kept (|dx|, id); every hit is above the start
+    int idp = -1;
+    int r = 0;
+    for (; r < k1; ++r) {
+        float bd = inf;
+        int bid = 0x7fffffff, bpos = -1;
+        for (int sct = s_lo; sct <= s_hi; ++sct) {
+            const int row = (3 * g.n_sec + sct) * kNXB;
+            const int i0 = Tb[row + b0], i1 = Tb[row + b1 + 1];
+            for (int i = i0; i < i1; ++i) {
+                const float dx = fabsf(X0[i] - u);
+                if (!(dx < w) || dx < dp || dx > bd) continue;
+                const float4 h = hit_record(H, i);
+                if (!(h.y - dy <= y && y <= h.z + dy)) continue;
+                const int id = __float_as_int(h.w);
+                if (key_less(dx, id, dp, idp) || (dx == dp && id == idp)) continue;   // kept by an earlier pass
+                if (key_less(dx, id, bd, bid)) {
+                    bd = dx;
+                    bid = id;
+                    bpos = i;
+                }
+            }
+        }
+        if (bpos < 0) break;
+        out[r * T] = (uint16_t)bpos;
+        dp = bd;
+        idp = bid;
+    }
+    return r;
 }
 
 // Dv1: the UTaX strip coordinate predicted by the line through the magnet
@@ -406,21 +470,29 @@ __device__ __forceinline__ float dv1_ua(const DevGeom &g, const SeedCtx &sc, con
 }
 
 // V = 0: Dv0.  V = 1: Dv1, whose first stage is the triplet search.
-template <int V>
-__global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchArgs a)
+// F: fused network and pick (FP32 network 16-32-32-1).
+template <int V, bool F>
+__global__ void __launch_bounds__(T, F ? kSearchFusedCtas : 4) k_search(const __grid_constant__ SearchArgs a)
 {
     extern __shared__ __align__(16) unsigned char s_dyn[];   // bin table, then staged x0
     __shared__ uint16_t s_bx[kK1Max][T];
-    __shared__ uint16_t s_sel[kK1Max][5][T];
+    // refined-window hits; in the fused form also the staging area of the
+    // winner records once the candidates are done (128 x 64 bytes)
+    __shared__ __align__(16) uint16_t s_sel[kK1Max][5][T];
     __shared__ uint8_t s_nc[kK1Max][T];
     __shared__ SeedCtx s_sc[T];
     __shared__ uint16_t s_wsec[3][T];   // window_sectors of the refined windows (layers 0-2)
-    // (seed, UTbX rank) of each refined-window pair, then the candidate offsets
-    __shared__ union {
+    // (seed, UTbX rank) of each refined-window pair, then the candidate
+    // offsets (and, fused, each seed's best key + hit indices and its fit)
+    __shared__ __align__(16) union {
         uint16_t pair[kK1Max * T];
-        int base[T + 1];
+        struct {
+            int base[T + 4];
+            KeyIds best[F ? T : 1];
+            float4 win[F ? T : 1];      // x_ref, tx, q/p, chi2 of the best
+        } c;
     } s_pb;
-    int *s_base = s_pb.base;
+    int *s_base = s_pb.c.base;
     __shared__ int s_cand0;
     __shared__ int s_scan[32];
     __shared__ int s_nx[6];     // next work item: index, event, seed begin, seed end, h0, h1
@@ -770,10 +842,11 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     const int base = block_exclusive_scan(n_cand, s_scan, &total);
     s_base[tid] = base;
     if (tid == T - 1) s_base[T] = base + n_cand;
+    if (F) s_pb.c.best[tid] = KeyIds{kNoKey, ~0ull};
     if (tid == 0) {
         if (total > 0) atomicAdd(&a.cnt->n_candidates, (unsigned long long)total);
-        int c0 = total > 0 ? atomicAdd(&a.cnt->cand_used, total) : 0;
-        if (total > 0 && c0 + total > a.cand_cap) {   // candidate buffer full: flagged, seeds left empty
+        int c0 = total > 0 && !F ? atomicAdd(&a.cnt->cand_used, total) : 0;
+        if (!F && total > 0 && c0 + total > a.cand_cap) {   // candidate buffer full: flagged, seeds left empty
             raise_flag(a.cnt, DS_FLAG_CAND_CAPACITY);
             c0 = -1;
         }
@@ -781,8 +854,117 @@ __global__ void __launch_bounds__(T, 4) k_search(const __grid_constant__ SearchA
     }
     __syncthreads();
     const int cand0 = s_cand0;
-    if (active) a.seed_cand[s] = cand0 >= 0 ? make_int4(cand0 + base, n_cand, e, 0) : make_int4(0, 0, e, 0);
-    if (cand0 >= 0) {
+    if (!F && active) a.seed_cand[s] = cand0 >= 0 ? make_int4(cand0 + base, n_cand, e, 0) : make_int4(0, 0, e, 0);
+    if (F) {
+        // fused: rounds of T candidates; each merges into its seed's minimum,
+        // then (after the round's barrier) the candidate holding the minimum
+        // keeps its fit beside it.  A later round's merge can only lower the
+        // minimum, and its holder then writes its own fit after that round's
+        // barrier, so the fit kept is always the minimum's.
+        for (int c0 = 0; c0 < total; c0 += T) {
+            const int c = c0 + tid;
+            KeyIds mine{kNoKey, 0ull};
+            float4 fw = make_float4(0.f, 0.f, 0.f, 0.f);
+            int o = 0;
+            if (c < total) {
+                int lo = 0, hi = T;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_base[mid] <= c) lo = mid;
+                    else hi = mid;
+                }
+                o = lo;
+                int k = c - s_base[o];
+                int j = 0;
+                while (j < kK1Max - 1 && k >= s_nc[j][o]) {
+                    k -= s_nc[j][o];
+                    ++j;
+                }
+                const int nv = s_sel[j][4][o] != kNone ? 2 : 1;
+                const int iu = k / nv, iv = k - iu * nv;
+                const uint16_t a0 = s_sel[j][0][o], u0 = s_sel[j][1 + iu][o], v0 = s_sel[j][3 + iv][o];
+                int loc[4];
+                loc[0] = a0 == kNone ? -1 : a0;
+                loc[1] = u0 == kNone ? -1 : u0;
+                loc[2] = v0 == kNone ? -1 : v0;
+                loc[3] = s_bx[j][o];
+                const SeedCtx sc = s_sc[o];
+                const CandFit f = fit_candidate(g, sc, X0, loc);
+                float phi[16];
+                phi[0] = f.xr * 1e-3f;
+                phi[1] = f.yr * 1e-3f;
+                phi[2] = f.t;
+                phi[3] = sc.ty;
+                phi[4] = 1e3f * f.qop;
+                phi[5] = f.chi2 / (float)f.ndof;
+                phi[6] = 1e3f * sc.qop;
+                phi[7] = sc.chi2;
+#pragma unroll
+                for (int l = 0; l < 4; ++l) phi[8 + l] = f.res[l] * g.inv_sigma_hit;
+                phi[12] = 0.25f * (float)f.nh;
+                phi[13] = V == 1 ? fabsf(X0[loc[0]] - dv1_ua(g, sc, X0, loc[3])) / P.dv1_w_tri
+                                 : fabsf(X0[loc[3]] - sc.u_bx) / sc.w1;
+                phi[14] = sc.tx;
+                phi[15] = sc.ty;
+                // what the pick needs is formed before the network, so that
+                // little else is live while it runs
+#pragma unroll
+                for (int l = 0; l < 4; ++l)
+                    mine.ids = (mine.ids << 16) | (loc[l] >= 0 ? (unsigned long long)__ldg(H.perm + loc[l]) : 0xFFFFull);
+                fw = make_float4(f.xr, f.t, f.qop, f.chi2);
+                const float chi2_ndof = phi[5];
+                const float lg = mlp_logit_fp32<16, 32, 32>(a.nn, phi);
+                if (P.pick_chi2) mine.key = pack_key(chi2_ndof, lg);
+                else if (lg < P.thr_logit) mine.key = pack_key(lg, fw.w);
+                if (mine.key != kNoKey) keyids_min(&s_pb.c.best[o], mine);
+            }
+            __syncthreads();
+            if (mine.key != kNoKey) {
+                const KeyIds b = s_pb.c.best[o];
+                if (b.key == mine.key && b.ids == mine.ids) s_pb.c.win[o] = fw;
+            }
+        }
+        __syncthreads();
+        // each seed's winner as k_pick writes it: the 64-byte record (staged
+        // in s_sel, written below as contiguous 16-byte chunks), the pick key
+        // and the hit ids; a seed without one gets no record
+        int4 *s_rec = reinterpret_cast<int4 *>(&s_sel[0][0][0]);
+        bool have = false;
+        if (active) {
+            const KeyIds b = s_pb.c.best[tid];
+            have = b.key != kNoKey;
+            float lg = 0.f;
+            if (have) lg = P.pick_chi2 ? unord_f32((unsigned)b.key) : unord_f32((unsigned)(b.key >> 32));
+            if (have && P.pick_chi2 && !(lg < P.thr_logit)) have = false;
+            int hid[4];
+            int nh = 0;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const unsigned q = (unsigned)(b.ids >> (16 * (3 - l))) & 0xFFFFu;
+                hid[l] = have && q != 0xFFFFu ? h0 + (int)q : -1;
+                nh += hid[l] >= 0;
+            }
+            a.key_ws[s] = have ? b.key : kNoKey;
+            a.hit_ws[s] = make_int4(hid[0], hid[1], hid[2], hid[3]);
+            if (have) {
+                const float4 fw = s_pb.c.win[tid];
+                const SeedCtx &sc = s_sc[tid];
+                const float yr = fmaf(sc.ty, g.z_ref - sc.zm, sc.ym);
+                // ds_track: event, seed, hit[4], x, y, tx, ty, qop, chi2, ndof, nn, flags, n_candidates
+                s_rec[4 * tid + 0] = make_int4(e, s, hid[0], hid[1]);
+                s_rec[4 * tid + 1] = make_int4(hid[2], hid[3], __float_as_int(fw.x), __float_as_int(yr));
+                s_rec[4 * tid + 2] = make_int4(__float_as_int(fw.y), __float_as_int(sc.ty), __float_as_int(fw.z),
+                                               __float_as_int(fw.w));
+                s_rec[4 * tid + 3] = make_int4(nh - 1, __float_as_int(sigmoid_fast(lg)), 0, n_cand);
+            }
+        }
+        s_nc[0][tid] = have ? 1 : 0;
+        __syncthreads();
+        int4 *dst = reinterpret_cast<int4 *>(a.trk_ws + s_begin);
+        for (int k = tid; k < 4 * (s_end - s_begin); k += T)
+            if (s_nc[0][k >> 2]) dst[k] = s_rec[k];
+    }
+    if (!F && cand0 >= 0) {
 
     // fit + network inputs, one candidate per thread; candidate c of the CTA
     // decodes to (seed, UTbX rank j, stereo options) in enumeration order
@@ -849,17 +1031,19 @@ cudaError_t init_search_attributes()
 {
     // shared memory, not L1, limits residency: ask for the largest carveout
     const int smem = (int)(sizeof(uint16_t) * table_stride_for(kMaxSectors) + sizeof(float) * (kStageHitsMax + 4));
-    cudaFuncAttributes fa;
     int dev = 0, optin = 0;
-    cudaError_t e = cudaFuncGetAttributes(&fa, k_search<0>);
-    cudaFuncAttributes fa1;
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa1, k_search<1>);
-    if (e == cudaSuccess && fa1.sharedSizeBytes > fa.sharedSizeBytes) fa = fa1;
+    size_t static_max = 0;
+    cudaError_t e = cudaSuccess;
+    for (auto fn : {k_search<0, false>, k_search<1, false>, k_search<0, true>, k_search<1, true>}) {
+        cudaFuncAttributes fa;
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+        if (e == cudaSuccess && fa.sharedSizeBytes > static_max) static_max = fa.sharedSizeBytes;
+    }
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    if ((size_t)smem + fa.sharedSizeBytes > (size_t)optin) return cudaErrorInvalidValue;
-    for (auto fn : {k_search<0>, k_search<1>}) {
+    if ((size_t)smem + static_max > (size_t)optin) return cudaErrorInvalidValue;
+    for (auto fn : {k_search<0, false>, k_search<1, false>, k_search<0, true>, k_search<1, true>}) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     }
@@ -877,8 +1061,13 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof)
     if (grid > items_max) grid = items_max;
     const size_t smem = sizeof(uint16_t) * a.g.table_stride + sizeof(float) * (a.stage_hits + 4);
     prof->begin("k_search", st);
-    if (a.p.variant == 1) k_search<1><<<grid, T, smem, st>>>(a);
-    else k_search<0><<<grid, T, smem, st>>>(a);
+    if (a.fused) {
+        if (a.p.variant == 1) k_search<1, true><<<grid, T, smem, st>>>(a);
+        else k_search<0, true><<<grid, T, smem, st>>>(a);
+    } else {
+        if (a.p.variant == 1) k_search<1, false><<<grid, T, smem, st>>>(a);
+        else k_search<0, false><<<grid, T, smem, st>>>(a);
+    }
     prof->end(st);
     return cudaGetLastError();
 }

@@ -13,12 +13,18 @@
 // pairs whose opening satisfies sin^2 < eps_par and whose FP32 DOCA is near
 // or below the cut are re-solved in FP64 (flag bit 0).
 //
-// One CTA per event.  Tracks are staged in shared memory; opposite-charge
-// partner lists make every thread's pair valid, enumerated in (i, j) order.
-// Kept vertices of each 256-pair chunk are ranked by a block scan and written
-// to a pool slice reserved with one atomicAdd; their position inside the event
-// is recorded, so the scatter kernel places them in (event, i, j) order
-// whatever order the pool was filled in.
+// Small-capacity launch: one CTA per event (up to 512 tracks).  Tracks are
+// staged in shared memory; opposite-charge partner lists make every thread's
+// pair valid, enumerated in (i, j) order.  Kept vertices of each segment are
+// ranked by a block scan and written to a pool slice reserved with one
+// atomicAdd; their position inside the event is recorded, so the scatter
+// kernel places them in (event, i, j) order whatever order the pool was
+// filled in.  Larger events are listed with their pair count (npos x nneg).
+// Large-capacity launch: its work items are (listed event, segment of 65536
+// pairs of its (i, j) enumeration), so that the pairs of one large event are
+// spread over many SMs; an item ranks its kept vertices inside the item, and
+// the launch's last CTA turns per-item counts into each item's offset inside
+// its event.
 #include "ds_args.cuh"
 
 namespace ds {
@@ -26,13 +32,12 @@ namespace ds {
 constexpr int kVtxThreads = 256;
 constexpr int kVtxLargeThreads = 1024;  // the large-capacity launch: one CTA per SM, all of its warps
 constexpr int kVtxSmallCap = 512;
-constexpr int kVtxOrderMax = 4096;    // large events ordered largest first, up to this many
 constexpr int kVtxCtasPerSm = 4;      // resident CTAs of the small-capacity launch per SM
 // pairs per two-phase segment and candidate results kept in shared memory per
 // segment: larger for the large-capacity launch (one CTA per SM), whose
 // events have up to millions of pairs
 template <bool LARGE> struct VtxSeg {
-    static constexpr int seg = LARGE ? 65536 : 8192;
+    static constexpr int seg = LARGE ? kVtxLargeSeg : 8192;
     static constexpr int store = LARGE ? 2048 : 1024;
 };
 
@@ -258,44 +263,38 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
     const DevGeom &g = a.g;
     const DevParams &P = a.p;
     const bool straight = g.gamma0 == 0.f && g.gamma1 == 0.f;
-    __shared__ int s_e;
+    __shared__ int s_e, s_item, s_seg;
     // the small-capacity launch pulls every event from its queue and lists the
-    // larger ones; the large-capacity launch pulls from that list only
-    const int n_mine = LARGE ? min(*(volatile const int *)&a.cnt->n_large, a.n_events) : a.n_events;
+    // larger ones; the large-capacity launch pulls (listed event, pair
+    // segment) items, numbered by the small launch's last CTA
+    const int n_list = LARGE ? min(*(volatile const int *)&a.cnt->n_large, a.n_events) : 0;
     // no large event: the small-capacity launch has laid out the offsets already
-    if (LARGE && n_mine == 0) return;
-    // the large-capacity launch takes its events largest first (track count,
-    // then list position), so that the biggest ones do not start last: every
-    // CTA ranks the listed events the same way (up to kVtxOrderMax of them;
-    // beyond that, list order)
-    __shared__ uint16_t s_order[LARGE ? kVtxOrderMax : 1];
-    if (LARGE && n_mine <= kVtxOrderMax) {
-        int *s_nt = reinterpret_cast<int *>(s_dyn);   // free until the first event
-        const int tcap0 = min(__ldg(a.n_tracks), a.trk_capacity);
-        for (int j = threadIdx.x; j < n_mine; j += blockDim.x) {
-            const int ej = __ldcg(a.large_list + j);
-            s_nt[j] = min(__ldg(a.trk_off + ej + 1), tcap0) - min(__ldg(a.trk_off + ej), tcap0);
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < n_mine; j += blockDim.x) {
-            const int nj = s_nt[j];
-            int rank = 0;
-            for (int m = 0; m < n_mine; ++m) {
-                const int nm = s_nt[m];
-                rank += nm > nj || (nm == nj && m < j);
-            }
-            s_order[rank] = (uint16_t)j;
-        }
-        __syncthreads();
-    }
+    if (LARGE && n_list == 0) return;
+    const int n_items = LARGE ? min(__ldcg(a.large_item_off + n_list), a.max_items) : 0;
     for (;;) {
-    if (threadIdx.x == 0) {
-        const int k = atomicAdd(&a.cnt->vtx_queue[LARGE ? 1 : 0], 1);
-        s_e = k < n_mine ? (LARGE ? __ldcg(a.large_list + (n_mine <= kVtxOrderMax ? (int)s_order[k] : k)) : k)
-                         : a.n_events;
+    if (LARGE) {
+        if (threadIdx.x < 32) {
+            int k = 0;
+            if (threadIdx.x == 0) k = atomicAdd(&a.cnt->vtx_queue[1], 1);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (k < n_items) {
+                const int j = warp_find_segment(a.large_item_off, n_list, k);
+                if (threadIdx.x == 0) {
+                    s_e = __ldcg(a.large_list + j);
+                    s_item = k;
+                    s_seg = k - __ldcg(a.large_item_off + j);
+                }
+            } else if (threadIdx.x == 0) {
+                s_e = a.n_events;
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        const int k = atomicAdd(&a.cnt->vtx_queue[0], 1);
+        s_e = k < a.n_events ? k : a.n_events;
     }
     __syncthreads();
     const int e = s_e;
+    const int item = LARGE ? s_item : 0, seg_k = LARGE ? s_seg : 0;
     __syncthreads();
     if (e >= a.n_events) break;
     const int tcap = min(__ldg(a.n_tracks), a.trk_capacity);
@@ -305,9 +304,25 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
     // the small-capacity launch takes events with nt <= kVtxSmallCap, the
     // large one the rest (clamped to its capacity, flagged)
     const bool mine = LARGE ? nt > kVtxSmallCap : nt <= kVtxSmallCap;
-    if (!LARGE && !mine && threadIdx.x == 0) a.large_list[atomicAdd(&a.cnt->n_large, 1)] = e;
+    if (!LARGE && !mine) {
+        // list the event with its opposite-charge pair count (of the tracks
+        // the large-capacity launch stages)
+        const int ntc = min(nt, kMaxVertexTracks);
+        int cnt = 0;
+        for (int i = threadIdx.x; i < ntc; i += blockDim.x) {
+            const float q = a.tracks[t0 + i].qop;
+            cnt += (q > 0.f ? 1 : 0) | (q < 0.f ? 0x10000 : 0);
+        }
+        int tot;
+        block_exclusive_scan(cnt, s_scan, &tot);
+        if (threadIdx.x == 0) {
+            const int slot = atomicAdd(&a.cnt->n_large, 1);
+            a.large_list[slot] = e;
+            a.large_pairs[slot] = (tot & 0xffff) * (tot >> 16);
+        }
+    }
     if (LARGE && nt > CAP) {
-        if (threadIdx.x == 0) raise_flag(a.cnt, DS_FLAG_VERTEX_CAPACITY);
+        if (threadIdx.x == 0 && seg_k == 0) raise_flag(a.cnt, DS_FLAG_VERTEX_CAPACITY);
         nt = CAP;
     }
     int ev_count = 0;
@@ -351,7 +366,10 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
         if (threadIdx.x == 0) s_row[nt] = run;
         __syncthreads();
         const int npairs = run;
-        if (threadIdx.x == 0 && npairs > 0) atomicAdd(&a.cnt->n_pairs, (unsigned long long)npairs);
+        // the pairs this CTA solves: all of the event's, or one item's segment
+        const int p_begin = LARGE ? min(seg_k * kVtxSeg, npairs) : 0;
+        const int p_end = LARGE ? min(p_begin + kVtxSeg, npairs) : npairs;
+        if (threadIdx.x == 0 && p_end > p_begin) atomicAdd(&a.cnt->n_pairs, (unsigned long long)(p_end - p_begin));
         // pair p of the current segment (first pair seg0) -> (i, j), i < j,
         // opposite charges, (i, j) order: from the row of p's mask word, a
         // short walk over the rows starting inside the word
@@ -364,8 +382,8 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
         int n64 = 0;
         bool store = false;
-        for (int seg0 = 0; seg0 < npairs; seg0 += kVtxSeg) {
-            const int nseg = min(kVtxSeg, npairs - seg0);
+        for (int seg0 = p_begin; seg0 < p_end; seg0 += kVtxSeg) {
+            const int nseg = min(kVtxSeg, p_end - seg0);
             const int nwords = (nseg + 31) >> 5;
             const int seg1 = seg0 + nseg;
             // each row records the mask words whose first pair it holds
@@ -485,6 +503,7 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
                     dst[0] = make_int4(e, t0 + i, t0 + j, __float_as_int(o.x));
                     dst[1] = make_int4(__float_as_int(o.y), __float_as_int(o.z), __float_as_int(o.doca), (int)o.flags);
                     a.pool_pos[slot] = ev_count + k;
+                    if (LARGE) a.pool_item[slot] = item;
                 } else {
                     raise_flag(a.cnt, DS_FLAG_VERTEX_CAPACITY);
                 }
@@ -495,23 +514,54 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
         if (n64) atomicAdd(&a.cnt->n_pairs_fp64, (unsigned long long)n64);
     }
 
-    if (threadIdx.x == 0 && mine) a.count_ws[e] = ev_count;
-    }   // event loop
+    if (threadIdx.x == 0 && mine) {
+        if (LARGE) a.item_count[item] = ev_count;
+        else a.count_ws[e] = ev_count;
+    }
+    }   // event / item loop
 
-    // the last CTA of the launch that finishes the batch turns the per-event
-    // counts into offsets: the small-capacity launch when it listed no large
-    // event, otherwise the large-capacity one
+    // the last CTA of the small-capacity launch records how many pool slots
+    // its vertices took and numbers the large launch's items; the last CTA of
+    // the launch that finishes the batch turns the per-event counts into
+    // offsets: the small-capacity launch when it listed no large event,
+    // otherwise the large-capacity one, after the items' offsets
     if (threadIdx.x == 0) {
         __threadfence();
         unsigned int *done = LARGE ? &a.cnt->done_vtx_large : &a.cnt->done_vtx;
         const unsigned int t = atomicAdd(done, 1u);
         s_last = t == gridDim.x - 1;
         if (s_last) *done = 0;
-        if (!LARGE && s_last) s_last = *(volatile const int *)&a.cnt->n_large == 0;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    if (!LARGE) {
+        const int n_large = *(volatile const int *)&a.cnt->n_large;
+        if (threadIdx.x == 0) a.cnt->pool_small = *(volatile const int *)&a.cnt->pool_used;
+        if (n_large > 0) {
+            const int tot = block_offsets_f(
+                [&a](int j) { return (__ldcg(a.large_pairs + j) + VtxSeg<true>::seg - 1) / VtxSeg<true>::seg; },
+                n_large, a.large_item_off, s_scan);
+            if (threadIdx.x == 0) {
+                a.large_item_off[n_large] = tot;
+                if (tot > a.max_items) raise_flag(a.cnt, DS_FLAG_VERTEX_CAPACITY);
+            }
+            return;
+        }
+    } else {
+        // per listed event: each item's offset inside the event, the event's count
+        for (int j = threadIdx.x; j < n_list; j += blockDim.x) {
+            const int i0 = min(__ldcg(a.large_item_off + j), n_items), i1 = min(__ldcg(a.large_item_off + j + 1), n_items);
+            int run = 0;
+            for (int it = i0; it < i1; ++it) {
+                a.item_base[it] = run;
+                run += __ldcg(a.item_count + it);
+            }
+            a.count_ws[__ldcg(a.large_list + j)] = run;
+        }
+        __syncthreads();
+        __threadfence();
+    }
     const int run = block_offsets(a.count_ws, a.n_events, a.vtx_off, s_scan);
     if (threadIdx.x == 0) {
         a.vtx_off[a.n_events] = run;
@@ -526,11 +576,13 @@ __global__ void __launch_bounds__(256) k_scatter_vertices(const __grid_constant_
 {
     // records move as two 16-byte chunks (pool and output are 16-byte aligned)
     const int used = min(*(volatile const int *)&a.cnt->pool_used, a.pool_cap);
+    const int small = *(volatile const int *)&a.cnt->pool_small;   // slots of the small-capacity launch
     const int4 *src = reinterpret_cast<const int4 *>(a.pool);
     int4 *dst = reinterpret_cast<int4 *>(a.out);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < used; k += gridDim.x * blockDim.x) {
         const int4 lo = __ldcs(src + 2 * k), hi = __ldcs(src + 2 * k + 1);
-        const int pos = __ldg(a.vtx_off + lo.x) + __ldcs(a.pool_pos + k);
+        int pos = __ldg(a.vtx_off + lo.x) + __ldcs(a.pool_pos + k);
+        if (k >= small) pos += __ldg(a.item_base + __ldcs(a.pool_item + k));
         if (pos < a.capacity) {
             dst[2 * pos] = lo;
             dst[2 * pos + 1] = hi;
@@ -559,7 +611,9 @@ cudaError_t launch_vertex(const VertexArgs &a0, const ScatterVtxArgs &sa, int sm
     VertexArgs a = a0;
     const size_t sm_small = vtx_smem<false>(kVtxSmallCap), sm_large = vtx_smem<true>(kMaxVertexTracks);
     const int g_small = a.n_events < kVtxCtasPerSm * sm_count ? a.n_events : kVtxCtasPerSm * sm_count;
-    const int g_large = a.n_events < sm_count ? a.n_events : sm_count;
+    // persistent over (event, pair segment) items: at most kVtxItemsPerEvent per event
+    const long long items_max = (long long)kVtxItemsPerEvent * a.n_events;
+    const int g_large = items_max < sm_count ? (int)items_max : sm_count;
     prof->begin("k_vertex_small", st);
     k_vertex<kVtxSmallCap, false><<<g_small, kVtxThreads, sm_small, st>>>(a);
     prof->end(st);

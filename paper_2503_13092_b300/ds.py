@@ -49,7 +49,7 @@ class ds_params(C.Structure):
                 ("pick_chi2", C.c_int32), ("clone_kill", C.c_int32), ("training", C.c_int32),
                 ("nr_max_iter", C.c_int32), ("mlp_precision", C.c_int32), ("fault_inject", C.c_int32),
                 ("cand_per_seed", C.c_int32), ("variant", C.c_int32), ("dv1_dtx_max", C.c_double),
-                ("dv1_w_tri", C.c_double)]
+                ("dv1_w_tri", C.c_double), ("fuse_network", C.c_int32), ("reserved2", C.c_int32)]
 
 
 class ds_event_batch(C.Structure):

@@ -400,14 +400,43 @@ def test_exact_window_edges(torch_cuda, case):
         k1 = 4 if case == "first_k4" else 10
         ev, cfg = sel.first_window_event(), sel.edge_config(k1=k1, w2=10.0)
         want = sorted((0, 1, -1, hb) for hb in sel.FIRST_WINDOW_KEPT[k1])
-    d = make(torch_cuda, cfg, w)
-    g = d.run(ev)
-    assert g["stats"]["status"] == 0, g["stats"]
-    c = d.candidates(64)
-    assert sorted(tuple(h) for h in c["hits"].tolist()) == want
-    o = oracle.reconstruct(ev, cfg, w)
-    gp = parity.gpu_per_seed(g, 1)
-    assert gp["has"][0] == (o["status"][0] == 2) and gp["hits"][0].tolist() == o["hits"][0].tolist()
+    from paper_2503_13092_b300 import ds
+    for fuse in (0, 1):          # candidates through the buffer, then scored inside the search
+        keep = not fuse
+        d = make(torch_cuda, cfg, w, fuse_network=fuse)
+        dev = d.to_device(ev)
+        out = d.alloc_tracks(1, 4)
+        d.reconstruct(dev, out)
+        if keep:
+            c = d.candidates(64)          # before the counters are cleared
+            assert sorted(tuple(h) for h in c["hits"].tolist()) == want
+        st = d.sync()
+        assert st["status"] == 0 and st["n_candidates"] == len(want), st
+        g = ds.decode(out)
+        o = oracle.reconstruct(ev, cfg, w)
+        gp = parity.gpu_per_seed(g, 1)
+        assert gp["has"][0] == (o["status"][0] == 2) and gp["hits"][0].tolist() == o["hits"][0].tolist()
+        d.close()
+
+
+@pytest.mark.parametrize("variant,pick", [(0, "nn"), (0, "chi2"), (1, "nn"), (1, "chi2")])
+def test_fused_equals_unfused(torch_cuda, weights, variant, pick):
+    """The candidate buffer with the separate network and pick kernels
+    (default) against the network and the pick inside the search kernel
+    (fuse_network = 1): byte-identical track records, offsets and vertices."""
+    b = synth.config_batch("c2", n_events=60)
+    over = dict(pick_chi2=1, nn_threshold=0.9) if pick == "chi2" else {}
+    cfg = synth.default_config(variant=variant, **over)
+    d = make(torch_cuda, cfg, weights)
+    g0 = d.run(b)
+    d.set_params(fuse_network=1)
+    g1 = d.run(b)
+    assert g0["stats"]["status"] == 0 and g1["stats"]["status"] == 0
+    assert g0["stats"]["n_candidates"] == g1["stats"]["n_candidates"]
+    assert g0["n_tracks"] == g1["n_tracks"] > 1000
+    assert g0["tracks"].tobytes() == g1["tracks"].tobytes()
+    assert np.array_equal(g0["trk_off"], g1["trk_off"])
+    assert g0["vertices"].tobytes() == g1["vertices"].tobytes()
 
 
 @pytest.mark.parametrize("pick", ["nn", "chi2"])
@@ -432,3 +461,62 @@ def test_chi2_margin_study(torch_cuda, weights, pick):
                                           unexcused_scale1=len(rep1["unexcused"]),
                                           max_rel_chi2=rep.get("max_rel_chi2"), rel_chi2_q=rep.get("rel_chi2_q")))
     parity.assert_tracks_match(rep)
+
+
+def _vertex_only(torch_cuda, cfg, weights, sizes, seed):
+    """Track records written directly (events of the given track counts, each
+    track from one of a few common points so that many pairs are kept) and
+    ds_vertex on them; returns the decoded GPU result."""
+    from paper_2503_13092_b300 import ds
+    rng = np.random.default_rng(seed)
+    n = int(sum(sizes))
+    t = np.zeros(n, ds.TRACK_DTYPE)
+    t["event"] = np.repeat(np.arange(len(sizes)), sizes)
+    t["seed"] = np.arange(n)
+    t["hit"] = -1
+    zr = cfg["z_ref"]
+    k = 0
+    for e, m in enumerate(sizes):
+        pts = np.stack([rng.uniform(-30, 30, 12), rng.uniform(-30, 30, 12), rng.uniform(0, 2000, 12)], 1)
+        for q in range(m):
+            p = pts[rng.integers(12)]
+            tx, ty = rng.uniform(-0.2, 0.2, 2)
+            dz = zr - p[2]
+            t["x"][k] = p[0] + tx * dz + rng.normal(0, 0.3)
+            t["y"][k] = p[1] + ty * dz + rng.normal(0, 0.3)
+            t["tx"][k], t["ty"][k] = tx, ty
+            t["qop"][k] = rng.choice([-1.0, 1.0]) * rng.uniform(1e-5, 5e-4)
+            k += 1
+    t["ndof"] = 2
+    trk_off = np.zeros(len(sizes) + 1, np.int32)
+    trk_off[1:] = np.cumsum(sizes)
+    d = make(torch_cuda, cfg, weights)
+    dev = f"cuda:{d.device}"
+    out = d.alloc_tracks(len(sizes), n)
+    out["tracks"].copy_(torch_cuda.from_numpy(t.view(np.uint8).reshape(n, 64)).to(dev))
+    out["trk_off"].copy_(torch_cuda.from_numpy(trk_off).to(dev))
+    out["n_tracks"].fill_(n)
+    from paper_2503_13092_b300.ds import ds_tracks, _ptr
+    out["_struct"] = ds_tracks(_ptr(out["tracks"]), _ptr(out["trk_off"]), _ptr(out["n_tracks"]), n, len(sizes))
+    vout = d.alloc_vertices(len(sizes), 1 << 22)
+    d.vertex(out, vout)
+    st = d.sync()
+    g = ds.decode(out, vout)
+    d.close()
+    return g, st
+
+
+def test_large_event_vertexing(torch_cuda, weights):
+    """Events above the small launch's 512 tracks are vertexed as (event, pair
+    segment) work items spread over the SMs: events of 513 to 4096 tracks (1
+    to 64 segments each) between small ones; the vertices, in (event, i, j)
+    order, equal the oracle vertexer fed the same track records."""
+    cfg = synth.default_config()
+    sizes = [3, 700, 40, 1500, 0, 513, 512, 2600, 1, 4096, 90]
+    g, st = _vertex_only(torch_cuda, cfg, weights, sizes, seed=3)
+    assert st["status"] == 0, st
+    assert st["n_pairs"] == sum((np.sum(g["tracks"]["qop"][a:b] > 0) * np.sum(g["tracks"]["qop"][a:b] < 0))
+                                for a, b in zip(g["trk_off"][:-1], g["trk_off"][1:]))
+    assert g["n_vertices"] > 100000
+    vrep = parity.compare_vertices(cfg, g)
+    parity.assert_vertices_match(vrep)

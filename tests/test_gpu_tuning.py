@@ -52,10 +52,10 @@ def run_with(d, ds, dev, tuning):
 def test_outputs_do_not_depend_on_tuning(torch_cuda, weights):
     from paper_2503_13092_b300 import ds
     b = mixed_batch()
-    assert np.diff(b["hit_off"]).max() > 2 * 5632      # larger than the default staging buffer
+    assert np.diff(b["hit_off"]).max() > 2 * 5120      # larger than the default staging buffer
     d = ds.Downstream(synth.default_config(), weights)
     dev = d.to_device(b)
-    shapes = [(128, 4, 2, 5632), (32, 1, 1, 0), (64, 3, 8, 32768), (1, 2, 16, 2048), (96, 4, 4, 47104)]
+    shapes = [(128, 4, 2, 5632), (32, 1, 1, 0), (64, 3, 8, 32768), (1, 2, 16, 2048), (96, 4, 4, 46080)]
     ref = None
     for chunk, ctas, group, stage in shapes:
         t = ds.ds_tuning(chunk, ctas, group, stage)
@@ -73,7 +73,7 @@ def test_invalid_tuning_refused(torch_cuda, weights):
     d = ds.Downstream(synth.default_config(), weights)
     before = ds.ds_get_tuning(d.ctx).as_dict()
     for bad in [(0, 4, 2, 5632), (129, 4, 2, 5632), (128, 0, 2, 5632), (128, 5, 2, 5632), (128, 4, 0, 5632),
-                (128, 4, 17, 5632), (128, 4, 2, -1), (128, 4, 2, 47105)]:
+                (128, 4, 17, 5632), (128, 4, 2, -1), (128, 4, 2, 46081)]:
         with pytest.raises(ds.DSError):
             ds.ds_set_tuning(d.ctx, ds.ds_tuning(*bad))
     assert ds.ds_get_tuning(d.ctx).as_dict() == before
