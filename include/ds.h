@@ -161,10 +161,18 @@ typedef struct {
     int32_t n_events;
     int32_t n_seeds;          /* = seed_off[n_events] (host copy, used for launch sizes) */
     int32_t n_hits;           /* = hit_off[n_events] */
-    int32_t reserved0;
+    int32_t flags;            /* 0, or DS_BATCH_CAPACITY */
     const int32_t *seed_off;  /* [n_events + 1], seed_off[0] = 0, non-decreasing */
     const int32_t *hit_off;   /* [n_events + 1], hit_off[0] = 0, non-decreasing */
 } ds_event_batch;
+
+/* ds_event_batch.flags: n_seeds and n_hits are the capacities of the seed and
+ * hit arrays, and the totals are seed_off[n_events] <= n_seeds and
+ * hit_off[n_events] <= n_hits, read on the device.  With it, one launch
+ * sequence (a captured CUDA graph) serves every batch that fits those
+ * capacities and n_events (events beyond the data: repeat the last offsets,
+ * i.e. empty events).  Launch sizes follow the capacities. */
+enum { DS_BATCH_CAPACITY = 1 };
 
 /* SciFi seeds, device SoA float32 [n_seeds] each, grouped by event. */
 typedef struct {

@@ -47,7 +47,16 @@ typedef struct {
                                    a batch is admitted only when its buffers fit (0: 25 % of
                                    the device memory free at creation) */
     int32_t mlp_precision;      /* DS_MLP_FP32 / DS_MLP_BF16 / DS_MLP_FP8 for every batch */
-    int32_t reserved0;
+    int32_t graphs;             /* 1 (default): every slot keeps fixed device buffers sized to
+                                   the batch limits, taken from hbm_budget at creation, and runs
+                                   each batch's kernels as one replay of a CUDA graph captured at
+                                   creation for that slot and the batch's event-count bucket
+                                   (powers of two up to max_batch_events; a batch is padded with
+                                   empty events to its bucket, see DS_BATCH_CAPACITY).  A batch
+                                   is admitted when a slot is free.  0, or when the slots'
+                                   buffers do not fit hbm_budget: buffers per batch from the
+                                   budget (admission by free device memory), kernels launched
+                                   one by one.  Results are identical. */
 } ds_server_config;
 
 /* One request: n_events events with their seeds and hits, HOST memory in the
@@ -95,6 +104,8 @@ typedef struct {
     double worker_launch_s;              /* worker thread time spent enqueueing batches */
     double worker_finish_s;              /* ... returning results to the requests */
     double worker_wall_s;                /* worker thread lifetime so far */
+    int32_t graphs;                      /* 1: batches replay captured CUDA graphs */
+    int32_t graphs_captured;             /* graphs instantiated at creation (slots x buckets) */
 } ds_server_stats;
 
 DS_API void ds_server_default_config(ds_server_config *cfg);

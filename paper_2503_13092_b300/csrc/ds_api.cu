@@ -465,6 +465,7 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     if (!ctx->has_geom || !ctx->has_nn) return fail(ctx, DS_ERR_NOT_READY, "geometry or weights not loaded");
     if (b->n_events < 0 || b->n_seeds < 0 || b->n_hits < 0 || out->capacity < 0)
         return fail(ctx, DS_ERR_ARG, "negative size");
+    if (b->flags & ~DS_BATCH_CAPACITY) return fail(ctx, DS_ERR_ARG, "unknown batch flags");
     if (b->n_events > 0 && (!b->seed_off || !b->hit_off || !out->trk_off || !out->n_tracks))
         return fail(ctx, DS_ERR_ARG, "null offsets or outputs");
     if (b->n_seeds > 0 && (!sd->x || !sd->y || !sd->tx || !sd->ty || !sd->qop || !sd->chi2))
@@ -500,6 +501,7 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     ba.bins = ctx->bins;
     ba.item_off = ctx->item_off;
     ba.chunk = ctx->tune.search_chunk;
+    ba.capacity_sizes = (b->flags & DS_BATCH_CAPACITY) ? 1 : 0;
     ba.cnt = ctx->d_cnt;
     DS_CUDA(ds::launch_bucket(ba, st, &ctx->prof), "bucket kernel");
 

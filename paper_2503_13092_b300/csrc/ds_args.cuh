@@ -34,6 +34,7 @@ struct BucketArgs {
     uint16_t *bins;
     int *item_off;         // [n_events + 1]
     int chunk;             // max seeds per search work item (<= kSearchThreads)
+    int capacity_sizes;    // 1: n_seeds, n_hits are capacities (DS_BATCH_CAPACITY)
     DevCounters *cnt;
 };
 

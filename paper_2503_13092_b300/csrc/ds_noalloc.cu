@@ -90,6 +90,7 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
     using namespace ds;
     if (!geom || !params || !weights || !b || !sd || !ht || !out) return DS_ERR_ARG;
     if (b->n_events < 0 || b->n_seeds < 0 || b->n_hits < 0 || out->capacity < 0) return DS_ERR_ARG;
+    if (b->flags & ~DS_BATCH_CAPACITY) return DS_ERR_ARG;
     if (b->n_events > kNAEvents || b->n_seeds > kNASeeds || b->n_hits > kNAHits) return DS_ERR_CAPACITY;
     // candidates are limited to kNACandPerSeed per seed on average (DS_FLAG_CAND_CAPACITY beyond)
     if (b->n_events > 0 && (!b->seed_off || !b->hit_off || !out->trk_off || !out->n_tracks)) return DS_ERR_ARG;
@@ -137,6 +138,7 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         ba.bins = reinterpret_cast<uint16_t *>(base + kOffBins);
         ba.item_off = reinterpret_cast<int *>(base + kOffItemOff);
         ba.chunk = kSearchThreads;
+        ba.capacity_sizes = (b->flags & DS_BATCH_CAPACITY) ? 1 : 0;
         ba.cnt = cnt;
         if (launch_bucket(ba, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
 

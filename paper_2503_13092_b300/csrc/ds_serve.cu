@@ -13,6 +13,12 @@
 // Each slot owns a library context (workspaces reserved at creation, so no
 // allocation or device-wide synchronisation happens while serving) and a
 // non-blocking stream; batches in different slots overlap on the device.
+// Graph mode (default when the budget holds it): each slot also owns fixed
+// device buffers for the largest batch, and a batch's kernels (reconstruct,
+// vertex, renumber) are one replay of a CUDA graph captured at creation for
+// the slot and the batch's event-count bucket (a power of two; the batch is
+// padded with empty events and launched with its arrays' capacities,
+// DS_BATCH_CAPACITY); only the copies are issued per batch.
 // Results are renumbered into each request's own event, seed, hit and track
 // indices on the GPU (k_renumber, on the slot's stream after ds_vertex) and
 // copied straight into the caller's output buffers.
@@ -113,7 +119,7 @@ struct Seg {
 
 // Device buffers of one batch inside the arena, in this order.
 struct BatchLayout {
-    size_t seed_off, hit_off, seed[6], hit[3], layer, trk, trk_off, ntrk, vtx, vtx_off, nvtx, seg, bytes;
+    size_t seed_off, hit_off, seed[6], hit[3], layer, trk, trk_off, ntrk, vtx, vtx_off, nvtx, seg, nseg, bytes;
     BatchLayout(int E, int S, int H, int V)
     {
         size_t o = 0;
@@ -130,6 +136,7 @@ struct BatchLayout {
         vtx_off = take(4 * (size_t)(E + 1));
         nvtx = take(4);
         seg = take(16 * (size_t)E);       // at most one segment per event
+        nseg = take(4);                   // the number of segments (read on the device)
         bytes = o;
     }
 };
@@ -145,10 +152,17 @@ struct Slot {
     size_t off = 0, bytes = 0;
     char *dev = nullptr;               // arena base + off
     int n_t = 0, n_v = 0;
+    // graph mode: fixed buffers (layout of the largest batch) and one graph per bucket
+    bool fixed = false;
+    char *fixed_dev = nullptr;
+    std::vector<int> buckets;          // event counts, ascending
+    std::vector<cudaGraphExec_t> graphs;
+    int cap_t = 0, cap_v = 0;          // track / vertex capacities of the current batch's buffers
     // pinned staging
     int32_t *h_seed_off = nullptr, *h_hit_off = nullptr, *h_trk_off = nullptr, *h_vtx_off = nullptr;
     int32_t *h_counts = nullptr;
     int4 *h_seg = nullptr;             // segment table of the batch
+    int32_t *h_seg_n = nullptr;        // its length
     ds_track *h_trk = nullptr;
     ds_vertex_rec *h_vtx = nullptr;
 };
@@ -164,6 +178,8 @@ struct ds_server {
     int64_t context_bytes = 0;
     int max_vtx = 0;
     int sm_count = 148;
+    bool graph_mode = false;
+    int graphs_captured = 0;
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -185,6 +201,8 @@ struct ds_server {
     void copy_back(Slot &sl);
     void finish(Slot &sl);
     void fail_batch(Slot &sl, ds_status st);
+    BatchLayout layout(const Slot &sl) const;
+    ds_status capture_graphs(Slot &sl);
     ds_completion finalize(Req *q);
     void publish(const std::vector<std::pair<ds_completion, Req *>> &fin);   // mu held
     void release();          // CUDA resources (worker stopped)
@@ -215,9 +233,11 @@ namespace {
 // shift, seed shift, hit shift}; vertex track indices become relative to the
 // segment's first track (trk_off at its first event).
 __global__ void k_renumber(ds_track *trk, const int32_t *n_trk, int cap_t, ds_vertex_rec *vtx,
-                           const int32_t *n_vtx, int cap_v, const int32_t *trk_off, const int4 *seg, int n_seg)
+                           const int32_t *n_vtx, int cap_v, const int32_t *trk_off, const int4 *seg,
+                           const int32_t *n_seg_dev)
 {
     const int nt = min(max(*n_trk, 0), cap_t), nv = min(max(*n_vtx, 0), cap_v);
+    const int n_seg = *n_seg_dev;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nt + nv; i += gridDim.x * blockDim.x) {
         const bool is_t = i < nt;
         const int ev = is_t ? trk[i].event : vtx[i - nt].event;
@@ -335,7 +355,9 @@ bool ds_server::admit()
     const int V = vtx_capacity(cfg, S);
     BatchLayout L(E, S, H, V);
     size_t off = 0;
-    if (!arena.alloc(L.bytes, &off)) return false;    // admission by device memory: wait for a batch to finish
+    // admission by device memory (arena mode): wait for a batch to finish;
+    // graph mode: the slot's fixed buffers hold any batch
+    if (!sl->fixed && !arena.alloc(L.bytes, &off)) return false;
     sl->segs.assign(queue.begin(), queue.begin() + n);
     queue.erase(queue.begin(), queue.begin() + n);
     ++inflight;
@@ -348,17 +370,86 @@ bool ds_server::admit()
     }
     sl->E = E; sl->S = S; sl->H = H; sl->V = V;
     sl->off = off;
-    sl->bytes = L.bytes;
-    sl->dev = d_arena + off;
+    sl->bytes = sl->fixed ? 0 : L.bytes;
+    sl->dev = sl->fixed ? sl->fixed_dev : d_arena + off;
+    sl->cap_t = sl->fixed ? cfg.max_batch_seeds : S;
+    sl->cap_v = sl->fixed ? max_vtx : V;
     const double tl = now();
     launch(*sl);
     t_launch = t_launch + (now() - tl);
     return true;
 }
 
+BatchLayout ds_server::layout(const Slot &sl) const
+{
+    return sl.fixed ? BatchLayout(cfg.max_batch_events, cfg.max_batch_seeds, cfg.max_batch_hits, max_vtx)
+                    : BatchLayout(sl.E, sl.S, sl.H, sl.V);
+}
+
+// Graph mode, at creation: one graph per event-count bucket of the slot's
+// launch sequence over its fixed buffers, with the arrays' capacities
+// (DS_BATCH_CAPACITY); the batch's sizes live in the offsets and the segment
+// count on the device.
+ds_status ds_server::capture_graphs(Slot &sl)
+{
+    BatchLayout L = layout(sl);
+    char *d = sl.fixed_dev;
+    ds_event_batch b{};
+    b.n_seeds = cfg.max_batch_seeds;
+    b.n_hits = cfg.max_batch_hits;
+    b.flags = DS_BATCH_CAPACITY;
+    b.seed_off = reinterpret_cast<int32_t *>(d + L.seed_off);
+    b.hit_off = reinterpret_cast<int32_t *>(d + L.hit_off);
+    ds_seeds sd{};
+    const float **sc[6] = {&sd.x, &sd.y, &sd.tx, &sd.ty, &sd.qop, &sd.chi2};
+    for (int c = 0; c < 6; ++c) *sc[c] = reinterpret_cast<float *>(d + L.seed[c]);
+    ds_ut_hits ht{reinterpret_cast<float *>(d + L.hit[0]), reinterpret_cast<float *>(d + L.hit[1]),
+                  reinterpret_cast<float *>(d + L.hit[2]), reinterpret_cast<uint8_t *>(d + L.layer)};
+    for (int eb = 1;; eb = std::min(2 * eb, cfg.max_batch_events)) {
+        sl.buckets.push_back(eb);
+        if (eb == cfg.max_batch_events) break;
+    }
+    for (int eb : sl.buckets) {
+        b.n_events = eb;
+        ds_tracks tr{};
+        tr.tracks = reinterpret_cast<ds_track *>(d + L.trk);
+        tr.trk_off = reinterpret_cast<int32_t *>(d + L.trk_off);
+        tr.n_tracks = reinterpret_cast<int32_t *>(d + L.ntrk);
+        tr.capacity = cfg.max_batch_seeds;
+        ds_vertices vx{};
+        vx.vertices = reinterpret_cast<ds_vertex_rec *>(d + L.vtx);
+        vx.vtx_off = reinterpret_cast<int32_t *>(d + L.vtx_off);
+        vx.n_vertices = reinterpret_cast<int32_t *>(d + L.nvtx);
+        vx.capacity = max_vtx;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(sl.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DS_ERR_CUDA;
+        ds_status s = ds_reconstruct(sl.ctx, &b, &sd, &ht, &tr, sl.st);
+        if (s == DS_OK) s = ds_vertex(sl.ctx, &tr, &vx, sl.st);
+        if (s == DS_OK) {
+            k_renumber<<<2 * sm_count, 256, 0, sl.st>>>(tr.tracks, tr.n_tracks, cfg.max_batch_seeds, vx.vertices,
+                                                        vx.n_vertices, max_vtx, tr.trk_off,
+                                                        reinterpret_cast<const int4 *>(d + L.seg),
+                                                        reinterpret_cast<const int32_t *>(d + L.nseg));
+            if (cudaGetLastError() != cudaSuccess) s = DS_ERR_CUDA;
+        }
+        const cudaError_t ec = cudaStreamEndCapture(sl.st, &g);
+        if (s != DS_OK || ec != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            return s != DS_OK ? s : DS_ERR_CUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return DS_ERR_CUDA;
+        sl.graphs.push_back(ex);
+        ++graphs_captured;
+    }
+    return DS_OK;
+}
+
 void ds_server::launch(Slot &sl)
 {
-    BatchLayout L(sl.E, sl.S, sl.H, sl.V);
+    BatchLayout L = layout(sl);
     char *d = sl.dev;
     int32_t *d_seed_off = reinterpret_cast<int32_t *>(d + L.seed_off);
     int32_t *d_hit_off = reinterpret_cast<int32_t *>(d + L.hit_off);
@@ -395,9 +486,22 @@ void ds_server::launch(Slot &sl)
         eb += g.e1 - g.e0; sb += ns; hb += nh;
     }
     const int n_seg = (int)sl.segs.size();
-    h2d(d_seed_off, sl.h_seed_off, 4 * (size_t)(sl.E + 1));
-    h2d(d_hit_off, sl.h_hit_off, 4 * (size_t)(sl.E + 1));
+    // graph mode: the batch padded with empty events to its bucket
+    int bucket = -1, E_launch = sl.E;
+    if (sl.fixed) {
+        bucket = 0;
+        while (sl.buckets[bucket] < sl.E) ++bucket;
+        E_launch = sl.buckets[bucket];
+        for (int e = sl.E + 1; e <= E_launch; ++e) {
+            sl.h_seed_off[e] = sb;
+            sl.h_hit_off[e] = hb;
+        }
+    }
+    sl.h_seg_n[0] = n_seg;
+    h2d(d_seed_off, sl.h_seed_off, 4 * (size_t)(E_launch + 1));
+    h2d(d_hit_off, sl.h_hit_off, 4 * (size_t)(E_launch + 1));
     h2d(d_seg, sl.h_seg, sizeof(int4) * (size_t)n_seg);
+    h2d(d + L.nseg, sl.h_seg_n, 4);
     if (ce != cudaSuccess) return fail_batch(sl, DS_ERR_CUDA);
     ds_event_batch b{};
     b.n_events = sl.E; b.n_seeds = sl.S; b.n_hits = sl.H;
@@ -408,18 +512,22 @@ void ds_server::launch(Slot &sl)
     tr.tracks = reinterpret_cast<ds_track *>(d + L.trk);
     tr.trk_off = reinterpret_cast<int32_t *>(d + L.trk_off);
     tr.n_tracks = reinterpret_cast<int32_t *>(d + L.ntrk);
-    tr.capacity = sl.S;
+    tr.capacity = sl.cap_t;
     ds_vertices vx{};
     vx.vertices = reinterpret_cast<ds_vertex_rec *>(d + L.vtx);
     vx.vtx_off = reinterpret_cast<int32_t *>(d + L.vtx_off);
     vx.n_vertices = reinterpret_cast<int32_t *>(d + L.nvtx);
-    vx.capacity = sl.V;
-    ds_status s = ds_reconstruct(sl.ctx, &b, &sd, &ht, &tr, sl.st);
-    if (s == DS_OK) s = ds_vertex(sl.ctx, &tr, &vx, sl.st);
-    if (s != DS_OK) return fail_batch(sl, s);
-    k_renumber<<<2 * sm_count, 256, 0, sl.st>>>(tr.tracks, tr.n_tracks, sl.S, vx.vertices, vx.n_vertices, sl.V,
-                                                tr.trk_off, d_seg, n_seg);
-    ce = cudaGetLastError();
+    vx.capacity = sl.cap_v;
+    if (sl.fixed) {
+        ce = cudaGraphLaunch(sl.graphs[bucket], sl.st);
+    } else {
+        ds_status s = ds_reconstruct(sl.ctx, &b, &sd, &ht, &tr, sl.st);
+        if (s == DS_OK) s = ds_vertex(sl.ctx, &tr, &vx, sl.st);
+        if (s != DS_OK) return fail_batch(sl, s);
+        k_renumber<<<2 * sm_count, 256, 0, sl.st>>>(tr.tracks, tr.n_tracks, sl.S, vx.vertices, vx.n_vertices, sl.V,
+                                                    tr.trk_off, d_seg, reinterpret_cast<const int32_t *>(d + L.nseg));
+        ce = cudaGetLastError();
+    }
     auto d2h = [&](void *dst, const void *src, size_t n) {
         if (n && ce == cudaSuccess) ce = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, sl.st);
     };
@@ -437,10 +545,10 @@ void ds_server::copy_back(Slot &sl)
     // Records of a request carried whole by this batch go straight into the
     // caller's buffers (DMA when they are pinned); those of requests cut into
     // several segments go to the slot's staging and are joined on completion.
-    BatchLayout L(sl.E, sl.S, sl.H, sl.V);
-    sl.n_t = std::min(std::max(sl.h_counts[0], 0), sl.S);
-    sl.n_v = std::min(std::max(sl.h_counts[1], 0), sl.V);
-    const bool vtx_ok = sl.h_counts[1] <= sl.V;
+    BatchLayout L = layout(sl);
+    sl.n_t = std::min(std::max(sl.h_counts[0], 0), sl.cap_t);
+    sl.n_v = std::min(std::max(sl.h_counts[1], 0), sl.cap_v);
+    const bool vtx_ok = sl.h_counts[1] <= sl.cap_v;
     const ds_track *d_trk = reinterpret_cast<const ds_track *>(sl.dev + L.trk);
     const ds_vertex_rec *d_vtx = reinterpret_cast<const ds_vertex_rec *>(sl.dev + L.vtx);
     cudaError_t ce = cudaSuccess;
@@ -471,7 +579,7 @@ void ds_server::finish(Slot &sl)
     ds_stats stt{};
     const ds_status bs = ds_sync_status(sl.ctx, sl.st, &stt);
     // a batch whose vertices overflowed returns no vertex records (counts only)
-    const bool vtx_ok = sl.h_counts[1] <= sl.V;
+    const bool vtx_ok = sl.h_counts[1] <= sl.cap_v;
     std::vector<std::pair<ds_completion, Req *>> fin;
     for (size_t k = 0; k < sl.segs.size(); ++k) {
         const Seg &g = sl.segs[k];
@@ -508,7 +616,7 @@ void ds_server::finish(Slot &sl)
     }
     {
         std::lock_guard<std::mutex> lk(mu);
-        arena.release(sl.off, sl.bytes);
+        if (!sl.fixed) arena.release(sl.off, sl.bytes);
         publish(fin);
         --inflight;
     }
@@ -536,7 +644,7 @@ void ds_server::fail_batch(Slot &sl, ds_status st)
     }
     {
         std::lock_guard<std::mutex> lk(mu);
-        arena.release(sl.off, sl.bytes);
+        if (!sl.fixed) arena.release(sl.off, sl.bytes);
         publish(fin);
         --inflight;
     }
@@ -583,12 +691,14 @@ void ds_server::release()
     cudaSetDevice(device);
     for (Slot &sl : slots) {
         if (sl.st) cudaStreamSynchronize(sl.st);
+        for (cudaGraphExec_t g : sl.graphs)
+            if (g) cudaGraphExecDestroy(g);
         if (sl.ctx) ds_destroy(sl.ctx);
         if (sl.st) cudaStreamDestroy(sl.st);
         if (sl.ev_a) cudaEventDestroy(sl.ev_a);
         if (sl.ev_b) cudaEventDestroy(sl.ev_b);
         void *hp[] = {sl.h_seed_off, sl.h_hit_off, sl.h_trk_off, sl.h_vtx_off, sl.h_counts, sl.h_seg, sl.h_trk,
-                      sl.h_vtx};
+                      sl.h_vtx, sl.h_seg_n};
         for (void *p : hp)
             if (p) cudaFreeHost(p);
         sl = Slot();
@@ -613,6 +723,7 @@ void ds_server_default_config(ds_server_config *c)
     c->vertices_per_seed = 16;
     c->hbm_budget = 0;
     c->mlp_precision = DS_MLP_FP32;
+    c->graphs = 1;
 }
 
 ds_status ds_server_create(ds_server **out, int device, const ds_geometry *geom, const ds_nn_weights *weights,
@@ -661,6 +772,7 @@ ds_status ds_server_create(ds_server **out, int device, const ds_geometry *geom,
             cudaHostAlloc((void **)&sl.h_trk_off, 4 * E1, 0) != cudaSuccess ||
             cudaHostAlloc((void **)&sl.h_vtx_off, 4 * E1, 0) != cudaSuccess ||
             cudaHostAlloc((void **)&sl.h_counts, 8, 0) != cudaSuccess ||
+            cudaHostAlloc((void **)&sl.h_seg_n, 4, 0) != cudaSuccess ||
             cudaHostAlloc((void **)&sl.h_seg, sizeof(int4) * E1, 0) != cudaSuccess ||
             cudaHostAlloc((void **)&sl.h_trk, sizeof(ds_track) * (size_t)cfg->max_batch_seeds, 0) != cudaSuccess ||
             cudaHostAlloc((void **)&sl.h_vtx, sizeof(ds_vertex_rec) * (size_t)s->max_vtx, 0) != cudaSuccess)
@@ -673,6 +785,21 @@ ds_status ds_server_create(ds_server **out, int device, const ds_geometry *geom,
     if (cudaMalloc((void **)&s->d_arena, budget) != cudaSuccess) return DS_ERR_OOM;
     s->arena.init(budget);
     s->cfg.hbm_budget = (int64_t)budget;
+    // graph mode when every slot's fixed buffers fit the budget
+    const size_t slot_bytes =
+        BatchLayout(cfg->max_batch_events, cfg->max_batch_seeds, cfg->max_batch_hits, s->max_vtx).bytes;
+    if (cfg->graphs && slot_bytes * s->slots.size() <= budget) {
+        s->graph_mode = true;
+        for (Slot &sl : s->slots) {
+            size_t off = 0;
+            if (!s->arena.alloc(slot_bytes, &off)) return DS_ERR_OOM;
+            sl.fixed = true;
+            sl.fixed_dev = s->d_arena + off;
+            ds_status st = s->capture_graphs(sl);
+            if (st != DS_OK) return st;
+        }
+        if (cudaDeviceSynchronize() != cudaSuccess) return DS_ERR_CUDA;
+    }
     s->t0 = Clock::now();
     s->worker = std::thread([s] { s->run(); });
     guard.p = nullptr;
@@ -713,7 +840,7 @@ ds_status ds_server_submit(ds_server *s, const ds_request *req, int64_t *id)
         if (e1 == e) return DS_ERR_CAPACITY;            // one event larger than a batch
         Seg g{q.get(), (int)segs.size(), e, e1};
         BatchLayout L(e1 - e, g.seeds(), g.hits(), vtx_capacity(c, g.seeds()));
-        if (L.bytes > s->arena.size) return DS_ERR_CAPACITY;
+        if (!s->graph_mode && L.bytes > s->arena.size) return DS_ERR_CAPACITY;
         segs.push_back(g);
         e = e1;
     }
@@ -776,6 +903,8 @@ ds_status ds_server_stats_get(ds_server *s, ds_server_stats *o)
     o->worker_launch_s = s->t_launch;
     o->worker_finish_s = s->t_finish;
     o->worker_wall_s = s->now();
+    o->graphs = s->graph_mode ? 1 : 0;
+    o->graphs_captured = s->graphs_captured;
     int64_t q = 0;
     const Req *last = nullptr;
     for (const Seg &g : s->queue)

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kBucketThreads, 3) k_bucket(const __grid_const
     uint16_t *table = a.bins + (size_t)e * g.table_stride;
     bool bad = h0 < 0 || h1 < h0 || h1 > a.n_hits;
     if (e == 0 && h0 != 0) bad = true;
-    if (e == a.n_events - 1 && h1 != a.n_hits) bad = true;
+    if (e == a.n_events - 1 && h1 != a.n_hits && !a.capacity_sizes) bad = true;
     if (bad) {
         if (tid == 0) raise_flag(a.cnt, DS_FLAG_BAD_OFFSETS);
         h0 = h1 = 0;
@@ -91,7 +91,9 @@ __global__ void __launch_bounds__(kBucketThreads, 3) k_bucket(const __grid_const
             a.n_events, a.item_off, s_scan);
         if (tid == 0) {
             a.item_off[a.n_events] = n_items;
-            if (__ldg(so) != 0 || __ldg(so + a.n_events) != a.n_seeds) raise_flag(a.cnt, DS_FLAG_BAD_OFFSETS);
+            const int s_end = __ldg(so + a.n_events);
+            if (__ldg(so) != 0 || (a.capacity_sizes ? s_end > a.n_seeds : s_end != a.n_seeds))
+                raise_flag(a.cnt, DS_FLAG_BAD_OFFSETS);
         }
     }
 

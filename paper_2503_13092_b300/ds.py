@@ -54,7 +54,7 @@ class ds_params(C.Structure):
 
 class ds_event_batch(C.Structure):
     _fields_ = [("n_events", C.c_int32), ("n_seeds", C.c_int32), ("n_hits", C.c_int32),
-                ("reserved0", C.c_int32), ("seed_off", C.c_void_p), ("hit_off", C.c_void_p)]
+                ("flags", C.c_int32), ("seed_off", C.c_void_p), ("hit_off", C.c_void_p)]
 
 
 class ds_seeds(C.Structure):
@@ -101,7 +101,7 @@ class ds_tune_entry(C.Structure):
 class ds_server_config(C.Structure):
     _fields_ = [("n_slots", C.c_int32), ("max_batch_events", C.c_int32), ("max_batch_seeds", C.c_int32),
                 ("max_batch_hits", C.c_int32), ("events_per_launch", C.c_int32), ("vertices_per_seed", C.c_int32),
-                ("hbm_budget", C.c_int64), ("mlp_precision", C.c_int32), ("reserved0", C.c_int32)]
+                ("hbm_budget", C.c_int64), ("mlp_precision", C.c_int32), ("graphs", C.c_int32)]
 
 
 class ds_request(C.Structure):
@@ -123,7 +123,8 @@ class ds_server_stats(C.Structure):
     _fields_ = [("requests_done", C.c_int64), ("events_done", C.c_int64), ("batches", C.c_int64),
                 ("hbm_budget", C.c_int64), ("hbm_peak", C.c_int64), ("context_bytes", C.c_int64),
                 ("peak_inflight", C.c_int32), ("queued", C.c_int32), ("worker_launch_s", C.c_double),
-                ("worker_finish_s", C.c_double), ("worker_wall_s", C.c_double)]
+                ("worker_finish_s", C.c_double), ("worker_wall_s", C.c_double), ("graphs", C.c_int32),
+                ("graphs_captured", C.c_int32)]
 
 
 VINFO_DTYPE = np.dtype([("m_pipi", "<f4"), ("m_ppi", "<f4"), ("m_pip", "<f4"), ("p", "<f4"), ("pt", "<f4"),

@@ -116,6 +116,7 @@ def test_admission_by_device_memory(torch_cuda, weights, pool):
     st = srv.stats()
     assert all(got[i]["status"] == 0 for i in ids)
     assert st["peak_inflight"] == 1 and st["hbm_peak"] <= st["hbm_budget"]
+    assert st["graphs"] == 0          # the slots' fixed buffers do not fit this budget
     srv.close()
 
 
@@ -135,3 +136,52 @@ def test_request_errors_and_timing_fields(torch_cuda, weights, pool):
     (c,) = collect(srv, 1).values()
     assert c["t_arrival"] == pytest.approx(t) and c["t_admit"] >= t and c["t_done"] >= c["t_admit"]
     srv.close()
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_served_mix_matches_oracle(torch_cuda, weights, pool, split):
+    """Every request of a concurrent, continuously batched mix against the
+    FP64 oracle run on that request alone, under the parity rules (tracks:
+    identical hits except within the decision margin, parameters to 1e-4,
+    chi2 to 1e-3; vertices: the oracle vertexer fed the served tracks, to
+    1 um).  split: batches of at most 7 events, so that requests are cut into
+    segments and renumbered back."""
+    import oracle
+    from tests import parity
+    reqs = make_requests(pool, 12, seed=9, max_events=20)
+    cfg = synth.default_config()
+    over = dict(max_batch_events=7) if split else {}
+    srv = server(torch_cuda, weights, **over)
+    ids = [srv.submit(r) for r in reqs]
+    got = collect(srv, len(reqs))
+    srv.close()
+    if split:
+        assert any(got[i]["n_batches"] > 1 for i in ids)
+    for rid, r in zip(ids, reqs):
+        c = got[rid]
+        assert c["status"] == 0, c
+        o = oracle.reconstruct(r, cfg, weights, n_threads=8)
+        g = dict(tracks=c["tracks"], trk_off=c["trk_off"], vertices=c["vertices"], vtx_off=c["vtx_off"])
+        parity.assert_tracks_match(parity.compare_tracks(r, o, g))
+        parity.assert_vertices_match(parity.compare_vertices(cfg, g))
+
+
+def test_graph_replay_equals_launches(torch_cuda, weights, pool):
+    """Graph mode (each batch one replay of a graph captured per slot and
+    event-count bucket, batches padded with empty events) against kernels
+    launched batch by batch: identical records for a mix that spans several
+    buckets, split requests included."""
+    reqs = make_requests(pool, 30, seed=10, max_events=40)
+    res = {}
+    for graphs in (1, 0):
+        srv = server(torch_cuda, weights, graphs=graphs, max_batch_events=64)
+        ids = [srv.submit(r) for r in reqs]
+        got = collect(srv, len(reqs))
+        st = srv.stats()
+        srv.close()
+        assert st["graphs"] == graphs
+        if graphs:
+            assert st["graphs_captured"] == 4 * 7        # 4 slots x buckets 1, 2, 4, ..., 64
+        assert all(got[i]["status"] == 0 for i in ids)
+        res[graphs] = [key(got[i]) for i in ids]
+    assert res[1] == res[0]
