@@ -195,35 +195,33 @@ def step_traffic():
     return tot
 
 
-def h2d_ceiling(torch, nbytes, reps=5):
-    """Pinned host -> device copy rate for nbytes per step, issued as plain
-    cudaMemcpyAsync calls: one copy on one stream, the same bytes as two
-    copies on two streams, and as four copies on one and on two streams."""
+def h2d_ceiling(torch, arrays, reps=5):
+    """Upload rate of the e2e step's own pinned host arrays with nothing else
+    running: one cudaMemcpyAsync per array (as the serving path issues them)
+    on one stream, and the same copies spread over two streams."""
     from cuda.bindings import runtime as rt
-    src = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    nbytes = sum(a.nbytes for a in arrays)
     dst = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     h2d = rt.cudaMemcpyKind.cudaMemcpyHostToDevice
 
-    def issue(n_chunks, n_streams):
-        step = (nbytes + n_chunks - 1) // n_chunks
-        for c in range(n_chunks):
-            off = c * step
-            n = min(step, nbytes - off)
-            st = streams[c % n_streams]
-            err, = rt.cudaMemcpyAsync(dst.data_ptr() + off, src.data_ptr() + off, n, h2d, st.cuda_stream)
+    def issue(n_streams):
+        off = 0
+        for k, a in enumerate(arrays):
+            st = streams[k % n_streams]
+            err, = rt.cudaMemcpyAsync(dst.data_ptr() + off, a.ctypes.data, a.nbytes, h2d, st.cuda_stream)
             assert err == rt.cudaError_t.cudaSuccess, err
+            off += a.nbytes
 
-    res = dict(bytes=nbytes)
-    for name, nc, ns in (("one_copy", 1, 1), ("two_copies_two_streams", 2, 2), ("four_copies_one_stream", 4, 1),
-                         ("four_copies_two_streams", 4, 2)):
-        issue(nc, ns)
+    res = dict(bytes=nbytes, copies=len(arrays))
+    for name, ns in (("one_stream", 1), ("two_streams", 2)):
+        issue(ns)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(streams[0])
         streams[1].wait_stream(streams[0])
         for _ in range(reps):
-            issue(nc, ns)
+            issue(ns)
         streams[0].wait_stream(streams[1])
         e1.record(streams[0])
         torch.cuda.synchronize()
@@ -1022,7 +1020,9 @@ def main():
                       note="ds_process_host: one call per step, upload, compute and download in sequence")
     e2e = e2e_pipelined(ds, torch, cfg, w, pin, E, S, H, dev_index, n_steps=max(args.steps, 10))
     e2e["value"] *= ws
-    ceil = h2d_ceiling(torch, e2e["h2d_bytes_per_step"])
+    ceil = h2d_ceiling(torch, [pin[k] for k in ("seed_off", "hit_off", "seed_x", "seed_y", "seed_tx", "seed_ty",
+                                                "seed_qop", "seed_chi2", "hit_x0", "hit_ybeg", "hit_yend",
+                                                "hit_layer")])
     best = max(v for k, v in ceil.items() if k.endswith("_gbs"))
     e2e["h2d_ceiling_gbs"] = best
     e2e["h2d_ceiling"] = ceil

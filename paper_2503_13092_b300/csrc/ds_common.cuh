@@ -285,7 +285,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 }
 
 constexpr int kWaitLimit = 1 << 22;
-constexpr int kMlpTcCtasPerSm = 4;        // persistent tensor-core network CTAs per SM (64 TMEM columns each)
+constexpr int kMlpTcCtasPerSm = 8;        // persistent tensor-core network CTAs per SM: 8 x 64 TMEM columns = all 512, 8 x 128 threads x 64 registers = all 64K
 
 // Exclusive scan of one int per thread over the block; returns the prefix,
 // *total receives the block sum.  `scratch` holds >= 32 ints.  All threads call.

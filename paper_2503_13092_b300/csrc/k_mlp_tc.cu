@@ -15,7 +15,8 @@
 // epilogue; inputs and hidden activations are converted with saturation at
 // +-448.
 //
-// Persistent CTAs of 4 warps (one per TMEM sub-partition); every mbarrier wait
+// Persistent CTAs of 4 warps (one per TMEM sub-partition), 8 per SM so that
+// one SM has 8 tiles in flight (all 512 TMEM columns); every mbarrier wait
 // is bounded: on time-out the kernel raises DS_FLAG_TIMEOUT, releases its TMEM
 // and returns.
 
@@ -38,7 +39,7 @@ constexpr int kTcCols = 64;          // TMEM columns: layer-1 and layer-2 accumu
 }  // namespace
 
 template <bool FP8>
-__global__ void __launch_bounds__(128) k_mlp_tc(const __grid_constant__ MlpArgs a)
+__global__ void __launch_bounds__(128, kMlpTcCtasPerSm) k_mlp_tc(const __grid_constant__ MlpArgs a)
 {
     // K-major no-swizzle layouts: byte(r, k) = (r/8)*SBO + (k/epr)*LBO + (r%8)*16 + (k%epr)*esize,
     // epr = 16 / esize, LBO = 128 (core matrices adjacent along K)
