@@ -279,12 +279,17 @@ typedef struct {
     int32_t search_stage_hits;  /* events with at most this many hits have their x0 array
                                    staged in shared memory, 0..46080 (default 5120);
                                    larger events read it from global memory */
+    int32_t vertex_ctas_per_sm; /* CTAs per SM of the vertexing launch that takes one event
+                                   per CTA, 1..4 (default 4) */
+    int32_t vertex_small_cap;   /* events with at most this many tracks are vertexed one per
+                                   CTA; larger ones as (event, 65536-pair segment) work items
+                                   spread over the SMs, 2..512 (default 512) */
 } ds_tuning;
 
 /* One configuration measured by ds_autotune. */
 typedef struct {
     ds_tuning tuning;
-    double ms;                  /* mean ds_reconstruct time on the tuning batch */
+    double ms;                  /* mean ds_reconstruct + ds_vertex time on the tuning batch */
 } ds_tune_entry;
 
 /* ------------------------------------------------------------------ lifetime */
@@ -447,14 +452,17 @@ DS_API ds_status ds_profile_read(ds_ctx *ctx, ds_kernel_time *out, int32_t max_o
 DS_API ds_status ds_get_tuning(ds_ctx *ctx, ds_tuning *out);
 DS_API ds_status ds_set_tuning(ds_ctx *ctx, const ds_tuning *t);
 
-/* Autotuner: times ds_reconstruct on the caller's batch (device inputs as for
- * ds_reconstruct; `out` receives the tracks of the last run) for candidate
- * tunings by coordinate descent over stage size, chunk size, CTAs per SM and
- * queue group (two sweeps, each configuration run `reps` times after one
- * warm-up run, CUDA events on `stream`), keeps the fastest in the context and
- * copies it to *best.  Every configuration measured is written to entries
- * (at most max_entries; *n_entries = number measured).  Synchronous; must not
- * be called while `stream` is being captured.  Errors as ds_reconstruct. */
+/* Autotuner: times ds_reconstruct + ds_vertex on the caller's batch (device
+ * inputs as for ds_reconstruct; `out` receives the tracks of the last run, the
+ * vertices go to context-owned buffers) for candidate tunings by coordinate
+ * descent over the search's stage size, chunk size, CTAs per SM and queue
+ * group and the vertexing's CTAs per SM and one-event-per-CTA track limit (two
+ * sweeps, each configuration run `reps` times after one warm-up run, CUDA
+ * events on `stream`), keeps the fastest in the context and copies it to
+ * *best.  Every configuration measured is written to entries (at most
+ * max_entries; *n_entries = number measured).  Synchronous; may allocate the
+ * vertex buffers; must not be called while `stream` is being captured.  Errors
+ * as ds_reconstruct. */
 DS_API ds_status ds_autotune(ds_ctx *ctx, const ds_event_batch *batch, const ds_seeds *seeds,
                              const ds_ut_hits *hits, ds_tracks *out, int32_t reps, ds_tuning *best,
                              ds_tune_entry *entries, int32_t max_entries, int32_t *n_entries, void *stream);

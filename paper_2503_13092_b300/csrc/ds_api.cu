@@ -1,5 +1,6 @@
 // C ABI of libds.so: contexts, device-resident state, launches.
 // Declarations and the contract of every call are in include/ds.h.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -10,13 +11,15 @@
 #include "ds_args.cuh"
 
 static constexpr ds_tuning kDefaultTuning = {ds::kSearchThreads, ds::kSearchCtasPerSm, ds::kSearchGroup,
-                                             ds::kStageHits};
+                                             ds::kStageHits, ds::kVtxCtasPerSmMax, ds::kVtxSmallCapMax};
 
 static bool tuning_valid(const ds_tuning &t)
 {
     return t.search_chunk >= 1 && t.search_chunk <= ds::kSearchThreads && t.search_ctas_per_sm >= 1 &&
            t.search_ctas_per_sm <= 4 && t.search_group >= 1 && t.search_group <= 16 &&
-           t.search_stage_hits >= 0 && t.search_stage_hits <= ds::kStageHitsMax;
+           t.search_stage_hits >= 0 && t.search_stage_hits <= ds::kStageHitsMax && t.vertex_ctas_per_sm >= 1 &&
+           t.vertex_ctas_per_sm <= ds::kVtxCtasPerSmMax && t.vertex_small_cap >= 2 &&
+           t.vertex_small_cap <= ds::kVtxSmallCapMax;
 }
 
 struct ds_ctx {
@@ -748,6 +751,8 @@ ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tr, ds_vertices *out, void *st
     va.n_vertices = out->n_vertices;
     va.capacity = out->capacity;
     va.cnt = ctx->d_cnt;
+    va.small_cap = ctx->tune.vertex_small_cap;
+    va.ctas_per_sm = ctx->tune.vertex_ctas_per_sm;
     ds::ScatterVtxArgs xa{};
     xa.pool = ctx->pool;
     xa.pool_pos = ctx->pool_pos;
@@ -825,13 +830,42 @@ ds_status ds_autotune(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *sd, 
     ctx->prof.on = false;
     int n = 0;
     ds_status rs = DS_OK;
+    // the vertices of the tuning runs go to the context's host-path buffers
+    const int vcap = (int)std::min<long long>(16LL * b->n_seeds + 4096, 0x7fffffffLL / 64);
+    auto &h = ctx->h;
+    if (b->n_events + 1 > h.cap_events) {
+        if ((rs = grow(ctx, &h.seed_off, (size_t)b->n_events + 1)) != DS_OK ||
+            (rs = grow(ctx, &h.hit_off, (size_t)b->n_events + 1)) != DS_OK ||
+            (rs = grow(ctx, &h.trk_off, (size_t)b->n_events + 1)) != DS_OK ||
+            (rs = grow(ctx, &h.vtx_off, (size_t)b->n_events + 1)) != DS_OK ||
+            (rs = grow(ctx, &h.counts, (size_t)2)) != DS_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return rs;
+        }
+        h.cap_events = b->n_events + 1;
+    }
+    if (vcap > h.cap_vtx) {
+        if ((rs = grow(ctx, &h.vertices, (size_t)vcap)) != DS_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return rs;
+        }
+        h.cap_vtx = vcap;
+    }
+    ds_vertices vx{h.vertices, h.vtx_off, h.counts + 1, vcap, 0};
+    auto step = [&]() -> ds_status {
+        ds_status s = ds_reconstruct(ctx, b, sd, ht, out, stream);
+        if (s == DS_OK) s = ds_vertex(ctx, out, &vx, stream);
+        return s;
+    };
     auto measure = [&](const ds_tuning &t, double *ms) -> ds_status {
         ctx->tune = t;
-        ds_status s = ds_reconstruct(ctx, b, sd, ht, out, stream);   // warm-up (and workspace growth)
+        ds_status s = step();   // warm-up (and workspace growth)
         if (s != DS_OK) return s;
         if (cudaEventRecord(e0, st) != cudaSuccess) return fail(ctx, DS_ERR_CUDA, "cudaEventRecord");
         for (int r = 0; r < reps; ++r)
-            if ((s = ds_reconstruct(ctx, b, sd, ht, out, stream)) != DS_OK) return s;
+            if ((s = step()) != DS_OK) return s;
         if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
             return fail(ctx, DS_ERR_CUDA, "timing event");
         float f = 0.f;
@@ -848,14 +882,18 @@ ds_status ds_autotune(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *sd, 
     static const int chunk_opts[] = {32, 64, 96, 128};
     static const int ctas_opts[] = {1, 2, 3, 4};
     static const int group_opts[] = {1, 2, 4, 8};
+    static const int vctas_opts[] = {1, 2, 3, 4};
+    static const int vcap_opts[] = {64, 128, 256, 512};
+    const int *dim_opts[6] = {stage_opts, chunk_opts, ctas_opts, group_opts, vctas_opts, vcap_opts};
     for (int sweep = 0; sweep < 2 && rs == DS_OK; ++sweep) {
-        for (int dim = 0; dim < 4 && rs == DS_OK; ++dim) {
-            const int *opts = dim == 0 ? stage_opts : dim == 1 ? chunk_opts : dim == 2 ? ctas_opts : group_opts;
+        for (int dim = 0; dim < 6 && rs == DS_OK; ++dim) {
+            const int *opts = dim_opts[dim];
             const int n_opts = dim == 0 ? 7 : 4;
             for (int k = 0; k < n_opts && rs == DS_OK; ++k) {
                 ds_tuning t = cur;
-                int32_t *field = dim == 0 ? &t.search_stage_hits : dim == 1 ? &t.search_chunk
-                                 : dim == 2 ? &t.search_ctas_per_sm : &t.search_group;
+                int32_t *fields[6] = {&t.search_stage_hits, &t.search_chunk, &t.search_ctas_per_sm, &t.search_group,
+                                      &t.vertex_ctas_per_sm, &t.vertex_small_cap};
+                int32_t *field = fields[dim];
                 if (*field == opts[k]) continue;
                 *field = opts[k];
                 double ms = 0.0;

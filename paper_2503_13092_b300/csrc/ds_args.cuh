@@ -154,6 +154,8 @@ struct VertexArgs {
     int *item_count;        // per work item: vertices kept
     int *item_base;         // per work item: vertices of the event's earlier items
     int max_items;
+    int small_cap;          // events with at most this many tracks: one per CTA (<= kVtxSmallCapMax)
+    int ctas_per_sm;        // of the one-event-per-CTA launch
     int32_t *vtx_off;
     int32_t *n_vertices;
     int capacity;

@@ -39,6 +39,8 @@ constexpr int kBucketThreads = 512;
 constexpr int kBucketVecRows = 3;    // 16-byte loads (4 hits) per bucketing thread
 constexpr int kBucketStage = 6144;   // events up to this many hits are sorted in shared memory
 constexpr int kMaxVertexTracks = 4096; // tracks per event staged for vertexing
+constexpr int kVtxCtasPerSmMax = 4;   // one-event-per-CTA vertexing: resident CTAs per SM at most (default)
+constexpr int kVtxSmallCapMax = 512;  // its largest event (tracks staged per CTA); default limit
 constexpr int kVtxLargeSeg = 65536;  // pairs per work item of the large-capacity vertex launch
 // items of one event: its opposite-charge pairs, at most (4096 / 2)^2, in segments
 constexpr int kVtxItemsPerEvent = (kMaxVertexTracks / 2) * (kMaxVertexTracks / 2) / kVtxLargeSeg;

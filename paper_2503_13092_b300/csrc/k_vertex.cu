@@ -31,8 +31,8 @@ namespace ds {
 
 constexpr int kVtxThreads = 256;
 constexpr int kVtxLargeThreads = 1024;  // the large-capacity launch: one CTA per SM, all of its warps
-constexpr int kVtxSmallCap = 512;
-constexpr int kVtxCtasPerSm = 4;      // resident CTAs of the small-capacity launch per SM
+constexpr int kVtxSmallCap = kVtxSmallCapMax;   // tracks staged per CTA by the small-capacity launch
+constexpr int kVtxCtasPerSm = kVtxCtasPerSmMax;   // resident CTAs of the small-capacity launch per SM (at most)
 // pairs per two-phase segment and candidate results kept in shared memory per
 // segment: larger for the large-capacity launch (one CTA per SM), whose
 // events have up to millions of pairs
@@ -51,6 +51,19 @@ struct PairOut {
     unsigned int flags;
 };
 
+// 1/x in FP64 from a FP32 reciprocal refined by two Newton steps r <- r (2 - x r)
+// (each doubles the correct bits: 23 -> 46 -> beyond 53), a few FP64 FMAs
+// instead of a full FP64 division; x outside the FP32 range takes the division.
+__device__ __forceinline__ double recip_fp64(double x)
+{
+    const float xf = (float)x;
+    double r = (double)(1.0f / xf);
+    if (!(fabs(r) > 0.0 && fabs(r) < 1e38)) return 1.0 / x;
+    r = r * fma(-x, r, 2.0);
+    r = r * fma(-x, r, 2.0);
+    return r;
+}
+
 __device__ __noinline__ PairOut solve_fp64(const DevGeom &g, const DevParams &P, const Trk &A, const Trk &B)
 {
     const double gi = -(double)g.mp * ((double)g.gamma0 + (double)g.gamma1 * (double)A.q);
@@ -65,8 +78,9 @@ __device__ __noinline__ PairOut solve_fp64(const DevGeom &g, const DevParams &P,
     const double d = txi * wx + tyi * wy, m = dtx * wx + dty * wy;
     double u1 = 0.0, u2 = 0.0;
     if (den > 1e-12 * a * c) {
-        u1 = ((txj * dtx + tyj * dty) * d - b * m) / den;
-        u2 = ((txi * dtx + tyi * dty) * d - a * m) / den;
+        const double rden = recip_fp64(den);
+        u1 = ((txj * dtx + tyj * dty) * d - b * m) * rden;
+        u2 = ((txi * dtx + tyi * dty) * d - a * m) * rden;
     }
     bool conv = false;
     for (int it = 0; it < P.nr_max_iter; ++it) {
@@ -86,7 +100,8 @@ __device__ __noinline__ PairOut solve_fp64(const DevGeom &g, const DevParams &P,
         const double id_x = tyi * dz - dy, id_y = dx - pi * dz, id_z = pi * dy - tyi * dx;
         const double n1 = -(cx * jd_x + cy * jd_y + cc * jd_z) - 2.0 * gj * dx * dPi;
         const double n2 = -(cx * id_x + cy * id_y + cc * id_z) - 2.0 * gi * dx * dPj;
-        const double s1 = -n1 / det, s2 = -n2 / det;
+        const double rdet = recip_fp64(det);
+        const double s1 = -n1 * rdet, s2 = -n2 * rdet;
         u1 += s1;
         u2 += s2;
         if (fabs(s1) < (double)P.nr_tol && fabs(s2) < (double)P.nr_tol) {
@@ -102,7 +117,7 @@ __device__ __noinline__ PairOut solve_fp64(const DevGeom &g, const DevParams &P,
     o.x = (float)(x1 - 0.5 * dx);
     o.y = (float)(y1 - 0.5 * dy);
     o.z = (float)(0.5 * (u1 + u2) + (double)g.z_ref);
-    o.doca = (float)sqrt(dx * dx + dy * dy + du * du);
+    o.doca = sqrtf((float)(dx * dx + dy * dy + du * du));   // stored as FP32: a FP32 root suffices
     o.flags = 1u | (conv ? 0u : 2u);
     return o;
 }
@@ -301,9 +316,9 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
     int t0 = min(__ldg(a.trk_off + e), tcap), t1 = min(__ldg(a.trk_off + e + 1), tcap);
     if (t1 < t0) t1 = t0;
     int nt = t1 - t0;
-    // the small-capacity launch takes events with nt <= kVtxSmallCap, the
-    // large one the rest (clamped to its capacity, flagged)
-    const bool mine = LARGE ? nt > kVtxSmallCap : nt <= kVtxSmallCap;
+    // the small-capacity launch takes events with nt <= small_cap (at most
+    // kVtxSmallCap), the large one the rest (clamped to its capacity, flagged)
+    const bool mine = LARGE ? nt > a.small_cap : nt <= a.small_cap;
     if (!LARGE && !mine) {
         // list the event with its opposite-charge pair count (of the tracks
         // the large-capacity launch stages)
@@ -610,7 +625,9 @@ cudaError_t launch_vertex(const VertexArgs &a0, const ScatterVtxArgs &sa, int sm
     if (a0.n_events <= 0) return cudaSuccess;
     VertexArgs a = a0;
     const size_t sm_small = vtx_smem<false>(kVtxSmallCap), sm_large = vtx_smem<true>(kMaxVertexTracks);
-    const int g_small = a.n_events < kVtxCtasPerSm * sm_count ? a.n_events : kVtxCtasPerSm * sm_count;
+    if (a.small_cap < 2 || a.small_cap > kVtxSmallCap || a.ctas_per_sm < 1 || a.ctas_per_sm > kVtxCtasPerSm)
+        return cudaErrorInvalidValue;
+    const int g_small = a.n_events < a.ctas_per_sm * sm_count ? a.n_events : a.ctas_per_sm * sm_count;
     // persistent over (event, pair segment) items: at most kVtxItemsPerEvent per event
     const long long items_max = (long long)kVtxItemsPerEvent * a.n_events;
     const int g_large = items_max < sm_count ? (int)items_max : sm_count;

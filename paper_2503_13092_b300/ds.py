@@ -88,7 +88,17 @@ class ds_kernel_time(C.Structure):
 
 class ds_tuning(C.Structure):
     _fields_ = [("search_chunk", C.c_int32), ("search_ctas_per_sm", C.c_int32), ("search_group", C.c_int32),
-                ("search_stage_hits", C.c_int32)]
+                ("search_stage_hits", C.c_int32), ("vertex_ctas_per_sm", C.c_int32), ("vertex_small_cap", C.c_int32)]
+    _defaults = dict(search_chunk=128, search_ctas_per_sm=4, search_group=1, search_stage_hits=5120,
+                     vertex_ctas_per_sm=4, vertex_small_cap=512)
+
+    def __init__(self, *args, **kw):
+        """Positional values in field order; fields not given take the library's defaults."""
+        names = [n for n, _ in self._fields_]
+        vals = dict(self._defaults)
+        vals.update(zip(names, args))
+        vals.update(kw)
+        super().__init__(**vals)
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

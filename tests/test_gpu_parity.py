@@ -141,11 +141,12 @@ def test_partial_strips(torch_cuda, weights, training):
     assert g["stats"]["n_candidates"] < d.run(full)["stats"]["n_candidates"]
 
 
-@pytest.mark.parametrize("name,n_events,n_sample", [("c2", 1000, 24), ("c3", 2000, 16)])
+@pytest.mark.parametrize("name,n_events,n_sample", [("c2", 1000, 24), ("c3", 2000, 16), ("c3", None, 16)])
 def test_full_size_sampled(torch_cuda, weights, name, n_events, n_sample):
     """The benchmark's launch (whole batch in one call); the oracle recomputes
-    sampled events one by one (events are independent), including the largest."""
-    b = synth.config_batch(name, n_events=n_events)
+    sampled events one by one (events are independent), including the largest.
+    n_events None: the benchmark's own batch (c3: all 10000 events, seed 3)."""
+    b = synth.config_batch(name, n_events=n_events) if n_events else synth.config_batch(name, seed=3)
     cfg = synth.default_config()
     d = make(torch_cuda, cfg, weights)
     g = d.run(b)

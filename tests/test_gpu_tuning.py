@@ -55,10 +55,13 @@ def test_outputs_do_not_depend_on_tuning(torch_cuda, weights):
     assert np.diff(b["hit_off"]).max() > 2 * 5120      # larger than the default staging buffer
     d = ds.Downstream(synth.default_config(), weights)
     dev = d.to_device(b)
-    shapes = [(128, 4, 2, 5632), (32, 1, 1, 0), (64, 3, 8, 32768), (1, 2, 16, 2048), (96, 4, 4, 46080)]
+    # search: chunk, CTAs per SM, group, staging; vertexing: CTAs per SM, one-event-per-CTA
+    # track limit (2: every event with two or more tracks goes to the pair-segment items)
+    shapes = [(128, 4, 2, 5632, 4, 512), (32, 1, 1, 0, 1, 64), (64, 3, 8, 32768, 2, 128), (1, 2, 16, 2048, 3, 256),
+              (96, 4, 4, 46080, 4, 2)]
     ref = None
-    for chunk, ctas, group, stage in shapes:
-        t = ds.ds_tuning(chunk, ctas, group, stage)
+    for shape in shapes:
+        t = ds.ds_tuning(*shape)
         r = run_with(d, ds, dev, t)
         assert r[0]["status"] == 0, (t.as_dict(), r[0])
         assert r[0]["n_tracks"] > 0
@@ -73,7 +76,8 @@ def test_invalid_tuning_refused(torch_cuda, weights):
     d = ds.Downstream(synth.default_config(), weights)
     before = ds.ds_get_tuning(d.ctx).as_dict()
     for bad in [(0, 4, 2, 5632), (129, 4, 2, 5632), (128, 0, 2, 5632), (128, 5, 2, 5632), (128, 4, 0, 5632),
-                (128, 4, 17, 5632), (128, 4, 2, -1), (128, 4, 2, 46081)]:
+                (128, 4, 17, 5632), (128, 4, 2, -1), (128, 4, 2, 46081), (128, 4, 2, 5632, 0, 512),
+                (128, 4, 2, 5632, 5, 512), (128, 4, 2, 5632, 4, 1), (128, 4, 2, 5632, 4, 513)]:
         with pytest.raises(ds.DSError):
             ds.ds_set_tuning(d.ctx, ds.ds_tuning(*bad))
     assert ds.ds_get_tuning(d.ctx).as_dict() == before
@@ -89,9 +93,9 @@ def test_autotune(torch_cuda, weights):
     best, entries = ds.ds_autotune(d.ctx, dev, out, reps=2)
     d.sync()
     # coordinate descent from the default: one measurement, then two sweeps over
-    # 7 stage sizes, 4 chunks, 4 CTA counts and 4 groups, each skipping the value
-    # current when it is reached
-    assert 1 + 2 * (6 + 3 + 3 + 3) <= len(entries) <= 1 + 2 * (7 + 4 + 4 + 4)
+    # 7 stage sizes, 4 chunks, 4 CTA counts, 4 groups, 4 vertex CTA counts and 4
+    # vertex track limits, each skipping the value current when it is reached
+    assert 1 + 2 * (6 + 3 * 5) <= len(entries) <= 1 + 2 * (7 + 4 * 5)
     assert all(ms > 0 for _, ms in entries)
     cur = ds.ds_get_tuning(d.ctx).as_dict()
     assert cur == best.as_dict()
