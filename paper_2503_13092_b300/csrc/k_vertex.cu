@@ -37,7 +37,7 @@ constexpr int kVtxCtasPerSm = kVtxCtasPerSmMax;   // resident CTAs of the small-
 // segment: larger for the large-capacity launch (one CTA per SM), whose
 // events have up to millions of pairs
 template <bool LARGE> struct VtxSeg {
-    static constexpr int seg = LARGE ? kVtxLargeSeg : 8192;
+    static constexpr int seg = LARGE ? kVtxLargeSeg : 12288;
     static constexpr int store = LARGE ? 2048 : 1024;
 };
 
@@ -66,8 +66,10 @@ __device__ __forceinline__ double recip_fp64(double x)
 
 __device__ __noinline__ PairOut solve_fp64(const DevGeom &g, const DevParams &P, const Trk &A, const Trk &B)
 {
-    const double gi = -(double)g.mp * ((double)g.gamma0 + (double)g.gamma1 * (double)A.q);
-    const double gj = -(double)g.mp * ((double)g.gamma0 + (double)g.gamma1 * (double)B.q);
+    // two straight lines when gamma = 0 (field mode A)
+    const bool line = g.gamma0 == 0.f && g.gamma1 == 0.f;
+    const double gi = line ? 0.0 : -(double)g.mp * ((double)g.gamma0 + (double)g.gamma1 * (double)A.q);
+    const double gj = line ? 0.0 : -(double)g.mp * ((double)g.gamma0 + (double)g.gamma1 * (double)B.q);
     const double txi = A.tx, tyi = A.ty, txj = B.tx, tyj = B.ty;
     const double wx = (double)A.x - (double)B.x, wy = (double)A.y - (double)B.y;
     const double dtx = txi - txj, dty = tyi - tyj;
@@ -76,14 +78,21 @@ __device__ __noinline__ PairOut solve_fp64(const DevGeom &g, const DevParams &P,
     const double cz = txi * tyj - tyi * txj;
     const double den = dtx * dtx + dty * dty + cz * cz;
     const double d = txi * wx + tyi * wy, m = dtx * wx + dty * wy;
+    // Two straight lines: F is quadratic in (u1, u2), so the first Newton step
+    // lands on the closed-form closest approach from any start and later
+    // steps only repeat it to within rounding.  The closed form is then the
+    // converged solution whenever the lines are not parallel and at least one
+    // step is allowed (every FP64 operation counts here: this part issues
+    // FP64 at a small fraction of its FP32 rate).
+    const bool line_conv = line && den > 0.0 && P.nr_max_iter > 0;
     double u1 = 0.0, u2 = 0.0;
-    if (den > 1e-12 * a * c) {
+    if (den > 1e-12 * a * c || line_conv) {
         const double rden = recip_fp64(den);
         u1 = ((txj * dtx + tyj * dty) * d - b * m) * rden;
         u2 = ((txi * dtx + tyi * dty) * d - a * m) * rden;
     }
-    bool conv = false;
-    for (int it = 0; it < P.nr_max_iter; ++it) {
+    bool conv = line_conv;
+    for (int it = 0; it < (line ? 0 : P.nr_max_iter); ++it) {
         const double du = u1 - u2;
         const double pi = txi + 2.0 * gi * u1, pj = txj + 2.0 * gj * u2;
         const double dx = (wx + dtx * u2) + txi * du + gi * u1 * u1 - gj * u2 * u2;
@@ -110,10 +119,14 @@ __device__ __noinline__ PairOut solve_fp64(const DevGeom &g, const DevParams &P,
         }
     }
     const double du = u1 - u2;
-    const double dx = (wx + dtx * u2) + txi * du + gi * u1 * u1 - gj * u2 * u2;
+    double dx = (wx + dtx * u2) + txi * du, x1 = (double)A.x + txi * u1;
+    if (!line) {
+        dx = dx + gi * u1 * u1 - gj * u2 * u2;
+        x1 = x1 + gi * u1 * u1;
+    }
     const double dy = (wy + dty * u2) + tyi * du;
     PairOut o;
-    const double x1 = (double)A.x + txi * u1 + gi * u1 * u1, y1 = (double)A.y + tyi * u1;
+    const double y1 = (double)A.y + tyi * u1;
     o.x = (float)(x1 - 0.5 * dx);
     o.y = (float)(y1 - 0.5 * dy);
     o.z = (float)(0.5 * (u1 + u2) + (double)g.z_ref);
@@ -244,36 +257,40 @@ __device__ __noinline__ PairOut solve_pair(const DevGeom &g, const DevParams &P,
     return o;
 }
 
-__device__ __forceinline__ Trk trk_of(const float4 *tr, const float *q, int i)
-{
-    const float4 v = tr[i];
-    return Trk{v.x, v.y, v.z, v.w, q[i]};
-}
-
 template <int CAP, bool LARGE>
 __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE ? 1 : kVtxCtasPerSm)
     k_vertex(const __grid_constant__ VertexArgs a)
 {
-    constexpr int kVtxSeg = VtxSeg<LARGE>::seg, kVtxStore = VtxSeg<LARGE>::store;
+    constexpr int kVtxSeg = VtxSeg<LARGE>::seg, kVtxStore = VtxSeg<LARGE>::store, kWords = kVtxSeg / 32;
+    constexpr int kThreads = LARGE ? kVtxLargeThreads : kVtxThreads;
+    constexpr int kTpt = CAP / kThreads;   // tracks staged per thread
+    constexpr int kWarpCap = kVtxStore / (kThreads / 32);   // listed candidates per warp
+    static_assert(CAP % kThreads == 0 && CAP % 2 == 0 && CAP <= 65535, "track staging layout");
+    static_assert((sizeof(float4) + sizeof(unsigned)) * kVtxStore + 5 * sizeof(unsigned) * kWords >=
+                      sizeof(float4) * CAP, "tracks parked below the charge-ordered copy");
     // dynamic: candidate results, segment masks, then the event's tracks
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ int s_scan[32];
-    __shared__ int s_pool_base;
+    __shared__ int s_pool_base, s_wcnt[32];
     __shared__ bool s_last;
     float4 *s_res = reinterpret_cast<float4 *>(s_dyn);          // candidate results: x, y, z, doca
     unsigned *s_resf = reinterpret_cast<unsigned *>(s_res + kVtxStore);   // and flags
-    unsigned *s_mask = s_resf + kVtxStore;
-    unsigned *s_keep = s_mask + kVtxSeg / 32;
-    int *s_wbase = reinterpret_cast<int *>(s_keep + kVtxSeg / 32);
-    unsigned *s_cmask = reinterpret_cast<unsigned *>(s_wbase + kVtxSeg / 32);   // candidates of the segment
-    int *s_cbase = reinterpret_cast<int *>(s_cmask + kVtxSeg / 32);            // their word prefix
-    int *s_wrow = s_cbase + kVtxSeg / 32;              // row holding each mask word's first pair
-    float4 *s_tr = reinterpret_cast<float4 *>(s_wrow + kVtxSeg / 32);          // x, y, tx, ty
-    float *s_q = reinterpret_cast<float *>(s_tr + CAP);         // q/p
-    uint16_t *s_pos = reinterpret_cast<uint16_t *>(s_q + CAP);
-    uint16_t *s_neg = s_pos + CAP;
-    uint16_t *s_start = s_neg + CAP;
-    int *s_row = reinterpret_cast<int *>(s_start + CAP + (CAP & 1));  // CAP + 1 entries
+    unsigned *s_cmask = s_resf + kVtxStore;                      // candidates of the segment, a bit per pair
+    int *s_cbase = reinterpret_cast<int *>(s_cmask + kWords);   // their word prefix
+    unsigned *s_keep = reinterpret_cast<unsigned *>(s_cbase + kWords);   // kept pairs
+    int *s_wbase = reinterpret_cast<int *>(s_keep + kWords);    // their word prefix
+    int *s_wrow = s_wbase + kWords;                              // row holding each mask word's first pair
+    // the event's tracks in charge order (positives, then negatives): x, y, tx, ty
+    float4 *s_ctr = reinterpret_cast<float4 *>(s_wrow + kWords);
+    float *s_cq = reinterpret_cast<float *>(s_ctr + CAP);       // and q/p
+    uint16_t *s_cidx = reinterpret_cast<uint16_t *>(s_cq + CAP);   // and the index in the event
+    uint16_t *s_self = s_cidx + CAP;       // slot of track i in that order
+    uint16_t *s_start = s_self + CAP;      // first partner of track i (after it) in the opposite list
+    int *s_row = reinterpret_cast<int *>(s_start + CAP);   // CAP + 1 entries: first pair of row i
+    // candidate list, a part of kWarpCap entries per warp: the two slots
+    // (lower | upper << 16), then (pair, slot of i | slot of j << 16)
+    int2 *s_clist = reinterpret_cast<int2 *>(s_row + CAP + 2);
+    int *s_rowoff = reinterpret_cast<int *>(s_clist + kVtxStore);   // per slot: first pair of its row less its s_start
 
     const DevGeom &g = a.g;
     const DevParams &P = a.p;
@@ -342,117 +359,205 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
     }
     int ev_count = 0;
     if (mine && nt >= 2) {
-        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-            const ds_track &r = a.tracks[t0 + i];
-            s_tr[i] = make_float4(r.x, r.y, r.tx, r.ty);
-            s_q[i] = r.qop;
-        }
-        __syncthreads();
-        // opposite-charge partner lists, in track order, from one scan of
-        // packed (positive, negative) counts: a track's place in its own list
-        // and, in the other list, the first partner after it
-        int npos = 0, nneg = 0;
-        for (int c0 = 0; c0 < nt; c0 += blockDim.x) {
-            const int i = c0 + threadIdx.x;
-            const float q = i < nt ? s_q[i] : 0.f;
-            int tot;
-            const int r = block_exclusive_scan((q > 0.f ? 1 : 0) | (q < 0.f ? 0x10000 : 0), s_scan, &tot);
-            const int pb = npos + (r & 0xffff), nb = nneg + (r >> 16);
-            if (q > 0.f) s_pos[pb] = (uint16_t)i;
-            if (q < 0.f) s_neg[nb] = (uint16_t)i;
-            if (i < nt) s_start[i] = (uint16_t)(q > 0.f ? nb : pb);
-            npos += tot & 0xffff;
-            nneg += tot >> 16;
-        }
-        // row i holds partners j > i of opposite charge
-        int run = 0;
-        for (int c0 = 0; c0 < nt; c0 += blockDim.x) {
-            const int i = c0 + threadIdx.x;
-            int cnt = 0;
+        // stage the tracks in charge order: thread t takes tracks kTpt t ..
+        // kTpt t + kTpt - 1; one scan of packed (positive, negative) counts of
+        // their charges gives each its slot, its first partner after it in the
+        // opposite list, and the first pair of its row
+        // (one load of each track, parked in event order in the head of the
+        // dynamic shared memory, which the segment loop only uses after the
+        // staging barrier)
+        float4 *s_park = reinterpret_cast<float4 *>(s_dyn);
+        float qv[kTpt];
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < kTpt; ++k) {
+            const int i = kTpt * threadIdx.x + k;
+            qv[k] = 0.f;
             if (i < nt) {
-                const float q = s_q[i];
-                cnt = q > 0.f ? nneg - s_start[i] : (q < 0.f ? npos - s_start[i] : 0);
+                const ds_track &r = a.tracks[t0 + i];
+                s_park[i] = make_float4(r.x, r.y, r.tx, r.ty);
+                qv[k] = r.qop;
             }
-            int tot;
-            const int r = block_exclusive_scan(cnt, s_scan, &tot);
-            if (i < nt) s_row[i] = run + r;
-            run += tot;
+            cnt += (qv[k] > 0.f ? 1 : 0) | (qv[k] < 0.f ? 0x10000 : 0);
         }
-        if (threadIdx.x == 0) s_row[nt] = run;
+        int tot;
+        const int r0 = block_exclusive_scan(cnt, s_scan, &tot);
+        const int npos = tot & 0xffff, nneg = tot >> 16;
+        int pb = r0 & 0xffff, nb = r0 >> 16;   // positives and negatives before the track
+#pragma unroll
+        for (int k = 0; k < kTpt; ++k) {
+            const int i = kTpt * threadIdx.x + k;
+            if (i < nt) {
+                const float q = qv[k];
+                // pairs in the rows before i: the pb positives before i pair with
+                // all nneg negatives and the nb negatives with all npos
+                // positives, which counts the pb nb pairs of two tracks before
+                // i twice
+                s_row[i] = pb * nneg + nb * npos - pb * nb;
+                int slot = -1;
+                if (q > 0.f) {
+                    s_start[i] = (uint16_t)nb;
+                    slot = pb++;
+                } else if (q < 0.f) {
+                    s_start[i] = (uint16_t)pb;
+                    slot = npos + nb++;
+                } else {
+                    s_start[i] = 0;   // no partner: an empty row
+                }
+                s_self[i] = (uint16_t)(slot < 0 ? 0xffff : slot);
+                if (slot >= 0) {
+                    if (!LARGE) s_rowoff[slot] = s_row[i] - s_start[i];
+                    s_ctr[slot] = s_park[i];   // parked by this thread
+                    s_cq[slot] = q;
+                    s_cidx[slot] = (uint16_t)i;
+                }
+            }
+        }
+        const int npairs = npos * nneg;
+        if (threadIdx.x == 0) s_row[nt] = npairs;
         __syncthreads();
-        const int npairs = run;
         // the pairs this CTA solves: all of the event's, or one item's segment
         const int p_begin = LARGE ? min(seg_k * kVtxSeg, npairs) : 0;
         const int p_end = LARGE ? min(p_begin + kVtxSeg, npairs) : npairs;
         if (threadIdx.x == 0 && p_end > p_begin) atomicAdd(&a.cnt->n_pairs, (unsigned long long)(p_end - p_begin));
         // pair p of the current segment (first pair seg0) -> (i, j), i < j,
-        // opposite charges, (i, j) order: from the row of p's mask word, a
-        // short walk over the rows starting inside the word
-        auto pair_of = [&](int p, int seg0, int &i, int &j) {
+        // opposite charges, (i, j) order, and their slots: from the row of p's
+        // mask word, a short walk over the rows starting inside the word
+        auto pair_of = [&](int p, int seg0, int &i, int &j, int &si, int &sj) {
             i = s_wrow[(p - seg0) >> 5];
             while (s_row[i + 1] <= p) ++i;
-            const uint16_t *opp = s_q[i] > 0.f ? s_neg : s_pos;
-            j = opp[s_start[i] + (p - s_row[i])];
+            si = s_self[i];
+            sj = (si < npos ? npos : 0) + s_start[i] + (p - s_row[i]);
+            j = s_cidx[sj];
+        };
+        auto trk = [&](int slot) {
+            const float4 v = s_ctr[slot];
+            return Trk{v.x, v.y, v.z, v.w, s_cq[slot]};
         };
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        const unsigned lt = (1u << lane) - 1u;
         int n64 = 0;
-        bool store = false;
+        // events of one segment with gamma = 0 take the tiled prefilter and a
+        // candidate list; the others the per-pair enumeration and the mask
+        const bool tiled = !LARGE && straight && npairs <= kVtxSeg;
         for (int seg0 = p_begin; seg0 < p_end; seg0 += kVtxSeg) {
             const int nseg = min(kVtxSeg, p_end - seg0);
             const int nwords = (nseg + 31) >> 5;
             const int seg1 = seg0 + nseg;
-            // each row records the mask words whose first pair it holds
+            // each row records the mask words whose first pair it holds; the
+            // masks start empty (with gamma != 0 every pair is a candidate)
             for (int i = threadIdx.x; i < nt; i += blockDim.x) {
                 const int lo = max(s_row[i], seg0), hi = min(s_row[i + 1], seg1);
                 for (int w = (lo - seg0 + 31) >> 5; seg0 + (w << 5) < hi; ++w) s_wrow[w] = i;
+            }
+            for (int w = threadIdx.x; w < nwords; w += blockDim.x) {
+                s_cmask[w] = straight ? 0u : (w == nwords - 1 && (nseg & 31)) ? (1u << (nseg & 31)) - 1u : 0xffffffffu;
+                s_keep[w] = 0u;
             }
             __syncthreads();
             // phase 1a: is each pair of the segment a candidate?  With gamma = 0
             // both trajectories are lines and the solve converges to their
             // closest approach, whose distance |w.(Di x Dj)| / |Di x Dj| is exact
             // in closed form: pairs more than 1 um above the cut are not
-            // candidates.  With gamma != 0 every pair is a candidate.  One warp
-            // per mask word, one pair per lane.
-            if (!straight) {
-                for (int w = threadIdx.x; w < nwords; w += blockDim.x)
-                    s_mask[w] = (w == nwords - 1 && (nseg & 31)) ? (1u << (nseg & 31)) - 1u : 0xffffffffu;
-            } else {
-                // (|num| > lim sqrt(den)) squared; the 1 um margin dwarfs the rounding
-                const float lim2 = (P.doca_max + 1e-3f) * (P.doca_max + 1e-3f);
+            // candidates.
+            // (|num| > lim sqrt(den)) squared; the 1 um margin dwarfs the
+            // rounding, so the test does not depend on the pair's order
+            const float lim2 = (P.doca_max + 1e-3f) * (P.doca_max + 1e-3f);
+            auto is_cand = [lim2](const float4 &A, const float4 &B) {
+                const float dtx = A.z - B.z, dty = A.w - B.w;
+                const float cz = fmaf(A.z, B.w, -A.w * B.z);
+                const float den = fmaf(dtx, dtx, fmaf(dty, dty, cz * cz));
+                const float num = fmaf(A.x - B.x, dty, -(A.y - B.y) * dtx);
+                return !(den > 1e-12f && num * num > lim2 * den);
+            };
+            bool listed = false;
+            int ncand = 0;
+            if (tiled) {
+                // tiles of the (positive, negative) product: the lanes hold 32
+                // tracks of the longer charge list, the loop broadcasts 8 of the
+                // shorter one; each warp lists its candidates' two slots in its
+                // own part of the list, with a count in a register
+                const bool lpos = npos >= nneg;
+                const int nl = lpos ? npos : nneg, ns = lpos ? nneg : npos;
+                const int lb = lpos ? 0 : npos, sb = lpos ? npos : 0;
+                const int nchunk = (nl + 31) >> 5, units = nchunk * ((ns + 7) >> 3);
+                int2 *wl = s_clist + warp * kWarpCap;
+                int wcnt = 0;
+                for (int u = warp; u < units; u += nwarps) {
+                    const int c = u % nchunk, s0 = (u / nchunk) << 3;
+                    const int sl = lb + (c << 5) + lane;
+                    const bool lv = (c << 5) + lane < nl;
+                    const float4 B = s_ctr[lv ? sl : 0];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int sidx = min(s0 + t, ns - 1);
+                        const bool cand = lv && s0 + t < ns && is_cand(s_ctr[sb + sidx], B);
+                        const unsigned m = __ballot_sync(0xffffffffu, cand);
+                        const int k = wcnt + __popc(m & lt);
+                        if (cand && k < kWarpCap) wl[k].x = (sb + sidx) | (sl << 16);
+                        wcnt += __popc(m);
+                    }
+                }
+                if (lane == 0) s_wcnt[warp] = wcnt;
+                __syncthreads();
+                int over = 0;
+                for (int w = 0; w < nwarps; ++w) {
+                    ncand += s_wcnt[w];
+                    over |= s_wcnt[w] > kWarpCap;
+                }
+                listed = !over;
+            }
+            if (straight && !listed) {
+                // one pair per lane, 32 consecutive pairs of the enumeration per warp
                 for (int w = warp; w < nwords; w += nwarps) {
                     const int p = seg0 + (w << 5) + lane;
                     bool cand = false;
                     if (p < seg1) {
-                        int i, j;
-                        pair_of(p, seg0, i, j);
-                        const float4 A = s_tr[i], B = s_tr[j];   // x, y, tx, ty
-                        const float dtx = A.z - B.z, dty = A.w - B.w;
-                        const float cz = fmaf(A.z, B.w, -A.w * B.z);
-                        const float den = fmaf(dtx, dtx, fmaf(dty, dty, cz * cz));
-                        const float num = fmaf(A.x - B.x, dty, -(A.y - B.y) * dtx);
-                        cand = !(den > 1e-12f && num * num > lim2 * den);
+                        int i, j, si, sj;
+                        pair_of(p, seg0, i, j, si, sj);
+                        cand = is_cand(s_ctr[si], s_ctr[sj]);
                     }
                     const unsigned m = __ballot_sync(0xffffffffu, cand);
-                    if (lane == 0) s_mask[w] = m;
+                    if (lane == 0) s_cmask[w] = m;
                 }
+                __syncthreads();
             }
-            __syncthreads();
+            // the k-th listed candidate: warp parts in order
+            auto entry = [&](int k) -> int2 & {
+                int r = 0;
+                while (k >= s_wcnt[r]) k -= s_wcnt[r++];
+                return s_clist[r * kWarpCap + k];
+            };
             // phase 1b: solve the candidates only, one per thread; keep bits
-            {
+            bool store = listed;
+            if (listed) {
+                for (int k = threadIdx.x; k < ncand; k += blockDim.x) {
+                    int2 &en = entry(k);
+                    // order the two tracks; the pair's place in the (i, j)
+                    // enumeration: the row of the first, then the partner's
+                    // place in the opposite list
+                    const int ss = en.x & 0xffff, sl = en.x >> 16;
+                    const bool sfirst = s_cidx[ss] < s_cidx[sl];
+                    const int sx = sfirst ? ss : sl, sy = sfirst ? sl : ss;
+                    const int p = s_rowoff[sx] + sy - (sy >= npos ? npos : 0);
+                    en = make_int2(p, sx | (sy << 16));
+                    int f64;
+                    const PairOut o = solve_pair(g, P, trk(sx), trk(sy), f64);
+                    n64 += f64;
+                    s_res[k] = make_float4(o.x, o.y, o.z, o.doca);
+                    s_resf[k] = o.flags;
+                    if (o.doca < P.doca_max) atomicOr(&s_keep[(p - seg0) >> 5], 1u << ((p - seg0) & 31));
+                }
+            } else {
                 int ctot = 0;
                 for (int w0 = 0; w0 < nwords; w0 += blockDim.x) {
                     const int w = w0 + threadIdx.x;
-                    const int c = w < nwords ? __popc(s_mask[w]) : 0;
+                    const int c = w < nwords ? __popc(s_cmask[w]) : 0;
                     int t;
                     const int r = block_exclusive_scan(c, s_scan, &t);
-                    if (w < nwords) {
-                        s_cbase[w] = ctot + r;
-                        s_cmask[w] = s_mask[w];
-                    }
+                    if (w < nwords) s_cbase[w] = ctot + r;
                     ctot += t;
                 }
-                __syncthreads();
-                for (int w = threadIdx.x; w < nwords; w += blockDim.x) s_keep[w] = 0u;
                 __syncthreads();
                 store = ctot <= kVtxStore;
                 for (int k = threadIdx.x; k < ctot; k += blockDim.x) {
@@ -463,9 +568,9 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
                         else hi = mid;
                     }
                     const int bit = __fns(s_cmask[lo], 0, k - s_cbase[lo] + 1);
-                    int i, j, f64;
-                    pair_of(seg0 + (lo << 5) + bit, seg0, i, j);
-                    const PairOut o = solve_pair(g, P, trk_of(s_tr, s_q, i), trk_of(s_tr, s_q, j), f64);
+                    int i, j, si, sj, f64;
+                    pair_of(seg0 + (lo << 5) + bit, seg0, i, j, si, sj);
+                    const PairOut o = solve_pair(g, P, trk(si), trk(sj), f64);
                     n64 += f64;
                     if (store) {
                         s_res[k] = make_float4(o.x, o.y, o.z, o.doca);
@@ -473,15 +578,13 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
                     }
                     if (o.doca < P.doca_max) atomicOr(&s_keep[lo], 1u << bit);
                 }
-                __syncthreads();
-                for (int w = threadIdx.x; w < nwords; w += blockDim.x) s_mask[w] = s_keep[w];
-                __syncthreads();
             }
+            __syncthreads();
             // ranks of the kept pairs: one scan over the segment's mask words
             int tot = 0;
             for (int w0 = 0; w0 < nwords; w0 += blockDim.x) {
                 const int w = w0 + threadIdx.x;
-                const int c = w < nwords ? __popc(s_mask[w]) : 0;
+                const int c = w < nwords ? __popc(s_keep[w]) : 0;
                 int t;
                 const int r = block_exclusive_scan(c, s_scan, &t);
                 if (w < nwords) s_wbase[w] = tot + r;
@@ -489,38 +592,56 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
             }
             if (threadIdx.x == 0 && tot > 0) s_pool_base = atomicAdd(&a.cnt->pool_used, tot);
             __syncthreads();
-            // phase 2: re-solve only the kept pairs and write them in (i, j) order
-            for (int k = threadIdx.x; k < tot; k += blockDim.x) {
-                int lo = 0, hi = nwords;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (s_wbase[mid] <= k) lo = mid;
-                    else hi = mid;
-                }
-                const int bit = __fns(s_mask[lo], 0, k - s_wbase[lo] + 1);
-                const int p = seg0 + (lo << 5) + bit;
-                int i, j;
-                pair_of(p, seg0, i, j);
-                PairOut o;
-                if (store) {           // the candidate's result from phase 1b
-                    const int kc = s_cbase[lo] + __popc(s_cmask[lo] & ((1u << bit) - 1u));
-                    const float4 r4 = s_res[kc];
-                    o.x = r4.x; o.y = r4.y; o.z = r4.z; o.doca = r4.w;
-                    o.flags = s_resf[kc];
-                } else {               // too many candidates to keep: the same solve again
-                    int f64;
-                    o = solve_pair(g, P, trk_of(s_tr, s_q, i), trk_of(s_tr, s_q, j), f64);
-                }
-                const int slot = s_pool_base + k;
+            // phase 2: write the kept pairs at their (i, j) rank: from the list,
+            // or by rank from the mask (re-solved when the segment had more
+            // candidates than results kept)
+            auto put = [&](int rank, int i, int j, const PairOut &o) {
+                const int slot = s_pool_base + rank;
                 if (slot < a.pool_cap) {
                     // the 32-byte record as two 16-byte stores (the pool is 16-byte aligned)
                     int4 *dst = reinterpret_cast<int4 *>(a.pool + slot);
                     dst[0] = make_int4(e, t0 + i, t0 + j, __float_as_int(o.x));
                     dst[1] = make_int4(__float_as_int(o.y), __float_as_int(o.z), __float_as_int(o.doca), (int)o.flags);
-                    a.pool_pos[slot] = ev_count + k;
+                    a.pool_pos[slot] = ev_count + rank;
                     if (LARGE) a.pool_item[slot] = item;
                 } else {
                     raise_flag(a.cnt, DS_FLAG_VERTEX_CAPACITY);
+                }
+            };
+            if (listed) {
+                for (int k = threadIdx.x; k < ncand; k += blockDim.x) {
+                    const int2 c = entry(k);
+                    const int b = c.x - seg0, w = b >> 5, bit = b & 31;
+                    const unsigned kw = s_keep[w];
+                    if (!((kw >> bit) & 1u)) continue;
+                    const float4 r4 = s_res[k];
+                    PairOut o;
+                    o.x = r4.x; o.y = r4.y; o.z = r4.z; o.doca = r4.w;
+                    o.flags = s_resf[k];
+                    put(s_wbase[w] + __popc(kw & ((1u << bit) - 1u)), s_cidx[c.y & 0xffff], s_cidx[c.y >> 16], o);
+                }
+            } else {
+                for (int k = threadIdx.x; k < tot; k += blockDim.x) {
+                    int lo = 0, hi = nwords;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (s_wbase[mid] <= k) lo = mid;
+                        else hi = mid;
+                    }
+                    const int bit = __fns(s_keep[lo], 0, k - s_wbase[lo] + 1);
+                    int i, j, si, sj;
+                    pair_of(seg0 + (lo << 5) + bit, seg0, i, j, si, sj);
+                    PairOut o;
+                    if (store) {           // the candidate's result from phase 1b
+                        const int kc = s_cbase[lo] + __popc(s_cmask[lo] & ((1u << bit) - 1u));
+                        const float4 r4 = s_res[kc];
+                        o.x = r4.x; o.y = r4.y; o.z = r4.z; o.doca = r4.w;
+                        o.flags = s_resf[kc];
+                    } else {               // too many candidates to keep: the same solve again
+                        int f64;
+                        o = solve_pair(g, P, trk(si), trk(sj), f64);
+                    }
+                    put(k, i, j, o);
                 }
             }
             ev_count += tot;
@@ -609,12 +730,17 @@ template <bool LARGE>
 static size_t vtx_smem(int cap)
 {
     constexpr int seg = VtxSeg<LARGE>::seg, store = VtxSeg<LARGE>::store;
-    return (sizeof(float4) + sizeof(unsigned)) * store + 6 * sizeof(unsigned) * (seg / 32) +
-           (sizeof(float4) + sizeof(float)) * cap + sizeof(uint16_t) * (3 * cap + (cap & 1)) + sizeof(int) * (cap + 1);
+    return (sizeof(float4) + sizeof(unsigned)) * store + 5 * sizeof(unsigned) * (seg / 32) +
+           (sizeof(float4) + sizeof(float)) * cap + sizeof(uint16_t) * 3 * cap + sizeof(int) * (cap + 2) +
+           sizeof(int2) * store + (LARGE ? 0 : sizeof(int) * cap);
 }
 
 cudaError_t init_vertex_attributes()
 {
+    const cudaError_t e = cudaFuncSetAttribute(k_vertex<kVtxSmallCap, false>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)vtx_smem<false>(kVtxSmallCap));
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_vertex<kMaxVertexTracks, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)vtx_smem<true>(kMaxVertexTracks));
 }
