@@ -508,17 +508,30 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
                 listed = !over;
             }
             if (straight && !listed) {
-                // one pair per lane, 32 consecutive pairs of the enumeration per warp
-                for (int w = warp; w < nwords; w += nwarps) {
-                    const int p = seg0 + (w << 5) + lane;
-                    bool cand = false;
-                    if (p < seg1) {
-                        int i, j, si, sj;
-                        pair_of(p, seg0, i, j, si, sj);
-                        cand = is_cand(s_ctr[si], s_ctr[sj]);
+                // one warp per row of the segment, one partner per lane: the
+                // row's track is one broadcast load and its partners are
+                // consecutive in the opposite list; a ballot covers 32
+                // consecutive pairs of the enumeration
+                for (int i = s_wrow[0] + warp; i < nt; i += nwarps) {
+                    const int rb = s_row[i], re = min(s_row[i + 1], seg1);
+                    if (rb >= seg1) break;   // rows are in pair order
+                    const int k0 = max(seg0 - rb, 0), k1 = re - rb;
+                    if (k0 >= k1) continue;
+                    const int si = s_self[i];
+                    const float4 A = s_ctr[si];
+                    const int ob = (si < npos ? npos : 0) + s_start[i];
+                    for (int kb = k0; kb < k1; kb += 32) {
+                        const int k = kb + lane;
+                        const bool cand = k < k1 && is_cand(A, s_ctr[ob + min(k, k1 - 1)]);
+                        const unsigned m = __ballot_sync(0xffffffffu, cand);
+                        // pairs rb + kb .. rb + kb + 31 are bits b .. b + 31 of
+                        // the segment's mask (set bits all below nseg)
+                        if (lane == 0 && m) {
+                            const int b = rb + kb - seg0, w = b >> 5, sh = b & 31;
+                            atomicOr(&s_cmask[w], m << sh);
+                            if (sh && (m >> (32 - sh))) atomicOr(&s_cmask[w + 1], m >> (32 - sh));
+                        }
                     }
-                    const unsigned m = __ballot_sync(0xffffffffu, cand);
-                    if (lane == 0) s_cmask[w] = m;
                 }
                 __syncthreads();
             }
