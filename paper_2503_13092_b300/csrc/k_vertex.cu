@@ -268,6 +268,8 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
     static_assert(CAP % kThreads == 0 && CAP % 2 == 0 && CAP <= 65535, "track staging layout");
     static_assert((sizeof(float4) + sizeof(unsigned)) * kVtxStore + 5 * sizeof(unsigned) * kWords >=
                       sizeof(float4) * CAP, "tracks parked below the charge-ordered copy");
+    static_assert(LARGE || sizeof(float4) * kVtxStore >= sizeof(float4) * CAP + 2 * sizeof(float4) * (CAP / 4),
+                  "packed shorter list inside the candidate results");
     // dynamic: candidate results, segment masks, then the event's tracks
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ int s_scan[32];
@@ -291,6 +293,10 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
     // (lower | upper << 16), then (pair, slot of i | slot of j << 16)
     int2 *s_clist = reinterpret_cast<int2 *>(s_row + CAP + 2);
     int *s_rowoff = reinterpret_cast<int *>(s_clist + kVtxStore);   // per slot: first pair of its row less its s_start
+    // small launch: the shorter charge list packed in pairs for the tile
+    // test, (x, x', -y, -y') (tx, tx', ty, ty'), in the candidate results'
+    // space past the parked tracks (both free until phase 1b)
+    float4 *s_pk = reinterpret_cast<float4 *>(s_dyn + sizeof(float4) * CAP);
 
     const DevGeom &g = a.g;
     const DevParams &P = a.p;
@@ -406,8 +412,22 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
                 }
                 s_self[i] = (uint16_t)(slot < 0 ? 0xffff : slot);
                 if (slot >= 0) {
-                    if (!LARGE) s_rowoff[slot] = s_row[i] - s_start[i];
-                    s_ctr[slot] = s_park[i];   // parked by this thread
+                    const float4 t4 = s_park[i];   // parked by this thread
+                    if (!LARGE) {
+                        s_rowoff[slot] = s_row[i] - s_start[i];
+                        // the shorter charge list (negatives on a tie) again,
+                        // two tracks per 32 bytes for the packed tile test
+                        const bool neg_short = npos >= nneg;
+                        if (neg_short ? q < 0.f : q > 0.f) {
+                            const int si = neg_short ? slot - npos : slot;
+                            float *pk = reinterpret_cast<float *>(s_pk + 2 * (si >> 1)) + (si & 1);
+                            pk[0] = t4.x;
+                            pk[2] = -t4.y;
+                            pk[4] = t4.z;
+                            pk[6] = t4.w;
+                        }
+                    }
+                    s_ctr[slot] = t4;
                     s_cq[slot] = q;
                     s_cidx[slot] = (uint16_t)i;
                 }
@@ -483,19 +503,40 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
                 const int nchunk = (nl + 31) >> 5, units = nchunk * ((ns + 7) >> 3);
                 int2 *wl = s_clist + warp * kWarpCap;
                 int wcnt = 0;
+                // two partners per packed FP32 instruction, the operations of
+                // is_cand in the same order (each lane of a packed op rounds as
+                // the scalar op does)
+                const float2 lim2v = make_float2(lim2, lim2);
                 for (int u = warp; u < units; u += nwarps) {
                     const int c = u % nchunk, s0 = (u / nchunk) << 3;
                     const int sl = lb + (c << 5) + lane;
                     const bool lv = (c << 5) + lane < nl;
                     const float4 B = s_ctr[lv ? sl : 0];
+                    const float2 nBx = make_float2(-B.x, -B.x), By = make_float2(B.y, B.y);
+                    const float2 nBtx = make_float2(-B.z, -B.z), nBty = make_float2(-B.w, -B.w);
+                    const float2 Bty = make_float2(B.w, B.w);
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) {
-                        const int sidx = min(s0 + t, ns - 1);
-                        const bool cand = lv && s0 + t < ns && is_cand(s_ctr[sb + sidx], B);
-                        const unsigned m = __ballot_sync(0xffffffffu, cand);
-                        const int k = wcnt + __popc(m & lt);
-                        if (cand && k < kWarpCap) wl[k].x = (sb + sidx) | (sl << 16);
-                        wcnt += __popc(m);
+                    for (int pp = 0; pp < 4; ++pp) {
+                        const int pi = min((s0 >> 1) + pp, (ns - 1) >> 1);
+                        const float4 P0 = s_pk[2 * pi], P1 = s_pk[2 * pi + 1];
+                        const float2 wx = __fadd2_rn(make_float2(P0.x, P0.y), nBx);
+                        const float2 nwy = __fadd2_rn(By, make_float2(P0.z, P0.w));
+                        const float2 dtx = __fadd2_rn(make_float2(P1.x, P1.y), nBtx);
+                        const float2 dty = __fadd2_rn(make_float2(P1.z, P1.w), nBty);
+                        const float2 cz = __ffma2_rn(make_float2(P1.x, P1.y), Bty, __fmul2_rn(make_float2(P1.z, P1.w), nBtx));
+                        const float2 den = __ffma2_rn(dtx, dtx, __ffma2_rn(dty, dty, __fmul2_rn(cz, cz)));
+                        const float2 num = __ffma2_rn(wx, dty, __fmul2_rn(nwy, dtx));
+                        const float2 nn = __fmul2_rn(num, num), ld = __fmul2_rn(lim2v, den);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int t = 2 * pp + h;
+                            const float dh = h ? den.y : den.x, nh = h ? nn.y : nn.x, lh = h ? ld.y : ld.x;
+                            const bool cand = lv && s0 + t < ns && !(dh > 1e-12f && nh > lh);
+                            const unsigned m = __ballot_sync(0xffffffffu, cand);
+                            const int k = wcnt + __popc(m & lt);
+                            if (cand && k < kWarpCap) wl[k].x = (sb + s0 + t) | (sl << 16);
+                            wcnt += __popc(m);
+                        }
                     }
                 }
                 if (lane == 0) s_wcnt[warp] = wcnt;
