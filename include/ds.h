@@ -274,7 +274,8 @@ typedef struct {
  * valid tuning. */
 typedef struct {
     int32_t search_chunk;       /* max seeds per work item, 1..128 (default 128) */
-    int32_t search_ctas_per_sm; /* persistent search CTAs per SM, 1..4 (default 4) */
+    int32_t search_ctas_per_sm; /* persistent search CTAs per SM, 1..8 (default 5; at most 5 are
+                                   resident with the default staging, larger values only queue) */
     int32_t search_group;       /* consecutive work items per queue pull, 1..16 (default 1) */
     int32_t search_stage_hits;  /* events with at most this many hits have their x0 array
                                    staged in shared memory, 0..46080 (default 5120);

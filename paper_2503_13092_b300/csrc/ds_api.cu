@@ -16,7 +16,7 @@ static constexpr ds_tuning kDefaultTuning = {ds::kSearchThreads, ds::kSearchCtas
 static bool tuning_valid(const ds_tuning &t)
 {
     return t.search_chunk >= 1 && t.search_chunk <= ds::kSearchThreads && t.search_ctas_per_sm >= 1 &&
-           t.search_ctas_per_sm <= 4 && t.search_group >= 1 && t.search_group <= 16 &&
+           t.search_ctas_per_sm <= 8 && t.search_group >= 1 && t.search_group <= 16 &&
            t.search_stage_hits >= 0 && t.search_stage_hits <= ds::kStageHitsMax && t.vertex_ctas_per_sm >= 1 &&
            t.vertex_ctas_per_sm <= ds::kVtxCtasPerSmMax && t.vertex_small_cap >= 2 &&
            t.vertex_small_cap <= ds::kVtxSmallCapMax;
@@ -880,7 +880,7 @@ ds_status ds_autotune(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *sd, 
     rs = measure(cur, &cur_ms);
     static const int stage_opts[] = {2048, 5120, 8192, 12288, 16384, 24576, 32768};
     static const int chunk_opts[] = {32, 64, 96, 128};
-    static const int ctas_opts[] = {1, 2, 3, 4};
+    static const int ctas_opts[] = {2, 3, 4, 5};
     static const int group_opts[] = {1, 2, 4, 8};
     static const int vctas_opts[] = {1, 2, 3, 4};
     static const int vcap_opts[] = {64, 128, 256, 512};

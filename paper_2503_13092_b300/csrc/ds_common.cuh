@@ -32,7 +32,7 @@ constexpr int kMaxEventHits = 65535; // uint16 offsets
 constexpr int kSearchThreads = 128;  // threads per CTA in the search kernel (max seeds per work item)
 // run-time search shape (ds_tuning): defaults and limits
 constexpr int kSearchGroup = 1;      // consecutive work items per queue pull
-constexpr int kSearchCtasPerSm = 4;
+constexpr int kSearchCtasPerSm = 5;   // resident search CTAs per SM (shared memory and registers sized for 5)
 constexpr int kStageHits = 5120;     // event x0 arrays up to this size are staged in shared memory (4 fused search CTAs per SM fit)
 constexpr int kStageHitsMax = 46080; // largest staging buffer: 32-sector table + x0 + static arrays (fused form) < 227 KB
 constexpr int kBucketThreads = 512;

@@ -287,8 +287,9 @@ __device__ __forceinline__ WinBest window_best(const DevGeom &g, const float *X0
     for (int s = s_lo; s <= s_hi; ++s) {
         const int row = (layer * g.n_sec + s) * kNXB;
         const int i0 = Tb[row + b0], i1 = Tb[row + b1 + 1];
-        for (int i = i0; i < i1; ++i) {
-            const float dx = fabsf(X0[i] - u);
+        // two hits per iteration: both loads in flight together
+        auto take = [&](float xv, int i) {
+            const float dx = fabsf(xv - u);
             if (dx < w) {
                 ++r.cnt;
                 slow |= dx == r.d0 || (N > 1 && dx == d1);
@@ -309,7 +310,14 @@ __device__ __forceinline__ WinBest window_best(const DevGeom &g, const float *X0
                     }
                 }
             }
+        };
+        int i = i0;
+        for (; i + 1 < i1; i += 2) {
+            const float xa = X0[i], xb = X0[i + 1];
+            take(xa, i);
+            take(xb, i + 1);
         }
+        if (i < i1) take(X0[i], i);
     }
     if (slow) return window_best_exact<N>(g, X0, H, Tb, Part, layer, u, y, w, dy);
     return r;
@@ -469,35 +477,75 @@ __device__ __forceinline__ float dv1_ua(const DevGeom &g, const SeedCtx &sc, con
     return fmaf(txp, g.z[0] - g.z[3], x_h) - g.dxdy[0] * sc.yl[0];
 }
 
+// Static shared memory of one search CTA (per template instance).  The first
+// window collects each seed's x-passing UTbX hits in a column of kColRows
+// rows (row r of seed o at [r][o]); the selection leaves the kept hits in
+// rows 0..k1-1, which stay until the item is done (Dv1 also keeps each
+// triplet's UTaX hit in rows kK1Max..2 kK1Max-1).  The rows above the kept
+// ones then hold the refined-window pairs of one chunk of consecutive seeds:
+// per pair its (seed, UTbX rank), the five refined hits and its candidate
+// count.  An item whose pairs exceed kPairCap is processed in several
+// seed-aligned chunks.  The fused form keeps more rows (its winner records
+// are staged there at the end of an item).
+template <int V, bool F>
+struct SearchLayout {
+    static constexpr int kKeepRows = V == 1 ? 2 * kK1Max : kK1Max;
+    static constexpr int kPairBytes = 2 + 5 * 2 + 1;
+    static constexpr int kPairCap = F ? 784 : 640;
+    static constexpr int kColRows = kKeepRows + (kPairCap * kPairBytes + 2 * T - 1) / (2 * T);
+    static_assert(kPairCap >= kK1Max, "a chunk holds at least one seed's pairs");
+};
+
+// A seed's SeedCtx from its two shared-memory records, (z_m, x_m, y_m, ty)
+// and (tx, q/p, w1, u_bX), and its chi2; y at each layer is recomputed as
+// the first phase computed it.
+__device__ __forceinline__ SeedCtx seed_ctx_of(const DevGeom &g, const float4 &A, const float4 &B, float chi2)
+{
+    SeedCtx sc;
+    sc.zm = A.x;
+    sc.xm = A.y;
+    sc.ym = A.z;
+    sc.ty = A.w;
+    sc.tx = B.x;
+    sc.qop = B.y;
+    sc.w1 = B.z;
+    sc.u_bx = B.w;
+    sc.chi2 = chi2;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) sc.yl[l] = fmaf(sc.ty, g.z[l] - sc.zm, sc.ym);
+    return sc;
+}
+// first-window column in the dynamic staging area of an event too large to
+// stage (at most this many rows)
+constexpr int kColRowsBig = 50;
+
 // V = 0: Dv0.  V = 1: Dv1, whose first stage is the triplet search.
 // F: fused network and pick (FP32 network 16-32-32-1).
 template <int V, bool F>
-__global__ void __launch_bounds__(T, F ? kSearchFusedCtas : 4) k_search(const __grid_constant__ SearchArgs a)
+__global__ void __launch_bounds__(T, F ? kSearchFusedCtas : (V == 0 ? kSearchCtasPerSm : 4))
+    k_search(const __grid_constant__ SearchArgs a)
 {
+    using L = SearchLayout<V, F>;
+    constexpr int PC = L::kPairCap;
     extern __shared__ __align__(16) unsigned char s_dyn[];   // bin table, then staged x0
-    __shared__ uint16_t s_bx[kK1Max][T];
-    // refined-window hits; in the fused form also the staging area of the
-    // winner records once the candidates are done (128 x 64 bytes)
-    __shared__ __align__(16) uint16_t s_sel[kK1Max][5][T];
-    __shared__ uint8_t s_nc[kK1Max][T];
-    __shared__ SeedCtx s_sc[T];
+    // first-window columns, kept UTbX hits, pair arrays of a chunk; in the
+    // fused form also the staging area of the winner records (128 x 64 bytes)
+    __shared__ __align__(16) uint16_t s_col[L::kColRows][T];
+    __shared__ float4 s_sa[T];          // per seed: z_m, x_m, y_m, ty
+    __shared__ float4 s_sb[T];          // per seed: tx, q/p, w1, u_bX (chi2 is re-read from the seeds)
     __shared__ uint16_t s_wsec[3][T];   // window_sectors of the refined windows (layers 0-2)
-    // (seed, UTbX rank) of each refined-window pair, then the candidate
-    // offsets (and, fused, each seed's best key + hit indices and its fit)
-    __shared__ __align__(16) union {
-        uint16_t pair[kK1Max * T];
-        struct {
-            int base[T + 4];
-            KeyIds best[F ? T : 1];
-            float4 win[F ? T : 1];      // x_ref, tx, q/p, chi2 of the best
-        } c;
-    } s_pb;
-    int *s_base = s_pb.c.base;
+    __shared__ int s_base[T + 4];       // candidate offsets of the chunk's seeds
+    __shared__ uint16_t s_j0[T + 2];    // first pair of each seed in the item, then the item's total
+    __shared__ __align__(16) KeyIds s_best[F ? T : 1];   // fused: each seed's best key + hit indices
+    __shared__ __align__(16) float4 s_win[F ? T : 1];    // fused: x_ref, tx, q/p, chi2 of the best
     __shared__ int s_cand0;
     __shared__ int s_scan[32];
     __shared__ int s_nx[6];     // next work item: index, event, seed begin, seed end, h0, h1
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ __align__(8) uint64_t s_bar_fi;   // fault injection only: a barrier no copy targets
+    uint16_t *const p_oj = &s_col[L::kKeepRows][0];                     // pair: seed << 4 | rank
+    uint16_t *const p_sel = p_oj + PC;                                   // [5][PC] refined hits
+    uint8_t *const p_nc = reinterpret_cast<uint8_t *>(p_sel + 5 * PC);   // candidates of the pair
 
     const DevGeom &g = a.g;
     const DevParams &P = a.p;
@@ -614,7 +662,12 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : 4) k_search(const __
     }
 
     // ---------------------------------------------------------------- search
-    int n_cand = 0;
+    // the first-window column: the static rows, or for an event too large
+    // to stage (its x0 is read from global memory) the unused staging area
+    const int big_rows = min(kColRowsBig, (int)((sizeof(float) * (a.stage_hits + 4)) / (sizeof(uint16_t) * T)));
+    const bool col_dyn = !staged && big_rows > L::kColRows;
+    uint16_t *const colb = col_dyn ? reinterpret_cast<uint16_t *>(xs) : &s_col[0][0];
+    const int kCap = col_dyn ? big_rows : L::kColRows;
     int nbx = 0;
     // first window (Dv0): 0 keep the survivors as collected, 1 select the k1
     // closest (warp), 2 exact sort (training mode or a distance tie), 3 done
@@ -640,22 +693,20 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : 4) k_search(const __
         const float u_bx = fmaf(tx_ut, g.z[3] - sc.zm, sc.xm) - g.dxdy[3] * sc.yl[3];
         sc.w1 = P.training ? 100.f : fmaf(P.w1b, aq, P.w1a);
         sc.u_bx = u_bx;
-        s_sc[tid] = sc;
+        s_sa[tid] = make_float4(sc.zm, sc.xm, sc.ym, sc.ty);
+        s_sb[tid] = make_float4(sc.tx, sc.qop, sc.w1, sc.u_bx);
 #pragma unroll
         for (int l = 0; l < 3; ++l) s_wsec[l][tid] = (uint16_t)window_sectors(g, Part, l, sc.yl[l], P.dy_tol);
 
-        float d[kK1Max];
-        int id[kK1Max], p[kK1Max];
+        uint16_t *col = colb + tid;
         if (V == 0) {
             // UTbX window: x-passing positions collected in this thread's
-            // column of s_sel (free until the refined windows); the hits of
-            // sectors whose strips all cover the sector pass the strip test as
-            // a whole, otherwise their strips are looked up together.  The
-            // kept hits are the k1 closest by (|dx|, id); their order matters
-            // only for the candidate export, so they are sorted in training
-            // mode only (the pick breaks exact key ties by hit ids)
-            uint16_t *col = &s_sel[0][0][0] + tid;
-            constexpr int kCap = kK1Max * 5;
+            // column; the hits of sectors whose strips all cover the sector
+            // pass the strip test as a whole, otherwise their strips are
+            // looked up together.  The kept hits are the k1 closest by
+            // (|dx|, id); their order matters only for the candidate export,
+            // so they are sorted in training mode only (the pick breaks exact
+            // key ties by hit ids)
             const float u = u_bx, w = sc.w1, y3 = sc.yl[3], dy = P.dy_tol;
             const int s_lo = sector_of(g, y3 - dy - 0.01f), s_hi = sector_of(g, y3 + dy + 0.01f);
             const int b0 = xbin_of(g, u - w - 1e-3f), b1 = xbin_of(g, u + w + 1e-3f);
@@ -672,7 +723,7 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : 4) k_search(const __
                     }
             }
             if (nq > kCap) {
-                nbx = wide_first_window(g, X0, H, Tb, Part, u_bx, sc.yl[3], sc.w1, P.dy_tol, P.k1, &s_bx[0][tid]);
+                nbx = wide_first_window(g, X0, H, Tb, Part, u_bx, sc.yl[3], sc.w1, P.dy_tol, P.k1, col);
                 sel_state = 3;
             } else {
                 int nok = per_hit ? 0 : nq;   // otherwise every collected hit passes the strip test
@@ -701,10 +752,11 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : 4) k_search(const __
             // half-width dtx_max (z_m - z_bX) around the seed's straight
             // extrapolation) whose magnet-point line meets a UTaX hit within
             // w_tri; ranked by (residual, UTbX id).  p packs (UTbX, UTaX) positions.
+            float d[kK1Max];
+            int p[kK1Max];
 #pragma unroll
             for (int k = 0; k < kK1Max; ++k) {
                 d[k] = __int_as_float(0x7f800000);
-                id[k] = 0x7fffffff;
                 p[k] = -1;
             }
             const float w_b = P.dv1_dtx * (sc.zm - g.z[3]);
@@ -734,8 +786,8 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : 4) k_search(const __
             nbx = min(n_tri, P.k1);
 #pragma unroll
             for (int j = 0; j < kK1Max; ++j) {
-                s_bx[j][tid] = (uint16_t)(p[j] & 0xffff);
-                s_sel[j][0][tid] = j < nbx ? (uint16_t)((unsigned)p[j] >> 16) : kNone;   // the triplet's UTaX hit
+                col[j * T] = (uint16_t)(p[j] & 0xffff);
+                col[(kK1Max + j) * T] = j < nbx ? (uint16_t)((unsigned)p[j] >> 16) : kNone;   // the triplet's UTaX hit
             }
         }
     }
@@ -751,9 +803,9 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : 4) k_search(const __
         while (wm) {
             const int src = __ffs(wm) - 1;
             wm &= wm - 1;
-            const int n = __shfl_sync(0xffffffffu, sel_n, src);         // <= kCap < 64
+            const int n = __shfl_sync(0xffffffffu, sel_n, src);         // <= kCap <= 64
             const float uu = __shfl_sync(0xffffffffu, sel_u, src);
-            uint16_t *cc = &s_sel[0][0][0] + (tid - lane + src);
+            uint16_t *cc = colb + (tid - lane + src);
             const int p0 = lane < n ? cc[lane * T] : 0, p1 = lane + 32 < n ? cc[(lane + 32) * T] : 0;
             const float d0 = lane < n ? fabsf(X0[p0] - uu) : inf, d1 = lane + 32 < n ? fabsf(X0[p1] - uu) : inf;
             int r0 = 0, r1 = 0;
@@ -778,7 +830,7 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : 4) k_search(const __
             __syncwarp();
         }
         if (active && sel_state != 3) {
-            uint16_t *col = &s_sel[0][0][0] + tid;
+            uint16_t *col = colb + tid;
             // exact insertion sort by (|dx|, id), ids looked up only on ties
             for (int a2 = 1; sel_state == 2 && a2 < sel_n; ++a2) {
                 const int v = col[a2 * T];
@@ -794,101 +846,171 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : 4) k_search(const __
                 }
                 col[(j + 1) * T] = (uint16_t)v;
             }
-            nbx = min(sel_n, P.k1);
-            for (int j = 0; j < kK1Max; ++j) s_bx[j][tid] = j < nbx ? col[j * T] : (uint16_t)0xFFFF;
+            nbx = min(sel_n, P.k1);   // the kept hits are the column's first nbx rows
         }
     }
+    // the item's (seed, UTbX hit) pairs in seed order, then rank order
     int total_j;
     const int jbase = block_exclusive_scan(nbx, s_scan, &total_j);
-    for (int j = 0; j < nbx; ++j) s_pb.pair[jbase + j] = (uint16_t)((tid << 4) | j);
-    __syncthreads();
+    s_j0[tid] = (uint16_t)jbase;
+    if (tid == T - 1) s_j0[T] = (uint16_t)(jbase + nbx);
+    if (F) s_best[tid] = KeyIds{kNoKey, ~0ull};
+    __syncthreads();   // every column is final; the rows above the kept ones are free
 
-    // refined windows, one (seed, UTbX hit) pair per thread: every lane does
-    // the same three window searches whatever the hits per seed
-    for (int t = tid; t < total_j; t += T) {
-        const int o = s_pb.pair[t] >> 4, j = s_pb.pair[t] & 15;
-        const SeedCtx sc = s_sc[o];
-        const float w2 = P.training ? 10.f : P.w2;
-        const float x0b = X0[s_bx[j][o]];
-        const float xh = x0b + g.dxdy[3] * sc.yl[3];
-        const float txp = (xh - sc.xm) / (g.z[3] - sc.zm);
-        int sel[5];
-        if (V == 1) {
-            sel[0] = s_sel[j][0][o];            // Dv1: the triplet's UTaX hit
-        } else {
-            const float ul = fmaf(txp, g.z[0] - g.z[3], xh) - g.dxdy[0] * sc.yl[0];
-            sel[0] = window_best<1>(g, X0, H, Tb, Part, 0, ul, sc.yl[0], w2, P.dy_tol, s_wsec[0][o]).p0;
+    const int n_item = s_end - s_begin;
+    int n_cand = 0;    // this thread's seed: its candidates (set in its chunk)
+    for (int c_lo = 0; c_lo < n_item;) {
+        // the chunk: seeds [c_lo, c_hi), as many as have at most PC pairs
+        const int p0 = s_j0[c_lo];
+        int c_hi = c_lo + 1;
+        {
+            int hi = n_item;
+            while (c_hi < hi) {
+                const int mid = (c_hi + hi + 1) >> 1;
+                if ((int)s_j0[mid] - p0 <= PC) c_hi = mid;
+                else hi = mid - 1;
+            }
         }
-#pragma unroll
-        for (int l = 1; l <= 2; ++l) {
-            const float ul = fmaf(txp, g.z[l] - g.z[3], xh) - g.dxdy[l] * sc.yl[l];
-            const WinBest wb = window_best<2>(g, X0, H, Tb, Part, l, ul, sc.yl[l], w2, P.dy_tol, s_wsec[l][o]);
-            sel[2 * l - 1] = wb.p0;
-            sel[2 * l] = wb.p1;
-        }
-#pragma unroll
-        for (int k = 0; k < 5; ++k) s_sel[j][k][o] = sel[k] >= 0 ? (uint16_t)sel[k] : kNone;
-        const int pa = sel[0] >= 0, pu = sel[1] >= 0, pv = sel[3] >= 0;
-        const int nu = sel[2] >= 0 ? 2 : 1, nv = sel[4] >= 0 ? 2 : 1;
-        const int valid = (1 + pa + pu + pv >= 3) && (pa || pu);
-        s_nc[j][o] = (uint8_t)(valid ? nu * nv : 0);
-    }
-    if (next_warp) resolve_next();
-    __syncthreads();
-    for (int j = 0; j < nbx; ++j) n_cand += s_nc[j][tid];
-    for (int j = nbx; j < kK1Max; ++j) s_nc[j][tid] = 0;
+        const int np = (int)s_j0[c_hi] - p0;
+        const bool in_chunk = tid >= c_lo && tid < c_hi;
+        if (in_chunk)
+            for (int j = 0; j < nbx; ++j) p_oj[jbase - p0 + j] = (uint16_t)((tid << 4) | j);
+        __syncthreads();
 
-    int total;
-    const int base = block_exclusive_scan(n_cand, s_scan, &total);
-    s_base[tid] = base;
-    if (tid == T - 1) s_base[T] = base + n_cand;
-    if (F) s_pb.c.best[tid] = KeyIds{kNoKey, ~0ull};
-    if (tid == 0) {
-        if (total > 0) atomicAdd(&a.cnt->n_candidates, (unsigned long long)total);
-        int c0 = total > 0 && !F ? atomicAdd(&a.cnt->cand_used, total) : 0;
-        if (!F && total > 0 && c0 + total > a.cand_cap) {   // candidate buffer full: flagged, seeds left empty
-            raise_flag(a.cnt, DS_FLAG_CAND_CAPACITY);
-            c0 = -1;
+        // refined windows, one (seed, UTbX hit) pair per thread: every lane
+        // does the same three window searches whatever the hits per seed
+        for (int t = tid; t < np; t += T) {
+            const int o = p_oj[t] >> 4, j = p_oj[t] & 15;
+            const SeedCtx sc = seed_ctx_of(g, s_sa[o], s_sb[o], 0.f);
+            const float w2 = P.training ? 10.f : P.w2;
+            const float x0b = X0[colb[j * T + o]];
+            const float xh = x0b + g.dxdy[3] * sc.yl[3];
+            const float txp = (xh - sc.xm) / (g.z[3] - sc.zm);
+            int sel[5];
+            if (V == 1) {
+                sel[0] = colb[(kK1Max + j) * T + o];   // Dv1: the triplet's UTaX hit
+                if (sel[0] == kNone) sel[0] = -1;
+            } else {
+                const float ul = fmaf(txp, g.z[0] - g.z[3], xh) - g.dxdy[0] * sc.yl[0];
+                sel[0] = window_best<1>(g, X0, H, Tb, Part, 0, ul, sc.yl[0], w2, P.dy_tol, s_wsec[0][o]).p0;
+            }
+#pragma unroll
+            for (int l = 1; l <= 2; ++l) {
+                const float ul = fmaf(txp, g.z[l] - g.z[3], xh) - g.dxdy[l] * sc.yl[l];
+                const WinBest wb = window_best<2>(g, X0, H, Tb, Part, l, ul, sc.yl[l], w2, P.dy_tol, s_wsec[l][o]);
+                sel[2 * l - 1] = wb.p0;
+                sel[2 * l] = wb.p1;
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) p_sel[k * PC + t] = sel[k] >= 0 ? (uint16_t)sel[k] : kNone;
+            const int pa = sel[0] >= 0, pu = sel[1] >= 0, pv = sel[3] >= 0;
+            const int nu = sel[2] >= 0 ? 2 : 1, nv = sel[4] >= 0 ? 2 : 1;
+            const int valid = (1 + pa + pu + pv >= 3) && (pa || pu);
+            p_nc[t] = (uint8_t)(valid ? nu * nv : 0);
         }
-        s_cand0 = c0;
-    }
-    __syncthreads();
-    const int cand0 = s_cand0;
-    if (!F && active) a.seed_cand[s] = cand0 >= 0 ? make_int4(cand0 + base, n_cand, e, 0) : make_int4(0, 0, e, 0);
-    if (F) {
-        // fused: rounds of T candidates; each merges into its seed's minimum,
-        // then (after the round's barrier) the candidate holding the minimum
-        // keeps its fit beside it.  A later round's merge can only lower the
-        // minimum, and its holder then writes its own fit after that round's
-        // barrier, so the fit kept is always the minimum's.
-        for (int c0 = 0; c0 < total; c0 += T) {
-            const int c = c0 + tid;
-            KeyIds mine{kNoKey, 0ull};
-            float4 fw = make_float4(0.f, 0.f, 0.f, 0.f);
-            int o = 0;
-            if (c < total) {
-                int lo = 0, hi = T;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (s_base[mid] <= c) lo = mid;
-                    else hi = mid;
+        if (next_warp && c_lo == 0) resolve_next();
+        __syncthreads();
+        if (in_chunk)
+            for (int j = 0; j < nbx; ++j) n_cand += p_nc[jbase - p0 + j];
+
+        int total;
+        const int base = block_exclusive_scan(in_chunk ? n_cand : 0, s_scan, &total);
+        s_base[tid] = base;
+        if (tid == T - 1) s_base[T] = total;
+        if (tid == 0) {
+            if (total > 0) atomicAdd(&a.cnt->n_candidates, (unsigned long long)total);
+            int c0 = total > 0 && !F ? atomicAdd(&a.cnt->cand_used, total) : 0;
+            if (!F && total > 0 && c0 + total > a.cand_cap) {   // candidate buffer full: flagged, seeds left empty
+                raise_flag(a.cnt, DS_FLAG_CAND_CAPACITY);
+                c0 = -1;
+            }
+            s_cand0 = c0;
+        }
+        __syncthreads();
+        const int cand0 = s_cand0;
+        if (!F && active && in_chunk)
+            a.seed_cand[s] = cand0 >= 0 ? make_int4(cand0 + base, n_cand, e, 0) : make_int4(0, 0, e, 0);
+        // candidate c of the chunk decodes to (seed, pair, stereo options) in
+        // enumeration order
+        auto decode = [&](int c, int &o, int (&loc)[4], int &jr) {
+            int lo = 0, hi = T;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_base[mid] <= c) lo = mid;
+                else hi = mid;
+            }
+            o = lo;
+            int k = c - s_base[o];
+            int pp = (int)s_j0[o] - p0;
+            while (k >= p_nc[pp]) {
+                k -= p_nc[pp];
+                ++pp;
+            }
+            jr = p_oj[pp] & 15;
+            const int nv = p_sel[4 * PC + pp] != kNone ? 2 : 1;
+            const int iu = k / nv, iv = k - iu * nv;
+            const uint16_t a0 = p_sel[pp], u0 = p_sel[(1 + iu) * PC + pp], v0 = p_sel[(3 + iv) * PC + pp];
+            loc[0] = a0 == kNone ? -1 : a0;
+            loc[1] = u0 == kNone ? -1 : u0;
+            loc[2] = v0 == kNone ? -1 : v0;
+            loc[3] = colb[jr * T + o];
+        };
+        if (F) {
+            // fused: rounds of T candidates; each merges into its seed's
+            // minimum, then (after the round's barrier) the candidate holding
+            // the minimum keeps its fit beside it.  A later round's merge can
+            // only lower the minimum, and its holder then writes its own fit
+            // after that round's barrier, so the fit kept is always the minimum's.
+            for (int cr = 0; cr < total; cr += T) {
+                const int c = cr + tid;
+                KeyIds mine{kNoKey, 0ull};
+                float4 fw = make_float4(0.f, 0.f, 0.f, 0.f);
+                int o = 0;
+                if (c < total) {
+                    int loc[4], jr;
+                    decode(c, o, loc, jr);
+                    const SeedCtx sc = seed_ctx_of(g, s_sa[o], s_sb[o], __ldg(a.schi2 + s_begin + o));
+                    const CandFit f = fit_candidate(g, sc, X0, loc);
+                    float phi[16];
+                    phi[0] = f.xr * 1e-3f;
+                    phi[1] = f.yr * 1e-3f;
+                    phi[2] = f.t;
+                    phi[3] = sc.ty;
+                    phi[4] = 1e3f * f.qop;
+                    phi[5] = f.chi2 / (float)f.ndof;
+                    phi[6] = 1e3f * sc.qop;
+                    phi[7] = sc.chi2;
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) phi[8 + l] = f.res[l] * g.inv_sigma_hit;
+                    phi[12] = 0.25f * (float)f.nh;
+                    phi[13] = V == 1 ? fabsf(X0[loc[0]] - dv1_ua(g, sc, X0, loc[3])) / P.dv1_w_tri
+                                     : fabsf(X0[loc[3]] - sc.u_bx) / sc.w1;
+                    phi[14] = sc.tx;
+                    phi[15] = sc.ty;
+                    // what the pick needs is formed before the network, so that
+                    // little else is live while it runs
+#pragma unroll
+                    for (int l = 0; l < 4; ++l)
+                        mine.ids = (mine.ids << 16) | (loc[l] >= 0 ? (unsigned long long)__ldg(H.perm + loc[l]) : 0xFFFFull);
+                    fw = make_float4(f.xr, f.t, f.qop, f.chi2);
+                    const float chi2_ndof = phi[5];
+                    const float lg = mlp_logit_fp32<16, 32, 32>(a.nn, phi);
+                    if (P.pick_chi2) mine.key = pack_key(chi2_ndof, lg);
+                    else if (lg < P.thr_logit) mine.key = pack_key(lg, fw.w);
+                    if (mine.key != kNoKey) keyids_min(&s_best[o], mine);
                 }
-                o = lo;
-                int k = c - s_base[o];
-                int j = 0;
-                while (j < kK1Max - 1 && k >= s_nc[j][o]) {
-                    k -= s_nc[j][o];
-                    ++j;
+                __syncthreads();
+                if (mine.key != kNoKey) {
+                    const KeyIds b = s_best[o];
+                    if (b.key == mine.key && b.ids == mine.ids) s_win[o] = fw;
                 }
-                const int nv = s_sel[j][4][o] != kNone ? 2 : 1;
-                const int iu = k / nv, iv = k - iu * nv;
-                const uint16_t a0 = s_sel[j][0][o], u0 = s_sel[j][1 + iu][o], v0 = s_sel[j][3 + iv][o];
-                int loc[4];
-                loc[0] = a0 == kNone ? -1 : a0;
-                loc[1] = u0 == kNone ? -1 : u0;
-                loc[2] = v0 == kNone ? -1 : v0;
-                loc[3] = s_bx[j][o];
-                const SeedCtx sc = s_sc[o];
+            }
+        } else if (cand0 >= 0) {
+            // fit + network inputs, one candidate per thread
+            for (int c = tid; c < total; c += T) {
+                int o, loc[4], jr;
+                decode(c, o, loc, jr);
+                const SeedCtx sc = seed_ctx_of(g, s_sa[o], s_sb[o], __ldg(a.schi2 + s_begin + o));
                 const CandFit f = fit_candidate(g, sc, X0, loc);
                 float phi[16];
                 phi[0] = f.xr * 1e-3f;
@@ -906,32 +1028,33 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : 4) k_search(const __
                                  : fabsf(X0[loc[3]] - sc.u_bx) / sc.w1;
                 phi[14] = sc.tx;
                 phi[15] = sc.ty;
-                // what the pick needs is formed before the network, so that
-                // little else is live while it runs
+                const int slot = cand0 + c;
+                float4 *fd = a.cand_feat + 4 * (size_t)slot;
 #pragma unroll
-                for (int l = 0; l < 4; ++l)
-                    mine.ids = (mine.ids << 16) | (loc[l] >= 0 ? (unsigned long long)__ldg(H.perm + loc[l]) : 0xFFFFull);
-                fw = make_float4(f.xr, f.t, f.qop, f.chi2);
-                const float chi2_ndof = phi[5];
-                const float lg = mlp_logit_fp32<16, 32, 32>(a.nn, phi);
-                if (P.pick_chi2) mine.key = pack_key(chi2_ndof, lg);
-                else if (lg < P.thr_logit) mine.key = pack_key(lg, fw.w);
-                if (mine.key != kNoKey) keyids_min(&s_pb.c.best[o], mine);
-            }
-            __syncthreads();
-            if (mine.key != kNoKey) {
-                const KeyIds b = s_pb.c.best[o];
-                if (b.key == mine.key && b.ids == mine.ids) s_pb.c.win[o] = fw;
+                for (int q = 0; q < 4; ++q) fd[q] = make_float4(phi[4 * q], phi[4 * q + 1], phi[4 * q + 2], phi[4 * q + 3]);
+                CandMeta m;
+                m.xr = f.xr; m.yr = f.yr; m.t = f.t; m.qop = f.qop;
+                m.chi2 = f.chi2;
+                m.ndof = f.ndof;
+                m.seed = s_begin + o;
+                m.ty = sc.ty;
+#pragma unroll
+                for (int l = 0; l < 4; ++l) m.hit[l] = loc[l] >= 0 ? hit_id(H, loc[l]) : -1;
+                a.cand_meta[slot] = m;
             }
         }
-        __syncthreads();
+        __syncthreads();   // the next chunk rewrites the pair arrays
+        c_lo = c_hi;
+    }
+    if (F) {
         // each seed's winner as k_pick writes it: the 64-byte record (staged
-        // in s_sel, written below as contiguous 16-byte chunks), the pick key
-        // and the hit ids; a seed without one gets no record
-        int4 *s_rec = reinterpret_cast<int4 *>(&s_sel[0][0][0]);
+        // in the column rows, written below as contiguous 16-byte chunks),
+        // the pick key and the hit ids; a seed without one gets no record
+        int4 *s_rec = reinterpret_cast<int4 *>(&s_col[0][0]);
+        static_assert(!F || sizeof(s_col) >= 4 * T * sizeof(int4), "records fit the column rows");
         bool have = false;
         if (active) {
-            const KeyIds b = s_pb.c.best[tid];
+            const KeyIds b = s_best[tid];
             have = b.key != kNoKey;
             float lg = 0.f;
             if (have) lg = P.pick_chi2 ? unord_f32((unsigned)b.key) : unord_f32((unsigned)(b.key >> 32));
@@ -947,81 +1070,22 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : 4) k_search(const __
             a.key_ws[s] = have ? b.key : kNoKey;
             a.hit_ws[s] = make_int4(hid[0], hid[1], hid[2], hid[3]);
             if (have) {
-                const float4 fw = s_pb.c.win[tid];
-                const SeedCtx &sc = s_sc[tid];
-                const float yr = fmaf(sc.ty, g.z_ref - sc.zm, sc.ym);
+                const float4 fw = s_win[tid];
+                const float4 sa = s_sa[tid];
+                const float yr = fmaf(sa.w, g.z_ref - sa.x, sa.z);
                 // ds_track: event, seed, hit[4], x, y, tx, ty, qop, chi2, ndof, nn, flags, n_candidates
                 s_rec[4 * tid + 0] = make_int4(e, s, hid[0], hid[1]);
                 s_rec[4 * tid + 1] = make_int4(hid[2], hid[3], __float_as_int(fw.x), __float_as_int(yr));
-                s_rec[4 * tid + 2] = make_int4(__float_as_int(fw.y), __float_as_int(sc.ty), __float_as_int(fw.z),
+                s_rec[4 * tid + 2] = make_int4(__float_as_int(fw.y), __float_as_int(sa.w), __float_as_int(fw.z),
                                                __float_as_int(fw.w));
                 s_rec[4 * tid + 3] = make_int4(nh - 1, __float_as_int(sigmoid_fast(lg)), 0, n_cand);
             }
         }
-        s_nc[0][tid] = have ? 1 : 0;
+        s_base[tid] = have ? 1 : 0;
         __syncthreads();
         int4 *dst = reinterpret_cast<int4 *>(a.trk_ws + s_begin);
         for (int k = tid; k < 4 * (s_end - s_begin); k += T)
-            if (s_nc[0][k >> 2]) dst[k] = s_rec[k];
-    }
-    if (!F && cand0 >= 0) {
-
-    // fit + network inputs, one candidate per thread; candidate c of the CTA
-    // decodes to (seed, UTbX rank j, stereo options) in enumeration order
-    for (int c = tid; c < total; c += T) {
-        int lo = 0, hi = T;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_base[mid] <= c) lo = mid;
-            else hi = mid;
-        }
-        const int o = lo;
-        int k = c - s_base[o];
-        int j = 0;
-        while (j < kK1Max - 1 && k >= s_nc[j][o]) {
-            k -= s_nc[j][o];
-            ++j;
-        }
-        const int nv = s_sel[j][4][o] != kNone ? 2 : 1;
-        const int iu = k / nv, iv = k - iu * nv;
-        const uint16_t a0 = s_sel[j][0][o], u0 = s_sel[j][1 + iu][o], v0 = s_sel[j][3 + iv][o];
-        int loc[4];
-        loc[0] = a0 == kNone ? -1 : a0;
-        loc[1] = u0 == kNone ? -1 : u0;
-        loc[2] = v0 == kNone ? -1 : v0;
-        loc[3] = s_bx[j][o];
-        const SeedCtx sc = s_sc[o];
-        const CandFit f = fit_candidate(g, sc, X0, loc);
-        float phi[16];
-        phi[0] = f.xr * 1e-3f;
-        phi[1] = f.yr * 1e-3f;
-        phi[2] = f.t;
-        phi[3] = sc.ty;
-        phi[4] = 1e3f * f.qop;
-        phi[5] = f.chi2 / (float)f.ndof;
-        phi[6] = 1e3f * sc.qop;
-        phi[7] = sc.chi2;
-#pragma unroll
-        for (int l = 0; l < 4; ++l) phi[8 + l] = f.res[l] * g.inv_sigma_hit;
-        phi[12] = 0.25f * (float)f.nh;
-        phi[13] = V == 1 ? fabsf(X0[loc[0]] - dv1_ua(g, sc, X0, loc[3])) / P.dv1_w_tri
-                         : fabsf(X0[loc[3]] - sc.u_bx) / sc.w1;
-        phi[14] = sc.tx;
-        phi[15] = sc.ty;
-        const int slot = cand0 + c;
-        float4 *fd = a.cand_feat + 4 * (size_t)slot;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) fd[q] = make_float4(phi[4 * q], phi[4 * q + 1], phi[4 * q + 2], phi[4 * q + 3]);
-        CandMeta m;
-        m.xr = f.xr; m.yr = f.yr; m.t = f.t; m.qop = f.qop;
-        m.chi2 = f.chi2;
-        m.ndof = f.ndof;
-        m.seed = s_begin + o;
-        m.ty = sc.ty;
-#pragma unroll
-        for (int l = 0; l < 4; ++l) m.hit[l] = loc[l] >= 0 ? hit_id(H, loc[l]) : -1;
-        a.cand_meta[slot] = m;
-    }
+            if (s_base[k >> 2]) dst[k] = s_rec[k];
     }
     __syncthreads();   // shared state is reused by the next item; s_nx is visible
     }   // work items

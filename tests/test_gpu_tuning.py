@@ -57,7 +57,7 @@ def test_outputs_do_not_depend_on_tuning(torch_cuda, weights):
     dev = d.to_device(b)
     # search: chunk, CTAs per SM, group, staging; vertexing: CTAs per SM, one-event-per-CTA
     # track limit (2: every event with two or more tracks goes to the pair-segment items)
-    shapes = [(128, 4, 2, 5632, 4, 512), (32, 1, 1, 0, 1, 64), (64, 3, 8, 32768, 2, 128), (1, 2, 16, 2048, 3, 256),
+    shapes = [(128, 4, 2, 5632, 4, 512), (128, 5, 1, 5120, 4, 512), (32, 1, 1, 0, 1, 64), (64, 3, 8, 32768, 2, 128), (1, 2, 16, 2048, 3, 256),
               (96, 4, 4, 46080, 4, 2)]
     ref = None
     for shape in shapes:
@@ -75,7 +75,7 @@ def test_invalid_tuning_refused(torch_cuda, weights):
     from paper_2503_13092_b300 import ds
     d = ds.Downstream(synth.default_config(), weights)
     before = ds.ds_get_tuning(d.ctx).as_dict()
-    for bad in [(0, 4, 2, 5632), (129, 4, 2, 5632), (128, 0, 2, 5632), (128, 5, 2, 5632), (128, 4, 0, 5632),
+    for bad in [(0, 4, 2, 5632), (129, 4, 2, 5632), (128, 0, 2, 5632), (128, 9, 2, 5632), (128, 4, 0, 5632),
                 (128, 4, 17, 5632), (128, 4, 2, -1), (128, 4, 2, 46081), (128, 4, 2, 5632, 0, 512),
                 (128, 4, 2, 5632, 5, 512), (128, 4, 2, 5632, 4, 1), (128, 4, 2, 5632, 4, 513)]:
         with pytest.raises(ds.DSError):
