@@ -319,6 +319,32 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *scratch, int *to
     return base + x - v;
 }
 
+// block_exclusive_scan with one barrier: every warp scans the warp totals
+// itself.  The caller must not hand the same scratch to another scan before
+// the block has met again (the totals are read after the barrier).
+__device__ __forceinline__ int block_exclusive_scan1(int v, int *scratch, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) scratch[warp] = x;
+    __syncthreads();
+    int w = lane < nwarps ? scratch[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+    }
+    const int before = __shfl_sync(0xffffffffu, w, (warp + 31) & 31);   // inclusive total of the warps before
+    *total = __shfl_sync(0xffffffffu, w, nwarps - 1);
+    return (warp > 0 ? before : 0) + x - v;
+}
+
 // Exclusive prefix sums of n counts written by other CTAs (read from L2):
 // off[i] = cnt[0] + ... + cnt[i - 1] for i < n; returns the total to every
 // thread.  One contiguous chunk per thread, all of its loads issued before

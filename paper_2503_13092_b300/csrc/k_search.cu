@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : (V == 0 ? kSearchCta
     __shared__ __align__(16) KeyIds s_best[F ? T : 1];   // fused: each seed's best key + hit indices
     __shared__ __align__(16) float4 s_win[F ? T : 1];    // fused: x_ref, tx, q/p, chi2 of the best
     __shared__ int s_cand0;
-    __shared__ int s_scan[32];
+    __shared__ int s_scan[64];          // two scan scratch areas (first-window pairs, candidates)
     __shared__ int s_nx[6];     // next work item: index, event, seed begin, seed end, h0, h1
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ __align__(8) uint64_t s_bar_fi;   // fault injection only: a barrier no copy targets
@@ -849,13 +849,18 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : (V == 0 ? kSearchCta
             nbx = min(sel_n, P.k1);   // the kept hits are the column's first nbx rows
         }
     }
-    // the item's (seed, UTbX hit) pairs in seed order, then rank order
+    // the item's (seed, UTbX hit) pairs in seed order, then rank order.  The
+    // scan's barrier also ends every column's first-window use, so the rows
+    // above the kept ones are free for the pair arrays from here on.
     int total_j;
-    const int jbase = block_exclusive_scan(nbx, s_scan, &total_j);
+    const int jbase = block_exclusive_scan1(nbx, s_scan, &total_j);
     s_j0[tid] = (uint16_t)jbase;
     if (tid == T - 1) s_j0[T] = (uint16_t)(jbase + nbx);
     if (F) s_best[tid] = KeyIds{kNoKey, ~0ull};
-    __syncthreads();   // every column is final; the rows above the kept ones are free
+    const bool one_chunk = total_j <= PC;   // the usual case: the pairs are written here
+    if (one_chunk && active)
+        for (int j = 0; j < nbx; ++j) p_oj[jbase + j] = (uint16_t)((tid << 4) | j);
+    __syncthreads();
 
     const int n_item = s_end - s_begin;
     int n_cand = 0;    // this thread's seed: its candidates (set in its chunk)
@@ -873,9 +878,11 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : (V == 0 ? kSearchCta
         }
         const int np = (int)s_j0[c_hi] - p0;
         const bool in_chunk = tid >= c_lo && tid < c_hi;
-        if (in_chunk)
-            for (int j = 0; j < nbx; ++j) p_oj[jbase - p0 + j] = (uint16_t)((tid << 4) | j);
-        __syncthreads();
+        if (!one_chunk) {
+            if (in_chunk)
+                for (int j = 0; j < nbx; ++j) p_oj[jbase - p0 + j] = (uint16_t)((tid << 4) | j);
+            __syncthreads();
+        }
 
         // refined windows, one (seed, UTbX hit) pair per thread: every lane
         // does the same three window searches whatever the hits per seed
@@ -914,7 +921,7 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : (V == 0 ? kSearchCta
             for (int j = 0; j < nbx; ++j) n_cand += p_nc[jbase - p0 + j];
 
         int total;
-        const int base = block_exclusive_scan(in_chunk ? n_cand : 0, s_scan, &total);
+        const int base = block_exclusive_scan1(in_chunk ? n_cand : 0, s_scan + 32, &total);
         s_base[tid] = base;
         if (tid == T - 1) s_base[T] = total;
         if (tid == 0) {
@@ -1043,7 +1050,9 @@ __global__ void __launch_bounds__(T, F ? kSearchFusedCtas : (V == 0 ? kSearchCta
                 a.cand_meta[slot] = m;
             }
         }
-        __syncthreads();   // the next chunk rewrites the pair arrays
+        // the next chunk rewrites the pair arrays (after the last one the
+        // item's closing barrier covers the unfused form)
+        if (F || c_hi < n_item) __syncthreads();
         c_lo = c_hi;
     }
     if (F) {
