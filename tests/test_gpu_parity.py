@@ -275,6 +275,30 @@ def test_edge_cases(torch_cuda, weights):
     assert small["tracks"].tobytes() == full["tracks"][:100].tobytes()
 
 
+def test_candidate_buffer_overflow(torch_cuda, weights):
+    """A candidate buffer too small for the batch (one slot per seed, about 1.5
+    candidates per seed are found) is flagged; the seeds whose candidates were
+    written keep exactly the tracks of an unconstrained run, the others get none.
+    Clone killing is off, so a track does not depend on which other seeds of its
+    event were dropped."""
+    from paper_2503_13092_b300 import ds
+    cfg = synth.default_config()
+    b = synth.config_batch("c2", n_events=60)
+    full = make(torch_cuda, cfg, weights, clone_kill=0).run(b)
+    assert full["stats"]["status"] == 0
+    d = make(torch_cuda, cfg, weights, clone_kill=0, cand_per_seed=1)
+    dev = d.to_device(b)
+    out = d.alloc_tracks(b["n_events"], int(b["seed_off"][-1]))
+    d.reconstruct(dev, out)
+    st = d.sync(raise_on_error=False)
+    assert st["device_flags"] & ds.DS_FLAG_CAND_CAPACITY
+    got = ds.decode(out)
+    assert 0 < got["n_tracks"] < full["n_tracks"]
+    ref = {int(t["seed"]): t.tobytes() for t in full["tracks"]}
+    for t in got["tracks"]:
+        assert ref[int(t["seed"])] == t.tobytes()
+
+
 def concat(parts):
     out = dict(n_events=sum(p["n_events"] for p in parts))
     so, ho = [np.zeros(1, np.int32)], [np.zeros(1, np.int32)]
