@@ -12,7 +12,8 @@
 // k_mlp_fp32: one candidate per thread over the whole candidate buffer (every
 // lane busy); weights in the kernel's parameter bank with compile-time indices
 // (the paper's static network structure, GPU Implementation section).
-// k_pick: one thread per seed over its contiguous candidates.
+// k_pick: one warp per 32 consecutive seeds, its lanes over their (contiguous)
+// candidates, a segmented minimum per seed.
 #include "ds_args.cuh"
 
 namespace ds {
@@ -45,8 +46,17 @@ __device__ __forceinline__ bool hits_less(const CandMeta *x, const CandMeta *y)
     return false;
 }
 
-constexpr int kPickBatch = 8;
+// hits_less kept out of line: only exact key ties call it, and its loads
+// stay out of the common path.
+__device__ __noinline__ bool hits_less_ool(const CandMeta *x, const CandMeta *y) { return hits_less(x, y); }
 
+// One warp per 32 consecutive seeds (one per lane).  The warp's candidates
+// (each seed's are contiguous) are read 32 at a time, one per lane, with the
+// warp's prefix of the seeds' counts mapping a lane to its candidate; a
+// segmented minimum over the lanes of one seed (contiguous lanes) leaves each
+// run's best key in its first lane, which the seed's lane merges into its
+// running best.  Equal keys are ordered by the hit ids.  Every lane reads one
+// candidate per round, whatever the candidates per seed.
 __global__ void __launch_bounds__(256) k_pick(const __grid_constant__ PickArgs a)
 {
     // each warp stages its 32 winner records in shared memory and writes them
@@ -57,43 +67,69 @@ __global__ void __launch_bounds__(256) k_pick(const __grid_constant__ PickArgs a
     const int warp_s0 = s - lane;
     const bool valid = s < a.n_seeds && s >= __ldg(a.seed_off) && s < __ldg(a.seed_off + a.n_events);
     const DevParams &P = a.p;
+    const float thr = P.thr_logit;
+    const int4 sc = valid ? a.seed_cand[s] : make_int4(0, 0, 0, 0);   // first candidate, count, event
+    int incl = sc.y;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int off = incl - sc.y;                 // this seed's first position in the warp's list
+    const int n = __shfl_sync(0xffffffffu, incl, 31);
     unsigned long long best = kNoKey;
+    int bi = -1;
+    for (int r0 = 0; r0 < n; r0 += 32) {
+        const int k = r0 + lane;
+        // the seed (lane) owning list position k: the last lane starting at or before k
+        int L = 0;
+#pragma unroll
+        for (int st = 16; st >= 1; st >>= 1) {
+            const int o = __shfl_sync(0xffffffffu, off, L + st);
+            if (o <= k) L += st;
+        }
+        const int offL = __shfl_sync(0xffffffffu, off, L), firstL = __shfl_sync(0xffffffffu, sc.x, L);
+        const bool live = k < n;
+        const int c = firstL + k - offL;
+        unsigned long long key = kNoKey;
+        if (live) {
+            const float lg = __ldg(a.logit + c);
+            const float2 q = __ldg(reinterpret_cast<const float2 *>(a.meta + c) + 2);   // chi2, ndof
+            if (P.pick_chi2) key = pack_key(q.x / (float)__float_as_int(q.y), lg);
+            else if (lg < thr) key = pack_key(lg, q.x);
+        }
+        const int own = live ? L : -1 - lane;        // lanes past the end stay apart
+        unsigned long long bk = key;
+        int bc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long ok = __shfl_down_sync(0xffffffffu, bk, o);
+            const int oc = __shfl_down_sync(0xffffffffu, bc, o);
+            const int oo = __shfl_down_sync(0xffffffffu, own, o);
+            const bool same = lane + o < 32 && oo == own;
+            bool take = same && ok < bk;
+            const bool tie = same && ok == bk && ok != kNoKey;
+            if (__any_sync(0xffffffffu, tie) && tie) take = hits_less_ool(a.meta + oc, a.meta + bc);
+            if (take) {
+                bk = ok;
+                bc = oc;
+            }
+        }
+        // this seed's run inside the round starts at lane h
+        const bool in_round = sc.y > 0 && off < r0 + 32 && off + sc.y > r0;
+        const int h = max(off - r0, 0) & 31;
+        const unsigned long long vk = __shfl_sync(0xffffffffu, bk, h);
+        const int vc = __shfl_sync(0xffffffffu, bc, h);
+        if (in_round && (vk < best || (vk == best && vk != kNoKey && hits_less_ool(a.meta + vc, a.meta + bi)))) {
+            best = vk;
+            bi = vc;
+        }
+    }
     int4 hits = make_int4(-1, -1, -1, -1);
     int4 r0 = make_int4(0, 0, -1, -1), r1 = make_int4(-1, -1, 0, 0), r2 = make_int4(0, 0, 0, 0),
          r3 = make_int4(0, 0, 0, 0);
     if (valid) {
-        const int4 sc = a.seed_cand[s];        // first candidate, count, event
-        const float thr = P.thr_logit;
-        int bi = -1;
-        // candidates in rounds of kPickBatch whose loads are all in flight
-        // together: a seed with many candidates waits for a few round trips,
-        // not one per candidate
-        for (int k0 = 0; k0 < sc.y; k0 += kPickBatch) {
-            float lg[kPickBatch];
-            float2 q[kPickBatch];   // chi2, ndof
-#pragma unroll
-            for (int k = 0; k < kPickBatch; ++k)
-                if (k0 + k < sc.y) {
-                    const int c = sc.x + k0 + k;
-                    lg[k] = __ldg(a.logit + c);
-                    q[k] = __ldg(reinterpret_cast<const float2 *>(a.meta + c) + 2);
-                }
-#pragma unroll
-            for (int k = 0; k < kPickBatch; ++k)
-                if (k0 + k < sc.y) {
-                    const int c = sc.x + k0 + k;
-                    const float chi2 = q[k].x;
-                    const int ndof = __float_as_int(q[k].y);
-                    unsigned long long key = kNoKey;
-                    if (P.pick_chi2) key = pack_key(chi2 / (float)ndof, lg[k]);
-                    else if (lg[k] < thr) key = pack_key(lg[k], chi2);
-                    if (key < best || (key == best && key != kNoKey && hits_less(a.meta + c, a.meta + bi))) {
-                        best = key;
-                        bi = c;
-                    }
-                }
-        }
-        bool have = bi >= 0;
+        bool have = best != kNoKey;
         float lg_best = 0.f;
         if (have) lg_best = P.pick_chi2 ? unord_f32((unsigned)best) : unord_f32((unsigned)(best >> 32));
         if (have && P.pick_chi2 && !(lg_best < thr)) have = false;
@@ -114,6 +150,8 @@ __global__ void __launch_bounds__(256) k_pick(const __grid_constant__ PickArgs a
         }
         a.key_ws[s] = best;
         a.hit_ws[s] = hits;
+    } else {
+        best = kNoKey;
     }
     // only winners' records are read later (the clone kernel ranks winners
     // alone, the scatter copies ranked seeds): the others are not written
