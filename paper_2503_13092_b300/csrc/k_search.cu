@@ -522,7 +522,7 @@ constexpr int kColRowsBig = 50;
 // V = 0: Dv0.  V = 1: Dv1, whose first stage is the triplet search.
 // F: fused network and pick (FP32 network 16-32-32-1).
 template <int V, bool F>
-__global__ void __launch_bounds__(T, F ? kSearchFusedCtas : (V == 0 ? kSearchCtasPerSm : 4))
+__global__ void __launch_bounds__(T, F ? (V == 1 ? 3 : kSearchFusedCtas) : (V == 0 ? kSearchCtasPerSm : 4))
     k_search(const __grid_constant__ SearchArgs a)
 {
     using L = SearchLayout<V, F>;
