@@ -12,9 +12,10 @@
 //   magnet point) and its 16 network inputs are formed.  The network and the
 //   best pick run in k_mlp.cu over all candidates of the batch.
 //
-// Work decomposition (B300): persistent CTAs, 4 per SM, take work items (up
-// to 128 seeds of one event) from a device queue; the last warp resolves the
-// next item while the block finishes the current one.  The event's bin table (with its partial-strip row bits) and
+// Work decomposition (B300): persistent CTAs, 5 per SM (the fused form 4, 3
+// for Dv1), take work items (up to 128 seeds of one event) from a device
+// queue; the last warp resolves the next item while the block finishes the
+// current one.  The event's bin table (with its partial-strip row bits) and
 // compact x0 array are staged in shared memory by two bulk copies (TMA) on an
 // mbarrier; every x test of every window reads shared memory, and a hit
 // passing it looks up its strip extent and id (through the sorted index map
@@ -22,10 +23,11 @@
 // the sector or its distance ties with another hit's; the ids of a
 // candidate's hits are looked up when it is written.
 // Three flattened phases keep lanes busy whatever the hits per seed: UTbX
-// window (thread per seed), refined windows (thread per (seed, UTbX hit)),
-// fit + features (thread per candidate).  Unfused form: candidates are
-// written to a compact buffer reserved with one atomicAdd per CTA, seed by
-// seed, for k_mlp / k_pick.  Fused form (FP32 network): each candidate's
+// window (thread per seed), refined windows (thread per (seed, UTbX hit)
+// pair, in seed-aligned chunks of at most 640 pairs), fit + features (thread
+// per candidate of the chunk).  Unfused form: candidates are written to a
+// compact buffer reserved with one atomicAdd per chunk, seed by seed, for
+// k_mlp / k_pick.  Fused form (FP32 network): each candidate's
 // thread also evaluates the network (Ghost-Killer Neural Network section: the
 // network runs inside the tracking, weights in the parameter bank) and merges
 // its pick key with the hit ids of its layers into its seed's running minimum
