@@ -299,6 +299,35 @@ def test_candidate_buffer_overflow(torch_cuda, weights):
         assert ref[int(t["seed"])] == t.tobytes()
 
 
+@pytest.mark.parametrize("variant", [0, 1])
+def test_chunked_refined_windows(torch_cuda, weights, variant):
+    """An item whose (seed, UTbX hit) pairs exceed what the search keeps per
+    chunk (640): one event of 128 true seeds, each of whose UTbX hits gets 11
+    companions within 1.5 mm on the same strip, so every seed keeps k1 = 10
+    UTbX hits (Dv0; Dv1 keeps the triplets among them whose UTaX window holds
+    a hit) and the event's single work item holds far more pairs than one
+    chunk, processed in seed-aligned chunks.  Tracks must match the oracle
+    seed by seed."""
+    cfg = synth.default_config(variant=variant)
+    b = synth.generate(synth.spec_fixed(1, 128, 0, 1500), 11)
+    rng = np.random.Generator(np.random.PCG64(11))
+    bx = np.flatnonzero((b["hit_layer"] == 3) & (b["hit_track"] >= 0))
+    extra = np.repeat(bx, 11)
+    n0 = len(b["hit_x0"])
+    for k in ("hit_ybeg", "hit_yend", "hit_layer", "hit_track"):
+        b[k] = np.concatenate([b[k], b[k][extra]])
+    b["hit_track"][n0:] = -1
+    b["hit_x0"] = np.concatenate([b["hit_x0"], (b["hit_x0"][extra] +
+                                                rng.uniform(-1.5, 1.5, len(extra))).astype(np.float32)])
+    b["hit_off"] = np.array([0, len(b["hit_x0"])], np.int32)
+    assert int(b["seed_off"][-1]) == 128 and len(bx) >= 120
+    d = make(torch_cuda, cfg, weights, cand_per_seed=40)
+    g, o, rep, vrep = run_both(d, b, cfg, weights)
+    assert g["stats"]["n_candidates"] > (1280 if variant == 0 else 700)
+    parity.assert_tracks_match(rep)
+    parity.assert_vertices_match(vrep)
+
+
 def concat(parts):
     out = dict(n_events=sum(p["n_events"] for p in parts))
     so, ho = [np.zeros(1, np.int32)], [np.zeros(1, np.int32)]
