@@ -326,6 +326,12 @@ def test_chunked_refined_windows(torch_cuda, weights, variant):
     assert g["stats"]["n_candidates"] > (1280 if variant == 0 else 700)
     parity.assert_tracks_match(rep)
     parity.assert_vertices_match(vrep)
+    # the fused form (network and pick inside the search, 784 pairs per chunk)
+    # chunks the same item too and must give the same records byte for byte
+    gf = make(torch_cuda, cfg, weights, fuse_network=1).run(b)
+    assert gf["stats"]["status"] == 0
+    assert gf["tracks"].tobytes() == g["tracks"].tobytes()
+    assert gf["vertices"].tobytes() == g["vertices"].tobytes()
 
 
 def concat(parts):
