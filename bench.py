@@ -267,6 +267,23 @@ def _sub(b, events):
     return out
 
 
+def replicas_for(E, S, H):
+    """Input replicas the timed steps rotate over, so that every step reads
+    inputs that are not in L2 (more than three L2s of inputs in all)."""
+    in_bytes = 24 * S + 13 * H + 8 * (E + 1)
+    R = max(2, math.ceil(3 * L2_BYTES / in_bytes))
+    return STREAMS * math.ceil(R / STREAMS), in_bytes    # replica k % R belongs to stream k % STREAMS
+
+
+def workload_config(E, S, H, ws):
+    """The `config` of both arms' JSON lines: the workload and how L2 is kept
+    out of the timing (run statistics go to `step_stats`)."""
+    R, in_bytes = replicas_for(E, S, H)
+    return dict(workload=WORKLOAD, n_events=E, n_seeds=S, n_hits=H, mlp="fp32",
+                l2=f"inputs rotate over {R} replicas ({R * in_bytes / 2**20:.0f} MB > 3x L2)",
+                parallelism=f"replicas x{ws}" if ws > 1 else "single GPU")
+
+
 def bench_reference(args):
     """FP64 CPU oracle, as it stands, on the host cores (rank 0 only)."""
     ws, rank, _ = dist_info()
@@ -295,9 +312,10 @@ def bench_reference(args):
     line = dict(metric="events/s per B300 (Downstream+vertexing)", value=val, unit="events/s", n_gpus=args.gpus,
                 steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * t / args.steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=WORKLOAD, n_events=N_EVENTS, sample_events_per_step=per_step),
+                config=workload_config(int(batch["n_events"]), int(batch["seed_off"][-1]), int(batch["hit_off"][-1]), ws),
                 cpu_baseline=dict(value=val, unit="events/s", cores=cores, kind="oracle",
-                                  sample=f"{per_step} events per step of the same batch, {cores} threads"),
+                                  sample=f"{per_step} events per step of the same batch, {cores} threads",
+                                  sample_events_per_step=per_step),
                 e2e=dict(value=val, unit="events/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
     return 0
@@ -781,9 +799,7 @@ def main():
                               tracks=st["n_tracks"], vertices=st["n_vertices"])), flush=True)
         d.close()
         return 0
-    in_bytes = 24 * S + 13 * H + 8 * (E + 1)
-    R = max(2, math.ceil(3 * L2_BYTES / in_bytes))
-    R = STREAMS * math.ceil(R / STREAMS)     # replica k % R belongs to stream k % STREAMS
+    R, in_bytes = replicas_for(E, S, H)
     devs = [d.to_device(batch) for _ in range(R)]
     out = d.alloc_tracks(E, S)
     # size the vertex output from one run
@@ -1077,11 +1093,9 @@ def main():
             metric="events/s per B300 (Downstream+vertexing)", value=agg["value"], unit="events/s", n_gpus=ws,
             steps=args.steps, warmup=args.warmup, ms_per_step=agg["ms_per_step"], higher_is_better=True,
             scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-            config=dict(workload=WORKLOAD, n_events=E, n_seeds=S, n_hits=H, tracks=n_t, vertices=n_v,
-                        candidates=n_cand, pairs=n_pairs, pairs_fp64=n_fp64, mlp="fp32",
-                        l2=f"inputs rotate over {R} replicas ({R * in_bytes / 2**20:.0f} MB > 3x L2)",
-                        streams=STREAMS,
-                        parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
+            config=workload_config(E, S, H, ws),
+            step_stats=dict(tracks=n_t, vertices=n_v, candidates=n_cand, pairs=n_pairs, pairs_fp64=n_fp64,
+                            streams=STREAMS),
             single_stream=single,
             roofline=roof, path_roofline=path, kernels=kernels, clocks=clocks, e2e=e2e, e2e_single_call=e2e_single,
             mlp_forms=mlp_forms, network_in_search=fused_form, ghost_killer_training=trained, vertex_physics=vphys, variants=variants,
