@@ -283,7 +283,7 @@ typedef struct {
     int32_t vertex_ctas_per_sm; /* CTAs per SM of the vertexing launch that takes one event
                                    per CTA, 1..4 (default 4) */
     int32_t vertex_small_cap;   /* events with at most this many tracks are vertexed one per
-                                   CTA; larger ones as (event, 65536-pair segment) work items
+                                   CTA; larger ones as (event, 131072-pair range) work items
                                    spread over the SMs, 2..512 (default 512) */
 } ds_tuning;
 

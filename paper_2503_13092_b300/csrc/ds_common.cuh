@@ -41,9 +41,10 @@ constexpr int kBucketStage = 6144;   // events up to this many hits are sorted i
 constexpr int kMaxVertexTracks = 4096; // tracks per event staged for vertexing
 constexpr int kVtxCtasPerSmMax = 4;   // one-event-per-CTA vertexing: resident CTAs per SM at most (default)
 constexpr int kVtxSmallCapMax = 512;  // its largest event (tracks staged per CTA); default limit
-constexpr int kVtxLargeSeg = 65536;  // pairs per work item of the large-capacity vertex launch
+constexpr int kVtxLargeSeg = 65536;  // pairs per segment of the large-capacity vertex launch
+constexpr int kVtxItemPairs = 2 * kVtxLargeSeg;   // pairs per work item there: two segments, the event's tracks staged once
 // items of one event: its opposite-charge pairs, at most (4096 / 2)^2, in segments
-constexpr int kVtxItemsPerEvent = (kMaxVertexTracks / 2) * (kMaxVertexTracks / 2) / kVtxLargeSeg;
+constexpr int kVtxItemsPerEvent = (kMaxVertexTracks / 2) * (kMaxVertexTracks / 2) / kVtxItemPairs;
 constexpr unsigned long long kNoKey = ~0ull;
 
 // Per-event table: nb + 1 = 4 n_sec kNXB + 1 uint16 offsets padded to 8

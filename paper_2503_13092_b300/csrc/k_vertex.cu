@@ -437,8 +437,8 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
         if (threadIdx.x == 0) s_row[nt] = npairs;
         __syncthreads();
         // the pairs this CTA solves: all of the event's, or one item's segment
-        const int p_begin = LARGE ? min(seg_k * kVtxSeg, npairs) : 0;
-        const int p_end = LARGE ? min(p_begin + kVtxSeg, npairs) : npairs;
+        const int p_begin = LARGE ? min(seg_k * kVtxItemPairs, npairs) : 0;
+        const int p_end = LARGE ? min(p_begin + kVtxItemPairs, npairs) : npairs;
         if (threadIdx.x == 0 && p_end > p_begin) atomicAdd(&a.cnt->n_pairs, (unsigned long long)(p_end - p_begin));
         // pair p of the current segment (first pair seg0) -> (i, j), i < j,
         // opposite charges, (i, j) order, and their slots: from the row of p's
@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
         if (threadIdx.x == 0) a.cnt->pool_small = *(volatile const int *)&a.cnt->pool_used;
         if (n_large > 0) {
             const int tot = block_offsets_f(
-                [&a](int j) { return (__ldcg(a.large_pairs + j) + VtxSeg<true>::seg - 1) / VtxSeg<true>::seg; },
+                [&a](int j) { return (__ldcg(a.large_pairs + j) + kVtxItemPairs - 1) / kVtxItemPairs; },
                 n_large, a.large_item_off, s_scan);
             if (threadIdx.x == 0) {
                 a.large_item_off[n_large] = tot;
@@ -808,7 +808,7 @@ cudaError_t launch_vertex(const VertexArgs &a0, const ScatterVtxArgs &sa, int sm
     if (a.small_cap < 2 || a.small_cap > kVtxSmallCap || a.ctas_per_sm < 1 || a.ctas_per_sm > kVtxCtasPerSm)
         return cudaErrorInvalidValue;
     const int g_small = a.n_events < a.ctas_per_sm * sm_count ? a.n_events : a.ctas_per_sm * sm_count;
-    // persistent over (event, pair segment) items: at most kVtxItemsPerEvent per event
+    // persistent over (event, two-segment pair range) items: at most kVtxItemsPerEvent per event
     const long long items_max = (long long)kVtxItemsPerEvent * a.n_events;
     const int g_large = items_max < sm_count ? (int)items_max : sm_count;
     prof->begin("k_vertex_small", st);
