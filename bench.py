@@ -136,10 +136,7 @@ def algorithmic(E, S, H, n_t, n_v, n_cand, n_pairs, table_stride, fused=True):
         "k_bucket": dict(bytes=13 * H + 6 * H + tb),
         "k_search": dict(bytes=search, flop=mlp_flop * n_cand if fused else 0),
         "k_mlp": dict(bytes=68 * n_cand, flop=mlp_flop * n_cand),
-        # unfused step: the pick and clone killing per event in one kernel (the
-        # keys and hit ids are not read back from the workspace)
-        "k_pick_clone": dict(bytes=16 * S + 20 * n_cand + 48 * n_t + 88 * S + 4 * S + 8 * E),
-        # fused search: clone killing alone
+        "k_pick": dict(bytes=16 * S + 20 * n_cand + 48 * n_t + 88 * S),
         "k_clone": dict(bytes=28 * S + 8 * E),
         "k_scatter_tracks": dict(bytes=4 * S + 128 * n_t),
         "k_vertex_small": dict(bytes=20 * n_t + 36 * n_v),
@@ -968,7 +965,7 @@ def main():
     fused_form = dict(kernels_us=fused_form, step_us=sum(1e3 * v[1] for v in prf.values()) / n_prof,
                       separate_step_us=step_us,
                       note="network + pick inside k_search (fuse_network = 1) against the separate k_mlp and "
-                           "per-event k_pick_clone (default), CUDA-event time per kernel, same steps")
+                           "k_pick (default), CUDA-event time per kernel, same steps")
     dom = max(kernels, key=lambda k: kernels[k]["share"])
     hbm, sm_mhz, src = peaks()
     kd = kernels[dom]

@@ -566,7 +566,7 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     pa.trk_ws = ctx->trk_ws;
     pa.key_ws = ctx->key_ws;
     pa.hit_ws = ctx->hit_ws;
-    if (!sa.fused) DS_CUDA(ds::launch_network(ma, ctx->sm_count, st, &ctx->prof), "network kernel");
+    if (!sa.fused) DS_CUDA(ds::launch_mlp_pick(ma, pa, ctx->sm_count, st, &ctx->prof), "network kernel");
 
     ds::CloneArgs ca{};
     ca.n_events = b->n_events;
@@ -591,10 +591,7 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     xa.trk_off = out->trk_off;
     xa.out = out->tracks;
     xa.capacity = out->capacity;
-    // unfused: the pick runs per event with clone killing; the fused search
-    // has written the winners already
-    if (sa.fused) DS_CUDA(ds::launch_clone(ca, xa, st, &ctx->prof), "clone kernel");
-    else DS_CUDA(ds::launch_pick_clone(pa, ca, xa, st, &ctx->prof), "pick and clone kernel");
+    DS_CUDA(ds::launch_clone(ca, xa, st, &ctx->prof), "clone kernel");
     return DS_OK;
 }
 

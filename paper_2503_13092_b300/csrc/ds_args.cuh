@@ -58,7 +58,7 @@ struct SearchArgs {
     int *rank_ws;
     // fused form (fused = 1): every candidate is scored by the FP32 network
     // (16-32-32-1) inside the search and only each seed's winner leaves it,
-    // as the pick (pick.cuh) would write it: record, pick key and hit ids per seed
+    // as k_pick would write it: record, pick key and hit ids per seed
     int fused;
     DevNN nn;
     ds_track *trk_ws;
@@ -224,7 +224,7 @@ cudaError_t init_bucket_attributes();
 cudaError_t init_search_attributes();
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t st, Prof *prof);
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, Prof *prof);
-cudaError_t launch_network(const MlpArgs &m, int sm_count, cudaStream_t st, Prof *prof);
+cudaError_t launch_mlp_pick(const MlpArgs &m, const PickArgs &p, int sm_count, cudaStream_t st, Prof *prof);
 // the network alone over n_bound candidates at most (m.n_host or the device count)
 cudaError_t launch_mlp(const MlpArgs &m, int sm_count, int n_bound, cudaStream_t st);
 cudaError_t launch_mlp_tc(const MlpArgs &m, int sm_count, int n_bound, cudaStream_t st);
@@ -234,9 +234,6 @@ cudaError_t launch_export_candidates(const float4 *feat, const CandMeta *meta, c
                                      const DevCounters *cnt, float *o_feat, int32_t *o_seed, int32_t *o_hits,
                                      float *o_logit, int capacity, int32_t *o_count, int sm_count, cudaStream_t st);
 cudaError_t launch_clone(const CloneArgs &a, const ScatterTrkArgs &sa, cudaStream_t st, Prof *prof);
-// the pick (a7) and clone killing per event in one kernel, then the scatter
-cudaError_t launch_pick_clone(const PickArgs &p, const CloneArgs &a, const ScatterTrkArgs &sa, cudaStream_t st,
-                              Prof *prof);
 cudaError_t launch_vertex(const VertexArgs &a, const ScatterVtxArgs &sa, int sm_count, cudaStream_t st,
                           Prof *prof);
 

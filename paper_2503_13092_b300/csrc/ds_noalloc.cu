@@ -190,7 +190,7 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         pa.trk_ws = reinterpret_cast<ds_track *>(base + kOffTrk);
         pa.key_ws = reinterpret_cast<unsigned long long *>(base + kOffKey);
         pa.hit_ws = reinterpret_cast<int4 *>(base + kOffHit);
-        if (launch_network(ma, sm_count, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
+        if (launch_mlp_pick(ma, pa, sm_count, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
 
         CloneArgs ca{};
         ca.n_events = b->n_events;
@@ -215,7 +215,7 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         xa.trk_off = out->trk_off;
         xa.out = out->tracks;
         xa.capacity = out->capacity;
-        if (launch_pick_clone(pa, ca, xa, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
+        if (launch_clone(ca, xa, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
     }
     if (d_flags) {
         k_noalloc_flags<<<1, 1, 0, s>>>(cnt, d_flags);

@@ -15,7 +15,6 @@
 // turns the per-event counts into trk_off with one scan; a second kernel
 // scatters the surviving records to the packed output in (event, seed) order.
 #include "ds_args.cuh"
-#include "pick.cuh"
 
 namespace ds {
 
@@ -141,147 +140,6 @@ __global__ void __launch_bounds__(kCloneThreads, kCloneCtasPerSm) k_clone(const 
 }
 
 
-// The pick (a7) and clone killing of one event per CTA.  The CTA's warps
-// pick the event's seeds 32 at a time (pick.cuh); each seed's key and hit ids
-// go to the workspace and, for events up to kCloneSmem seeds, straight into
-// the shared arrays the clone killing reads, and each warp's winner records
-// are staged in the shared memory the hash chains use later and written as
-// 16-byte chunks.  Then the chains, the kills and the ranks as in k_clone.
-__global__ void __launch_bounds__(kCloneThreads, kCloneCtasPerSm) k_pick_clone(const __grid_constant__ PickArgs p,
-                                                                              const __grid_constant__ CloneArgs a)
-{
-    constexpr int kHeads = 1 << kCloneHashBits;
-    constexpr int kWarps = kCloneThreads / 32;
-    __shared__ unsigned long long s_key[kCloneSmem];
-    __shared__ int4 s_hit[kCloneSmem];
-    // chain links and hash heads; during the pick, each warp's 32 staged
-    // winner records (kWarps x 32 x 64 bytes fit exactly)
-    __shared__ __align__(16) int s_pool[2 * kCloneSmem + 2 * kHeads];
-    static_assert(sizeof(int) * (2 * kCloneSmem + 2 * kHeads) >= kWarps * 32 * 64, "record staging fits");
-    int *s_next_bx = s_pool, *s_next_au = s_pool + kCloneSmem;
-    int *s_head_bx = s_pool + 2 * kCloneSmem, *s_head_au = s_head_bx + kHeads;
-    __shared__ int s_scan[32];
-    __shared__ bool s_last;
-    const int e = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int s0 = __ldg(a.seed_off + e), s1 = __ldg(a.seed_off + e + 1);
-    if (s0 < 0 || s1 < s0 || s1 > a.n_seeds) s0 = s1 = 0;
-    const int ns = s1 - s0;
-    const bool in_smem = ns <= kCloneSmem;
-
-    // the pick, 32 seeds per warp task
-    int4 *sr = reinterpret_cast<int4 *>(s_pool) + warp * 128;
-    for (int t0 = warp * 32; t0 < ns; t0 += kWarps * 32) {
-        const int i = t0 + lane, s = s0 + i;
-        const bool valid = i < ns;
-        const SeedPick r = warp_pick(p, s, valid);
-        if (valid) {
-            p.key_ws[s] = r.key;
-            p.hit_ws[s] = r.hits;
-            if (in_smem) {
-                s_key[i] = r.key;
-                s_hit[i] = r.hits;
-            }
-        }
-        // only winners' records are read later (ranked seeds are scattered)
-        const unsigned win = __ballot_sync(0xffffffffu, valid && r.key != kNoKey);
-        if (win) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) sr[lane * 4 + q] = r.rec[q];
-            __syncwarp();
-            int4 *dst = reinterpret_cast<int4 *>(p.trk_ws + s0 + t0);
-            for (int k = lane; k < 128; k += 32)
-                if ((win >> (k >> 2)) & 1u) dst[k] = sr[k];
-            __syncwarp();
-        }
-    }
-    __syncthreads();   // keys and hits complete (shared and workspace); the staging area is free
-
-    const unsigned long long *K = a.key_ws + s0;
-    const int4 *Hh = a.hit_ws + s0;
-    int *g_next_bx = a.next_ws + 2 * (size_t)s0, *g_next_au = g_next_bx + ns;   // chains of larger events
-    if (a.clone_kill) {
-        // two winners sharing more than two of their hits share the UTbX hit or
-        // the UTaU hit: chain the winners by those two hits
-        for (int i = threadIdx.x; i < kHeads; i += blockDim.x) s_head_bx[i] = s_head_au[i] = -1;
-        __syncthreads();
-        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-            const unsigned long long k = in_smem ? s_key[i] : K[i];
-            if (k != kNoKey) {
-                const int4 h = in_smem ? s_hit[i] : Hh[i];
-                const int nb = atomicExch(&s_head_bx[clone_hash(h.w)], i);
-                const int na = h.y >= 0 ? atomicExch(&s_head_au[clone_hash(h.y)], i) : -1;
-                if (in_smem) {
-                    s_next_bx[i] = nb;
-                    s_next_au[i] = na;
-                } else {
-                    g_next_bx[i] = nb;
-                    g_next_au[i] = na;
-                }
-            }
-        }
-        __syncthreads();
-    }
-
-    int base = 0;
-    for (int c0 = 0; c0 < ns; c0 += blockDim.x) {
-        const int b = c0 + threadIdx.x;
-        int alive = 0;
-        if (b < ns) {
-            const unsigned long long kb = in_smem ? s_key[b] : K[b];
-            if (kb != kNoKey) {
-                alive = 1;
-                if (a.clone_kill) {
-                    if (in_smem) {
-                        const int4 hb = s_hit[b];
-                        for (int o = s_head_bx[clone_hash(hb.w)]; o >= 0 && alive; o = s_next_bx[o])
-                            if (o != b && s_hit[o].w == hb.w && kills(s_key[o], o, kb, b, s_hit[o], hb)) alive = 0;
-                        if (hb.y >= 0)
-                            for (int o = s_head_au[clone_hash(hb.y)]; o >= 0 && alive; o = s_next_au[o])
-                                if (o != b && s_hit[o].y == hb.y && kills(s_key[o], o, kb, b, s_hit[o], hb))
-                                    alive = 0;
-                    } else {
-                        // the same chains, links in the workspace (written by this block)
-                        const int4 hb = Hh[b];
-                        for (int o = s_head_bx[clone_hash(hb.w)]; o >= 0 && alive; o = g_next_bx[o]) {
-                            const int4 ho = Hh[o];
-                            if (o != b && ho.w == hb.w && kills(K[o], o, kb, b, ho, hb)) alive = 0;
-                        }
-                        if (hb.y >= 0)
-                            for (int o = s_head_au[clone_hash(hb.y)]; o >= 0 && alive; o = g_next_au[o]) {
-                                const int4 ho = Hh[o];
-                                if (o != b && ho.y == hb.y && kills(K[o], o, kb, b, ho, hb)) alive = 0;
-                            }
-                    }
-                }
-            }
-        }
-        int tot;
-        const int r = block_exclusive_scan(alive, s_scan, &tot);
-        if (b < ns) a.rank_ws[s0 + b] = alive ? base + r : -1;
-        base += tot;
-    }
-
-    // last CTA: scan the per-event counts into trk_off
-    if (threadIdx.x == 0) {
-        a.count_ws[e] = base;
-        __threadfence();
-        const unsigned int t = atomicAdd(&a.cnt->done_trk, 1u);
-        s_last = t == (unsigned)gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const int run = block_offsets(a.count_ws, a.n_events, a.trk_off, s_scan);
-    if (threadIdx.x == 0) {
-        a.trk_off[a.n_events] = run;
-        *a.n_tracks = run;
-        a.cnt->n_tracks = run;
-        if (run > a.capacity) raise_flag(a.cnt, DS_FLAG_TRACK_CAPACITY);
-        a.cnt->done_trk = 0;
-    }
-}
-
 __global__ void __launch_bounds__(256) k_scatter_tracks(const __grid_constant__ ScatterTrkArgs a)
 {
     // warp-cooperative copy: 32 seeds' records move as 128 contiguous 16-byte
@@ -306,21 +164,6 @@ __global__ void __launch_bounds__(256) k_scatter_tracks(const __grid_constant__ 
         const int p = __shfl_sync(0xffffffffu, pos, rec);
         if (p >= 0) reinterpret_cast<int4 *>(a.out + p)[k & 3] = __ldg(src + k);
     }
-}
-
-cudaError_t launch_pick_clone(const PickArgs &p, const CloneArgs &a, const ScatterTrkArgs &sa, cudaStream_t st,
-                              Prof *prof)
-{
-    if (a.n_events <= 0) return cudaSuccess;
-    prof->begin("k_pick_clone", st);
-    k_pick_clone<<<a.n_events, kCloneThreads, 0, st>>>(p, a);
-    prof->end(st);
-    cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess || sa.n_seeds <= 0) return err;
-    prof->begin("k_scatter_tracks", st);
-    k_scatter_tracks<<<(sa.n_seeds + 255) / 256, 256, 0, st>>>(sa);
-    prof->end(st);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_clone(const CloneArgs &a, const ScatterTrkArgs &sa, cudaStream_t st, Prof *prof)

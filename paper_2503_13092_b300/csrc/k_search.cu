@@ -27,13 +27,13 @@
 // pair, in seed-aligned chunks of at most 640 pairs), fit + features (thread
 // per candidate of the chunk).  Unfused form: candidates are written to a
 // compact buffer reserved with one atomicAdd per chunk, seed by seed, for
-// the network kernel and the per-event pick.  Fused form (FP32 network): each candidate's
+// k_mlp / k_pick.  Fused form (FP32 network): each candidate's
 // thread also evaluates the network (Ghost-Killer Neural Network section: the
 // network runs inside the tracking, weights in the parameter bank) and merges
 // its pick key with the hit ids of its layers into its seed's running minimum
 // in shared memory (a 128-bit compare-and-swap); the fit of the current
 // minimum is kept beside it, and after the last candidate each seed's thread
-// writes the winner record, key and hit ids as the pick (pick.cuh) does.
+// writes the winner record, key and hit ids as k_pick does.
 #include "ds_args.cuh"
 
 namespace ds {
@@ -325,7 +325,7 @@ __device__ __forceinline__ WinBest window_best(const DevGeom &g, const float *X0
     return r;
 }
 
-// A seed's best candidate so far in the fused form: the pick key (as the pick
+// A seed's best candidate so far in the fused form: the pick key (as k_pick
 // packs it) and the hits' indices inside the event in layer order (16 bits
 // each, 0xFFFF = absent): as one 128-bit integer the order is the pick order,
 // hit ids breaking key ties with absent last.
@@ -1058,7 +1058,7 @@ __global__ void __launch_bounds__(T, F ? (V == 1 ? 3 : kSearchFusedCtas) : (V ==
         c_lo = c_hi;
     }
     if (F) {
-        // each seed's winner as the pick writes it: the 64-byte record (staged
+        // each seed's winner as k_pick writes it: the 64-byte record (staged
         // in the column rows, written below as contiguous 16-byte chunks),
         // the pick key and the hit ids; a seed without one gets no record
         int4 *s_rec = reinterpret_cast<int4 *>(&s_col[0][0]);
