@@ -57,12 +57,20 @@ typedef struct {
                                    buffers do not fit hbm_budget: buffers per batch from the
                                    budget (admission by free device memory), kernels launched
                                    one by one.  Results are identical. */
+    int32_t gather_max_bytes;   /* request arrays smaller than this many bytes whose whole range
+                                   the device can read at the same address (pinned memory that
+                                   cudaPointerGetAttributes reports as host memory mapped into
+                                   the device's address space) are read straight from host
+                                   memory by one gather kernel per batch, which moves many
+                                   small arrays without a copy-engine set-up for each; larger
+                                   arrays and pageable memory go through cudaMemcpyAsync.
+                                   0: copies only.  Default 1 MiB.  Results are identical. */
 } ds_server_config;
 
 /* One request: n_events events with their seeds and hits, HOST memory in the
  * layouts of ds_reconstruct (offsets relative to the request, starting at 0).
- * Pinned memory is copied asynchronously, pageable memory through the
- * driver's staging.  The caller keeps inputs and outputs alive and untouched
+ * Pinned memory is read asynchronously (gathered by the device or copied,
+ * see gather_max_bytes), pageable memory goes through the driver's staging.  The caller keeps inputs and outputs alive and untouched
  * until the request's completion is returned by ds_server_poll. */
 typedef struct {
     int32_t n_events;
@@ -106,6 +114,8 @@ typedef struct {
     double worker_wall_s;                /* worker thread lifetime so far */
     int32_t graphs;                      /* 1: batches replay captured CUDA graphs */
     int32_t graphs_captured;             /* graphs instantiated at creation (slots x buckets) */
+    int64_t bytes_gathered;              /* input bytes read by the gather kernel */
+    int64_t bytes_copied;                /* input bytes uploaded by cudaMemcpyAsync */
 } ds_server_stats;
 
 DS_API void ds_server_default_config(ds_server_config *cfg);

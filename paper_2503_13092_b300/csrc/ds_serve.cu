@@ -19,6 +19,10 @@
 // the slot and the batch's event-count bucket (a power of two; the batch is
 // padded with empty events and launched with its arrays' capacities,
 // DS_BATCH_CAPACITY); only the copies are issued per batch.
+// A batch's inputs come from the requests' host arrays: small arrays in
+// device-readable pinned memory are read by one gather kernel (k_gather_host,
+// many arrays per launch, no copy-engine set-up per array), the rest by one
+// cudaMemcpyAsync each.
 // Results are renumbered into each request's own event, seed, hit and track
 // indices on the GPU (k_renumber, on the slot's stream after ds_vertex) and
 // copied straight into the caller's output buffers.
@@ -101,6 +105,7 @@ struct SegOut {
 struct Req {
     int64_t id = 0;
     ds_request r{};
+    int mapped = -1;                   // 1: every input array device-readable (-1: not yet checked)
     double t_arrival = 0, t_admit = -1;
     int n_segs = 0, segs_done = 0, n_batches = 0;
     ds_status status = DS_OK;
@@ -141,6 +146,14 @@ struct BatchLayout {
     }
 };
 
+// One host -> device range for k_gather_host; chunk0 = the number of
+// kGatherChunk-byte chunks of the descriptors before it.
+struct GatherDesc {
+    unsigned long long dst, src;
+    uint32_t n, chunk0;
+};
+static_assert(sizeof(GatherDesc) == 24, "descriptor layout");
+
 struct Slot {
     ds_ctx *ctx = nullptr;
     cudaStream_t st = nullptr;
@@ -165,7 +178,45 @@ struct Slot {
     int32_t *h_seg_n = nullptr;        // its length
     ds_track *h_trk = nullptr;
     ds_vertex_rec *h_vtx = nullptr;
+    bool own_mapped = false;           // the offset and segment tables above are device-readable
+    // gather descriptors of the batch (host staging, device copy)
+    GatherDesc *h_desc = nullptr, *d_desc = nullptr;
+    int desc_cap = 0;
 };
+
+constexpr int kGatherChunk = 16384;
+constexpr int kGatherCtas = 64;
+constexpr int kGatherThreads = 256;
+
+// True when the device can read [p, p + n) at address p: the first and last
+// bytes lie in host memory that the runtime reports mapped at the same
+// address (an array is one allocation, so the bytes between lie in it too).
+bool device_readable(const void *p, size_t n)
+{
+    if (n == 0) return true;
+    const char *ends[2] = {static_cast<const char *>(p), static_cast<const char *>(p) + n - 1};
+    for (const char *q : ends) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (a.type != cudaMemoryTypeHost || a.devicePointer != static_cast<const void *>(q)) return false;
+    }
+    return true;
+}
+
+bool request_readable(const ds_request &r)
+{
+    const size_t S = (size_t)r.seed_off[r.n_events], H = (size_t)r.hit_off[r.n_events];
+    const void *seeds[6] = {r.seed_x, r.seed_y, r.seed_tx, r.seed_ty, r.seed_qop, r.seed_chi2};
+    for (const void *a : seeds)
+        if (!device_readable(a, 4 * S)) return false;
+    const void *hits[3] = {r.hit_x0, r.hit_ybeg, r.hit_yend};
+    for (const void *a : hits)
+        if (!device_readable(a, 4 * H)) return false;
+    return device_readable(r.hit_layer, H);
+}
 
 }  // namespace
 
@@ -190,6 +241,7 @@ struct ds_server {
     int64_t events_done = 0, batches = 0;
     int inflight = 0, peak_inflight = 0;
     std::atomic<double> t_launch{0.0}, t_finish{0.0};
+    std::atomic<int64_t> bytes_gathered{0}, bytes_copied{0};
     bool stop = false;
     std::thread worker;
     Clock::time_point t0;
@@ -214,6 +266,7 @@ bool config_valid(const ds_server_config &c)
 {
     return c.n_slots >= 1 && c.n_slots <= 16 && c.max_batch_events >= 1 && c.max_batch_seeds >= 1 &&
            c.max_batch_hits >= 1 && c.events_per_launch >= 0 && c.vertices_per_seed >= 0 && c.hbm_budget >= 0 &&
+           c.gather_max_bytes >= 0 &&
            (c.mlp_precision == DS_MLP_FP32 || c.mlp_precision == DS_MLP_BF16 || c.mlp_precision == DS_MLP_FP8);
 }
 
@@ -261,6 +314,77 @@ __global__ void k_renumber(ds_track *trk, const int32_t *n_trk, int cap_t, ds_ve
             v.event += sg.y;
             v.i -= tb;
             v.j -= tb;
+        }
+    }
+}
+
+// Bytes [r, r + 16) of the 32-byte concatenation a|b, r = 4 q + s / 8
+// (q, s uniform over the warp).
+__device__ __forceinline__ uint4 bytes_at(const uint4 &a, const uint4 &b, int q, int s)
+{
+    uint32_t w0, w1, w2, w3, w4;
+    switch (q) {
+    case 0: w0 = a.x; w1 = a.y; w2 = a.z; w3 = a.w; w4 = b.x; break;
+    case 1: w0 = a.y; w1 = a.z; w2 = a.w; w3 = b.x; w4 = b.y; break;
+    case 2: w0 = a.z; w1 = a.w; w2 = b.x; w3 = b.y; w4 = b.z; break;
+    default: w0 = a.w; w1 = b.x; w2 = b.y; w3 = b.z; w4 = b.w; break;
+    }
+    return make_uint4(__funnelshift_r(w0, w1, s), __funnelshift_r(w1, w2, s), __funnelshift_r(w2, w3, s),
+                      __funnelshift_r(w3, w4, s));
+}
+
+// Host -> device gather: warps take kGatherChunk-byte chunks of the
+// descriptors' ranges.  A warp writes its chunk in aligned 16-byte blocks of
+// the destination; lane l reads the aligned 16-byte source block under its
+// output block (only blocks that hold bytes of the source range, so no read
+// leaves the pages of the source array) and takes the bytes it needs from its
+// own block and its right neighbour's; lane 31 only reads, so a step covers
+// 31 blocks.  Partial blocks at the ends of a chunk are written byte by byte.
+__global__ void __launch_bounds__(kGatherThreads) k_gather_host(const GatherDesc *__restrict__ d, int n_desc,
+                                                                 int n_chunks)
+{
+    const int lane = threadIdx.x & 31;
+    const int n_warps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += n_warps) {
+        int lo = 0, hi = n_desc - 1;             // the last descriptor with chunk0 <= c
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int)d[mid].chunk0 <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const GatherDesc e = d[lo];
+        const unsigned long long b0 = (unsigned long long)(c - (int)e.chunk0) * kGatherChunk;
+        const unsigned long long b1 = min((unsigned long long)e.n, b0 + kGatherChunk);
+        const unsigned long long src_end = e.src + e.n;
+        const unsigned long long w_lo = e.dst + b0, w_hi = e.dst + b1;   // bytes this warp writes
+        const unsigned long long D0 = w_lo & ~15ull;
+        const unsigned long long S0 = D0 + (e.src - e.dst);               // source byte under D0 (mod 2^64)
+        const int r = (int)(S0 & 15);
+        const int q = r >> 2, sh = (r & 3) * 8;
+        const unsigned long long A0 = S0 & ~15ull;
+        for (unsigned long long D = D0; D < w_hi; D += 31 * 16) {
+            const unsigned long long Dl = D + 16ull * lane;
+            const unsigned long long Al = A0 + (D - D0) + 16ull * lane;
+            uint4 a = make_uint4(0u, 0u, 0u, 0u);
+            if (Al < src_end && Al + 16 > e.src) a = __ldg(reinterpret_cast<const uint4 *>(Al));
+            uint4 b;
+            b.x = __shfl_down_sync(0xffffffffu, a.x, 1);
+            b.y = __shfl_down_sync(0xffffffffu, a.y, 1);
+            b.z = __shfl_down_sync(0xffffffffu, a.z, 1);
+            b.w = __shfl_down_sync(0xffffffffu, a.w, 1);
+            if (lane < 31 && Dl < w_hi) {
+                const uint4 v = bytes_at(a, b, q, sh);
+                const unsigned long long p0 = max(Dl, w_lo), p1 = min(Dl + 16, w_hi);
+                if (p0 == Dl && p1 == Dl + 16) {
+                    *reinterpret_cast<uint4 *>(Dl) = v;
+                } else {
+                    for (unsigned long long p = p0; p < p1; ++p) {
+                        const int k = (int)(p - Dl);
+                        const uint32_t wk = k < 8 ? (k < 4 ? v.x : v.y) : (k < 12 ? v.z : v.w);
+                        *reinterpret_cast<uint8_t *>(p) = (uint8_t)(wk >> (8 * (k & 3)));
+                    }
+                }
+            }
         }
     }
 }
@@ -464,12 +588,28 @@ void ds_server::launch(Slot &sl)
     sl.h_seed_off[0] = 0;
     sl.h_hit_off[0] = 0;
     cudaError_t ce = cudaSuccess;
-    auto h2d = [&](void *dst, const void *src, size_t n) {
-        if (n && ce == cudaSuccess) ce = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, sl.st);
+    // inputs: device-readable ranges below gather_max_bytes become gather
+    // descriptors, the others one cudaMemcpyAsync each
+    const size_t gmax = (size_t)cfg.gather_max_bytes;
+    int nd = 0;
+    uint32_t n_chunks = 0;
+    int64_t gathered = 0, copied = 0;
+    auto put = [&](void *dst, const void *src, size_t n, bool readable) {
+        if (!n || ce != cudaSuccess) return;
+        if (readable && n < gmax && nd < sl.desc_cap) {
+            sl.h_desc[nd++] = GatherDesc{(unsigned long long)dst, (unsigned long long)src, (uint32_t)n, n_chunks};
+            n_chunks += (uint32_t)((n + kGatherChunk - 1) / kGatherChunk);
+            gathered += (int64_t)n;
+        } else {
+            ce = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, sl.st);
+            copied += (int64_t)n;
+        }
     };
     for (size_t k = 0; k < sl.segs.size(); ++k) {
         const Seg &g = sl.segs[k];
         const ds_request &r = g.q->r;
+        if (gmax > 0 && g.q->mapped < 0) g.q->mapped = request_readable(r) ? 1 : 0;
+        const bool rd = gmax > 0 && g.q->mapped == 1;
         sl.ev_base.push_back(eb);
         const int s0 = r.seed_off[g.e0], h0 = r.hit_off[g.e0];
         sl.h_seg[k] = make_int4(eb, g.e0 - eb, s0 - sb, h0 - hb);
@@ -479,10 +619,10 @@ void ds_server::launch(Slot &sl)
         }
         const int ns = g.seeds(), nh = g.hits();
         const float *sc[6] = {r.seed_x, r.seed_y, r.seed_tx, r.seed_ty, r.seed_qop, r.seed_chi2};
-        for (int c = 0; c < 6; ++c) h2d(d_seed[c] + sb, sc[c] + s0, 4 * (size_t)ns);
+        for (int c = 0; c < 6; ++c) put(d_seed[c] + sb, sc[c] + s0, 4 * (size_t)ns, rd);
         const float *hc[3] = {r.hit_x0, r.hit_ybeg, r.hit_yend};
-        for (int c = 0; c < 3; ++c) h2d(d_hit[c] + hb, hc[c] + h0, 4 * (size_t)nh);
-        h2d(d_layer + hb, r.hit_layer + h0, (size_t)nh);
+        for (int c = 0; c < 3; ++c) put(d_hit[c] + hb, hc[c] + h0, 4 * (size_t)nh, rd);
+        put(d_layer + hb, r.hit_layer + h0, (size_t)nh, rd);
         eb += g.e1 - g.e0; sb += ns; hb += nh;
     }
     const int n_seg = (int)sl.segs.size();
@@ -498,10 +638,21 @@ void ds_server::launch(Slot &sl)
         }
     }
     sl.h_seg_n[0] = n_seg;
-    h2d(d_seed_off, sl.h_seed_off, 4 * (size_t)(E_launch + 1));
-    h2d(d_hit_off, sl.h_hit_off, 4 * (size_t)(E_launch + 1));
-    h2d(d_seg, sl.h_seg, sizeof(int4) * (size_t)n_seg);
-    h2d(d + L.nseg, sl.h_seg_n, 4);
+    put(d_seed_off, sl.h_seed_off, 4 * (size_t)(E_launch + 1), sl.own_mapped);
+    put(d_hit_off, sl.h_hit_off, 4 * (size_t)(E_launch + 1), sl.own_mapped);
+    put(d_seg, sl.h_seg, sizeof(int4) * (size_t)n_seg, sl.own_mapped);
+    put(d + L.nseg, sl.h_seg_n, 4, sl.own_mapped);
+    if (nd > 0 && ce == cudaSuccess) {
+        ce = cudaMemcpyAsync(sl.d_desc, sl.h_desc, sizeof(GatherDesc) * (size_t)nd, cudaMemcpyHostToDevice, sl.st);
+        if (ce == cudaSuccess) {
+            const int warps = kGatherThreads / 32;
+            const int grid = (int)std::min<uint32_t>(kGatherCtas, (n_chunks + warps - 1) / warps);
+            k_gather_host<<<grid, kGatherThreads, 0, sl.st>>>(sl.d_desc, nd, (int)n_chunks);
+            ce = cudaGetLastError();
+        }
+    }
+    bytes_gathered += gathered;
+    bytes_copied += copied;
     if (ce != cudaSuccess) return fail_batch(sl, DS_ERR_CUDA);
     ds_event_batch b{};
     b.n_events = sl.E; b.n_seeds = sl.S; b.n_hits = sl.H;
@@ -698,9 +849,10 @@ void ds_server::release()
         if (sl.ev_a) cudaEventDestroy(sl.ev_a);
         if (sl.ev_b) cudaEventDestroy(sl.ev_b);
         void *hp[] = {sl.h_seed_off, sl.h_hit_off, sl.h_trk_off, sl.h_vtx_off, sl.h_counts, sl.h_seg, sl.h_trk,
-                      sl.h_vtx, sl.h_seg_n};
+                      sl.h_vtx, sl.h_seg_n, sl.h_desc};
         for (void *p : hp)
             if (p) cudaFreeHost(p);
+        if (sl.d_desc) cudaFree(sl.d_desc);
         sl = Slot();
     }
     if (d_arena) cudaFree(d_arena);
@@ -724,6 +876,7 @@ void ds_server_default_config(ds_server_config *c)
     c->hbm_budget = 0;
     c->mlp_precision = DS_MLP_FP32;
     c->graphs = 1;
+    c->gather_max_bytes = 1 << 20;
 }
 
 ds_status ds_server_create(ds_server **out, int device, const ds_geometry *geom, const ds_nn_weights *weights,
@@ -767,16 +920,21 @@ ds_status ds_server_create(ds_server **out, int device, const ds_geometry *geom,
             cudaEventCreateWithFlags(&sl.ev_b, cudaEventDisableTiming) != cudaSuccess)
             return DS_ERR_CUDA;
         const size_t E1 = (size_t)cfg->max_batch_events + 1;
-        if (cudaHostAlloc((void **)&sl.h_seed_off, 4 * E1, 0) != cudaSuccess ||
-            cudaHostAlloc((void **)&sl.h_hit_off, 4 * E1, 0) != cudaSuccess ||
+        sl.desc_cap = 10 * cfg->max_batch_events + 4;
+        if (cudaHostAlloc((void **)&sl.h_seed_off, 4 * E1, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostAlloc((void **)&sl.h_hit_off, 4 * E1, cudaHostAllocMapped) != cudaSuccess ||
             cudaHostAlloc((void **)&sl.h_trk_off, 4 * E1, 0) != cudaSuccess ||
             cudaHostAlloc((void **)&sl.h_vtx_off, 4 * E1, 0) != cudaSuccess ||
             cudaHostAlloc((void **)&sl.h_counts, 8, 0) != cudaSuccess ||
-            cudaHostAlloc((void **)&sl.h_seg_n, 4, 0) != cudaSuccess ||
-            cudaHostAlloc((void **)&sl.h_seg, sizeof(int4) * E1, 0) != cudaSuccess ||
+            cudaHostAlloc((void **)&sl.h_seg_n, 4, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostAlloc((void **)&sl.h_seg, sizeof(int4) * E1, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostAlloc((void **)&sl.h_desc, sizeof(GatherDesc) * (size_t)sl.desc_cap, 0) != cudaSuccess ||
             cudaHostAlloc((void **)&sl.h_trk, sizeof(ds_track) * (size_t)cfg->max_batch_seeds, 0) != cudaSuccess ||
             cudaHostAlloc((void **)&sl.h_vtx, sizeof(ds_vertex_rec) * (size_t)s->max_vtx, 0) != cudaSuccess)
             return DS_ERR_OOM;
+        if (cudaMalloc((void **)&sl.d_desc, sizeof(GatherDesc) * (size_t)sl.desc_cap) != cudaSuccess) return DS_ERR_OOM;
+        sl.own_mapped = device_readable(sl.h_seed_off, 4 * E1) && device_readable(sl.h_hit_off, 4 * E1) &&
+                        device_readable(sl.h_seg, sizeof(int4) * E1) && device_readable(sl.h_seg_n, 4);
     }
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return DS_ERR_CUDA;
     s->context_bytes = (int64_t)(free_before - std::min(free_before, free_b));
@@ -905,6 +1063,8 @@ ds_status ds_server_stats_get(ds_server *s, ds_server_stats *o)
     o->worker_wall_s = s->now();
     o->graphs = s->graph_mode ? 1 : 0;
     o->graphs_captured = s->graphs_captured;
+    o->bytes_gathered = s->bytes_gathered.load();
+    o->bytes_copied = s->bytes_copied.load();
     int64_t q = 0;
     const Req *last = nullptr;
     for (const Seg &g : s->queue)

@@ -111,7 +111,8 @@ class ds_tune_entry(C.Structure):
 class ds_server_config(C.Structure):
     _fields_ = [("n_slots", C.c_int32), ("max_batch_events", C.c_int32), ("max_batch_seeds", C.c_int32),
                 ("max_batch_hits", C.c_int32), ("events_per_launch", C.c_int32), ("vertices_per_seed", C.c_int32),
-                ("hbm_budget", C.c_int64), ("mlp_precision", C.c_int32), ("graphs", C.c_int32)]
+                ("hbm_budget", C.c_int64), ("mlp_precision", C.c_int32), ("graphs", C.c_int32),
+                ("gather_max_bytes", C.c_int32)]
 
 
 class ds_request(C.Structure):
@@ -134,7 +135,7 @@ class ds_server_stats(C.Structure):
                 ("hbm_budget", C.c_int64), ("hbm_peak", C.c_int64), ("context_bytes", C.c_int64),
                 ("peak_inflight", C.c_int32), ("queued", C.c_int32), ("worker_launch_s", C.c_double),
                 ("worker_finish_s", C.c_double), ("worker_wall_s", C.c_double), ("graphs", C.c_int32),
-                ("graphs_captured", C.c_int32)]
+                ("graphs_captured", C.c_int32), ("bytes_gathered", C.c_int64), ("bytes_copied", C.c_int64)]
 
 
 VINFO_DTYPE = np.dtype([("m_pipi", "<f4"), ("m_ppi", "<f4"), ("m_pip", "<f4"), ("p", "<f4"), ("pt", "<f4"),
@@ -653,7 +654,8 @@ class Server:
                     trk_off=np.zeros(E + 1, np.int32), vtx_off=np.zeros(E + 1, np.int32))
 
     def submit(self, req: dict, arrival: float = 0.0, out: dict | None = None, vtx_capacity: int | None = None) -> int:
-        """Queue one request (host arrays; pinned inputs are uploaded by DMA).
+        """Queue one request (host arrays; pinned inputs are read by the device
+        directly or uploaded by DMA, pageable ones through the driver's staging).
         out: buffers from alloc_outputs (allocated here when None).  The
         request's arrays and out stay referenced until poll() returns it."""
         E = int(req["n_events"])

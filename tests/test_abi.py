@@ -86,3 +86,11 @@ def test_host_side_errors_without_gpu(libpath):
     assert L.ds_create(ctypes.byref(h), 0) in (ds.DS_OK, ds.DS_ERR_CUDA)
     if h.value:
         L.ds_destroy(h)
+
+
+def test_server_default_config(libpath):
+    """The serving defaults (no device involved): four slots, graphs on, and
+    inputs below 1 MiB per array gathered from pinned host memory."""
+    c = ds.ds_server_default_config()
+    assert (c.n_slots, c.graphs, c.gather_max_bytes) == (4, 1, 1 << 20)
+    assert c.max_batch_events == 1024 and c.mlp_precision == ds.DS_MLP_FP32

@@ -185,3 +185,38 @@ def test_graph_replay_equals_launches(torch_cuda, weights, pool):
         assert all(got[i]["status"] == 0 for i in ids)
         res[graphs] = [key(got[i]) for i in ids]
     assert res[1] == res[0]
+
+
+def test_gathered_inputs_equal_copies(torch_cuda, weights, pool):
+    """Inputs read from pinned host memory by the gather kernel against
+    inputs uploaded by cudaMemcpyAsync: identical records.  Pinned requests
+    are slices of a pinned pool starting at any event (hit layers at any byte
+    offset, so every source alignment occurs); pageable requests are copied
+    whatever gather_max_bytes says; split requests and requests larger than
+    the gather limit are in the mix."""
+    torch = torch_cuda
+    pinned = dict(pool)
+    for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2", "hit_x0", "hit_ybeg", "hit_yend",
+              "hit_layer"):
+        pinned[k] = torch.from_numpy(np.ascontiguousarray(pool[k])).pin_memory().numpy()
+    sizes, starts, _ = synth.c5_trace(36, 1000.0, pool["n_events"], seed=12, max_events=120)
+    reqs = [synth.slice_events(pinned if i % 3 else pool, int(s), int(s + k))
+            for i, (k, s) in enumerate(zip(sizes, starts))]
+    pageable_bytes = sum(24 * int(r["seed_off"][-1]) + 13 * int(r["hit_off"][-1]) for i, r in enumerate(reqs)
+                         if i % 3 == 0)
+    total_bytes = sum(24 * int(r["seed_off"][-1]) + 13 * int(r["hit_off"][-1]) for r in reqs)
+    res, stats = {}, {}
+    for gmax in (0, 1 << 17, 1 << 30):
+        srv = server(torch_cuda, weights, gather_max_bytes=gmax, max_batch_events=64)
+        ids = [srv.submit(r) for r in reqs]
+        got = collect(srv, len(reqs))
+        stats[gmax] = srv.stats()
+        srv.close()
+        assert all(got[i]["status"] == 0 for i in ids)
+        res[gmax] = [key(got[i]) for i in ids]
+    assert res[1 << 17] == res[0] and res[1 << 30] == res[0]
+    assert stats[0]["bytes_gathered"] == 0
+    assert 0 < stats[1 << 17]["bytes_gathered"] and stats[1 << 17]["bytes_copied"] > pageable_bytes
+    # every pinned request array gathered; pageable ones (and nothing else) copied
+    assert stats[1 << 30]["bytes_copied"] == pageable_bytes
+    assert stats[1 << 30]["bytes_gathered"] >= total_bytes - pageable_bytes
