@@ -285,6 +285,11 @@ typedef struct {
     int32_t vertex_small_cap;   /* events with at most this many tracks are vertexed one per
                                    CTA; larger ones as (event, 131072-pair range) work items
                                    spread over the SMs, 2..512 (default 512) */
+    int32_t search_order;       /* order of the search's work items: 0 = each event's seeds in
+                                   chunks of equal size (at most search_chunk), events in order;
+                                   1 = every full chunk of search_chunk seeds first, then one item
+                                   per event for its remaining seeds, largest first, so that the
+                                   queue ends with its smallest items (default 1) */
 } ds_tuning;
 
 /* One configuration measured by ds_autotune. */
@@ -457,7 +462,8 @@ DS_API ds_status ds_set_tuning(ds_ctx *ctx, const ds_tuning *t);
  * inputs as for ds_reconstruct; `out` receives the tracks of the last run, the
  * vertices go to context-owned buffers) for candidate tunings by coordinate
  * descent over the search's stage size, chunk size, CTAs per SM and queue
- * group and the vertexing's CTAs per SM and one-event-per-CTA track limit (two
+ * group, the search's work-item order, and the vertexing's CTAs per SM and
+ * one-event-per-CTA track limit (two
  * sweeps, each configuration run `reps` times after one warm-up run, CUDA
  * events on `stream`), keeps the fastest in the context and copies it to
  * *best.  Every configuration measured is written to entries (at most

@@ -11,7 +11,8 @@
 #include "ds_args.cuh"
 
 static constexpr ds_tuning kDefaultTuning = {ds::kSearchThreads, ds::kSearchCtasPerSm, ds::kSearchGroup,
-                                             ds::kStageHits, ds::kVtxCtasPerSmMax, ds::kVtxSmallCapMax};
+                                             ds::kStageHits,     ds::kVtxCtasPerSmMax, ds::kVtxSmallCapMax,
+                                             1};
 
 static bool tuning_valid(const ds_tuning &t)
 {
@@ -19,7 +20,7 @@ static bool tuning_valid(const ds_tuning &t)
            t.search_ctas_per_sm <= 8 && t.search_group >= 1 && t.search_group <= 16 &&
            t.search_stage_hits >= 0 && t.search_stage_hits <= ds::kStageHitsMax && t.vertex_ctas_per_sm >= 1 &&
            t.vertex_ctas_per_sm <= ds::kVtxCtasPerSmMax && t.vertex_small_cap >= 2 &&
-           t.vertex_small_cap <= ds::kVtxSmallCapMax;
+           t.vertex_small_cap <= ds::kVtxSmallCapMax && (t.search_order == 0 || t.search_order == 1);
 }
 
 struct ds_ctx {
@@ -418,7 +419,7 @@ ds_status ds_reserve(ds_ctx *ctx, int32_t E, int32_t S, int32_t H)
         if ((st = grow(ctx, &ctx->large_vtx, (size_t)E)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->large_aux, 2 * (size_t)E + 2)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->vtx_items, 2 * (size_t)ds::kVtxItemsPerEvent * E)) != DS_OK) return st;
-        if ((st = grow(ctx, &ctx->item_off, (size_t)E + 1)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->item_off, 2 * (size_t)E + 2)) != DS_OK) return st;
         ctx->cap_events = E;
     }
     const long long want_cand = (long long)(S > ctx->cap_seeds ? S : ctx->cap_seeds) * ctx->cand_per_seed;
@@ -504,6 +505,7 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     ba.bins = ctx->bins;
     ba.item_off = ctx->item_off;
     ba.chunk = ctx->tune.search_chunk;
+    ba.order = ctx->tune.search_order;
     ba.capacity_sizes = (b->flags & DS_BATCH_CAPACITY) ? 1 : 0;
     ba.cnt = ctx->d_cnt;
     DS_CUDA(ds::launch_bucket(ba, st, &ctx->prof), "bucket kernel");
@@ -523,6 +525,8 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     sa.sperm = ctx->sperm;
     sa.bins = ctx->bins;
     sa.item_off = ctx->item_off;
+    sa.chunk = ctx->tune.search_chunk;
+    sa.order = ctx->tune.search_order;
     sa.cand_feat = ctx->cand_feat;
     sa.cand_meta = ctx->cand_meta;
     sa.cand_cap = ctx->cap_cand;
@@ -884,15 +888,16 @@ ds_status ds_autotune(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *sd, 
     static const int group_opts[] = {1, 2, 4, 8};
     static const int vctas_opts[] = {1, 2, 3, 4};
     static const int vcap_opts[] = {64, 128, 256, 512};
-    const int *dim_opts[6] = {stage_opts, chunk_opts, ctas_opts, group_opts, vctas_opts, vcap_opts};
+    static const int order_opts[] = {0, 1};
+    const int *dim_opts[7] = {stage_opts, chunk_opts, ctas_opts, group_opts, vctas_opts, vcap_opts, order_opts};
     for (int sweep = 0; sweep < 2 && rs == DS_OK; ++sweep) {
-        for (int dim = 0; dim < 6 && rs == DS_OK; ++dim) {
+        for (int dim = 0; dim < 7 && rs == DS_OK; ++dim) {
             const int *opts = dim_opts[dim];
-            const int n_opts = dim == 0 ? 7 : 4;
+            const int n_opts = dim == 0 ? 7 : dim == 6 ? 2 : 4;
             for (int k = 0; k < n_opts && rs == DS_OK; ++k) {
                 ds_tuning t = cur;
-                int32_t *fields[6] = {&t.search_stage_hits, &t.search_chunk, &t.search_ctas_per_sm, &t.search_group,
-                                      &t.vertex_ctas_per_sm, &t.vertex_small_cap};
+                int32_t *fields[7] = {&t.search_stage_hits, &t.search_chunk, &t.search_ctas_per_sm, &t.search_group,
+                                      &t.vertex_ctas_per_sm, &t.vertex_small_cap, &t.search_order};
                 int32_t *field = fields[dim];
                 if (*field == opts[k]) continue;
                 *field = opts[k];

@@ -32,8 +32,9 @@ struct BucketArgs {
     float *sx0;
     uint16_t *sperm;
     uint16_t *bins;
-    int *item_off;         // [n_events + 1]
+    int *item_off;         // [2 n_events + 2] search work items (k_bucket.cu)
     int chunk;             // max seeds per search work item (<= kSearchThreads)
+    int order;             // work-item order (ds_tuning.search_order)
     int capacity_sizes;    // 1: n_seeds, n_hits are capacities (DS_BATCH_CAPACITY)
     DevCounters *cnt;
 };
@@ -50,7 +51,9 @@ struct SearchArgs {
     const float *sx0;
     const uint16_t *sperm;
     const uint16_t *bins;
-    const int *item_off;
+    const int *item_off;   // work items laid out by k_bucket
+    int chunk;             // max seeds per work item
+    int order;             // 0: equal chunks in event order; 1: full chunks, then remainders largest first
     float4 *cand_feat;     // [cand_cap][4]: the 16 network inputs
     CandMeta *cand_meta;   // [cand_cap]
     int cand_cap;

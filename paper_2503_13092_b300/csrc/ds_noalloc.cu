@@ -48,7 +48,7 @@ constexpr size_t kOffCloneNext = kOffRank + align256(sizeof(int) * (size_t)kNASe
 constexpr size_t kOffSeedCand = kOffCloneNext + align256(2 * sizeof(int) * (size_t)kNASeeds);
 constexpr size_t kOffCount = kOffSeedCand + align256(sizeof(int4) * (size_t)kNASeeds);
 constexpr size_t kOffItemOff = kOffCount + align256(sizeof(int) * (size_t)kNAEvents);
-constexpr size_t kOffCandFeat = kOffItemOff + align256(sizeof(int) * (size_t)(kNAEvents + 1));
+constexpr size_t kOffCandFeat = kOffItemOff + align256(sizeof(int) * (size_t)(2 * kNAEvents + 2));
 constexpr size_t kOffCandMeta = kOffCandFeat + align256(sizeof(float4) * 4 * (size_t)kNACand);
 constexpr size_t kOffCandLogit = kOffCandMeta + align256(sizeof(CandMeta) * (size_t)kNACand);
 constexpr size_t kScratchBytes = kOffCandLogit + align256(sizeof(float) * (size_t)kNACand);
@@ -138,6 +138,7 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         ba.bins = reinterpret_cast<uint16_t *>(base + kOffBins);
         ba.item_off = reinterpret_cast<int *>(base + kOffItemOff);
         ba.chunk = kSearchThreads;
+        ba.order = 1;
         ba.capacity_sizes = (b->flags & DS_BATCH_CAPACITY) ? 1 : 0;
         ba.cnt = cnt;
         if (launch_bucket(ba, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
@@ -157,6 +158,8 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         sa.sperm = ba.sperm;
         sa.bins = ba.bins;
         sa.item_off = ba.item_off;
+        sa.chunk = ba.chunk;
+        sa.order = ba.order;
         sa.cand_feat = reinterpret_cast<float4 *>(base + kOffCandFeat);
         sa.cand_meta = reinterpret_cast<CandMeta *>(base + kOffCandMeta);
         sa.cand_cap = kNACand;

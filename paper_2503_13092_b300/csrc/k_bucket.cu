@@ -17,7 +17,8 @@
 // shorter than its sector (one bit per row, written beside the bin table);
 // the search decides the strip test of an unmarked row from the sector's
 // bounds.  Block 0 also turns the per-event seed counts into the search
-// kernel's work items (chunks of at most `chunk` <= 128 seeds of one event).
+// kernel's work items (chunks of at most `chunk` <= 128 seeds of one event,
+// by default the full chunks first and the remainders largest first).
 // The order inside a bin comes from atomics and is not deterministic; every
 // consumer ranks hits by (|dx|, id), which does not depend on it.
 #include "ds_args.cuh"
@@ -80,18 +81,59 @@ __global__ void __launch_bounds__(kBucketThreads, 3) k_bucket(const __grid_const
 
     // search work items: chunks of at most a.chunk seeds of one event.  They
     // depend on the seed offsets only, so block 0 lays them out first.
+    // Order 0: event e's seeds in ceil(ns / chunk) chunks whose sizes differ
+    // by at most one, events in order; item_off[e] = e's first item.
+    // Order 1 (largest first): every full chunk of `chunk` seeds, events in
+    // order (item_off[e] = e's first full chunk), then one item per event for
+    // its remaining ns mod chunk seeds, the largest remainders first
+    // (item_off[n_events + 2 + r] = the event of remainder item r).  The
+    // queue then ends with its smallest items, so the persistent CTAs run
+    // out of work at nearly the same time instead of a last partial wave of
+    // full-size items running on a few SMs.  item_off[n_events] = all items;
+    // item_off[n_events + 1] = full chunks (order 1).
     if (e == 0) {
         const int32_t *so = a.seed_off;
-        const int n_items = block_offsets_f(
-            [so, &a](int k) {
-                const int s0 = __ldg(so + k), s1 = __ldg(so + k + 1);
-                const int ns = (s0 < 0 || s1 < s0 || s1 > a.n_seeds) ? 0 : s1 - s0;
-                return (ns + a.chunk - 1) / a.chunk;
-            },
-            a.n_events, a.item_off, s_scan);
+        const int E = a.n_events, C = a.chunk;
+        auto seeds_of = [so, &a](int k) {
+            const int s0 = __ldg(so + k), s1 = __ldg(so + k + 1);
+            return (s0 < 0 || s1 < s0 || s1 > a.n_seeds) ? 0 : s1 - s0;
+        };
+        int n_items;
+        if (a.order == 0) {
+            n_items = block_offsets_f([&](int k) { return (seeds_of(k) + C - 1) / C; }, E, a.item_off, s_scan);
+        } else {
+            const int n_full = block_offsets_f([&](int k) { return seeds_of(k) / C; }, E, a.item_off, s_scan);
+            // counting sort of the remainders by size, largest first (the
+            // order inside one size is free: it changes no output)
+            int *s_rc = reinterpret_cast<int *>(s_cnt);   // [kSearchThreads + 1]: counts, then cursors
+            for (int r = tid; r <= kSearchThreads; r += blockDim.x) s_rc[r] = 0;
+            __syncthreads();
+            for (int k = tid; k < E; k += blockDim.x) {
+                const int r = seeds_of(k) % C;
+                if (r) atomicAdd(s_rc + (C - r), 1);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int run = 0;
+                for (int r = 0; r < kSearchThreads; ++r) {
+                    const int c = s_rc[r];
+                    s_rc[r] = run;
+                    run += c;
+                }
+                s_rc[kSearchThreads] = run;
+                a.item_off[E + 1] = n_full;
+            }
+            __syncthreads();
+            for (int k = tid; k < E; k += blockDim.x) {
+                const int r = seeds_of(k) % C;
+                if (r) a.item_off[E + 2 + atomicAdd(s_rc + (C - r), 1)] = k;
+            }
+            n_items = n_full + s_rc[kSearchThreads];
+            __syncthreads();   // s_cnt is cleared below
+        }
         if (tid == 0) {
-            a.item_off[a.n_events] = n_items;
-            const int s_end = __ldg(so + a.n_events);
+            a.item_off[E] = n_items;
+            const int s_end = __ldg(so + E);
             if (__ldg(so) != 0 || (a.capacity_sizes ? s_end > a.n_seeds : s_end != a.n_seeds))
                 raise_flag(a.cnt, DS_FLAG_BAD_OFFSETS);
         }

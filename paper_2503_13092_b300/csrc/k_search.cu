@@ -565,7 +565,9 @@ __global__ void __launch_bounds__(T, F ? (V == 1 ? 3 : kSearchFusedCtas) : (V ==
     constexpr int kNextWarp = T / 32 - 1;
     const bool next_warp = (tid >> 5) == kNextWarp;
     int q_next = 0, q_end = 0;     // lane 0 of the next-item warp: rest of its queue group
-    // work item bi: chunk k of event e's seeds (sizes differ by at most one)
+    // work item bi (layouts in k_bucket.cu): order 0, chunk k of event e's
+    // seeds (sizes differ by at most one); order 1, full chunk k of event e,
+    // or, past the full chunks, the remainder of the event listed for it
     auto resolve_next = [&]() {    // the next-item warp, all 32 lanes
         int bi = 0;
         if ((tid & 31) == 0) {
@@ -580,17 +582,30 @@ __global__ void __launch_bounds__(T, F ? (V == 1 ? 3 : kSearchFusedCtas) : (V ==
             if ((tid & 31) == 0) s_nx[0] = n_items;
             return;
         }
-        const int e = warp_find_segment(a.item_off, a.n_events, bi);
+        const int n_full = a.order ? __ldg(a.item_off + a.n_events + 1) : n_items;
+        const int e = bi < n_full ? warp_find_segment(a.item_off, a.n_events, bi)
+                                  : __ldg(a.item_off + a.n_events + 2 + (bi - n_full));
         if ((tid & 31) == 0) {
-            const int i0 = __ldg(a.item_off + e), i1 = __ldg(a.item_off + e + 1);
             const int s0 = __ldg(a.seed_off + e), ns = __ldg(a.seed_off + e + 1) - s0;
             int h0 = __ldg(a.hit_off + e), h1 = __ldg(a.hit_off + e + 1);
             if (h0 < 0 || h1 < h0 || h1 > a.n_hits || h1 - h0 > kMaxEventHits) h1 = h0 = 0;
-            const int k = bi - i0, nc = i1 - i0;
+            int b0, b1;
+            if (!a.order) {
+                const int i0 = __ldg(a.item_off + e), i1 = __ldg(a.item_off + e + 1);
+                const int k = bi - i0, nc = i1 - i0;
+                b0 = (int)(((long long)k * ns) / nc);
+                b1 = (int)(((long long)(k + 1) * ns) / nc);
+            } else if (bi < n_full) {
+                b0 = (bi - __ldg(a.item_off + e)) * a.chunk;
+                b1 = b0 + a.chunk;
+            } else {
+                b0 = ns - ns % a.chunk;
+                b1 = ns;
+            }
             s_nx[0] = bi;
             s_nx[1] = e;
-            s_nx[2] = s0 + (int)(((long long)k * ns) / nc);
-            s_nx[3] = s0 + (int)(((long long)(k + 1) * ns) / nc);
+            s_nx[2] = s0 + b0;
+            s_nx[3] = s0 + b1;
             s_nx[4] = h0;
             s_nx[5] = h1;
         }

@@ -88,9 +88,10 @@ class ds_kernel_time(C.Structure):
 
 class ds_tuning(C.Structure):
     _fields_ = [("search_chunk", C.c_int32), ("search_ctas_per_sm", C.c_int32), ("search_group", C.c_int32),
-                ("search_stage_hits", C.c_int32), ("vertex_ctas_per_sm", C.c_int32), ("vertex_small_cap", C.c_int32)]
+                ("search_stage_hits", C.c_int32), ("vertex_ctas_per_sm", C.c_int32), ("vertex_small_cap", C.c_int32),
+                ("search_order", C.c_int32)]
     _defaults = dict(search_chunk=128, search_ctas_per_sm=5, search_group=1, search_stage_hits=5120,
-                     vertex_ctas_per_sm=4, vertex_small_cap=512)
+                     vertex_ctas_per_sm=4, vertex_small_cap=512, search_order=1)
 
     def __init__(self, *args, **kw):
         """Positional values in field order; fields not given take the library's defaults."""

@@ -56,9 +56,11 @@ def test_outputs_do_not_depend_on_tuning(torch_cuda, weights):
     d = ds.Downstream(synth.default_config(), weights)
     dev = d.to_device(b)
     # search: chunk, CTAs per SM, group, staging; vertexing: CTAs per SM, one-event-per-CTA
-    # track limit (2: every event with two or more tracks goes to the pair-segment items)
-    shapes = [(128, 4, 2, 5632, 4, 512), (128, 5, 1, 5120, 4, 512), (32, 1, 1, 0, 1, 64), (64, 3, 8, 32768, 2, 128), (1, 2, 16, 2048, 3, 256),
-              (96, 4, 4, 46080, 4, 2)]
+    # track limit (2: every event with two or more tracks goes to the pair-segment items);
+    # work-item order (0: equal chunks in event order, 1: full chunks, then remainders largest first)
+    shapes = [(128, 4, 2, 5632, 4, 512, 0), (128, 5, 1, 5120, 4, 512, 1), (32, 1, 1, 0, 1, 64, 1),
+              (64, 3, 8, 32768, 2, 128, 0), (1, 2, 16, 2048, 3, 256, 1), (96, 4, 4, 46080, 4, 2, 1),
+              (100, 5, 1, 5120, 4, 512, 1), (128, 5, 1, 5120, 4, 512, 0)]
     ref = None
     for shape in shapes:
         t = ds.ds_tuning(*shape)
@@ -93,9 +95,10 @@ def test_autotune(torch_cuda, weights):
     best, entries = ds.ds_autotune(d.ctx, dev, out, reps=2)
     d.sync()
     # coordinate descent from the default: one measurement, then two sweeps over
-    # 7 stage sizes, 4 chunks, 4 CTA counts, 4 groups, 4 vertex CTA counts and 4
-    # vertex track limits, each skipping the value current when it is reached
-    assert 1 + 2 * (6 + 3 * 5) <= len(entries) <= 1 + 2 * (7 + 4 * 5)
+    # 7 stage sizes, 4 chunks, 4 CTA counts, 4 groups, 4 vertex CTA counts, 4
+    # vertex track limits and 2 work-item orders, each skipping the value
+    # current when it is reached
+    assert 1 + 2 * (6 + 3 * 5 + 1) <= len(entries) <= 1 + 2 * (7 + 4 * 5 + 2)
     assert all(ms > 0 for _, ms in entries)
     cur = ds.ds_get_tuning(d.ctx).as_dict()
     assert cur == best.as_dict()
