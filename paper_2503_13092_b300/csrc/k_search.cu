@@ -23,7 +23,8 @@
 // the sector or its distance ties with another hit's; the ids of a
 // candidate's hits are looked up when it is written.
 // Three flattened phases keep lanes busy whatever the hits per seed: UTbX
-// window (thread per seed), refined windows (thread per (seed, UTbX hit)
+// window (thread per seed; Dv1's triplet search a warp per seed, its lanes
+// over the seed's UTbX hits), refined windows (thread per (seed, UTbX hit)
 // pair, in seed-aligned chunks of at most 640 pairs), fit + features (thread
 // per candidate of the chunk).  Unfused form: candidates are written to a
 // compact buffer reserved with one atomicAdd per chunk, seed by seed, for
@@ -77,27 +78,6 @@ __device__ __forceinline__ void topn_insert(float (&d)[N], int (&id)[N], int (&p
             if (sw) {
                 float td = d[k]; d[k] = d[k - 1]; d[k - 1] = td;
                 int ti = id[k]; id[k] = id[k - 1]; id[k - 1] = ti;
-                int tp = p[k]; p[k] = p[k - 1]; p[k - 1] = tp;
-            }
-        }
-    }
-}
-
-// Dv1: the N best triplets by (residual, UTbX id), p packing the UTbX
-// position in its low 16 bits; ids are looked up only on exact residual ties.
-template <int N>
-__device__ __forceinline__ void topn_insert_lazy(float (&d)[N], int (&p)[N], float dn, int pn, const EvHits &H)
-{
-    const float inf = __int_as_float(0x7f800000);
-    if (dn < d[N - 1] || (dn == d[N - 1] && hit_id(H, pn & 0xffff) < hit_id(H, p[N - 1] & 0xffff))) {
-        d[N - 1] = dn;
-        p[N - 1] = pn;
-#pragma unroll
-        for (int k = N - 1; k > 0; --k) {
-            const bool sw = d[k] < d[k - 1] ||
-                            (d[k] == d[k - 1] && d[k] != inf && hit_id(H, p[k] & 0xffff) < hit_id(H, p[k - 1] & 0xffff));
-            if (sw) {
-                float td = d[k]; d[k] = d[k - 1]; d[k - 1] = td;
                 int tp = p[k]; p[k] = p[k - 1]; p[k - 1] = tp;
             }
         }
@@ -470,6 +450,27 @@ __device__ __noinline__ int wide_first_window(const DevGeom &g, const float *X0,
     return r;
 }
 
+// Dv1: rank of triplet slot k among slots [0, c) of a warp's scratch by
+// (residual, UTbX id); slot = (residual bits, UTbX position | UTaX position
+// << 16).  Ids are looked up only on an exact residual tie.  Eight slots per
+// step, so that their shared-memory loads overlap.
+__device__ __forceinline__ int tri_rank(const int2 *tri, int k, int c, const EvHits &H)
+{
+    const int2 me = tri[k];
+    const float dm = __int_as_float(me.x);
+    int r = 0;
+    for (int j0 = 0; j0 < c; j0 += 8) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int j = j0 + q;
+            const int2 e = tri[j];
+            const float de = __int_as_float(e.x);
+            r += j < c && (de < dm || (de == dm && j != k && hit_id(H, e.y & 0xffff) < hit_id(H, me.y & 0xffff)));
+        }
+    }
+    return r;
+}
+
 // Dv1: the UTaX strip coordinate predicted by the line through the magnet
 // point and the UTbX hit at sorted position ib.
 __device__ __forceinline__ float dv1_ua(const DevGeom &g, const SeedCtx &sc, const float *X0, int ib)
@@ -764,48 +765,103 @@ __global__ void __launch_bounds__(T, F ? (V == 1 ? 3 : kSearchFusedCtas) : (V ==
                 sel_u = u;
                 sel_state = P.training ? 2 : (nok > P.k1 ? 1 : 0);
             }
-        } else {
-            // Dv1 triplets: every UTbX hit with a physical kink (a window of
-            // half-width dtx_max (z_m - z_bX) around the seed's straight
-            // extrapolation) whose magnet-point line meets a UTaX hit within
-            // w_tri; ranked by (residual, UTbX id).  p packs (UTbX, UTaX) positions.
-            float d[kK1Max];
-            int p[kK1Max];
-#pragma unroll
-            for (int k = 0; k < kK1Max; ++k) {
-                d[k] = __int_as_float(0x7f800000);
-                p[k] = -1;
-            }
+        }
+        // Dv1: the triplet search runs below, a warp per seed
+    }
+    if (V == 1) {
+        // Dv1 triplets: every UTbX hit with a physical kink (a window of
+        // half-width dtx_max (z_m - z_bX) around the seed's straight
+        // extrapolation) whose magnet-point line meets a UTaX hit within
+        // w_tri; the k1 best by (residual, UTbX id) are kept.  The warp takes
+        // its seeds one at a time, its lanes over the seed's UTbX hits (32 per
+        // step, each with its UTaX window); the triplets found are inserted
+        // into the seed's ranked list held by lanes 0..kK1Max-1 (lane j: the
+        // j-th best so far, residual and packed (UTbX, UTaX) positions), ids
+        // looked up only on an exact residual tie.
+        __syncwarp();
+        const unsigned full = 0xffffffffu;
+        const int lane = tid & 31;
+        const float inf = __int_as_float(0x7f800000);
+        // this warp's 32-slot triplet scratch: pair-array rows, unused until
+        // the refined windows
+        int2 *const tri = reinterpret_cast<int2 *>(&s_col[L::kKeepRows][0]) + (tid >> 5) * 32;
+        static_assert((L::kColRows - L::kKeepRows) * T * sizeof(uint16_t) >= T * sizeof(int2), "triplet scratch");
+        unsigned am = __ballot_sync(full, active);
+        while (am) {
+            const int src = __ffs(am) - 1;
+            am &= am - 1;
+            const int o = tid - lane + src;
+            const SeedCtx sc = seed_ctx_of(g, s_sa[o], s_sb[o], 0.f);
             const float w_b = P.dv1_dtx * (sc.zm - g.z[3]);
             const float u0 = fmaf(sc.tx, g.z[3] - sc.zm, sc.xm) - g.dxdy[3] * sc.yl[3];
             const float y3 = sc.yl[3], dy = P.dy_tol;
+            const int wsec0 = s_wsec[0][o];
             const int s_lo = sector_of(g, y3 - dy - 0.01f), s_hi = sector_of(g, y3 + dy + 0.01f);
             const int b0 = xbin_of(g, u0 - w_b - 1e-3f), b1 = xbin_of(g, u0 + w_b + 1e-3f);
-            int n_tri = 0;
+            // The seed's triplets are collected in this warp's scratch
+            // (slots 0..cnt-1, in the order found); when 32 slots do not hold
+            // the next ones, the kK1Max best so far are kept (a triplet
+            // dropped then has kK1Max better ones, which stay).  At the end
+            // each collected triplet's rank by (residual, UTbX id) places the
+            // kK1Max best in the seed's column.
+            int cnt = 0, n_tri = 0;
             for (int sct = s_lo; sct <= s_hi; ++sct) {
                 // rows whose strips all span the sector pass the strip test as a whole
                 const bool per_hit = sector_strip_class(g, Part, 3, sct, y3, dy) == 2;
                 const int row = (3 * g.n_sec + sct) * kNXB;
                 const int i0 = Tb[row + b0], i1 = Tb[row + b1 + 1];
-                for (int i = i0; i < i1; ++i) {
-                    if (!(fabsf(X0[i] - u0) < w_b)) continue;
-                    if (per_hit) {
+                for (int ib = i0; ib < i1; ib += 32) {
+                    const int i = ib + lane;
+                    bool ok = i < i1 && fabsf(X0[i] - u0) < w_b;
+                    if (ok && per_hit) {
                         const float4 hb = hit_record(H, i);
-                        if (!(hb.y - dy <= y3 && y3 <= hb.z + dy)) continue;
+                        ok = hb.y - dy <= y3 && y3 <= hb.z + dy;
                     }
-                    const float ua = dv1_ua(g, sc, X0, i);
-                    const WinBest wa = window_best<1>(g, X0, H, Tb, Part, 0, ua, sc.yl[0], P.dv1_w_tri, dy, s_wsec[0][tid]);
-                    if (wa.cnt == 0) continue;
-                    topn_insert_lazy<kK1Max>(d, p, wa.d0, i | (wa.p0 << 16), H);
-                    ++n_tri;
+                    float dn = inf;
+                    int pn = -1;
+                    if (ok) {
+                        const float ua = dv1_ua(g, sc, X0, i);
+                        const WinBest wa = window_best<1>(g, X0, H, Tb, Part, 0, ua, sc.yl[0], P.dv1_w_tri, dy, wsec0);
+                        ok = wa.cnt > 0;
+                        dn = wa.d0;
+                        pn = i | (wa.p0 << 16);
+                    }
+                    unsigned m = __ballot_sync(full, ok);
+                    n_tri += __popc(m);
+                    while (m) {
+                        if (cnt == 32) {
+                            const int r = tri_rank(tri, lane, 32, H);
+                            const int2 me = tri[lane];
+                            __syncwarp();
+                            if (r < kK1Max) tri[r] = me;
+                            __syncwarp();
+                            cnt = kK1Max;
+                        }
+                        // the new triplets in lane order, as many as fit
+                        const int nt = min(__popc(m), 32 - cnt);
+                        const int k = __popc(m & ((1u << lane) - 1u));
+                        const bool put = ((m >> lane) & 1u) && k < nt;
+                        if (put) tri[cnt + k] = make_int2(__float_as_int(dn), pn);
+                        m &= ~__ballot_sync(full, put);
+                        cnt += nt;
+                        __syncwarp();
+                    }
                 }
             }
-            nbx = min(n_tri, P.k1);
-#pragma unroll
-            for (int j = 0; j < kK1Max; ++j) {
-                col[j * T] = (uint16_t)(p[j] & 0xffff);
-                col[(kK1Max + j) * T] = j < nbx ? (uint16_t)((unsigned)p[j] >> 16) : kNone;   // the triplet's UTaX hit
+            const int nb = min(n_tri, P.k1);
+            if (lane < cnt) {
+                const int r = tri_rank(tri, lane, cnt, H);
+                if (r < kK1Max) {
+                    const int pk = tri[lane].y;
+                    colb[r * T + o] = (uint16_t)(pk & 0xffff);
+                    colb[(kK1Max + r) * T + o] = r < nb ? (uint16_t)((unsigned)pk >> 16) : kNone;   // the triplet's UTaX hit
+                }
+            } else if (lane < kK1Max) {
+                colb[lane * T + o] = kNone;
+                colb[(kK1Max + lane) * T + o] = kNone;
             }
+            __syncwarp();   // the scratch is refilled by the next seed
+            if (lane == src) nbx = nb;
         }
     }
     if (V == 0) {

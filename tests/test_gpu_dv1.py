@@ -48,3 +48,25 @@ def test_dv1_recovers_noise_free_truth(torch_cuda, weights):
     t = g["tracks"]
     assert len(t) == len(b["seed_track"])
     assert np.all(b["hit_track"][t["hit"]] == b["seed_track"][t["seed"]][:, None])
+
+
+def test_dv1_dense_event_keeps_k1_best(torch_cuda, weights):
+    """One event of 30000 UT hits (the largest C3 occupancy): about 535 hits
+    per (layer, sector) row over 1700 mm, so a 2 mm UTaX window holds a hit
+    for roughly half of a seed's ~535 UTbX hits and a seed forms a few
+    hundred triplets, of which only the k1 best by (residual, UTbX id) are
+    kept (the GPU keeps them through repeated selections over 32 at a time).
+    The event is too large to stage, so x0 is read from global memory.
+    Tracks must match the oracle seed by seed."""
+    from paper_2503_13092_b300 import ds
+    cfg = synth.default_config(variant=1)
+    b = synth.generate(synth.spec_fixed(1, 30, 30, 30000), 13)
+    g = ds.Downstream(cfg, weights, cand_per_seed=40).run(b)
+    assert g["stats"]["status"] == 0, g["stats"]
+    o = oracle.reconstruct(b, cfg, weights, n_threads=1)
+    assert np.all(o["nbx"] == cfg["k1"])    # every seed had more triplets than it keeps
+    rep = parity.compare_tracks(b, o, g)
+    print({k: rep[k] for k in ("n_tracks_oracle", "n_diff", "n_excused")})
+    assert rep["n_tracks_oracle"] > 0
+    parity.assert_tracks_match(rep)
+    parity.assert_vertices_match(parity.compare_vertices(cfg, g))
