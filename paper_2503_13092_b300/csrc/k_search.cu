@@ -850,7 +850,10 @@ __global__ void __launch_bounds__(T, F ? (V == 1 ? 3 : kSearchFusedCtas) : (V ==
             }
             const int nb = min(n_tri, P.k1);
             if (lane < cnt) {
-                const int r = tri_rank(tri, lane, cnt, H);
+                // every triplet is kept when there are at most k1: outside
+                // training mode their order is free (the pick breaks key
+                // ties by hit ids), so they keep the order found
+                const int r = cnt <= P.k1 && !P.training ? lane : tri_rank(tri, lane, cnt, H);
                 if (r < kK1Max) {
                     const int pk = tri[lane].y;
                     colb[r * T + o] = (uint16_t)(pk & 0xffff);
