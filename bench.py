@@ -246,9 +246,30 @@ def run_cpu_baseline(batch, cfg, w, target_s=12.0):
         if dt > 0.25 * target_s or n >= E:
             break
         n = min(E, int(n * max(2.0, 0.5 * target_s / max(dt, 1e-3))))
-    return dict(value=len(ev) / dt, unit="events/s", cores=cores, kind="oracle",
+    # the same oracle on one thread (a smaller sample of the same events)
+    n1 = min(16, E)
+    sb1 = _sub(batch, list(range(n1)))
+    t1 = time.perf_counter()
+    r1 = oracle.reconstruct(sb1, cfg, w, n_threads=1)
+    tk1 = oracle.tracks_from(r1, sb1["seed_off"])
+    st1 = tk1["state"].astype(np.float32)
+    oracle.vertex(cfg, tk1["trk_off"], st1[:, 0], st1[:, 1], st1[:, 2], st1[:, 3], st1[:, 4])
+    dt1 = time.perf_counter() - t1
+    return dict(value=len(ev) / dt, unit="events/s", cores=cores, kind="oracle", cpu_model=cpu_model(),
                 sample=f"first {len(ev)} events of the step's batch, reconstruct + vertex, "
-                       f"{cores} threads (one event per thread), {dt:.2f} s")
+                       f"{cores} threads (one event per thread), {dt:.2f} s",
+                single_thread=dict(value=n1 / dt1, unit="events/s", sample=f"first {n1} events, one thread, {dt1:.2f} s"))
+
+
+def cpu_model():
+    """The host CPU's model name (Linux /proc/cpuinfo), or None."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
 
 
 def _sub(b, events):
