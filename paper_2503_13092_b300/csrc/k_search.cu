@@ -774,10 +774,8 @@ __global__ void __launch_bounds__(T, F ? (V == 1 ? 3 : kSearchFusedCtas) : (V ==
         // extrapolation) whose magnet-point line meets a UTaX hit within
         // w_tri; the k1 best by (residual, UTbX id) are kept.  The warp takes
         // its seeds one at a time, its lanes over the seed's UTbX hits (32 per
-        // step, each with its UTaX window); the triplets found are inserted
-        // into the seed's ranked list held by lanes 0..kK1Max-1 (lane j: the
-        // j-th best so far, residual and packed (UTbX, UTaX) positions), ids
-        // looked up only on an exact residual tie.
+        // step, each with its UTaX window); the triplets found are collected
+        // in a scratch of the warp and ranked once per seed (below).
         __syncwarp();
         const unsigned full = 0xffffffffu;
         const int lane = tid & 31;
