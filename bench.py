@@ -195,10 +195,12 @@ def step_traffic():
     return tot
 
 
-def h2d_ceiling(torch, arrays, reps=5):
+def h2d_ceiling(torch, arrays, reps=5, d2h_bytes=0):
     """Upload rate of the e2e step's own pinned host arrays with nothing else
     running: one cudaMemcpyAsync per array (as the serving path issues them)
-    on one stream, and the same copies spread over two streams."""
+    on one stream, and the same copies spread over two streams; with
+    d2h_bytes, also the rate of one download of that size into pinned host
+    memory with nothing else running."""
     from cuda.bindings import runtime as rt
     nbytes = sum(a.nbytes for a in arrays)
     dst = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
@@ -213,19 +215,53 @@ def h2d_ceiling(torch, arrays, reps=5):
             assert err == rt.cudaError_t.cudaSuccess, err
             off += a.nbytes
 
+    def timed(fn, st):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        streams[1].wait_stream(streams[0])
+        for _ in range(reps):
+            fn()
+        streams[0].wait_stream(streams[1])
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
     res = dict(bytes=nbytes, copies=len(arrays))
     for name, ns in (("one_stream", 1), ("two_streams", 2)):
-        issue(ns)
+        res[name + "_gbs"] = nbytes * reps / timed(lambda: issue(ns), streams[0]) / 1e9
+    if d2h_bytes:
+        src = torch.empty(d2h_bytes, dtype=torch.uint8, device="cuda")
+        host = torch.empty(d2h_bytes, dtype=torch.uint8).pin_memory()
+        d2h = rt.cudaMemcpyKind.cudaMemcpyDeviceToHost
+
+        def down():
+            err, = rt.cudaMemcpyAsync(host.data_ptr(), src.data_ptr(), d2h_bytes, d2h, streams[0].cuda_stream)
+            assert err == rt.cudaError_t.cudaSuccess, err
+
+        res["d2h_bytes"] = d2h_bytes
+        res["d2h_gbs"] = d2h_bytes * reps / timed(down, streams[0]) / 1e9
+        # both directions at once: the uploads on one stream, the download on
+        # another; time until both are done
+        s3 = torch.cuda.Stream()
+
+        def both():
+            issue(1)
+            err, = rt.cudaMemcpyAsync(host.data_ptr(), src.data_ptr(), d2h_bytes, d2h, s3.cuda_stream)
+            assert err == rt.cudaError_t.cudaSuccess, err
+
+        both()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         e0.record(streams[0])
-        streams[1].wait_stream(streams[0])
+        s3.wait_stream(streams[0])
         for _ in range(reps):
-            issue(ns)
-        streams[0].wait_stream(streams[1])
+            both()
+        streams[0].wait_stream(s3)
         e1.record(streams[0])
         torch.cuda.synchronize()
-        res[name + "_gbs"] = nbytes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        res["up_and_down_concurrent_ms"] = e0.elapsed_time(e1) / reps
     return res
 
 
@@ -1072,13 +1108,21 @@ def main():
     e2e["value"] *= ws
     ceil = h2d_ceiling(torch, [pin[k] for k in ("seed_off", "hit_off", "seed_x", "seed_y", "seed_tx", "seed_ty",
                                                 "seed_qop", "seed_chi2", "hit_x0", "hit_ybeg", "hit_yend",
-                                                "hit_layer")])
-    best = max(v for k, v in ceil.items() if k.endswith("_gbs"))
+                                                "hit_layer")], d2h_bytes=e2e["d2h_bytes_per_step"])
+    best = max(ceil["one_stream_gbs"], ceil["two_streams_gbs"])
     e2e["h2d_ceiling_gbs"] = best
     e2e["h2d_ceiling"] = ceil
     # the rate the upload alone allows, and e2e as a fraction of it
     e2e["upload_bound_events_per_s"] = ws * E / (e2e["h2d_bytes_per_step"] / (best * 1e9))
     e2e["frac_of_upload_bound"] = e2e["value"] / e2e["upload_bound_events_per_s"]
+    # the rate with each step's upload and download in sequence at their
+    # measured rates (no overlap of the two directions)
+    t_serial = e2e["h2d_bytes_per_step"] / (best * 1e9) + e2e["d2h_bytes_per_step"] / (ceil["d2h_gbs"] * 1e9)
+    e2e["serial_copy_bound_events_per_s"] = ws * E / t_serial
+    e2e["frac_of_serial_copy_bound"] = e2e["value"] / e2e["serial_copy_bound_events_per_s"]
+    # and with the step's upload and download issued together
+    e2e["concurrent_copy_bound_events_per_s"] = ws * E / (ceil["up_and_down_concurrent_ms"] * 1e-3)
+    e2e["frac_of_concurrent_copy_bound"] = e2e["value"] / e2e["concurrent_copy_bound_events_per_s"]
 
     # ------------------------------------------------ plain form (1 event/launch)
     n_plain = min(args.plain_events, E)
