@@ -25,6 +25,8 @@ def torch_cuda():
     ("c1", {}, {"pick_chi2": 1}),
     ("c2", {"n_events": 40}, {}),
     ("c2", {"n_events": 20, "mode": "B"}, {"mode": "B"}),
+    ("c2", {"n_events": 20}, {"k1": 3}),          # most seeds keep 3 of more triplets (ranked)
+    ("c1", {}, {"training": 1}),                  # training mode: kept triplets always ranked
 ])
 def test_dv1_matches_oracle(torch_cuda, weights, name, kw, over):
     from paper_2503_13092_b300 import ds
