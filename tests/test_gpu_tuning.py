@@ -105,3 +105,51 @@ def test_autotune(torch_cuda, weights):
     assert min(ms for t, ms in entries if t == cur) == min(ms for _, ms in entries)
     got = run_with(d, ds, dev, best)
     assert got[1:] == ref[1:]
+
+
+def seed_count_batch(counts, seed=21):
+    """One event per entry of `counts` (that many SciFi seeds, 40 % true,
+    1500 UT hits), concatenated into one batch."""
+    parts = []
+    for k, n in enumerate(counts):
+        nt = 2 * ((4 * n) // 20)
+        parts.append(synth.generate(synth.spec_fixed(1, nt, n - nt, 1500), seed + k))
+    out = dict(n_events=len(parts), mode="A")
+    so, ho = [0], [0]
+    for p in parts:
+        so.append(so[-1] + int(p["seed_off"][-1]))
+        ho.append(ho[-1] + int(p["hit_off"][-1]))
+    out["seed_off"] = np.array(so, np.int32)
+    out["hit_off"] = np.array(ho, np.int32)
+    for k in ("seed_x", "seed_y", "seed_tx", "seed_ty", "seed_qop", "seed_chi2", "seed_track", "hit_x0",
+              "hit_ybeg", "hit_yend", "hit_layer", "hit_track"):
+        out[k] = np.concatenate([p[k] for p in parts])
+    return out
+
+
+def test_work_item_orders_on_uneven_seed_counts(torch_cuda, weights):
+    """Events with no seeds, fewer than a chunk, exactly one or two chunks and
+    a chunk plus a remainder: equal chunks in event order (order 0) and full
+    chunks then remainders largest first (order 1, chunks of 128 and 100
+    seeds) give the same bytes, and those match the oracle."""
+    import oracle
+    from paper_2503_13092_b300 import ds
+    counts = [0, 1, 127, 128, 129, 256, 300, 0, 77, 200]
+    b = seed_count_batch(counts)
+    assert np.diff(b["seed_off"]).tolist() == counts
+    cfg = synth.default_config()
+    d = ds.Downstream(cfg, weights)
+    dev = d.to_device(b)
+    ref = None
+    for shape in [(128, 5, 1, 5120, 4, 512, 0), (128, 5, 1, 5120, 4, 512, 1), (100, 5, 1, 5120, 4, 512, 1)]:
+        r = run_with(d, ds, dev, ds.ds_tuning(*shape))
+        assert r[0]["status"] == 0, (shape, r[0])
+        if ref is None:
+            ref = r
+        else:
+            assert r[1:] == ref[1:], shape
+    g = d.run(b, dev=dev)
+    o = oracle.reconstruct(b, cfg, weights, n_threads=8)
+    rep = parity.compare_tracks(b, o, g)
+    assert rep["n_tracks_oracle"] > 0
+    parity.assert_tracks_match(rep)
