@@ -43,7 +43,8 @@ struct ds_ctx {
     uint16_t *sperm = nullptr;
     float *sx0 = nullptr;
     uint16_t *bins = nullptr;
-    int *item_off = nullptr;
+    int *item_off = nullptr;      // search work items [2 E + 2], then the events largest first [E]
+    int order_events = -1;        // events of the batch the event order was laid out for
     ds_track *trk_ws = nullptr;
     unsigned long long *key_ws = nullptr;
     int4 *hit_ws = nullptr;
@@ -419,7 +420,7 @@ ds_status ds_reserve(ds_ctx *ctx, int32_t E, int32_t S, int32_t H)
         if ((st = grow(ctx, &ctx->large_vtx, (size_t)E)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->large_aux, 2 * (size_t)E + 2)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->vtx_items, 2 * (size_t)ds::kVtxItemsPerEvent * E)) != DS_OK) return st;
-        if ((st = grow(ctx, &ctx->item_off, 2 * (size_t)E + 2)) != DS_OK) return st;
+        if ((st = grow(ctx, &ctx->item_off, 3 * (size_t)E + 2)) != DS_OK) return st;
         ctx->cap_events = E;
     }
     const long long want_cand = (long long)(S > ctx->cap_seeds ? S : ctx->cap_seeds) * ctx->cand_per_seed;
@@ -506,9 +507,11 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     ba.item_off = ctx->item_off;
     ba.chunk = ctx->tune.search_chunk;
     ba.order = ctx->tune.search_order;
+    ba.ev_order = ctx->item_off + 2 * (size_t)ctx->cap_events + 2;
     ba.capacity_sizes = (b->flags & DS_BATCH_CAPACITY) ? 1 : 0;
     ba.cnt = ctx->d_cnt;
     DS_CUDA(ds::launch_bucket(ba, st, &ctx->prof), "bucket kernel");
+    ctx->order_events = b->n_events;
 
     ds::SearchArgs sa{};
     sa.g = ctx->g;
@@ -580,6 +583,7 @@ ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *b, const ds_seeds *s
     ca.key_ws = ctx->key_ws;
     ca.hit_ws = ctx->hit_ws;
     ca.rank_ws = ctx->rank_ws;
+    ca.ev_order = ba.ev_order;
     ca.next_ws = ctx->clone_next;
     ca.count_ws = ctx->count_trk;
     ca.trk_off = out->trk_off;
@@ -745,6 +749,10 @@ ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tr, ds_vertices *out, void *st
     va.pool_item = ctx->pool_item;
     va.pool_cap = out->capacity;
     va.count_ws = ctx->count_vtx;
+    // the events in the order the last ds_reconstruct laid out (largest
+    // first): any permutation of the events gives the same output, so it is
+    // used whenever the event count matches
+    va.ev_order = ctx->order_events == E ? ctx->item_off + 2 * (size_t)ctx->cap_events + 2 : nullptr;
     va.large_list = ctx->large_vtx;
     va.large_pairs = ctx->large_aux;
     va.large_item_off = ctx->large_aux + ctx->cap_events;

@@ -35,6 +35,7 @@ struct BucketArgs {
     int *item_off;         // [2 n_events + 2] search work items (k_bucket.cu)
     int chunk;             // max seeds per search work item (<= kSearchThreads)
     int order;             // work-item order (ds_tuning.search_order)
+    int *ev_order;         // [n_events]: events by seed count, largest first (NULL: not laid out)
     int capacity_sizes;    // 1: n_seeds, n_hits are capacities (DS_BATCH_CAPACITY)
     DevCounters *cnt;
 };
@@ -120,6 +121,7 @@ struct CloneArgs {
     const int4 *hit_ws;
     int *rank_ws;         // per seed: rank inside its event, -1 = not output
     int *next_ws;         // 2 ints per seed: clone chains of events larger than shared memory holds
+    const int *ev_order;  // events largest first (k_bucket), or NULL: CTA b takes event b
     int *count_ws;        // per event
     int32_t *trk_off;     // [n_events + 1] (caller's)
     int32_t *n_tracks;    // caller's device scalar
@@ -151,6 +153,7 @@ struct VertexArgs {
     int *pool_item;         // slot -> work item of the large-capacity launch
     int pool_cap;
     int *count_ws;          // per event
+    const int *ev_order;    // a permutation of the events to pull them in (largest first), or NULL
     int *large_list;        // events with more tracks than the small launch takes
     int *large_pairs;       // per listed event: opposite-charge pairs
     int *large_item_off;    // per listed event: first work item (pair segment); [n_large] = total

@@ -48,7 +48,7 @@ constexpr size_t kOffCloneNext = kOffRank + align256(sizeof(int) * (size_t)kNASe
 constexpr size_t kOffSeedCand = kOffCloneNext + align256(2 * sizeof(int) * (size_t)kNASeeds);
 constexpr size_t kOffCount = kOffSeedCand + align256(sizeof(int4) * (size_t)kNASeeds);
 constexpr size_t kOffItemOff = kOffCount + align256(sizeof(int) * (size_t)kNAEvents);
-constexpr size_t kOffCandFeat = kOffItemOff + align256(sizeof(int) * (size_t)(2 * kNAEvents + 2));
+constexpr size_t kOffCandFeat = kOffItemOff + align256(sizeof(int) * (size_t)(3 * kNAEvents + 2));
 constexpr size_t kOffCandMeta = kOffCandFeat + align256(sizeof(float4) * 4 * (size_t)kNACand);
 constexpr size_t kOffCandLogit = kOffCandMeta + align256(sizeof(CandMeta) * (size_t)kNACand);
 constexpr size_t kScratchBytes = kOffCandLogit + align256(sizeof(float) * (size_t)kNACand);
@@ -139,6 +139,7 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         ba.item_off = reinterpret_cast<int *>(base + kOffItemOff);
         ba.chunk = kSearchThreads;
         ba.order = 1;
+        ba.ev_order = ba.item_off + 2 * kNAEvents + 2;
         ba.capacity_sizes = (b->flags & DS_BATCH_CAPACITY) ? 1 : 0;
         ba.cnt = cnt;
         if (launch_bucket(ba, s, &no_prof) != cudaSuccess) return DS_ERR_CUDA;
@@ -203,6 +204,7 @@ extern "C" DS_API ds_status ds_reconstruct_noalloc(const ds_geometry *geom, cons
         ca.key_ws = pa.key_ws;
         ca.hit_ws = pa.hit_ws;
         ca.rank_ws = sa.rank_ws;
+        ca.ev_order = ba.ev_order;
         ca.next_ws = reinterpret_cast<int *>(base + kOffCloneNext);
         ca.count_ws = reinterpret_cast<int *>(base + kOffCount);
         ca.trk_off = out->trk_off;

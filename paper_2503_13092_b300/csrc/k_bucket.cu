@@ -25,6 +25,11 @@
 
 namespace ds {
 
+// Events by seed count, largest first: bucket of a count (steps of 16 seeds,
+// 2032 and more in the first bucket).
+constexpr int kEvBuckets = 128;
+__device__ __forceinline__ int ev_bucket(int ns) { return kEvBuckets - 1 - min(ns >> 4, kEvBuckets - 1); }
+
 // Bin counters per CTA: every thread scans a run of `per` consecutive
 // counters, a multiple of 4 (16-byte shared loads, 8-byte table stores).
 __host__ __device__ constexpr int bucket_counters_per_thread(int n_sec)
@@ -129,6 +134,28 @@ __global__ void __launch_bounds__(kBucketThreads, 3) k_bucket(const __grid_const
                 if (r) a.item_off[E + 2 + atomicAdd(s_rc + (C - r), 1)] = k;
             }
             n_items = n_full + s_rc[kSearchThreads];
+            __syncthreads();   // s_cnt is cleared below
+        }
+        if (a.ev_order) {
+            // the events by seed count, largest first (counting sort on the
+            // count in steps of 16; the order inside a step is free), the
+            // order in which the clone and vertex kernels take them
+            __syncthreads();
+            int *s_ec = reinterpret_cast<int *>(s_cnt);   // [kEvBuckets + 1]: counts, then cursors
+            for (int r = tid; r <= kEvBuckets; r += blockDim.x) s_ec[r] = 0;
+            __syncthreads();
+            for (int k = tid; k < E; k += blockDim.x) atomicAdd(s_ec + ev_bucket(seeds_of(k)), 1);
+            __syncthreads();
+            if (tid == 0) {
+                int run = 0;
+                for (int r = 0; r < kEvBuckets; ++r) {
+                    const int c = s_ec[r];
+                    s_ec[r] = run;
+                    run += c;
+                }
+            }
+            __syncthreads();
+            for (int k = tid; k < E; k += blockDim.x) a.ev_order[atomicAdd(s_ec + ev_bucket(seeds_of(k)), 1)] = k;
             __syncthreads();   // s_cnt is cleared below
         }
         if (tid == 0) {

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kCloneThreads, kCloneCtasPerSm) k_clone(const 
     __shared__ int s_head_bx[1 << kCloneHashBits], s_head_au[1 << kCloneHashBits];
     __shared__ int s_scan[32];
     __shared__ bool s_last;
-    const int e = blockIdx.x;
+    const int e = a.ev_order ? __ldg(a.ev_order + blockIdx.x) : (int)blockIdx.x;   // largest events first
     int s0 = __ldg(a.seed_off + e), s1 = __ldg(a.seed_off + e + 1);
     if (s0 < 0 || s1 < s0 || s1 > a.n_seeds) s0 = s1 = 0;
     const int ns = s1 - s0;

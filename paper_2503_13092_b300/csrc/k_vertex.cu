@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(LARGE ? kVtxLargeThreads : kVtxThreads, LARGE 
         }
     } else if (threadIdx.x == 0) {
         const int k = atomicAdd(&a.cnt->vtx_queue[0], 1);
-        s_e = k < a.n_events ? k : a.n_events;
+        s_e = k < a.n_events ? (a.ev_order ? __ldg(a.ev_order + k) : k) : a.n_events;
     }
     __syncthreads();
     const int e = s_e;
