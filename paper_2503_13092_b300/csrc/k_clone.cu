@@ -6,7 +6,8 @@
 // ties by seed order).  Every decision is taken against the full set before
 // killing, so the result does not depend on the order pairs are visited.
 //
-// One CTA per event: winners are chained by their UTbX and UTaU hits (hash
+// One CTA per event (largest events first, in the order the bucketing
+// kernel laid out): winners are chained by their UTbX and UTaU hits (hash
 // heads in shared memory; hits, keys and chain links staged in shared memory
 // for events up to kCloneSmem seeds, read from and kept in the workspace for
 // larger ones), each thread owns a seed and compares it with the winners on

@@ -13,7 +13,9 @@
 // pairs whose opening satisfies sin^2 < eps_par and whose FP32 DOCA is near
 // or below the cut are re-solved in FP64 (flag bit 0).
 //
-// Small-capacity launch: one CTA per event (up to 512 tracks).  Tracks are
+// Small-capacity launch: one CTA per event (up to 512 tracks), pulled from a
+// queue in the order given (largest first when the bucketing kernel's order
+// is passed).  Tracks are
 // staged in shared memory; opposite-charge partner lists make every thread's
 // pair valid, enumerated in (i, j) order.  Kept vertices of each segment are
 // ranked by a block scan and written to a pool slice reserved with one
