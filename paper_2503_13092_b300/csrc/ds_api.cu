@@ -414,6 +414,7 @@ ds_status ds_reserve(ds_ctx *ctx, int32_t E, int32_t S, int32_t H)
     ds_status st;
     if (E > ctx->cap_events || ctx->cap_events == 0) {
         E = E > ctx->cap_events ? E : ctx->cap_events;
+        ctx->order_events = -1;   // the event order lives in item_off, reallocated below
         if ((st = grow(ctx, &ctx->bins, (size_t)E * ctx->g.table_stride)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->count_trk, (size_t)E)) != DS_OK) return st;
         if ((st = grow(ctx, &ctx->count_vtx, (size_t)E)) != DS_OK) return st;

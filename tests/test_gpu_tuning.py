@@ -153,3 +153,46 @@ def test_work_item_orders_on_uneven_seed_counts(torch_cuda, weights):
     rep = parity.compare_tracks(b, o, g)
     assert rep["n_tracks_oracle"] > 0
     parity.assert_tracks_match(rep)
+
+
+def test_vertex_event_order_is_scheduling_only(torch_cuda, weights):
+    """ds_vertex takes its events in the order the last ds_reconstruct on its
+    context laid out (largest first).  Vertices must not depend on it: after a
+    ds_reserve that reallocates the workspaces between the two calls (the
+    order is dropped), and for the tracks of another batch with the same
+    event count (the order of the wrong batch is still a permutation of the
+    events), the vertices equal those of a plain reconstruct + vertex."""
+    from paper_2503_13092_b300 import ds
+    cfg = synth.default_config()
+    b1 = synth.config_batch("c2", seed=31, n_events=24)
+    b2 = synth.config_batch("c2", seed=32, n_events=24)
+
+    def plain(b):
+        d = ds.Downstream(cfg, weights)
+        r = run_with(d, ds, d.to_device(b), ds.ds_tuning())
+        d.close()
+        return r
+
+    ref1, ref2 = plain(b1), plain(b2)
+    d = ds.Downstream(cfg, weights)
+    dev1, dev2 = d.to_device(b1), d.to_device(b2)
+    # reconstruct, grow the workspaces, vertex
+    out = d.alloc_tracks(dev1["n_events"], dev1["n_seeds"])
+    d.reconstruct(dev1, out)
+    ds.ds_reserve(d.ctx, 4 * dev1["n_events"] + 100, dev1["n_seeds"], dev1["n_hits"])
+    vout = d.alloc_vertices(dev1["n_events"], 64 * dev1["n_seeds"] + 4096)
+    d.vertex(out, vout)
+    assert d.sync()["status"] == 0
+    n_v = int(vout["n_vertices"].cpu()[0])
+    assert vout["vertices"][:n_v].cpu().numpy().tobytes() == ref1[3]
+    # batch 2's tracks vertexed right after batch 1's reconstruct (same event count)
+    out2 = d.alloc_tracks(dev2["n_events"], dev2["n_seeds"])
+    d.reconstruct(dev2, out2)
+    d.reconstruct(dev1, out)
+    vout2 = d.alloc_vertices(dev2["n_events"], 64 * dev2["n_seeds"] + 4096)
+    d.vertex(out2, vout2)
+    assert d.sync()["status"] == 0
+    n_v2 = int(vout2["n_vertices"].cpu()[0])
+    assert vout2["vertices"][:n_v2].cpu().numpy().tobytes() == ref2[3]
+    assert vout2["vtx_off"].cpu().numpy().tobytes() == ref2[4]
+    d.close()
