@@ -347,7 +347,10 @@ DS_API ds_status ds_reconstruct(ds_ctx *ctx, const ds_event_batch *batch, const 
  * approach of the two quadratic-in-x trajectories, vertex = midpoint, kept if
  * DOCA < doca_max.  Pairs with sin^2(opening) < eps_parallel whose FP32 DOCA
  * is near or below the cut are re-solved in FP64.  `tracks` is the output of
- * ds_reconstruct (device), with n_events set. */
+ * ds_reconstruct (device), with n_events set.  Events are processed in the
+ * order (largest first) the last ds_reconstruct on this context laid out when
+ * the event counts match, else in index order: this changes speed only, the
+ * output is the same for any order. */
 DS_API ds_status ds_vertex(ds_ctx *ctx, const ds_tracks *tracks, ds_vertices *out, void *stream);
 
 /* The ghost-killer network alone (Ghost-Killer Neural Network section: inputs
