@@ -18,7 +18,9 @@
 // the search decides the strip test of an unmarked row from the sector's
 // bounds.  Block 0 also turns the per-event seed counts into the search
 // kernel's work items (chunks of at most `chunk` <= 128 seeds of one event,
-// by default the full chunks first and the remainders largest first).
+// by default the full chunks first and the remainders largest first) and the
+// events by seed count, largest first, the order in which the clone-killing
+// and vertex kernels take them.
 // The order inside a bin comes from atomics and is not deterministic; every
 // consumer ranks hits by (|dx|, id), which does not depend on it.
 #include "ds_args.cuh"
